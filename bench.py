@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Throughput of the time-reversible FDTD hot path on B300 (one JSON line on stdout).
+
+A bench step is one whole forward + time-reversal gradient solve of the workload (every row of the
+hot path: H and E updates with CPML, sources, detectors, face record, inverse step, adjoint sweep
+and dL/deps). The default workload is a 96^3 grid with a 10-cell CPML, a Gaussian-beam sheet
+source, a 40^3 random-density design box (eps = 1 + 11.1 rho, seed 1234) and a time-integrated
+|E|^2 plane objective, 2000 time steps forward and 2000 reversed.
+
+Metric: Gcell-steps/s = cells x time steps / device time of the fwd+grad solve (the forward-only
+rate is reported beside it). Under torchrun each rank solves its own replica (weak scaling, no
+collective on the data path); the value is the sum over ranks divided by the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded sample of the same
+workload (the full grid for a few time steps).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2412_12360_b300 import scenes  # noqa: E402
+
+METRIC = "Gcell-steps/s fwd+grad (time-reversal gradient)"
+UNIT = "Gcell-steps/s"
+
+
+def workload(name):
+    if name == "design_96":
+        sc = scenes.design_96()
+        desc = ("design_96: 96^3 Yee grid, 10-cell CPML, Gaussian-beam Ex sheet, 40^3 design box "
+                "eps=1+11.1*rho (rho~U[0,1), seed 1234), |E|^2 plane objective, 2000 steps fwd + 2000 reversed")
+    elif name == "cavity_32":
+        sc = scenes.cavity_32(500)
+        desc = "cavity_32: 32^3 PEC box, 8^3 eps=2.25 cube, Ez dipole, 500 steps fwd + 500 reversed"
+    elif name == "waveguide_600":
+        sc = scenes.waveguide_600()
+        desc = ("waveguide_600: 600^3 grid, 12-cell CPML, Si core eps=12.25 in SiO2 eps=2.085, 200^3 design "
+                "box, Poynting-flux objective, 4000 steps fwd + 4000 reversed")
+    else:
+        raise SystemExit("unknown workload " + name)
+    return sc, desc
+
+
+def objective_grad(sc, nsteps):
+    """dL/d(detector) for L = sum of every detector output (the |E|^2 plane sum or the flux sum)."""
+    n = 0
+    for d in sc.detectors:
+        n += nsteps if d.kind != scenes.DET_PLANE_E2_SUM else int(np.prod([d.hi[k] - d.lo[k] for k in range(3)]))
+    return np.ones(n, dtype=np.float64)
+
+
+# ---- algorithmic bytes per launch (the roofline numerator) ------------------------------------------
+def slab_cells(sc):
+    """Cells inside the layer of each axis, summed over axes (a cell in two layers counts twice)."""
+    nx, ny, nz = sc.n
+    tot = 0
+    for d in range(3):
+        w = sc.pml[2 * d] + sc.pml[2 * d + 1]
+        tot += w * (nx * ny * nz // sc.n[d])
+    return tot
+
+
+def algorithmic_bytes(kind, sc):
+    """Bytes one launch of kernel `kind` must move at minimum (fp32 fields, fp64 dL/da)."""
+    N = sc.ncells
+    slab = slab_cells(sc)
+    design = int(np.prod(sc.design_shape()))
+    if kind == "update_H":      # E r, H r/w; psi_H of 2 components per layer axis r/w
+        return 36 * N + 16 * slab
+    if kind == "update_E":      # H r, E r/w, a r; psi_E
+        return 40 * N + 16 * slab
+    if kind == "rev_E":         # H r, E r/w, a r, E-bar r, H-bar r/w; psi-bar_E r + w; dL/da r/w
+        return 76 * N + 16 * slab + 16 * design
+    if kind == "rev_H":         # E r, H r/w, H-bar r, E-bar r/w; psi-bar_H r + w
+        return 72 * N + 16 * slab
+    if kind == "fused_fwd":     # E, H r/w, a r; psi_E and psi_H of 4 components per layer axis
+        return 52 * N + 32 * slab
+    if kind == "fused_rev":     # primal E, H r/w, a r, adjoint E, H r/w; psi-bar; dL/da
+        return 100 * N + 32 * slab + 16 * design
+    return None
+
+
+# ---- clocks during the timed region ------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_id)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, power, reasons = [], None, [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        loaded = [s for s in sm if mx and s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ---- distributed helpers ------------------------------------------------------------------------------
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if (args.impl == "ours") else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU baseline (the oracle as it stands) ------------------------------------------------------------
+def oracle_sample(sc, nsteps):
+    """Time the oracle's forward + time-reversal gradient on the full grid for nsteps steps."""
+    from oracle import oracle as O
+    g = np.ones(O.detector_total(sc, nsteps))
+    t0 = time.perf_counter()
+    O.gradient(sc, nsteps, g, O.METHOD_TIME_REVERSAL)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(sc, target_s=15.0):
+    probe = 2
+    t = oracle_sample(sc, probe)
+    steps = max(probe, min(400, int(probe * target_s / max(t, 1e-3))))
+    t = oracle_sample(sc, steps)
+    cores = os.cpu_count()
+    return {"value": sc.ncells * steps / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "full %dx%dx%d grid, %d time steps fwd + %d reversed (FP64 C++ oracle, OpenMP over "
+                      "z-planes in the forward and inverse loops, serial adjoint loops), %.1f s"
+                      % (sc.n[0], sc.n[1], sc.n[2], steps, steps, t)}
+
+
+# ---- our arm ----------------------------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2412_12360_b300 import fdtd
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, desc = workload(args.workload)
+    T = sc.nsteps
+    stream = torch.cuda.Stream(device=dev)
+    solver = fdtd.Solver(sc, stream=stream)
+    gvec = objective_grad(sc, T)
+    g_dev = torch.from_numpy(gvec).to(dev)
+    grad_dev = torch.zeros(sc.design_shape(), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+
+    def solve():
+        solver.fdtd_forward(T, record_faces=True)
+        solver.fdtd_backward(g_dev, grad_dev)
+
+    def timed(fn, k):
+        times = []
+        for _ in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            times.append((a, b))
+        stream.synchronize()
+        return [a.elapsed_time(b) for a, b in times]
+
+    for _ in range(args.warmup):
+        solve()
+    stream.synchronize()
+
+    # forward-only rate (reported beside the headline)
+    fwd_ms = statistics.median(timed(lambda: solver.fdtd_forward(T, record_faces=False), max(3, args.steps // 2)))
+
+    # timed region: K fwd+grad solves, stencil kernels sampled with CUDA events
+    solver.fdtd_profile(True, args.profile_every)
+    l0 = solver.fdtd_launch_count()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    if rank == 0:
+        clocks.start()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    step_ms = timed(solve, args.steps)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop() if rank == 0 else None
+    launches = solver.fdtd_launch_count() - l0
+    prof = solver.fdtd_profile_read()
+    solver.fdtd_profile(False)
+    total_ms = sum(step_ms)
+    total_ms_max = max_over_ranks(total_ms, world, dev)
+    ms_per_step = total_ms_max / args.steps
+    value = world * sc.ncells * T * args.steps / (total_ms_max * 1e-3) / 1e9
+    fwd_value = sc.ncells * T / (fwd_ms * 1e-3) / 1e9 * world
+
+    # roofline of the dominant stencil kernel (largest share of sampled device time)
+    roof = None
+    if prof:
+        # every stencil kernel launches once per time step, so the largest share is the longest launch
+        shares = {k: v[0] / max(v[1], 1) for k, v in prof.items()}
+        kname = max(shares, key=shares.get)
+        avg_ms = shares[kname]
+        nbytes = algorithmic_bytes(kname, sc)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        peak = peaks.get("hbm_gbs")
+        src = "measured"
+        if not peak:
+            peak, src = 6400.0, "fallback"
+        achieved = nbytes / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": src, "traffic": args.traffic,
+                "bytes_per_launch": nbytes, "avg_launch_ms": round(avg_ms, 5),
+                "kernel_ms_per_launch": {k: round(v, 5) for k, v in shares.items()}}
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        dlo, dhi = sc.design_lo, sc.design_hi
+        box = np.ascontiguousarray(sc.eps_inv[dlo[2]:dhi[2], dlo[1]:dhi[1], dlo[0]:dhi[0]])
+        box_h = torch.from_numpy(box).pin_memory()
+        g_h = torch.from_numpy(gvec).pin_memory()
+        det_h = torch.zeros(solver.fdtd_detector_total(), dtype=torch.float64).pin_memory()
+        grad_h = torch.zeros(sc.design_shape(), dtype=torch.float32).pin_memory()
+        h2d = box_h.numel() * 4 + g_h.numel() * 8
+        d2h = det_h.numel() * 8 + grad_h.numel() * 4
+
+        def e2e_step():
+            solver.fdtd_set_design_eps_inv(box_h)
+            solver.fdtd_forward(T, record_faces=True)
+            solver.fdtd_read_detectors(det_h)
+            solver.fdtd_backward(g_h, grad_h)
+            solver.fdtd_synchronize()
+
+        e2e_step()
+        barrier(world)
+        tt = []
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            t1 = time.perf_counter()
+            e2e_step()
+            tt.append(time.perf_counter() - t1)
+        tmax = max_over_ranks(sum(tt), world, dev)
+        e2e = {"value": world * sc.ncells * T * args.steps / tmax / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    solver.close()
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "grid": list(sc.n), "cells": sc.ncells, "time_steps": T,
+                       "pml": list(sc.pml), "design": list(sc.design_shape()),
+                       "l2": "flushed between steps (256 MB write outside the timed events)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "fwd_value": round(fwd_value, 4), "fwd_ms": round(fwd_ms, 3),
+            "roofline": roof, "e2e": e2e, "gpu_launches": int(launches * world),
+            "wall_s": round(wall, 3), "clocks": clk}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+
+
+# ---- reference arm: the FP64 oracle on host cores -------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    sc, desc = workload(args.workload)
+    probe = oracle_sample(sc, 2)
+    # each step is a bounded sample: the full grid for a few time steps
+    per_step_budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    steps = max(2, min(200, int(2 * per_step_budget / max(probe, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(sc, steps)
+    ts = [oracle_sample(sc, steps) for _ in range(args.steps)]
+    total = sum(ts)
+    value = sc.ncells * steps * args.steps / total / 1e9
+    cores = os.cpu_count()
+    sample = ("full %dx%dx%d grid, %d time steps fwd + %d reversed per step (FP64 C++ oracle)"
+              % (sc.n[0], sc.n[1], sc.n[2], steps, steps))
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "grid": list(sc.n), "cells": sc.ncells,
+                                            "time_steps": sc.nsteps, "parallelism": "single"},
+            "cpu_baseline": {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="design_96")
+    ap.add_argument("--profile-every", type=int, default=16)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch of the dominant kernel from an ncu capture (null if stale)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

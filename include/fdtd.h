@@ -1,0 +1,189 @@
+/*
+ * fdtd.h: C ABI of the B300 (sm_103a) time-reversible 3D FDTD library (libfdtd.so).
+ *
+ * The library runs the Yee-grid leapfrog of arXiv 2412.12360 Sec. 2.1 (Faraday Eq. 1 and Ampere
+ * Eq. 2 as curl stencils with a per-cell inverse permittivity, a convolutional PML on the outer
+ * faces, soft sources and time-integrated detectors) and the reverse-mode gradient of Sec. 2.2:
+ * the inverse update step rebuilds the fields backward in time from t+1 to t inside the PML-free
+ * region, the tangential H on the six planes enclosing that region is recorded every forward step
+ * and replayed in reverse, and adjoint fields are swept alongside to accumulate dL/d(eps) per
+ * design cell.
+ *
+ * Units and conventions (the paper prints only Eqs. 1-2; these are this library's readings):
+ *   - normalised units: c = 1, grid spacing 1, H stored as eta0 * H, mu = 1;
+ *   - courant = S = c dt / dx, stable for S <= 1/sqrt(3);
+ *   - cell (i, j, k), x fastest; Ex at (i+1/2, j, k), Ey at (i, j+1/2, k), Ez at (i, j, k+1/2),
+ *     Hx at (i, j+1/2, k+1/2), Hy at (i+1/2, j, k+1/2), Hz at (i+1/2, j+1/2, k);
+ *   - field order Ex, Ey, Ez, Hx, Hy, Hz; PEC at integer planes 0 and N of every axis;
+ *   - one inverse permittivity per cell, applied to that cell's Ex, Ey, Ez;
+ *   - CPML: sigma = sigma_max (d/p)^m, kappa = 1 + (kappa_max - 1)(d/p)^m, alpha = alpha_max (1 - d/p),
+ *     b = exp(-(sigma/kappa + alpha)), c = sigma / (sigma kappa + kappa^2 alpha) (b - 1), d the depth
+ *     of the component's own position into the layer, psi <- b psi + c * difference;
+ *   - source waveform g(s) = sin(2 pi (s - t0)/P) exp(-((s - t0)/tau)^2), P = wavelength / S steps,
+ *     sampled at s = n + 1/2 and added to E after the E update of step n;
+ *   - detectors sample E^{n+1} and H^{n+1/2} after every step n (no interpolation).
+ *
+ * Memory: every pointer argument marked "host or device" may point to host memory or to device
+ * memory of the current CUDA device (the library copies with cudaMemcpyDefault). The handle owns all
+ * the device memory it allocates; inputs are copied, outputs are written into caller buffers.
+ *
+ * Streams: work is enqueued on the stream given at creation (NULL = legacy default stream). Calls
+ * that return data to a host pointer synchronise that stream before returning.
+ *
+ * Errors: every int-returning call returns FDTD_OK (0) or a negative FDTD_ERR_* code and never
+ * aborts; fdtd_last_error() gives a message for the calling thread's last failure.
+ */
+#ifndef FDTD_H_
+#define FDTD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FDTD_OK 0
+#define FDTD_ERR_INVALID_ARG (-1)
+#define FDTD_ERR_UNSTABLE (-2)     /* courant above 1/sqrt(3) */
+#define FDTD_ERR_OOM (-3)          /* device allocation failed or a byte budget would be exceeded */
+#define FDTD_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define FDTD_ERR_STATE (-5)        /* call out of order, e.g. backward without a recorded forward */
+#define FDTD_ERR_NONFINITE (-6)    /* a non-finite value was found in the fields */
+#define FDTD_ERR_TIMEOUT (-7)      /* a bounded device-side wait gave up */
+
+/* fdtd_forward flags */
+#define FDTD_RECORD_FACES 1u       /* keep the boundary-face history needed by fdtd_backward */
+
+/* detector kinds */
+#define FDTD_DET_POINT_SERIES 0    /* field `component` (0..5) at cell lo, one value per step */
+#define FDTD_DET_PLANE_E2_SUM 1    /* per cell of [lo, hi): sum over steps of Ex^2 + Ey^2 + Ez^2 */
+#define FDTD_DET_PLANE_FLUX 2      /* per step: sum over [lo, hi) of (E x H)[axis] */
+
+typedef struct fdtd_handle fdtd_handle;
+
+typedef struct {
+  int32_t nx, ny, nz;              /* cells per axis, each >= 2 */
+} fdtd_grid;
+
+typedef struct {
+  int32_t thickness[6];            /* cells: x-lo, x-hi, y-lo, y-hi, z-lo, z-hi; 0 = bare PEC wall */
+  double sigma_max;                /* normalised peak conductivity (sigma dt / eps0) */
+  double kappa_max;                /* >= 1 */
+  double alpha_max;                /* normalised, >= 0 */
+  int32_t grading_m;               /* polynomial grading order, >= 1 */
+} fdtd_pml;
+
+/* Soft source on an E component over the cell box [lo, hi) (Sec. 2.1 names sources; this library
+ * implements additive soft sources). */
+typedef struct {
+  int32_t component;               /* 0, 1, 2 = Ex, Ey, Ez */
+  int32_t lo[3], hi[3];            /* cell box, hi exclusive */
+  const float* profile;            /* host, box-shaped weights (x fastest) or NULL for 1 */
+  double amplitude;
+  double wavelength_cells;         /* vacuum wavelength in cells */
+  double tau_steps;                /* width of the Gaussian envelope, steps (> 0) */
+  double t0_steps;                 /* centre of the envelope, steps */
+} fdtd_source;
+
+/* Detector (Sec. 2.1: detectors record field values at intermediate time steps; composite values
+ * use same-index components without interpolation). Output sizes: POINT_SERIES and PLANE_FLUX give
+ * nsteps doubles, PLANE_E2_SUM gives one double per box cell (x fastest). */
+typedef struct {
+  int32_t kind;                    /* FDTD_DET_* */
+  int32_t component;               /* POINT_SERIES: 0..5 = Ex..Hz */
+  int32_t axis;                    /* PLANE_FLUX: normal axis 0, 1, 2 */
+  int32_t lo[3], hi[3];            /* cell box, hi exclusive */
+} fdtd_detector;
+
+/* Create a solver (Sec. 2.1). eps_inv: host or device, nx*ny*nz floats (x fastest), copied.
+ * design_lo/hi: the cell box [lo, hi) whose dL/d(eps) fdtd_backward returns (may be empty).
+ * spacing: metres per cell, recorded for reporting only (all arithmetic is in cells).
+ * When backward is wanted, detectors and the design box must lie in the PML-free cell box
+ * [thickness_lo, n - thickness_hi) of every axis; fdtd_forward with FDTD_RECORD_FACES checks this.
+ * Returns INVALID_ARG for malformed input, UNSTABLE for courant > 1/sqrt(3), OOM, CUDA. */
+int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double courant,
+                const float* eps_inv, const fdtd_source* src, int32_t nsrc, const fdtd_detector* det,
+                int32_t ndet, const fdtd_pml* pml, const int32_t design_lo[3], const int32_t design_hi[3],
+                void* cuda_stream);
+
+/* Free every device buffer of the handle (after finishing its stream). NULL is accepted. */
+int fdtd_destroy(fdtd_handle* h);
+
+/* Replace the inverse permittivity on the design box (host or device, box-shaped, x fastest). */
+int fdtd_set_design_eps_inv(fdtd_handle* h, const float* eps_inv_box);
+
+/* Set the initial state E^0, H^{-1/2} (host or device, 6*nx*ny*nz floats, field-major, x fastest);
+ * NULL restores zero fields. Used for round-trip and eigenmode tests. */
+int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6);
+
+/* Sec. 2.1: run nsteps steps from the initial state (a fresh solve each call). With
+ * FDTD_RECORD_FACES the tangential H on the six planes enclosing the PML-free region is recorded
+ * after every H update (Sec. 2.2), as needed by fdtd_backward. */
+int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags);
+
+/* Sec. 2.2: reverse-mode gradient of L = sum(dL_ddet * detectors) for the last forward.
+ * dL_ddet: host or device, fdtd_detector_total(h) doubles (concatenated in detector order).
+ * dL_deps: host or device, design-box-shaped floats (x fastest), written.
+ * The primal fields are rebuilt by the inverse update step; after return the handle's fields hold
+ * the reconstructed initial state on the PML-free region. STATE if the last forward did not record
+ * faces or a backward already consumed it. */
+int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps);
+
+/* Concatenated detector outputs of the last forward (host or device doubles). */
+int fdtd_read_detectors(fdtd_handle* h, double* out);
+
+/* Number of doubles fdtd_read_detectors writes for the last forward (or -1 on error). */
+int64_t fdtd_detector_total(fdtd_handle* h);
+
+/* Current fields (host or device, 6*nx*ny*nz floats, field-major, x fastest, pitch removed). */
+int fdtd_get_fields(fdtd_handle* h, float* out6);
+
+/* Bytes of device memory a solve of this size needs (fields, coefficients, adjoint state and a
+ * face history for nsteps when record_faces != 0); for admission by HBM footprint. -1 on bad input. */
+int64_t fdtd_footprint_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps,
+                             int32_t record_faces, const int32_t design_lo[3], const int32_t design_hi[3]);
+
+/* Cap the device bytes any one handle may allocate (-1 = no cap, the default). Allocations past the
+ * cap fail with FDTD_ERR_OOM before reaching the CUDA allocator; used to exercise admission and
+ * out-of-memory paths without exhausting the GPU. Process-wide. */
+int fdtd_set_byte_budget(int64_t bytes);
+
+/* Kernel kinds timed by fdtd_profile_read. */
+#define FDTD_KERNEL_UPDATE_H 0     /* forward H half-step */
+#define FDTD_KERNEL_UPDATE_E 1     /* forward E half-step */
+#define FDTD_KERNEL_REV_E 2        /* reverse: inverse E, adjoint into H-bar, dL/da */
+#define FDTD_KERNEL_REV_H 3        /* reverse: inverse H, adjoint into E-bar */
+#define FDTD_KERNEL_FUSED_FWD 4    /* forward H and E of one step in one sweep */
+#define FDTD_KERNEL_FUSED_REV 5    /* reverse step in one sweep */
+#define FDTD_KERNEL_KINDS 8
+
+/* Number of kernels this handle has launched since creation (or -1). */
+int64_t fdtd_launch_count(fdtd_handle* h);
+
+/* With enable != 0, fdtd_forward and fdtd_backward bracket every `every`-th launch of each stencil
+ * kernel with CUDA events on the handle's stream and synchronise that stream before returning, so
+ * that fdtd_profile_read can report the device time of those launches. enable = 0 stops it and
+ * clears the totals. */
+int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every);
+
+/* Per kernel kind (FDTD_KERNEL_*, up to nkinds): total device milliseconds of the timed launches
+ * and how many were timed. Either array may be NULL. */
+int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds);
+
+/* Device bytes currently held by the handle (or -1). */
+int64_t fdtd_bytes_allocated(fdtd_handle* h);
+
+/* Wait for all work of the handle's stream. */
+int fdtd_synchronize(fdtd_handle* h);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* fdtd_last_error(void);
+
+/* Library version string. */
+const char* fdtd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H_ */

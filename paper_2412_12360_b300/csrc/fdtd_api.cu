@@ -1,0 +1,804 @@
+// Host side of the libfdtd C ABI (include/fdtd.h): validation, device memory, CPML and source tables,
+// and the forward and reverse time loops of arXiv 2412.12360 Sec. 2.1-2.2.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/fdtd.h"
+#include "fdtd_internal.cuh"
+
+using namespace fdtd;
+
+namespace {
+
+thread_local std::string g_last_error;
+int64_t g_byte_budget = -1;  // process-wide cap on bytes one handle may allocate (-1 = none)
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) return fail(FDTD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// CPML grading of one position (depth d of the component's own position into the layer).
+void cpml_coef(double x, int N, int p0, int p1, const fdtd_pml& pm, double& b, double& c, double& ik) {
+  double d = 0.0;
+  if (p0 > 0 && x < p0) d = (p0 - x) / p0;
+  else if (p1 > 0 && x > N - p1) d = (x - (N - p1)) / p1;
+  if (d <= 0.0) { b = 1.0; c = 0.0; ik = 1.0; return; }
+  const double dm = std::pow(d, pm.grading_m);
+  const double sigma = pm.sigma_max * dm;
+  const double kappa = 1.0 + (pm.kappa_max - 1.0) * dm;
+  const double alpha = pm.alpha_max * (1.0 - d);
+  b = std::exp(-(sigma / kappa + alpha));
+  c = sigma == 0.0 ? 0.0 : sigma / (sigma * kappa + kappa * kappa * alpha) * (b - 1.0);
+  ik = 1.0 / kappa;
+}
+
+double pulse(const fdtd_source& s, double S, double t) {
+  const double P = s.wavelength_cells / S;
+  const double u = t - s.t0_steps;
+  return std::sin(2.0 * M_PI * u / P) * std::exp(-(u / s.tau_steps) * (u / s.tau_steps));
+}
+
+bool box_ok(const int32_t lo[3], const int32_t hi[3], const int n[3], bool allow_empty) {
+  for (int d = 0; d < 3; ++d) {
+    if (lo[d] < 0 || hi[d] > n[d] || lo[d] > hi[d]) return false;
+    if (!allow_empty && lo[d] == hi[d]) return false;
+  }
+  return true;
+}
+
+int64_t box_cells(const int32_t lo[3], const int32_t hi[3]) {
+  return int64_t(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+}
+
+Geo make_geo(const fdtd_grid& gr, const fdtd_pml& pm, double S) {
+  Geo g;
+  g.n[0] = gr.nx; g.n[1] = gr.ny; g.n[2] = gr.nz;
+  g.nxp = (int)round_up(gr.nx, kPitchAlign);
+  g.plane = (int64_t)g.nxp * gr.ny;
+  g.vol = g.plane * gr.nz;
+  for (int f = 0; f < 6; ++f) g.pml[f] = pm.thickness[f];
+  for (int d = 0; d < 3; ++d) {
+    g.slab[d] = pm.thickness[2 * d] + pm.thickness[2 * d + 1];
+    g.rint_lo[d] = pm.thickness[2 * d];
+    g.rint_hi[d] = std::min(g.n[d] - pm.thickness[2 * d + 1], g.n[d] - 1);
+    g.rhalf_lo[d] = pm.thickness[2 * d];
+    g.rhalf_hi[d] = g.n[d] - pm.thickness[2 * d + 1] - 1;
+  }
+  g.S = (float)S;
+  return g;
+}
+
+FaceSet make_faces(const Geo& g) {
+  FaceSet fs;
+  fs.nseg = 0;
+  fs.per_step = 0;
+  for (int d = 0; d < 3; ++d) {
+    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+    for (int side = 0; side < 2; ++side) {
+      const int p = g.pml[2 * d + side];
+      if (p == 0) continue;
+      for (int comp : {e1, e2}) {
+        FaceSeg& s = fs.seg[fs.nseg++];
+        s.axis = d;
+        s.idx = side == 0 ? p - 1 : g.n[d] - p;
+        s.comp = comp;
+        s.lo1 = g.rint_lo[e1];
+        s.n1 = g.rint_hi[e1] - g.rint_lo[e1] + 1;
+        s.lo2 = g.rint_lo[e2];
+        s.n2 = g.rint_hi[e2] - g.rint_lo[e2] + 1;
+        s.off = fs.per_step;
+        fs.per_step += (int64_t)s.n1 * s.n2;
+      }
+    }
+  }
+  return fs;
+}
+
+int64_t psi_bytes(const Geo& g) {
+  int64_t t = 0;
+  for (int d = 0; d < 3; ++d) t += 2 * psi_elems(g, d);  // two components per axis
+  return t * (int64_t)sizeof(float);
+}
+
+int validate(const fdtd_grid* grid, double courant, const fdtd_pml* pml) {
+  if (!grid || !pml) return fail(FDTD_ERR_INVALID_ARG, "grid and pml are required");
+  const int n[3] = {grid->nx, grid->ny, grid->nz};
+  for (int d = 0; d < 3; ++d)
+    if (n[d] < 2 || n[d] > (1 << 16)) return fail(FDTD_ERR_INVALID_ARG, "grid size %d out of range [2, 65536]", n[d]);
+  if (!(courant > 0.0)) return fail(FDTD_ERR_INVALID_ARG, "courant must be positive");
+  if (courant > (1.0 / std::sqrt(3.0)) * (1.0 + 1e-12))
+    return fail(FDTD_ERR_UNSTABLE, "courant %.9g exceeds the 3D stability limit 1/sqrt(3)", courant);
+  for (int d = 0; d < 3; ++d) {
+    const int p0 = pml->thickness[2 * d], p1 = pml->thickness[2 * d + 1];
+    if (p0 < 0 || p1 < 0) return fail(FDTD_ERR_INVALID_ARG, "negative PML thickness");
+    if (p0 + p1 > n[d] - 2) return fail(FDTD_ERR_INVALID_ARG, "PML thicker than the grid along axis %d", d);
+  }
+  if (pml->grading_m < 1 || pml->grading_m > 16) return fail(FDTD_ERR_INVALID_ARG, "grading_m out of range");
+  if (!(pml->kappa_max >= 1.0) || !(pml->sigma_max >= 0.0) || !(pml->alpha_max >= 0.0))
+    return fail(FDTD_ERR_INVALID_ARG, "PML parameters need kappa_max >= 1, sigma_max >= 0, alpha_max >= 0");
+  return FDTD_OK;
+}
+
+}  // namespace
+
+struct fdtd_handle {
+  Geo g{};
+  fdtd_pml pml{};
+  double spacing = 0, courant = 0;
+  cudaStream_t stream = nullptr;
+  int32_t design_lo[3] = {0, 0, 0}, design_hi[3] = {0, 0, 0};
+  FaceSet faces{};
+
+  std::vector<fdtd_source> src_host;
+  std::vector<std::vector<float>> src_profile;  // host copies of amplitude * profile
+  std::vector<SrcDev> srcs;
+  std::vector<DetDev> dets;
+  int64_t det_total_per_step = 0, det_total_fixed = 0;
+
+  // device memory
+  float* fields = nullptr;     // 6 * vol
+  float* a = nullptr;          // vol
+  float* psiE = nullptr;       // forward CPML memories of E (compact slabs)
+  float* psiH = nullptr;
+  float* tables = nullptr;     // 3 axes x 6 tables x n
+  float* init = nullptr;       // optional initial state, 6 * vol
+  std::vector<float*> src_w;   // per source box weights
+  float* gtab = nullptr;       // nsrc x gtab_cap waveform samples
+  int gtab_cap = 0;
+  double* det_out = nullptr;   // concatenated detector outputs
+  int64_t det_out_cap = 0;
+  double* partial = nullptr;   // flux partial sums (scratch)
+  int64_t partial_cap = 0;
+  float* face_hist = nullptr;  // steps x faces.per_step
+  int64_t face_cap_steps = 0;
+  float* adj = nullptr;        // 6 * vol adjoint fields
+  float* psibar = nullptr;     // 2 buffers x (psiE + psiH) adjoint memories
+  double* dLda = nullptr;      // design box
+  double* dLddet = nullptr;    // device copy of dL/d(detectors)
+  int64_t dLddet_cap = 0;
+  float* staging = nullptr;    // 6 * N, unpitched
+  int64_t bytes = 0;
+
+  int last_nsteps = -1;
+  bool recorded = false;
+  bool consumed = false;
+
+  // launch accounting and sampled event timing
+  int64_t launches = 0;
+  int prof_every = 0;                       // 0 = off
+  struct Ev { cudaEvent_t a, b; int kind; };
+  std::vector<Ev> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms[FDTD_KERNEL_KINDS] = {0};
+  int64_t prof_n[FDTD_KERNEL_KINDS] = {0};
+
+  Tables tab() const {
+    Tables T;
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int n = g.n[d];
+      for (int h = 0; h < 2; ++h) {
+        T.b[d][h] = tables + off; off += n;
+        T.c[d][h] = tables + off; off += n;
+        T.ik[d][h] = tables + off; off += n;
+      }
+    }
+    return T;
+  }
+  Fields F() const {
+    Fields f;
+    for (int c = 0; c < 6; ++c) f.f[c] = fields + c * g.vol;
+    return f;
+  }
+  Fields A() const {
+    Fields f;
+    for (int c = 0; c < 6; ++c) f.f[c] = adj + c * g.vol;
+    return f;
+  }
+  // psi pointer set over a base buffer laid out as axis-major pairs of components
+  PsiSet psi_set(float* base) const {
+    PsiSet P;
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) P.p[c][d] = nullptr;
+    int64_t off = 0;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t n = psi_elems(g, d);
+      for (int c = 0; c < 3; ++c) {
+        if (c == d) continue;
+        P.p[c][d] = (n > 0) ? base + off : nullptr;
+        off += n;
+      }
+    }
+    return P;
+  }
+  int64_t psi_floats() const { return psi_bytes(g) / (int64_t)sizeof(float); }
+};
+
+namespace {
+
+// Start/stop a sampled timing interval around one launch of kernel `kind` (no-op unless profiling
+// and `step` is a multiple of the sampling interval).
+struct ProfScope {
+  fdtd_handle* h;
+  int idx = -1;
+  ProfScope(fdtd_handle* h_, int kind, int step) : h(h_) {
+    if (h->prof_every <= 0 || step % h->prof_every != 0) return;
+    if (h->ev_used == h->ev_pool.size()) {
+      fdtd_handle::Ev e;
+      if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
+      h->ev_pool.push_back(e);
+    }
+    idx = (int)h->ev_used++;
+    h->ev_pool[idx].kind = kind;
+    cudaEventRecord(h->ev_pool[idx].a, h->stream);
+  }
+  ~ProfScope() {
+    if (idx >= 0) cudaEventRecord(h->ev_pool[idx].b, h->stream);
+  }
+};
+
+int prof_collect(fdtd_handle* h) {
+  if (h->prof_every <= 0 || h->ev_used == 0) return FDTD_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < h->ev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev_pool[i].a, h->ev_pool[i].b));
+    h->prof_ms[h->ev_pool[i].kind] += ms;
+    h->prof_n[h->ev_pool[i].kind] += 1;
+  }
+  h->ev_used = 0;
+  return FDTD_OK;
+}
+
+int dev_alloc(fdtd_handle* h, void** p, int64_t bytes) {
+  *p = nullptr;
+  if (bytes <= 0) return FDTD_OK;
+  if (g_byte_budget >= 0 && h->bytes + bytes > g_byte_budget)
+    return fail(FDTD_ERR_OOM, "byte budget %lld exceeded (%lld held, %lld requested)", (long long)g_byte_budget,
+                (long long)h->bytes, (long long)bytes);
+  cudaError_t e = cudaMalloc(p, (size_t)bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(FDTD_ERR_OOM, "cudaMalloc of %lld bytes failed", (long long)bytes);
+  }
+  if (e != cudaSuccess) return fail(FDTD_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  h->bytes += bytes;
+  return FDTD_OK;
+}
+
+void dev_free(fdtd_handle* h, void* p, int64_t bytes) {
+  if (p) {
+    cudaFree(p);
+    h->bytes -= bytes;
+  }
+}
+
+#define TRY(x)                  \
+  do {                          \
+    int rc_ = (x);              \
+    if (rc_ != FDTD_OK) return rc_; \
+  } while (0)
+
+int upload_tables(fdtd_handle* h) {
+  const Geo& g = h->g;
+  std::vector<float> host;
+  for (int d = 0; d < 3; ++d) {
+    const int n = g.n[d];
+    for (int half = 0; half < 2; ++half) {
+      std::vector<float> b(n), c(n), ik(n);
+      for (int i = 0; i < n; ++i) {
+        double bb, cc, kk;
+        cpml_coef(half ? i + 0.5 : (double)i, n, g.pml[2 * d], g.pml[2 * d + 1], h->pml, bb, cc, kk);
+        b[i] = (float)bb; c[i] = (float)cc; ik[i] = (float)kk;
+      }
+      host.insert(host.end(), b.begin(), b.end());
+      host.insert(host.end(), c.begin(), c.end());
+      host.insert(host.end(), ik.begin(), ik.end());
+    }
+  }
+  TRY(dev_alloc(h, (void**)&h->tables, (int64_t)host.size() * 4));
+  CK(cudaMemcpy(h->tables, host.data(), host.size() * 4, cudaMemcpyHostToDevice));
+  return FDTD_OK;
+}
+
+int ensure_gtab(fdtd_handle* h, int nsteps) {
+  const int ns = (int)h->srcs.size();
+  if (ns == 0) return FDTD_OK;
+  if (h->gtab_cap < nsteps) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->gtab, (int64_t)ns * h->gtab_cap * 4);
+    h->gtab = nullptr;
+    h->gtab_cap = 0;
+    TRY(dev_alloc(h, (void**)&h->gtab, (int64_t)ns * nsteps * 4));
+    std::vector<float> t((size_t)ns * nsteps);
+    for (int q = 0; q < ns; ++q)
+      for (int n = 0; n < nsteps; ++n) t[(size_t)q * nsteps + n] = (float)pulse(h->src_host[q], h->courant, n + 0.5);
+    CK(cudaMemcpy(h->gtab, t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+    h->gtab_cap = nsteps;
+  }
+  for (int q = 0; q < ns; ++q) h->srcs[q].g = h->gtab + (size_t)q * h->gtab_cap;
+  return FDTD_OK;
+}
+
+int64_t det_total_for(const fdtd_handle* h, int nsteps) {
+  return h->det_total_fixed + h->det_total_per_step * (int64_t)nsteps;
+}
+
+int ensure_det(fdtd_handle* h, int nsteps) {
+  const int64_t need = det_total_for(h, nsteps);
+  if (need > h->det_out_cap) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->det_out, h->det_out_cap * 8);
+    h->det_out = nullptr;
+    h->det_out_cap = 0;
+    TRY(dev_alloc(h, (void**)&h->det_out, need * 8));
+    h->det_out_cap = need;
+  }
+  // offsets for this step count
+  int64_t off = 0;
+  int64_t pneed = 0;
+  for (auto& d : h->dets) {
+    d.off = off;
+    off += d.kind == FDTD_DET_PLANE_E2_SUM ? box_cells(d.lo, d.hi) : nsteps;
+    if (d.kind == FDTD_DET_PLANE_FLUX) pneed += (int64_t)d.nblk * nsteps;
+  }
+  if (pneed > h->partial_cap) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->partial, h->partial_cap * 8);
+    h->partial = nullptr;
+    h->partial_cap = 0;
+    TRY(dev_alloc(h, (void**)&h->partial, pneed * 8));
+    h->partial_cap = pneed;
+  }
+  if (need > 0) CK(cudaMemsetAsync(h->det_out, 0, need * 8, h->stream));
+  return FDTD_OK;
+}
+
+double* flux_partial_base(fdtd_handle* h, int which, int nsteps) {
+  int64_t off = 0;
+  int k = 0;
+  for (auto& d : h->dets) {
+    if (d.kind != FDTD_DET_PLANE_FLUX) continue;
+    if (k == which) return h->partial + off;
+    off += (int64_t)d.nblk * nsteps;
+    ++k;
+  }
+  return nullptr;
+}
+
+int reset_state(fdtd_handle* h) {
+  if (h->init) CK(cudaMemcpyAsync(h->fields, h->init, 6 * h->g.vol * 4, cudaMemcpyDeviceToDevice, h->stream));
+  else CK(cudaMemsetAsync(h->fields, 0, 6 * h->g.vol * 4, h->stream));
+  const int64_t pf = h->psi_floats();
+  if (pf > 0) {
+    CK(cudaMemsetAsync(h->psiE, 0, pf * 4, h->stream));
+    CK(cudaMemsetAsync(h->psiH, 0, pf * 4, h->stream));
+  }
+  return FDTD_OK;
+}
+
+bool in_r_cells(const fdtd_handle* h, const int32_t lo[3], const int32_t hi[3]) {
+  for (int d = 0; d < 3; ++d) {
+    if (lo[d] == hi[d]) continue;
+    if (lo[d] < h->g.pml[2 * d] || hi[d] > h->g.n[d] - h->g.pml[2 * d + 1]) return false;
+  }
+  return true;
+}
+
+int ensure_staging(fdtd_handle* h) {
+  if (!h->staging) {
+    const int64_t N = (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2];
+    TRY(dev_alloc(h, (void**)&h->staging, 6 * N * 4));
+  }
+  return FDTD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fdtd_last_error(void) { return g_last_error.c_str(); }
+
+const char* fdtd_version(void) { return "libfdtd 0.1 (sm_103a)"; }
+
+int fdtd_set_byte_budget(int64_t bytes) {
+  g_byte_budget = bytes;
+  return FDTD_OK;
+}
+
+int64_t fdtd_footprint_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps, int32_t record_faces,
+                             const int32_t design_lo[3], const int32_t design_hi[3]) {
+  if (validate(grid, 0.5, pml) != FDTD_OK || nsteps < 0) return -1;
+  const Geo g = make_geo(*grid, *pml, 0.5);
+  int64_t b = 0;
+  b += 7 * g.vol * 4;                              // fields + a
+  b += 2 * psi_bytes(g);                           // forward psi of E and H
+  b += (int64_t)6 * 3 * (g.n[0] + g.n[1] + g.n[2]) * 4 / 3 * 3;  // tables (upper bound)
+  b += 6 * g.vol * 4;                              // adjoint fields
+  b += 4 * psi_bytes(g);                           // adjoint psi, double-buffered
+  int64_t design = 0;
+  if (design_lo && design_hi) design = box_cells(design_lo, design_hi);
+  b += design * 8;
+  if (record_faces) b += make_faces(g).per_step * (int64_t)nsteps * 4;
+  return b;
+}
+
+int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double courant, const float* eps_inv,
+                const fdtd_source* src, int32_t nsrc, const fdtd_detector* det, int32_t ndet, const fdtd_pml* pml,
+                const int32_t design_lo[3], const int32_t design_hi[3], void* cuda_stream) {
+  if (!out) return fail(FDTD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  TRY(validate(grid, courant, pml));
+  if (!eps_inv) return fail(FDTD_ERR_INVALID_ARG, "eps_inv is NULL");
+  if (nsrc < 0 || ndet < 0 || (nsrc > 0 && !src) || (ndet > 0 && !det))
+    return fail(FDTD_ERR_INVALID_ARG, "bad source or detector list");
+  const int n[3] = {grid->nx, grid->ny, grid->nz};
+  for (int q = 0; q < nsrc; ++q) {
+    const fdtd_source& s = src[q];
+    if (s.component < 0 || s.component > 2) return fail(FDTD_ERR_INVALID_ARG, "source %d: component must be 0..2", q);
+    if (!box_ok(s.lo, s.hi, n, false)) return fail(FDTD_ERR_INVALID_ARG, "source %d: box outside the grid", q);
+    if (!(s.tau_steps > 0) || !(s.wavelength_cells > 0))
+      return fail(FDTD_ERR_INVALID_ARG, "source %d: tau and wavelength must be positive", q);
+  }
+  for (int q = 0; q < ndet; ++q) {
+    const fdtd_detector& d = det[q];
+    if (d.kind < 0 || d.kind > 2) return fail(FDTD_ERR_INVALID_ARG, "detector %d: unknown kind", q);
+    if (!box_ok(d.lo, d.hi, n, false)) return fail(FDTD_ERR_INVALID_ARG, "detector %d: box outside the grid", q);
+    if (d.kind == FDTD_DET_POINT_SERIES && (d.component < 0 || d.component > 5))
+      return fail(FDTD_ERR_INVALID_ARG, "detector %d: component must be 0..5", q);
+    if (d.kind == FDTD_DET_PLANE_FLUX && (d.axis < 0 || d.axis > 2))
+      return fail(FDTD_ERR_INVALID_ARG, "detector %d: axis must be 0..2", q);
+  }
+  int32_t zlo[3] = {0, 0, 0};
+  const int32_t* dlo = design_lo ? design_lo : zlo;
+  const int32_t* dhi = design_hi ? design_hi : zlo;
+  if (!box_ok(dlo, dhi, n, true)) return fail(FDTD_ERR_INVALID_ARG, "design box outside the grid");
+
+  fdtd_handle* h = new fdtd_handle();
+  h->pml = *pml;
+  h->spacing = spacing;
+  h->courant = courant;
+  h->stream = (cudaStream_t)cuda_stream;
+  h->g = make_geo(*grid, *pml, courant);
+  h->faces = make_faces(h->g);
+  for (int d = 0; d < 3; ++d) {
+    h->design_lo[d] = dlo[d];
+    h->design_hi[d] = dhi[d];
+  }
+  auto cleanup = [&](int rc) {
+    fdtd_destroy(h);
+    return rc;
+  };
+  const Geo& g = h->g;
+  int rc;
+  if ((rc = dev_alloc(h, (void**)&h->fields, 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = dev_alloc(h, (void**)&h->a, g.vol * 4)) != FDTD_OK) return cleanup(rc);
+  const int64_t pf = h->psi_floats();
+  if ((rc = dev_alloc(h, (void**)&h->psiE, pf * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = dev_alloc(h, (void**)&h->psiH, pf * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = upload_tables(h)) != FDTD_OK) return cleanup(rc);
+  // a = eps_inv with pitch (padding cells hold 1)
+  {
+    const int64_t N = (int64_t)n[0] * n[1] * n[2];
+    float* tmp = nullptr;
+    if ((rc = dev_alloc(h, (void**)&tmp, N * 4)) != FDTD_OK) return cleanup(rc);
+    cudaError_t e = cudaMemcpy(tmp, eps_inv, N * 4, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemset(h->a, 0, g.vol * 4);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2D(h->a, (size_t)g.nxp * 4, tmp, (size_t)n[0] * 4, (size_t)n[0] * 4, (size_t)n[1] * n[2],
+                       cudaMemcpyDeviceToDevice);
+    dev_free(h, tmp, N * 4);
+    if (e != cudaSuccess) return cleanup(fail(FDTD_ERR_CUDA, "copy of eps_inv: %s", cudaGetErrorString(e)));
+  }
+  // sources: weights = amplitude * profile, zero where the component is held by a PEC wall
+  for (int q = 0; q < nsrc; ++q) {
+    const fdtd_source& s = src[q];
+    h->src_host.push_back(s);
+    h->src_host.back().profile = nullptr;
+    const int64_t m = box_cells(s.lo, s.hi);
+    std::vector<float> w((size_t)m);
+    const int c1 = (s.component + 1) % 3, c2 = (s.component + 2) % 3;
+    for (int64_t t = 0; t < m; ++t) {
+      const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
+      int p[3] = {s.lo[0] + int(t % bx), s.lo[1] + int((t / bx) % by), s.lo[2] + int(t / ((int64_t)bx * by))};
+      const double prof = s.profile ? (double)s.profile[t] : 1.0;
+      w[(size_t)t] = (p[c1] == 0 || p[c2] == 0) ? 0.f : (float)(s.amplitude * prof);
+    }
+    float* dw = nullptr;
+    if ((rc = dev_alloc(h, (void**)&dw, m * 4)) != FDTD_OK) return cleanup(rc);
+    h->src_w.push_back(dw);
+    if (cudaMemcpy(dw, w.data(), m * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cleanup(fail(FDTD_ERR_CUDA, "source upload failed"));
+    SrcDev sd;
+    sd.comp = s.component;
+    for (int d = 0; d < 3; ++d) { sd.lo[d] = s.lo[d]; sd.hi[d] = s.hi[d]; }
+    sd.w = dw;
+    sd.g = nullptr;
+    h->srcs.push_back(sd);
+  }
+  for (int q = 0; q < ndet; ++q) {
+    const fdtd_detector& d = det[q];
+    DetDev dd;
+    dd.kind = d.kind;
+    dd.comp = d.component;
+    dd.axis = d.axis;
+    for (int k = 0; k < 3; ++k) { dd.lo[k] = d.lo[k]; dd.hi[k] = d.hi[k]; }
+    dd.off = 0;
+    const int64_t m = box_cells(d.lo, d.hi);
+    dd.nblk = d.kind == FDTD_DET_PLANE_FLUX ? (int)std::min<int64_t>(148, std::max<int64_t>(1, (m + 4095) / 4096)) : 0;
+    if (d.kind == FDTD_DET_PLANE_E2_SUM) h->det_total_fixed += m;
+    else h->det_total_per_step += 1;
+    h->dets.push_back(dd);
+  }
+  *out = h;
+  return FDTD_OK;
+}
+
+int fdtd_destroy(fdtd_handle* h) {
+  if (!h) return FDTD_OK;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(h->fields);
+  cudaFree(h->a);
+  cudaFree(h->psiE);
+  cudaFree(h->psiH);
+  cudaFree(h->tables);
+  cudaFree(h->init);
+  for (float* p : h->src_w) cudaFree(p);
+  cudaFree(h->gtab);
+  cudaFree(h->det_out);
+  cudaFree(h->partial);
+  cudaFree(h->face_hist);
+  cudaFree(h->adj);
+  cudaFree(h->psibar);
+  cudaFree(h->dLda);
+  cudaFree(h->dLddet);
+  cudaFree(h->staging);
+  for (auto& e : h->ev_pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  delete h;
+  return FDTD_OK;
+}
+
+int fdtd_set_design_eps_inv(fdtd_handle* h, const float* eps_inv_box) {
+  if (!h || !eps_inv_box) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  const int64_t m = box_cells(h->design_lo, h->design_hi);
+  if (m == 0) return FDTD_OK;
+  TRY(ensure_staging(h));
+  if (m > 6 * (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2]) return fail(FDTD_ERR_INVALID_ARG, "design box too large");
+  CK(cudaMemcpyAsync(h->staging, eps_inv_box, m * 4, cudaMemcpyDefault, h->stream));
+  launch_set_box(h->g, h->a, h->design_lo, h->design_hi, h->staging, h->stream);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (!fields6) {
+    if (h->init) {
+      CK(cudaStreamSynchronize(h->stream));
+      dev_free(h, h->init, 6 * h->g.vol * 4);
+      h->init = nullptr;
+    }
+    return FDTD_OK;
+  }
+  if (!h->init) {
+    TRY(dev_alloc(h, (void**)&h->init, 6 * h->g.vol * 4));
+    CK(cudaMemsetAsync(h->init, 0, 6 * h->g.vol * 4, h->stream));
+  }
+  TRY(ensure_staging(h));
+  const int64_t N = (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2];
+  CK(cudaMemcpyAsync(h->staging, fields6, 6 * N * 4, cudaMemcpyDefault, h->stream));
+  Fields I;
+  for (int c = 0; c < 6; ++c) I.f[c] = h->init + c * h->g.vol;
+  launch_pack_fields(h->g, I, h->staging, 1, h->stream);
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (nsteps < 0) return fail(FDTD_ERR_INVALID_ARG, "nsteps must be >= 0");
+  const bool record = (flags & FDTD_RECORD_FACES) != 0;
+  if (record) {
+    for (const auto& d : h->dets)
+      if (!in_r_cells(h, d.lo, d.hi))
+        return fail(FDTD_ERR_INVALID_ARG, "a detector lies in the PML; backward needs detectors in the PML-free region");
+    if (!in_r_cells(h, h->design_lo, h->design_hi))
+      return fail(FDTD_ERR_INVALID_ARG, "the design box must lie in the PML-free region");
+  }
+  h->recorded = false;
+  h->consumed = false;
+  h->last_nsteps = nsteps;
+  TRY(ensure_gtab(h, nsteps));
+  TRY(ensure_det(h, nsteps));
+  if (record && h->faces.per_step > 0 && h->face_cap_steps < nsteps) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->face_hist, h->face_cap_steps * h->faces.per_step * 4);
+    h->face_hist = nullptr;
+    h->face_cap_steps = 0;
+    TRY(dev_alloc(h, (void**)&h->face_hist, (int64_t)nsteps * h->faces.per_step * 4));
+    h->face_cap_steps = nsteps;
+  }
+  TRY(reset_state(h));
+  const Geo& g = h->g;
+  const Fields F = h->F();
+  const Tables T = h->tab();
+  const PsiSet PE = h->psi_set(h->psiE), PH = h->psi_set(h->psiH);
+  const bool faces = record && h->faces.per_step > 0;
+  for (int n = 0; n < nsteps; ++n) {
+    {
+      ProfScope ps(h, FDTD_KERNEL_UPDATE_H, n);
+      launch_update_H(g, F, PH, T, h->stream);
+    }
+    if (faces) launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, h->stream);
+    {
+      ProfScope ps(h, FDTD_KERNEL_UPDATE_E, n);
+      launch_update_E(g, F, PE, T, h->a, h->stream);
+    }
+    for (const auto& s : h->srcs) launch_source(g, F, s, n, +1.f, 0, h->stream);
+    int fk = 0;
+    for (const auto& d : h->dets) {
+      double* part = d.kind == FDTD_DET_PLANE_FLUX ? flux_partial_base(h, fk++, nsteps) : nullptr;
+      launch_detector_sample(g, F, d, n, h->det_out, part, h->stream);
+    }
+    h->launches += 2 + (faces ? 1 : 0) + (int64_t)h->srcs.size() + (int64_t)h->dets.size();
+  }
+  int fk = 0;
+  for (const auto& d : h->dets)
+    if (d.kind == FDTD_DET_PLANE_FLUX) {
+      launch_flux_finalize(d, nsteps, flux_partial_base(h, fk++, nsteps), h->det_out, h->stream);
+      h->launches += 1;
+    }
+  CK(cudaGetLastError());
+  TRY(prof_collect(h));
+  h->recorded = record;
+  return FDTD_OK;
+}
+
+int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (!h->recorded || h->consumed)
+    return fail(FDTD_ERR_STATE, "backward needs a forward with FDTD_RECORD_FACES that no backward has consumed");
+  const int nsteps = h->last_nsteps;
+  const int64_t ndet = det_total_for(h, nsteps);
+  if (ndet > 0 && !dL_ddet) return fail(FDTD_ERR_INVALID_ARG, "dL_ddet is NULL");
+  const int64_t M = box_cells(h->design_lo, h->design_hi);
+  if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
+  const Geo& g = h->g;
+  if (!h->adj) TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
+  const int64_t pf = h->psi_floats();
+  if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
+  if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
+  if (ndet > h->dLddet_cap) {
+    CK(cudaStreamSynchronize(h->stream));
+    dev_free(h, h->dLddet, h->dLddet_cap * 8);
+    h->dLddet = nullptr;
+    h->dLddet_cap = 0;
+    TRY(dev_alloc(h, (void**)&h->dLddet, ndet * 8));
+    h->dLddet_cap = ndet;
+  }
+  if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
+  CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
+  if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
+  if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
+
+  const Fields F = h->F(), A = h->A();
+  const Tables T = h->tab();
+  // psibar layout: [E buf0][H buf0][E buf1][H buf1]
+  PsiSet PEb[2], PHb[2];
+  for (int k = 0; k < 2; ++k) {
+    PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
+    PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
+  }
+  int cur = 0;
+  for (int n = nsteps - 1; n >= 0; --n) {
+    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, h->stream);
+    if (h->faces.per_step > 0)
+      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, h->stream);
+    for (const auto& s : h->srcs) launch_source(g, F, s, n, -1.f, 1, h->stream);
+    {
+      ProfScope ps(h, FDTD_KERNEL_REV_E, n);
+      launch_rev_E(g, F, A, PEb[cur], PEb[1 - cur], T, h->a, h->design_lo, h->design_hi, h->dLda, h->stream);
+    }
+    {
+      ProfScope ps(h, FDTD_KERNEL_REV_H, n);
+      launch_rev_H(g, F, A, PHb[cur], PHb[1 - cur], T, h->stream);
+    }
+    cur = 1 - cur;
+    h->launches += 2 + (h->faces.per_step > 0 ? 1 : 0) + (int64_t)h->srcs.size() + (int64_t)h->dets.size();
+  }
+  if (M > 0) {
+    TRY(ensure_staging(h));
+    launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, h->stream);
+    h->launches += 1;
+    CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaGetLastError());
+  TRY(prof_collect(h));
+  h->consumed = true;
+  cudaPointerAttributes at;
+  if (M > 0 && cudaPointerGetAttributes(&at, dL_deps) == cudaSuccess && at.type != cudaMemoryTypeDevice &&
+      at.type != cudaMemoryTypeManaged)
+    CK(cudaStreamSynchronize(h->stream));
+  cudaGetLastError();
+  return FDTD_OK;
+}
+
+int fdtd_read_detectors(fdtd_handle* h, double* out) {
+  if (!h || !out) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  if (h->last_nsteps < 0) return fail(FDTD_ERR_STATE, "no forward has run");
+  const int64_t n = det_total_for(h, h->last_nsteps);
+  if (n == 0) return FDTD_OK;
+  CK(cudaMemcpyAsync(out, h->det_out, n * 8, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int64_t fdtd_detector_total(fdtd_handle* h) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  return det_total_for(h, h->last_nsteps < 0 ? 0 : h->last_nsteps);
+}
+
+int fdtd_get_fields(fdtd_handle* h, float* out6) {
+  if (!h || !out6) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  TRY(ensure_staging(h));
+  launch_pack_fields(h->g, h->F(), h->staging, 0, h->stream);
+  const int64_t N = (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2];
+  CK(cudaMemcpyAsync(out6, h->staging, 6 * N * 4, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int64_t fdtd_bytes_allocated(fdtd_handle* h) { return h ? h->bytes : -1; }
+
+int64_t fdtd_launch_count(fdtd_handle* h) { return h ? h->launches : -1; }
+
+int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (enable && every < 1) return fail(FDTD_ERR_INVALID_ARG, "every must be >= 1");
+  h->prof_every = enable ? every : 0;
+  for (int k = 0; k < FDTD_KERNEL_KINDS; ++k) {
+    h->prof_ms[k] = 0;
+    h->prof_n[k] = 0;
+  }
+  h->ev_used = 0;
+  return FDTD_OK;
+}
+
+int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds) {
+  if (!h || nkinds < 0) return fail(FDTD_ERR_INVALID_ARG, "bad argument");
+  TRY(prof_collect(h));
+  for (int k = 0; k < nkinds && k < FDTD_KERNEL_KINDS; ++k) {
+    if (ms) ms[k] = h->prof_ms[k];
+    if (count) count[k] = h->prof_n[k];
+  }
+  return FDTD_OK;
+}
+
+int fdtd_synchronize(fdtd_handle* h) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Internal device-side types and kernel launchers of libfdtd (not part of the C ABI).
+//
+// Data layout in HBM (one solver):
+//   - six field arrays Ex, Ey, Ez, Hx, Hy, Hz, float32, [nz][ny][nxp] with x fastest and the row pitch
+//     nxp rounded up to 32 floats (128-byte rows);
+//   - a = 1/eps, float32, same layout;
+//   - CPML memories psi only inside the layers: for the derivative along axis d, component c != d,
+//     a compact array whose axis-d extent is the total layer width (x: [nz][ny][Lx], y: [nz][Ly][nxp],
+//     z: [Lz][ny][nxp]);
+//   - per-axis CPML tables b, c, 1/kappa at integer and half positions (float32);
+//   - boundary-face history: per step, the tangential H on the planes just outside the PML-free
+//     region, packed segment by segment;
+//   - adjoint fields with the same layout as the fields; dL/da accumulated in float64 over the design box.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+constexpr int kMaxFaceSeg = 12;
+constexpr int kPitchAlign = 32;
+
+struct Geo {
+  int n[3];           // cells nx, ny, nz
+  int nxp;            // row pitch in floats
+  int64_t plane;      // nxp * ny
+  int64_t vol;        // plane * nz
+  int pml[6];         // layer widths x-lo, x-hi, y-lo, y-hi, z-lo, z-hi
+  int slab[3];        // pml[2d] + pml[2d+1]
+  float S;            // Courant number
+  // PML-free region R, inclusive index ranges along each axis for integer and half positions
+  int rint_lo[3], rint_hi[3], rhalf_lo[3], rhalf_hi[3];
+};
+
+struct Tables {
+  // [axis][0 = integer positions, 1 = half positions], n[axis] entries each
+  const float* b[3][2];
+  const float* c[3][2];
+  const float* ik[3][2];   // 1 / kappa
+};
+
+struct Fields {
+  float* f[6];
+};
+
+struct PsiSet {
+  float* p[3][3];          // [component][axis]; nullptr on the diagonal or when the axis has no layer
+};
+
+struct FaceSeg {
+  int axis, idx, comp;     // plane normal, index along it, H component
+  int lo1, n1, lo2, n2;    // box along e1 = axis+1 and e2 = axis+2 (mod 3)
+  int64_t off;             // offset of the segment inside one step's record
+};
+
+struct FaceSet {
+  int nseg;
+  int64_t per_step;        // floats per step
+  FaceSeg seg[kMaxFaceSeg];
+};
+
+struct SrcDev {
+  int comp;
+  int lo[3], hi[3];
+  const float* w;          // box-shaped amplitude * profile (0 where E is held by a PEC wall)
+  const float* g;          // waveform samples g(n + 1/2), one per step
+};
+
+struct DetDev {
+  int kind, comp, axis;
+  int lo[3], hi[3];
+  int64_t off;             // offset into the concatenated detector output
+  int nblk;                // flux: partial-sum blocks per step
+};
+
+__host__ __device__ inline int64_t cell_index(const Geo& g, int i, int j, int k) {
+  return (int64_t)k * g.plane + (int64_t)j * g.nxp + i;
+}
+
+__host__ __device__ inline int slab_index(const Geo& g, int d, int x) {
+  const int p0 = g.pml[2 * d], p1 = g.pml[2 * d + 1];
+  if (x < p0) return x;
+  if (x >= g.n[d] - p1) return p0 + x - (g.n[d] - p1);
+  return -1;
+}
+
+__host__ __device__ inline int64_t psi_index(const Geo& g, int d, int i, int j, int k, int s) {
+  if (d == 0) return ((int64_t)k * g.n[1] + j) * g.slab[0] + s;
+  if (d == 1) return ((int64_t)k * g.slab[1] + s) * g.nxp + i;
+  return ((int64_t)s * g.n[1] + j) * g.nxp + i;
+}
+
+__host__ __device__ inline int64_t psi_elems(const Geo& g, int d) {
+  if (d == 0) return (int64_t)g.n[2] * g.n[1] * g.slab[0];
+  if (d == 1) return (int64_t)g.n[2] * g.slab[1] * g.nxp;
+  return (int64_t)g.slab[2] * g.n[1] * g.nxp;
+}
+
+// ---- launchers (fdtd_kernels.cu) --------------------------------------------------------------
+void launch_update_H(const Geo& g, const Fields& F, const PsiSet& psiH, const Tables& T, cudaStream_t s);
+void launch_update_E(const Geo& g, const Fields& F, const PsiSet& psiE, const Tables& T, const float* a,
+                     cudaStream_t s);
+void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, float sign, int only_R,
+                   cudaStream_t s);
+void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,
+                            double* partial, cudaStream_t s);
+void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s);
+void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record,
+                      cudaStream_t s);
+void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
+                             const double* dL_ddet, cudaStream_t s);
+void launch_rev_E(const Geo& g, const Fields& F, const Fields& A, const PsiSet& psiE_old, const PsiSet& psiE_new,
+                  const Tables& T, const float* a, const int* dlo, const int* dhi, double* dLda, cudaStream_t s);
+void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& psiH_old, const PsiSet& psiH_new,
+                  const Tables& T, cudaStream_t s);
+void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
+                          float* dL_deps, cudaStream_t s);
+void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);
+void launch_set_box(const Geo& g, float* a, const int* lo, const int* hi, const float* box, cudaStream_t s);
+
+}  // namespace fdtd

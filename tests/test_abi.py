@@ -1,0 +1,124 @@
+"""The C ABI library loads, exports every symbol the header declares, and validates its input on the
+host (no GPU needed: these calls fail before any CUDA work)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2412_12360_b300 import fdtd as F
+from paper_2412_12360_b300 import scenes as S
+from paper_2412_12360_b300.csrc import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return F.lib()
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|int64_t|char\s*\*|void)\s*\**\s*(fdtd_\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = _declared_symbols()
+    assert "fdtd_create" in names and "fdtd_backward" in names and len(names) >= 14
+    for n in names:
+        assert hasattr(L, n), n
+    bound = {s[0] for s in F.SIGNATURES}
+    assert names <= bound, names - bound
+
+
+def test_version_and_error_string(L):
+    assert b"sm_103a" in L.fdtd_version()
+    assert isinstance(F.last_error(), str)
+
+
+def _create(scene, courant=None, pml=None, src=None, det=None, design=None):
+    """Call fdtd_create with possibly broken arguments; return (rc, message)."""
+    sc = scene
+    g = F.make_grid(sc.n)
+    p = F.make_pml(sc)
+    if pml is not None:
+        for f in range(6):
+            p.thickness[f] = pml[f]
+    srcs = (F.fdtd_source * 2)()
+    ns = 0
+    for s in (src if src is not None else sc.sources):
+        srcs[ns].component = s[0] if isinstance(s, tuple) else s.component
+        lo, hi = (s[1], s[2]) if isinstance(s, tuple) else (s.lo, s.hi)
+        for d in range(3):
+            srcs[ns].lo[d] = lo[d]
+            srcs[ns].hi[d] = hi[d]
+        srcs[ns].amplitude = 1.0
+        srcs[ns].wavelength_cells = 20.0
+        srcs[ns].tau_steps = 30.0
+        srcs[ns].t0_steps = 90.0
+        ns += 1
+    dets = (F.fdtd_detector * 2)()
+    nd = 0
+    for d in (det if det is not None else []):
+        dets[nd].kind, dets[nd].component, dets[nd].axis = d[0], d[1], d[2]
+        for k in range(3):
+            dets[nd].lo[k] = d[3][k]
+            dets[nd].hi[k] = d[4][k]
+        nd += 1
+    eps = np.ones(sc.n[::-1], dtype=np.float32)
+    dlo, dhi = design if design is not None else (sc.design_lo, sc.design_hi)
+    h = C.c_void_p()
+    rc = F.lib().fdtd_create(C.byref(h), C.byref(g), 0.0, float(sc.courant if courant is None else courant),
+                             eps.ctypes.data, srcs, ns, dets, nd, C.byref(p), F._I3(*dlo), F._I3(*dhi), None)
+    return rc, F.last_error()
+
+
+def test_create_rejects_bad_input_before_any_device_work(L):
+    sc = S.cavity_32(10)
+    rc, msg = _create(sc, courant=0.6)
+    assert rc == F.FDTD_ERR_UNSTABLE and "stability" in msg
+    rc, _ = _create(sc, courant=-1.0)
+    assert rc == F.FDTD_ERR_INVALID_ARG
+    rc, msg = _create(sc, pml=(16, 16, 0, 0, 0, 0))
+    assert rc == F.FDTD_ERR_INVALID_ARG and "PML" in msg
+    rc, msg = _create(sc, src=[(3, (1, 1, 1), (2, 2, 2))])
+    assert rc == F.FDTD_ERR_INVALID_ARG and "component" in msg
+    rc, msg = _create(sc, src=[(2, (30, 1, 1), (33, 2, 2))])
+    assert rc == F.FDTD_ERR_INVALID_ARG and "box" in msg
+    rc, msg = _create(sc, det=[(7, 0, 0, (1, 1, 1), (2, 2, 2))])
+    assert rc == F.FDTD_ERR_INVALID_ARG and "kind" in msg
+    rc, msg = _create(sc, det=[(0, 6, 0, (1, 1, 1), (2, 2, 2))])
+    assert rc == F.FDTD_ERR_INVALID_ARG
+    rc, msg = _create(sc, det=[(2, 0, 3, (1, 1, 1), (2, 2, 2))])
+    assert rc == F.FDTD_ERR_INVALID_ARG and "axis" in msg
+    rc, msg = _create(sc, design=((4, 4, 4), (40, 8, 8)))
+    assert rc == F.FDTD_ERR_INVALID_ARG and "design" in msg
+
+
+def test_null_handle_calls_fail_cleanly(L):
+    assert L.fdtd_forward(None, 10, 0) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_backward(None, None, None) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_destroy(None) == F.FDTD_OK
+    assert L.fdtd_bytes_allocated(None) == -1
+
+
+def test_footprint_grows_with_steps_and_faces(L):
+    sc = S.design_96(2000)
+    f0 = F.footprint_bytes(sc, 2000, record_faces=False)
+    f1 = F.footprint_bytes(sc, 2000, record_faces=True)
+    f2 = F.footprint_bytes(sc, 4000, record_faces=True)
+    assert 0 < f0 < f1 < f2
+    # face history: 2 tangential H per face cell per step, fp32, on 6 planes of 77 x 77
+    per_step = 6 * 2 * 77 * 77 * 4
+    assert f2 - f1 == 2000 * per_step
+    # fields (6) + a + adjoint fields (6), each 96^3 fp32 (pitch 96)
+    assert f0 >= 13 * 96 ** 3 * 4

@@ -1,0 +1,193 @@
+"""GPU (CUDA, fp32 fields, fp64 accumulators) against the FP64 oracle on the same seeded inputs.
+
+Bars: fields after the run within 1e-4 relative L2; detector outputs within 1e-4 relative; dL/deps
+within 1e-3 relative L2 over the design box (and the max error is reported). Grids span several
+32 x 8 thread tiles with ragged tails; layers differ per face.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2412_12360_b300 import scenes as S
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F(cuda_ok):
+    from paper_2412_12360_b300 import fdtd
+    fdtd.lib()
+    return fdtd
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def ragged_scene(nsteps=600, seed=41):
+    n = (70, 45, 38)
+    pml = (6, 5, 7, 6, 5, 8)
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    eps_inv = np.ones((nz, ny, nx), dtype=np.float32)
+    dlo, dhi = (20, 14, 12), (46, 33, 27)
+    eps_inv[dlo[2]:dhi[2], dlo[1]:dhi[1], dlo[0]:dhi[0]] = S.inv(
+        1.0 + 11.1 * rng.random((dhi[2] - dlo[2], dhi[1] - dlo[1], dhi[0] - dlo[0])))
+    prof = S.gaussian_sheet((ny - 12, nx - 11), 12.0)[None]
+    sheet = S.default_pulse(S.Source(S.EX, (6, 7, 10), (nx - 5, ny - 5, 11), prof, 1.0, 12.0), S.courant_from_factor())
+    pt = H.point_source(S.EZ, (30, 10, 20), wavelength=10.0, amplitude=0.5)
+    dets = [H.point_probe(S.HY, (50, 30, 25)),
+            S.Detector(S.DET_PLANE_E2_SUM, (6, 7, 28), (64, 39, 29)),
+            S.Detector(S.DET_PLANE_FLUX, (58, 7, 8), (59, 39, 30), axis=0),
+            S.Detector(S.DET_PLANE_FLUX, (6, 7, 29), (64, 39, 30), axis=2)]
+    return H.box_scene(n, pml=pml, eps_inv=eps_inv, sources=[sheet, pt], detectors=dets, design=(dlo, dhi),
+                       nsteps=nsteps, name="ragged")
+
+
+def test_forward_pec_cavity_1000_steps(F):
+    sc = S.cavity_32(1000)
+    f_o, d_o = O.forward(sc, 1000)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(1000)
+        f_g = s.fields()
+        d_g = s.detectors()
+    e = rel_l2(f_g, f_o)
+    print("cavity_32 1000 steps: fields rel L2 %.3e" % e)
+    assert e < 1e-4
+    assert rel_l2(d_g, d_o) < 1e-4
+
+
+def test_forward_cpml_ragged_grid(F):
+    sc = ragged_scene(600)
+    f_o, d_o = O.forward(sc, 600)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(600)
+        f_g = s.fields()
+        d_g = s.detectors()
+    e = rel_l2(f_g, f_o)
+    print("ragged 600 steps: fields rel L2 %.3e" % e)
+    assert e < 1e-4
+    off = 0
+    for d in sc.detectors:
+        m = 600 if d.kind != S.DET_PLANE_E2_SUM else int(np.prod([d.hi[k] - d.lo[k] for k in range(3)]))
+        ed = rel_l2(d_g[off:off + m], d_o[off:off + m])
+        print("  detector kind %d rel %.3e" % (d.kind, ed))
+        assert ed < 1e-4
+        off += m
+
+
+def test_forward_from_initial_state_and_zero_steps(F):
+    sc = S.cavity_32(200)
+    init = S.random_fields(sc, 3)
+    with F.Solver(sc) as s:
+        s.fdtd_set_initial_fields(init)
+        s.fdtd_forward(0)
+        assert np.array_equal(s.fields(), init)
+        s.fdtd_forward(200)
+        f_g = s.fields()
+    f_o, _ = O.forward(sc, 200, init.astype(np.float64))
+    assert rel_l2(f_g, f_o) < 1e-4
+
+
+def test_time_reversal_roundtrip_drift(F):
+    """Forward then the inverse update step (inside backward) returns the initial state on R."""
+    for sc in (S.cavity_32(500), ragged_scene(500)):
+        init = S.random_fields(sc, 5)
+        with F.Solver(sc) as s:
+            s.fdtd_set_initial_fields(init)
+            s.fdtd_forward(500, record_faces=True)
+            fwd = s.fields()
+            s.gradient(np.zeros(s.fdtd_detector_total()))
+            back = s.fields()
+        m = H.r_masks(sc)
+        drift = rel_l2(back[m], init[m])
+        print("%s: fp32 round-trip drift after 500+500 steps: rel L2 %.3e, max %.3e" % (
+            sc.name, drift, np.max(np.abs(back[m] - init[m]))))
+        assert rel_l2(fwd[m], init[m]) > 0.1
+        assert drift < 1e-4
+
+
+def test_gradient_matches_oracle_ragged(F):
+    sc = ragged_scene(400)
+    rng = np.random.default_rng(7)
+    g = rng.standard_normal(O.detector_total(sc, 400))
+    grad_o, _, det_o = O.gradient(sc, 400, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(400, record_faces=True)
+        det_g = s.detectors()
+        grad_g = s.gradient(g)
+    e = rel_l2(grad_g, grad_o)
+    print("ragged 400 steps: dL/deps rel L2 %.3e, max abs err / max %.3e" % (
+        e, np.max(np.abs(grad_g - grad_o)) / np.max(np.abs(grad_o))))
+    assert rel_l2(det_g, det_o) < 1e-4
+    assert e < 1e-3
+
+
+def test_gradient_pec_point_detectors(F):
+    sc = S.cavity_32(300)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal(O.detector_total(sc, 300))
+    grad_o, _, _ = O.gradient(sc, 300, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(300, record_faces=True)
+        grad_g = s.gradient(g)
+    e = rel_l2(grad_g, grad_o)
+    print("cavity_32 300 steps: dL/deps rel L2 %.3e" % e)
+    assert e < 1e-3
+
+
+def test_device_and_host_buffers_agree_and_runs_are_deterministic(F):
+    import torch
+    sc = ragged_scene(150)
+    g = np.random.default_rng(9).standard_normal(O.detector_total(sc, 150))
+    outs = []
+    for _ in range(2):
+        with F.Solver(sc, eps_inv=torch.from_numpy(sc.eps_inv).cuda()) as s:
+            s.fdtd_forward(150, record_faces=True)
+            det_d = torch.zeros(s.fdtd_detector_total(), dtype=torch.float64, device="cuda")
+            s.fdtd_read_detectors(det_d)
+            gd = torch.from_numpy(g).cuda()
+            out_d = torch.zeros(sc.design_shape(), dtype=torch.float32, device="cuda")
+            s.fdtd_backward(gd, out_d)
+            torch.cuda.synchronize()
+            outs.append((det_d.cpu().numpy(), out_d.cpu().numpy()))
+    with F.Solver(sc) as s:
+        s.fdtd_forward(150, record_faces=True)
+        det_h = s.detectors()
+        out_h = s.gradient(g)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0], det_h) and np.array_equal(outs[0][1], out_h)
+
+
+def test_state_errors_and_byte_budget(F):
+    sc = S.cavity_32(20)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(20)
+        with pytest.raises(F.FDTDError) as ei:
+            s.gradient(np.zeros(s.fdtd_detector_total()))
+        assert ei.value.code == F.FDTD_ERR_STATE
+        s.fdtd_forward(20, record_faces=True)
+        s.gradient(np.zeros(s.fdtd_detector_total()))
+        with pytest.raises(F.FDTDError) as ei:
+            s.gradient(np.zeros(s.fdtd_detector_total()))
+        assert ei.value.code == F.FDTD_ERR_STATE
+    F.set_byte_budget(1 << 20)
+    try:
+        with pytest.raises(F.FDTDError) as ei:
+            F.Solver(sc)
+        assert ei.value.code == F.FDTD_ERR_OOM
+    finally:
+        F.set_byte_budget(-1)
+
+
+def test_backward_rejects_detectors_in_the_pml(F):
+    sc = ragged_scene(10)
+    sc.detectors = [S.Detector(S.DET_PLANE_E2_SUM, (1, 7, 28), (64, 40, 29))]
+    with F.Solver(sc) as s:
+        s.fdtd_forward(10)  # plain forward is fine
+        with pytest.raises(F.FDTDError) as ei:
+            s.fdtd_forward(10, record_faces=True)
+        assert ei.value.code == F.FDTD_ERR_INVALID_ARG
