@@ -47,6 +47,11 @@ def workload(name):
         sc = scenes.waveguide_600()
         desc = ("waveguide_600: 600^3 grid, 12-cell CPML, Si core eps=12.25 in SiO2 eps=2.085, 200^3 design "
                 "box, Poynting-flux objective, 4000 steps fwd + 4000 reversed")
+    elif name.startswith("design_") and name[7:].isdigit():
+        n = int(name[7:])
+        sc = scenes.design_box_scene((n, n, n), 10, max(8, (2 * n) // 5), 2000, 1234, name=name)
+        desc = ("%s: %d^3 Yee grid, 10-cell CPML, Gaussian-beam Ex sheet, centred design box, |E|^2 plane "
+                "objective, 2000 steps fwd + 2000 reversed" % (name, n))
     else:
         raise SystemExit("unknown workload " + name)
     return sc, desc
@@ -206,6 +211,9 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc, desc = workload(args.workload)
+    if args.time_steps:
+        sc.nsteps = args.time_steps
+        desc += " [time steps overridden: %d]" % args.time_steps
     T = sc.nsteps
     stream = torch.cuda.Stream(device=dev)
     solver = fdtd.Solver(sc, stream=stream)
@@ -375,6 +383,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="design_96")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override the workload's time steps (profiling runs only; not a bench line)")
     ap.add_argument("--profile-every", type=int, default=16)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (null if stale)")

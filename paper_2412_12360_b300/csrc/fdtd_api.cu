@@ -1,5 +1,10 @@
 // Host side of the libfdtd C ABI (include/fdtd.h): validation, device memory, CPML and source tables,
 // and the forward and reverse time loops of arXiv 2412.12360 Sec. 2.1-2.2.
+//
+// The time loops are captured once into CUDA graphs (one per phase, keyed by step count and flags)
+// and replayed for every later solve of the same shape, so a solve costs one graph launch per phase
+// instead of thousands of kernel launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -27,20 +32,31 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define CK(call)                                                                          \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess) return fail(FDTD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+#define CK(call)                                                                                    \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return fail(FDTD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+#define TRY(x)                      \
+  do {                              \
+    int rc_ = (x);                  \
+    if (rc_ != FDTD_OK) return rc_; \
   } while (0)
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-// CPML grading of one position (depth d of the component's own position into the layer).
+// CPML grading at one position (d = depth of the component's own position into the layer).
 void cpml_coef(double x, int N, int p0, int p1, const fdtd_pml& pm, double& b, double& c, double& ik) {
   double d = 0.0;
   if (p0 > 0 && x < p0) d = (p0 - x) / p0;
   else if (p1 > 0 && x > N - p1) d = (x - (N - p1)) / p1;
-  if (d <= 0.0) { b = 1.0; c = 0.0; ik = 1.0; return; }
+  if (d <= 0.0) {
+    b = 1.0;
+    c = 0.0;
+    ik = 1.0;
+    return;
+  }
   const double dm = std::pow(d, pm.grading_m);
   const double sigma = pm.sigma_max * dm;
   const double kappa = 1.0 + (pm.kappa_max - 1.0) * dm;
@@ -70,7 +86,9 @@ int64_t box_cells(const int32_t lo[3], const int32_t hi[3]) {
 
 Geo make_geo(const fdtd_grid& gr, const fdtd_pml& pm, double S) {
   Geo g;
-  g.n[0] = gr.nx; g.n[1] = gr.ny; g.n[2] = gr.nz;
+  g.n[0] = gr.nx;
+  g.n[1] = gr.ny;
+  g.n[2] = gr.nz;
   g.nxp = (int)round_up(gr.nx, kPitchAlign);
   g.plane = (int64_t)g.nxp * gr.ny;
   g.vol = g.plane * gr.nz;
@@ -86,6 +104,9 @@ Geo make_geo(const fdtd_grid& gr, const fdtd_pml& pm, double S) {
   return g;
 }
 
+// Tangential H on the planes just outside the PML-free region R (Sec. 2.2, "six two-dimensional
+// slices"): along axis d, components d+1 and d+2 at index p_lo - 1 and at n - p_hi, over the
+// integer-position range of R on the two other axes.
 FaceSet make_faces(const Geo& g) {
   FaceSet fs;
   fs.nseg = 0;
@@ -123,6 +144,9 @@ int validate(const fdtd_grid* grid, double courant, const fdtd_pml* pml) {
   const int n[3] = {grid->nx, grid->ny, grid->nz};
   for (int d = 0; d < 3; ++d)
     if (n[d] < 2 || n[d] > (1 << 16)) return fail(FDTD_ERR_INVALID_ARG, "grid size %d out of range [2, 65536]", n[d]);
+  // the kernels index each field array with 32-bit offsets
+  if ((int64_t)round_up(n[0], kPitchAlign) * n[1] * n[2] >= (int64_t(1) << 31))
+    return fail(FDTD_ERR_INVALID_ARG, "grid of %d x %d x %d cells exceeds 2^31 cells per field array", n[0], n[1], n[2]);
   if (!(courant > 0.0)) return fail(FDTD_ERR_INVALID_ARG, "courant must be positive");
   if (courant > (1.0 / std::sqrt(3.0)) * (1.0 + 1e-12))
     return fail(FDTD_ERR_UNSTABLE, "courant %.9g exceeds the 3D stability limit 1/sqrt(3)", courant);
@@ -137,29 +161,58 @@ int validate(const fdtd_grid* grid, double courant, const fdtd_pml* pml) {
   return FDTD_OK;
 }
 
+struct Ev {
+  cudaEvent_t a, b;
+  int kind;
+};
+
+// A captured time loop, replayed while its shape and buffers stay the same.
+struct LoopGraph {
+  cudaGraphExec_t exec = nullptr;
+  int nsteps = -1;
+  int key = -1;
+  uint64_t gen = 0;
+  std::vector<Ev> ev;      // timing events recorded by the graph (profiling only)
+  int64_t launches = 0;    // kernels per replay
+  int cur_after = 0;       // field buffer holding the state after the loop
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (auto& e : ev) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    ev.clear();
+    nsteps = -1;
+    key = -1;
+  }
+};
+
 }  // namespace
 
 struct fdtd_handle {
   Geo g{};
   fdtd_pml pml{};
   double spacing = 0, courant = 0;
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;  // caller's stream
+  cudaStream_t cap = nullptr;     // private stream used only to capture the time loops
   int32_t design_lo[3] = {0, 0, 0}, design_hi[3] = {0, 0, 0};
   FaceSet faces{};
+  int tz = 8;                     // z-planes per block of the fused kernels
 
   std::vector<fdtd_source> src_host;
-  std::vector<std::vector<float>> src_profile;  // host copies of amplitude * profile
   std::vector<SrcDev> srcs;
   std::vector<DetDev> dets;
   int64_t det_total_per_step = 0, det_total_fixed = 0;
 
   // device memory
-  float* fields = nullptr;     // 6 * vol
+  float* fields = nullptr;     // 2 x 6 x vol: double-buffered (the fused kernels read cur, write 1 - cur)
+  int cur = 0;
   float* a = nullptr;          // vol
-  float* psiE = nullptr;       // forward CPML memories of E (compact slabs)
+  float* psiE = nullptr;       // CPML memories of E (compact slabs), double-buffered like the fields
   float* psiH = nullptr;
-  float* tables = nullptr;     // 3 axes x 6 tables x n
-  float* init = nullptr;       // optional initial state, 6 * vol
+  float* tables = nullptr;     // 3 axes x 2 positions x (b, c, 1/kappa) x n
+  float* init = nullptr;       // optional initial state, 6 x vol
   std::vector<float*> src_w;   // per source box weights
   float* gtab = nullptr;       // nsrc x gtab_cap waveform samples
   int gtab_cap = 0;
@@ -169,24 +222,24 @@ struct fdtd_handle {
   int64_t partial_cap = 0;
   float* face_hist = nullptr;  // steps x faces.per_step
   int64_t face_cap_steps = 0;
-  float* adj = nullptr;        // 6 * vol adjoint fields
-  float* psibar = nullptr;     // 2 buffers x (psiE + psiH) adjoint memories
+  float* adj = nullptr;        // 6 x vol adjoint fields
+  float* psibar = nullptr;     // 2 buffers x (psi-bar E + psi-bar H)
   double* dLda = nullptr;      // design box
   double* dLddet = nullptr;    // device copy of dL/d(detectors)
   int64_t dLddet_cap = 0;
-  float* staging = nullptr;    // 6 * N, unpitched
+  float* staging = nullptr;    // 6 x N, unpitched
   int64_t bytes = 0;
+  uint64_t gen = 1;            // bumped whenever a buffer used by a captured loop is reallocated
 
   int last_nsteps = -1;
   bool recorded = false;
   bool consumed = false;
 
+  LoopGraph gfwd, gbwd;
+
   // launch accounting and sampled event timing
   int64_t launches = 0;
-  int prof_every = 0;                       // 0 = off
-  struct Ev { cudaEvent_t a, b; int kind; };
-  std::vector<Ev> ev_pool;
-  size_t ev_used = 0;
+  int prof_every = 0;  // 0 = off
   double prof_ms[FDTD_KERNEL_KINDS] = {0};
   int64_t prof_n[FDTD_KERNEL_KINDS] = {0};
 
@@ -196,24 +249,32 @@ struct fdtd_handle {
     for (int d = 0; d < 3; ++d) {
       const int n = g.n[d];
       for (int h = 0; h < 2; ++h) {
-        T.b[d][h] = tables + off; off += n;
-        T.c[d][h] = tables + off; off += n;
-        T.ik[d][h] = tables + off; off += n;
+        T.b[d][h] = tables + off;
+        off += n;
+        T.c[d][h] = tables + off;
+        off += n;
+        T.ik[d][h] = tables + off;
+        off += n;
       }
+    }
+    for (int d = 0; d < 3; ++d) {
+      T.sidx[d] = reinterpret_cast<const int*>(tables + off);
+      off += g.n[d];
     }
     return T;
   }
-  Fields F() const {
+  Fields F(int b) const {
     Fields f;
-    for (int c = 0; c < 6; ++c) f.f[c] = fields + c * g.vol;
+    for (int c = 0; c < 6; ++c) f.f[c] = fields + (int64_t)b * 6 * g.vol + c * g.vol;
     return f;
   }
+  Fields F() const { return F(cur); }
   Fields A() const {
     Fields f;
     for (int c = 0; c < 6; ++c) f.f[c] = adj + c * g.vol;
     return f;
   }
-  // psi pointer set over a base buffer laid out as axis-major pairs of components
+  // psi pointers over a buffer laid out axis by axis, two components per axis
   PsiSet psi_set(float* base) const {
     PsiSet P;
     for (int c = 0; c < 3; ++c)
@@ -234,39 +295,28 @@ struct fdtd_handle {
 
 namespace {
 
-// Start/stop a sampled timing interval around one launch of kernel `kind` (no-op unless profiling
-// and `step` is a multiple of the sampling interval).
+// Brackets every `every`-th launch of kernel `kind` with events recorded into `evs` (profiling only).
 struct ProfScope {
-  fdtd_handle* h;
+  std::vector<Ev>* evs;
+  cudaStream_t st;
   int idx = -1;
-  ProfScope(fdtd_handle* h_, int kind, int step) : h(h_) {
-    if (h->prof_every <= 0 || step % h->prof_every != 0) return;
-    if (h->ev_used == h->ev_pool.size()) {
-      fdtd_handle::Ev e;
-      if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return;
-      h->ev_pool.push_back(e);
+  ProfScope(fdtd_handle* h, std::vector<Ev>* evs_, cudaStream_t st_, int kind, int step) : evs(evs_), st(st_) {
+    if (!evs || h->prof_every <= 0 || step % h->prof_every != 0) return;
+    Ev e;
+    if (cudaEventCreate(&e.a) != cudaSuccess) return;
+    if (cudaEventCreate(&e.b) != cudaSuccess) {
+      cudaEventDestroy(e.a);
+      return;
     }
-    idx = (int)h->ev_used++;
-    h->ev_pool[idx].kind = kind;
-    cudaEventRecord(h->ev_pool[idx].a, h->stream);
+    e.kind = kind;
+    evs->push_back(e);
+    idx = (int)evs->size() - 1;
+    cudaEventRecordWithFlags((*evs)[idx].a, st, cudaEventRecordExternal);
   }
   ~ProfScope() {
-    if (idx >= 0) cudaEventRecord(h->ev_pool[idx].b, h->stream);
+    if (idx >= 0) cudaEventRecordWithFlags((*evs)[idx].b, st, cudaEventRecordExternal);
   }
 };
-
-int prof_collect(fdtd_handle* h) {
-  if (h->prof_every <= 0 || h->ev_used == 0) return FDTD_OK;
-  CK(cudaStreamSynchronize(h->stream));
-  for (size_t i = 0; i < h->ev_used; ++i) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, h->ev_pool[i].a, h->ev_pool[i].b));
-    h->prof_ms[h->ev_pool[i].kind] += ms;
-    h->prof_n[h->ev_pool[i].kind] += 1;
-  }
-  h->ev_used = 0;
-  return FDTD_OK;
-}
 
 int dev_alloc(fdtd_handle* h, void** p, int64_t bytes) {
   *p = nullptr;
@@ -281,6 +331,7 @@ int dev_alloc(fdtd_handle* h, void** p, int64_t bytes) {
   }
   if (e != cudaSuccess) return fail(FDTD_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
   h->bytes += bytes;
+  h->gen += 1;
   return FDTD_OK;
 }
 
@@ -288,14 +339,22 @@ void dev_free(fdtd_handle* h, void* p, int64_t bytes) {
   if (p) {
     cudaFree(p);
     h->bytes -= bytes;
+    h->gen += 1;
   }
 }
 
-#define TRY(x)                  \
-  do {                          \
-    int rc_ = (x);              \
-    if (rc_ != FDTD_OK) return rc_; \
-  } while (0)
+// (Re)allocate *p to hold at least `need` elements of `esize` bytes, tracking the capacity.
+template <class T>
+int ensure_buf(fdtd_handle* h, T** p, int64_t* cap, int64_t need, int64_t esize) {
+  if (need <= *cap) return FDTD_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  dev_free(h, *p, *cap * esize);
+  *p = nullptr;
+  *cap = 0;
+  TRY(dev_alloc(h, (void**)p, need * esize));
+  *cap = need;
+  return FDTD_OK;
+}
 
 int upload_tables(fdtd_handle* h) {
   const Geo& g = h->g;
@@ -307,13 +366,22 @@ int upload_tables(fdtd_handle* h) {
       for (int i = 0; i < n; ++i) {
         double bb, cc, kk;
         cpml_coef(half ? i + 0.5 : (double)i, n, g.pml[2 * d], g.pml[2 * d + 1], h->pml, bb, cc, kk);
-        b[i] = (float)bb; c[i] = (float)cc; ik[i] = (float)kk;
+        b[i] = (float)bb;
+        c[i] = (float)cc;
+        ik[i] = (float)kk;
       }
       host.insert(host.end(), b.begin(), b.end());
       host.insert(host.end(), c.begin(), c.end());
       host.insert(host.end(), ik.begin(), ik.end());
     }
   }
+  for (int d = 0; d < 3; ++d)  // slab index tables, stored as int bit patterns after the float tables
+    for (int i = 0; i < g.n[d]; ++i) {
+      const int si = slab_index(g, d, i);
+      float f;
+      std::memcpy(&f, &si, 4);
+      host.push_back(f);
+    }
   TRY(dev_alloc(h, (void**)&h->tables, (int64_t)host.size() * 4));
   CK(cudaMemcpy(h->tables, host.data(), host.size() * 4, cudaMemcpyHostToDevice));
   return FDTD_OK;
@@ -344,53 +412,29 @@ int64_t det_total_for(const fdtd_handle* h, int nsteps) {
 
 int ensure_det(fdtd_handle* h, int nsteps) {
   const int64_t need = det_total_for(h, nsteps);
-  if (need > h->det_out_cap) {
-    CK(cudaStreamSynchronize(h->stream));
-    dev_free(h, h->det_out, h->det_out_cap * 8);
-    h->det_out = nullptr;
-    h->det_out_cap = 0;
-    TRY(dev_alloc(h, (void**)&h->det_out, need * 8));
-    h->det_out_cap = need;
-  }
-  // offsets for this step count
-  int64_t off = 0;
-  int64_t pneed = 0;
+  TRY(ensure_buf(h, &h->det_out, &h->det_out_cap, need, 8));
+  int64_t off = 0, pneed = 0;
   for (auto& d : h->dets) {
     d.off = off;
     off += d.kind == FDTD_DET_PLANE_E2_SUM ? box_cells(d.lo, d.hi) : nsteps;
-    if (d.kind == FDTD_DET_PLANE_FLUX) pneed += (int64_t)d.nblk * nsteps;
+    if (d.kind == FDTD_DET_PLANE_FLUX) {
+      d.poff = pneed;
+      pneed += (int64_t)d.nblk * nsteps;
+    }
   }
-  if (pneed > h->partial_cap) {
-    CK(cudaStreamSynchronize(h->stream));
-    dev_free(h, h->partial, h->partial_cap * 8);
-    h->partial = nullptr;
-    h->partial_cap = 0;
-    TRY(dev_alloc(h, (void**)&h->partial, pneed * 8));
-    h->partial_cap = pneed;
-  }
+  TRY(ensure_buf(h, &h->partial, &h->partial_cap, pneed, 8));
   if (need > 0) CK(cudaMemsetAsync(h->det_out, 0, need * 8, h->stream));
   return FDTD_OK;
 }
 
-double* flux_partial_base(fdtd_handle* h, int which, int nsteps) {
-  int64_t off = 0;
-  int k = 0;
-  for (auto& d : h->dets) {
-    if (d.kind != FDTD_DET_PLANE_FLUX) continue;
-    if (k == which) return h->partial + off;
-    off += (int64_t)d.nblk * nsteps;
-    ++k;
-  }
-  return nullptr;
-}
-
 int reset_state(fdtd_handle* h) {
+  h->cur = 0;
   if (h->init) CK(cudaMemcpyAsync(h->fields, h->init, 6 * h->g.vol * 4, cudaMemcpyDeviceToDevice, h->stream));
   else CK(cudaMemsetAsync(h->fields, 0, 6 * h->g.vol * 4, h->stream));
   const int64_t pf = h->psi_floats();
   if (pf > 0) {
-    CK(cudaMemsetAsync(h->psiE, 0, pf * 4, h->stream));
-    CK(cudaMemsetAsync(h->psiH, 0, pf * 4, h->stream));
+    CK(cudaMemsetAsync(h->psiE, 0, 2 * pf * 4, h->stream));
+    CK(cudaMemsetAsync(h->psiH, 0, 2 * pf * 4, h->stream));
   }
   return FDTD_OK;
 }
@@ -411,13 +455,156 @@ int ensure_staging(fdtd_handle* h) {
   return FDTD_OK;
 }
 
+bool is_host_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
+}
+
+// ---- the time loops -------------------------------------------------------------------------------
+
+// Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
+// fused kernel's slots), then the fixed-order flux sums. Mutates h->cur as it goes.
+int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st, std::vector<Ev>* evs) {
+  const Geo& g = h->g;
+  const int64_t pf = h->psi_floats();
+  const bool faces = record && h->faces.per_step > 0;
+  int64_t launches = 0;
+  FwdArgs fa;
+  fa.g = g;
+  fa.T = h->tab();
+  fa.a = h->a;
+  fa.tz = h->tz;
+  fa.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
+  for (int q = 0; q < fa.nsrc; ++q) fa.src[q] = h->srcs[q];
+  fa.ndet = (int)std::min<size_t>(h->dets.size(), kMaxDet);
+  for (int q = 0; q < fa.ndet; ++q) fa.det[q] = h->dets[q];
+  fa.det_out = h->det_out;
+  fa.partial = h->partial;
+  fa.faces = h->faces;
+  for (int n = 0; n < nsteps; ++n) {
+    const int c = h->cur, x = 1 - c;
+    fa.cur = h->F(c);
+    fa.nxt = h->F(x);
+    fa.psiE_cur = h->psi_set(h->psiE + c * pf);
+    fa.psiE_nxt = h->psi_set(h->psiE + x * pf);
+    fa.psiH_cur = h->psi_set(h->psiH + c * pf);
+    fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
+    fa.step = n;
+    fa.rec = faces ? h->face_hist + (int64_t)n * h->faces.per_step : nullptr;
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
+      launch_fwd_fused(fa, st);
+    }
+    launches += 1;
+    const Fields Fn = h->F(x);
+    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
+    for (size_t q = kMaxDet; q < h->dets.size(); ++q, ++launches)
+      launch_detector_sample(g, Fn, h->dets[q], n, h->det_out, h->partial, st);
+    h->cur = x;
+  }
+  for (const auto& d : h->dets)
+    if (d.kind == FDTD_DET_PLANE_FLUX && nsteps > 0) {
+      launch_flux_finalize(d, nsteps, h->partial, h->det_out, st);
+      launches += 1;
+    }
+  return launches;
+}
+
+// Reverse (Sec. 2.2): per step, detector adjoints, face replay, source removal, then the inverse-E /
+// adjoint-H kernel and the inverse-H / adjoint-E kernel, in place on the current field buffer.
+int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
+  const Geo& g = h->g;
+  const int64_t pf = h->psi_floats();
+  const Fields F = h->F(), A = h->A();
+  const Tables T = h->tab();
+  PsiSet PEb[2], PHb[2];  // psi-bar layout: [E 0][H 0][E 1][H 1]
+  for (int k = 0; k < 2; ++k) {
+    PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
+    PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
+  }
+  int64_t launches = 0;
+  int pb = 0;
+  for (int n = nsteps - 1; n >= 0; --n) {
+    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
+    launches += (int64_t)h->dets.size();
+    if (h->faces.per_step > 0) {
+      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, st);
+      launches += 1;
+    }
+    for (const auto& s : h->srcs) launch_source(g, F, s, n, -1.f, 1, st);
+    launches += (int64_t)h->srcs.size();
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
+      launch_rev_E(g, F, A, PEb[pb], PEb[1 - pb], T, h->a, h->design_lo, h->design_hi, h->dLda, st);
+    }
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
+      launch_rev_H(g, F, A, PHb[pb], PHb[1 - pb], T, st);
+    }
+    launches += 2;
+    pb = 1 - pb;
+  }
+  return launches;
+}
+
+int prof_collect(fdtd_handle* h, LoopGraph& lg) {
+  if (h->prof_every <= 0 || lg.ev.empty()) return FDTD_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto& e : lg.ev) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e.a, e.b));
+    h->prof_ms[e.kind] += ms;
+    h->prof_n[e.kind] += 1;
+  }
+  return FDTD_OK;
+}
+
+// Replay the cached graph of a time loop, capturing it first if its shape or buffers changed.
+template <class Enqueue>
+int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int key, Enqueue enqueue) {
+  if (nsteps == 0) return FDTD_OK;
+  const int cur0 = h->cur;
+  if (!(lg.exec && lg.nsteps == nsteps && lg.key == key && lg.gen == h->gen)) {
+    lg.reset();
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    lg.launches = enqueue(h->cap, h->prof_every > 0 ? &lg.ev : nullptr);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (e != cudaSuccess) {
+      h->cur = cur0;
+      lg.reset();
+      return fail(FDTD_ERR_CUDA, "capture of the time loop failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&lg.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->cur = cur0;
+      lg.reset();
+      return fail(FDTD_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    lg.cur_after = h->cur;
+    lg.nsteps = nsteps;
+    lg.key = key;
+    lg.gen = h->gen;
+  }
+  CK(cudaGraphLaunch(lg.exec, h->stream));
+  h->cur = lg.cur_after;
+  h->launches += lg.launches;
+  TRY(prof_collect(h, lg));
+  return FDTD_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char* fdtd_last_error(void) { return g_last_error.c_str(); }
 
-const char* fdtd_version(void) { return "libfdtd 0.1 (sm_103a)"; }
+const char* fdtd_version(void) { return "libfdtd 0.2 (sm_103a)"; }
 
 int fdtd_set_byte_budget(int64_t bytes) {
   g_byte_budget = bytes;
@@ -429,11 +616,11 @@ int64_t fdtd_footprint_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t
   if (validate(grid, 0.5, pml) != FDTD_OK || nsteps < 0) return -1;
   const Geo g = make_geo(*grid, *pml, 0.5);
   int64_t b = 0;
-  b += 7 * g.vol * 4;                              // fields + a
-  b += 2 * psi_bytes(g);                           // forward psi of E and H
-  b += (int64_t)6 * 3 * (g.n[0] + g.n[1] + g.n[2]) * 4 / 3 * 3;  // tables (upper bound)
-  b += 6 * g.vol * 4;                              // adjoint fields
-  b += 4 * psi_bytes(g);                           // adjoint psi, double-buffered
+  b += 13 * g.vol * 4;                                // fields (double-buffered) + a
+  b += 4 * psi_bytes(g);                              // forward psi of E and H, double-buffered
+  b += (int64_t)7 * (g.n[0] + g.n[1] + g.n[2]) * 4;   // CPML and slab-index tables
+  b += 6 * g.vol * 4;                                 // adjoint fields
+  b += 4 * psi_bytes(g);                              // adjoint psi, double-buffered
   int64_t design = 0;
   if (design_lo && design_hi) design = box_cells(design_lo, design_hi);
   b += design * 8;
@@ -489,14 +676,27 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   };
   const Geo& g = h->g;
   int rc;
-  if ((rc = dev_alloc(h, (void**)&h->fields, 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaError_t e = cudaGetLastError();
+    h->cap = nullptr;
+    return cleanup(fail(FDTD_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+  }
+  {
+    // z-chunk of the fused kernels: enough blocks to fill every SM several times over
+    const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
+                        ((n[1] + fused_tile_y() - 1) / fused_tile_y());
+    const int64_t want = 148 * 8;
+    const int tz = (int)std::max<int64_t>(1, (int64_t)n[2] * nxy / want);
+    h->tz = std::max(4, std::min(tz, n[2]));
+  }
+  if ((rc = dev_alloc(h, (void**)&h->fields, 2 * 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = dev_alloc(h, (void**)&h->a, g.vol * 4)) != FDTD_OK) return cleanup(rc);
   const int64_t pf = h->psi_floats();
-  if ((rc = dev_alloc(h, (void**)&h->psiE, pf * 4)) != FDTD_OK) return cleanup(rc);
-  if ((rc = dev_alloc(h, (void**)&h->psiH, pf * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = dev_alloc(h, (void**)&h->psiE, 2 * pf * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = dev_alloc(h, (void**)&h->psiH, 2 * pf * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = upload_tables(h)) != FDTD_OK) return cleanup(rc);
-  // a = eps_inv with pitch (padding cells hold 1)
   {
+    // a = eps_inv with the row pitch (padding cells hold 0 and are never read)
     const int64_t N = (int64_t)n[0] * n[1] * n[2];
     float* tmp = nullptr;
     if ((rc = dev_alloc(h, (void**)&tmp, N * 4)) != FDTD_OK) return cleanup(rc);
@@ -514,11 +714,11 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     h->src_host.push_back(s);
     h->src_host.back().profile = nullptr;
     const int64_t m = box_cells(s.lo, s.hi);
-    std::vector<float> w((size_t)m);
+    const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
     const int c1 = (s.component + 1) % 3, c2 = (s.component + 2) % 3;
+    std::vector<float> w((size_t)m);
     for (int64_t t = 0; t < m; ++t) {
-      const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
-      int p[3] = {s.lo[0] + int(t % bx), s.lo[1] + int((t / bx) % by), s.lo[2] + int(t / ((int64_t)bx * by))};
+      const int p[3] = {s.lo[0] + int(t % bx), s.lo[1] + int((t / bx) % by), s.lo[2] + int(t / ((int64_t)bx * by))};
       const double prof = s.profile ? (double)s.profile[t] : 1.0;
       w[(size_t)t] = (p[c1] == 0 || p[c2] == 0) ? 0.f : (float)(s.amplitude * prof);
     }
@@ -529,7 +729,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       return cleanup(fail(FDTD_ERR_CUDA, "source upload failed"));
     SrcDev sd;
     sd.comp = s.component;
-    for (int d = 0; d < 3; ++d) { sd.lo[d] = s.lo[d]; sd.hi[d] = s.hi[d]; }
+    for (int d = 0; d < 3; ++d) {
+      sd.lo[d] = s.lo[d];
+      sd.hi[d] = s.hi[d];
+    }
     sd.w = dw;
     sd.g = nullptr;
     h->srcs.push_back(sd);
@@ -540,10 +743,23 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     dd.kind = d.kind;
     dd.comp = d.component;
     dd.axis = d.axis;
-    for (int k = 0; k < 3; ++k) { dd.lo[k] = d.lo[k]; dd.hi[k] = d.hi[k]; }
+    for (int k = 0; k < 3; ++k) {
+      dd.lo[k] = d.lo[k];
+      dd.hi[k] = d.hi[k];
+    }
     dd.off = 0;
+    dd.nblk = 0;
+    dd.poff = 0;
     const int64_t m = box_cells(d.lo, d.hi);
-    dd.nblk = d.kind == FDTD_DET_PLANE_FLUX ? (int)std::min<int64_t>(148, std::max<int64_t>(1, (m + 4095) / 4096)) : 0;
+    if (d.kind == FDTD_DET_PLANE_FLUX) {
+      if (q < kMaxDet) {  // summed inside the fused kernel: one slot per block that meets the box
+        const int tx = fused_tile_x(), ty = fused_tile_y();
+        dd.nblk = ((d.hi[0] - 1) / tx - d.lo[0] / tx + 1) * ((d.hi[1] - 1) / ty - d.lo[1] / ty + 1) *
+                  ((d.hi[2] - 1) / h->tz - d.lo[2] / h->tz + 1);
+      } else {
+        dd.nblk = (int)std::min<int64_t>(148, std::max<int64_t>(1, (m + 4095) / 4096));
+      }
+    }
     if (d.kind == FDTD_DET_PLANE_E2_SUM) h->det_total_fixed += m;
     else h->det_total_per_step += 1;
     h->dets.push_back(dd);
@@ -555,6 +771,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
 int fdtd_destroy(fdtd_handle* h) {
   if (!h) return FDTD_OK;
   cudaStreamSynchronize(h->stream);
+  h->gfwd.reset();
+  h->gbwd.reset();
+  if (h->cap) cudaStreamDestroy(h->cap);
   cudaFree(h->fields);
   cudaFree(h->a);
   cudaFree(h->psiE);
@@ -571,10 +790,6 @@ int fdtd_destroy(fdtd_handle* h) {
   cudaFree(h->dLda);
   cudaFree(h->dLddet);
   cudaFree(h->staging);
-  for (auto& e : h->ev_pool) {
-    cudaEventDestroy(e.a);
-    cudaEventDestroy(e.b);
-  }
   delete h;
   return FDTD_OK;
 }
@@ -584,9 +799,9 @@ int fdtd_set_design_eps_inv(fdtd_handle* h, const float* eps_inv_box) {
   const int64_t m = box_cells(h->design_lo, h->design_hi);
   if (m == 0) return FDTD_OK;
   TRY(ensure_staging(h));
-  if (m > 6 * (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2]) return fail(FDTD_ERR_INVALID_ARG, "design box too large");
   CK(cudaMemcpyAsync(h->staging, eps_inv_box, m * 4, cudaMemcpyDefault, h->stream));
   launch_set_box(h->g, h->a, h->design_lo, h->design_hi, h->staging, h->stream);
+  h->launches += 1;
   CK(cudaGetLastError());
   return FDTD_OK;
 }
@@ -611,6 +826,7 @@ int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6) {
   Fields I;
   for (int c = 0; c < 6; ++c) I.f[c] = h->init + c * h->g.vol;
   launch_pack_fields(h->g, I, h->staging, 1, h->stream);
+  h->launches += 1;
   CK(cudaGetLastError());
   return FDTD_OK;
 }
@@ -631,46 +847,14 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   h->last_nsteps = nsteps;
   TRY(ensure_gtab(h, nsteps));
   TRY(ensure_det(h, nsteps));
-  if (record && h->faces.per_step > 0 && h->face_cap_steps < nsteps) {
-    CK(cudaStreamSynchronize(h->stream));
-    dev_free(h, h->face_hist, h->face_cap_steps * h->faces.per_step * 4);
-    h->face_hist = nullptr;
-    h->face_cap_steps = 0;
-    TRY(dev_alloc(h, (void**)&h->face_hist, (int64_t)nsteps * h->faces.per_step * 4));
-    h->face_cap_steps = nsteps;
-  }
+  if (record && h->faces.per_step > 0)
+    TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)nsteps, h->faces.per_step * 4));
   TRY(reset_state(h));
-  const Geo& g = h->g;
-  const Fields F = h->F();
-  const Tables T = h->tab();
-  const PsiSet PE = h->psi_set(h->psiE), PH = h->psi_set(h->psiH);
-  const bool faces = record && h->faces.per_step > 0;
-  for (int n = 0; n < nsteps; ++n) {
-    {
-      ProfScope ps(h, FDTD_KERNEL_UPDATE_H, n);
-      launch_update_H(g, F, PH, T, h->stream);
-    }
-    if (faces) launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, h->stream);
-    {
-      ProfScope ps(h, FDTD_KERNEL_UPDATE_E, n);
-      launch_update_E(g, F, PE, T, h->a, h->stream);
-    }
-    for (const auto& s : h->srcs) launch_source(g, F, s, n, +1.f, 0, h->stream);
-    int fk = 0;
-    for (const auto& d : h->dets) {
-      double* part = d.kind == FDTD_DET_PLANE_FLUX ? flux_partial_base(h, fk++, nsteps) : nullptr;
-      launch_detector_sample(g, F, d, n, h->det_out, part, h->stream);
-    }
-    h->launches += 2 + (faces ? 1 : 0) + (int64_t)h->srcs.size() + (int64_t)h->dets.size();
-  }
-  int fk = 0;
-  for (const auto& d : h->dets)
-    if (d.kind == FDTD_DET_PLANE_FLUX) {
-      launch_flux_finalize(d, nsteps, flux_partial_base(h, fk++, nsteps), h->det_out, h->stream);
-      h->launches += 1;
-    }
+  const int key = (record ? 1 : 0) | (h->prof_every << 1);
+  TRY(run_loop(h, h->gfwd, nsteps, key, [&](cudaStream_t st, std::vector<Ev>* evs) {
+    return enqueue_forward(h, nsteps, record, st, evs);
+  }));
   CK(cudaGetLastError());
-  TRY(prof_collect(h));
   h->recorded = record;
   return FDTD_OK;
 }
@@ -685,62 +869,27 @@ int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
   const int64_t M = box_cells(h->design_lo, h->design_hi);
   if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
   const Geo& g = h->g;
-  if (!h->adj) TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
   const int64_t pf = h->psi_floats();
+  if (!h->adj) TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
   if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
   if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
-  if (ndet > h->dLddet_cap) {
-    CK(cudaStreamSynchronize(h->stream));
-    dev_free(h, h->dLddet, h->dLddet_cap * 8);
-    h->dLddet = nullptr;
-    h->dLddet_cap = 0;
-    TRY(dev_alloc(h, (void**)&h->dLddet, ndet * 8));
-    h->dLddet_cap = ndet;
-  }
+  TRY(ensure_buf(h, &h->dLddet, &h->dLddet_cap, ndet, 8));
+  if (M > 0) TRY(ensure_staging(h));
   if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
   CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
-
-  const Fields F = h->F(), A = h->A();
-  const Tables T = h->tab();
-  // psibar layout: [E buf0][H buf0][E buf1][H buf1]
-  PsiSet PEb[2], PHb[2];
-  for (int k = 0; k < 2; ++k) {
-    PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
-    PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
-  }
-  int cur = 0;
-  for (int n = nsteps - 1; n >= 0; --n) {
-    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, h->stream);
-    if (h->faces.per_step > 0)
-      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, h->stream);
-    for (const auto& s : h->srcs) launch_source(g, F, s, n, -1.f, 1, h->stream);
-    {
-      ProfScope ps(h, FDTD_KERNEL_REV_E, n);
-      launch_rev_E(g, F, A, PEb[cur], PEb[1 - cur], T, h->a, h->design_lo, h->design_hi, h->dLda, h->stream);
-    }
-    {
-      ProfScope ps(h, FDTD_KERNEL_REV_H, n);
-      launch_rev_H(g, F, A, PHb[cur], PHb[1 - cur], T, h->stream);
-    }
-    cur = 1 - cur;
-    h->launches += 2 + (h->faces.per_step > 0 ? 1 : 0) + (int64_t)h->srcs.size() + (int64_t)h->dets.size();
-  }
+  const int key = h->cur | (h->prof_every << 1);
+  TRY(run_loop(h, h->gbwd, nsteps, key,
+               [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
   if (M > 0) {
-    TRY(ensure_staging(h));
     launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, h->stream);
     h->launches += 1;
     CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
   }
   CK(cudaGetLastError());
-  TRY(prof_collect(h));
   h->consumed = true;
-  cudaPointerAttributes at;
-  if (M > 0 && cudaPointerGetAttributes(&at, dL_deps) == cudaSuccess && at.type != cudaMemoryTypeDevice &&
-      at.type != cudaMemoryTypeManaged)
-    CK(cudaStreamSynchronize(h->stream));
-  cudaGetLastError();
+  if (M > 0 && is_host_pointer(dL_deps)) CK(cudaStreamSynchronize(h->stream));
   return FDTD_OK;
 }
 
@@ -750,7 +899,7 @@ int fdtd_read_detectors(fdtd_handle* h, double* out) {
   const int64_t n = det_total_for(h, h->last_nsteps);
   if (n == 0) return FDTD_OK;
   CK(cudaMemcpyAsync(out, h->det_out, n * 8, cudaMemcpyDefault, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  if (is_host_pointer(out)) CK(cudaStreamSynchronize(h->stream));
   return FDTD_OK;
 }
 
@@ -763,6 +912,7 @@ int fdtd_get_fields(fdtd_handle* h, float* out6) {
   if (!h || !out6) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
   TRY(ensure_staging(h));
   launch_pack_fields(h->g, h->F(), h->staging, 0, h->stream);
+  h->launches += 1;
   const int64_t N = (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2];
   CK(cudaMemcpyAsync(out6, h->staging, 6 * N * 4, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -781,13 +931,11 @@ int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every) {
     h->prof_ms[k] = 0;
     h->prof_n[k] = 0;
   }
-  h->ev_used = 0;
   return FDTD_OK;
 }
 
 int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds) {
   if (!h || nkinds < 0) return fail(FDTD_ERR_INVALID_ARG, "bad argument");
-  TRY(prof_collect(h));
   for (int k = 0; k < nkinds && k < FDTD_KERNEL_KINDS; ++k) {
     if (ms) ms[k] = h->prof_ms[k];
     if (count) count[k] = h->prof_n[k];

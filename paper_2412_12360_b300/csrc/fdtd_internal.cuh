@@ -20,6 +20,8 @@ namespace fdtd {
 
 constexpr int kMaxFaceSeg = 12;
 constexpr int kPitchAlign = 32;
+constexpr int kMaxSrc = 4;    // sources handled inside the fused kernels (the rest by extra launches)
+constexpr int kMaxDet = 4;    // detectors handled inside the fused kernels
 
 struct Geo {
   int n[3];           // cells nx, ny, nz
@@ -38,6 +40,7 @@ struct Tables {
   const float* b[3][2];
   const float* c[3][2];
   const float* ik[3][2];   // 1 / kappa
+  const int* sidx[3];      // slab index of each position along the axis, -1 off the layers
 };
 
 struct Fields {
@@ -71,7 +74,27 @@ struct DetDev {
   int kind, comp, axis;
   int lo[3], hi[3];
   int64_t off;             // offset into the concatenated detector output
-  int nblk;                // flux: partial-sum blocks per step
+  int nblk;                // flux: partial-sum slots per step
+  int64_t poff;            // flux: offset of this detector's slots in the partial-sum buffer
+};
+
+// Arguments of one fused forward step (read `cur`, write `nxt`).
+struct FwdArgs {
+  Geo g;
+  Tables T;
+  Fields cur, nxt;
+  PsiSet psiE_cur, psiE_nxt, psiH_cur, psiH_nxt;
+  const float* a;
+  int step;
+  int tz;                  // z-planes per block
+  int nsrc;
+  SrcDev src[kMaxSrc];
+  int ndet;
+  DetDev det[kMaxDet];
+  double* det_out;
+  double* partial;
+  float* rec;              // this step's face record, or nullptr
+  FaceSet faces;
 };
 
 __host__ __device__ inline int64_t cell_index(const Geo& g, int i, int j, int k) {
@@ -116,6 +139,9 @@ void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& 
                   const Tables& T, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, cudaStream_t s);
+void launch_fwd_fused(const FwdArgs& a, cudaStream_t s);
+int fused_tile_x();
+int fused_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);
 void launch_set_box(const Geo& g, float* a, const int* lo, const int* hi, const float* box, cudaStream_t s);
 

@@ -179,14 +179,14 @@ __global__ void __launch_bounds__(kFluxThreads) k_det_flux(Geo g, Fields F, DetD
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) partial[(int64_t)step * gridDim.x + blockIdx.x] = sh[0];
+  if (threadIdx.x == 0) partial[d.poff + (int64_t)step * gridDim.x + blockIdx.x] = sh[0];
 }
 
 __global__ void k_flux_finalize(DetDev d, int nsteps, const double* partial, double* out) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nsteps) return;
   double s = 0.0;
-  for (int b = 0; b < d.nblk; ++b) s += partial[(int64_t)n * d.nblk + b];
+  for (int b = 0; b < d.nblk; ++b) s += partial[d.poff + (int64_t)n * d.nblk + b];
   out[d.off + n] = s;
 }
 
