@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -514,36 +515,52 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   return launches;
 }
 
-// Reverse (Sec. 2.2): per step, detector adjoints, face replay, source removal, then the inverse-E /
-// adjoint-H kernel and the inverse-H / adjoint-E kernel, in place on the current field buffer.
+// Reverse (Sec. 2.2): per step, the detector adjoints, then the inverse-E / adjoint-H kernel (which also
+// replays the face record and removes the sources) and the inverse-H / adjoint-E kernel, in place on
+// the current field buffer.
 int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
   const Fields F = h->F(), A = h->A();
-  const Tables T = h->tab();
   PsiSet PEb[2], PHb[2];  // psi-bar layout: [E 0][H 0][E 1][H 1]
   for (int k = 0; k < 2; ++k) {
     PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
     PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
   }
+  RevArgs ra;
+  ra.g = g;
+  ra.T = h->tab();
+  ra.F = F;
+  ra.B = A;
+  ra.a = h->a;
+  ra.tz = h->tz;
+  for (int d = 0; d < 3; ++d) {
+    ra.dlo[d] = h->design_lo[d];
+    ra.dhi[d] = h->design_hi[d];
+  }
+  ra.dLda = h->dLda;
+  ra.faces = h->faces;
+  ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
+  for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
   int64_t launches = 0;
   int pb = 0;
   for (int n = nsteps - 1; n >= 0; --n) {
     for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
     launches += (int64_t)h->dets.size();
-    if (h->faces.per_step > 0) {
-      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, st);
-      launches += 1;
-    }
-    for (const auto& s : h->srcs) launch_source(g, F, s, n, -1.f, 1, st);
-    launches += (int64_t)h->srcs.size();
+    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
+    ra.step = n;
+    ra.rec = h->faces.per_step > 0 ? h->face_hist + (int64_t)n * h->faces.per_step : nullptr;
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
-      launch_rev_E(g, F, A, PEb[pb], PEb[1 - pb], T, h->a, h->design_lo, h->design_hi, h->dLda, st);
+      ra.pin = PEb[pb];
+      ra.pout = PEb[1 - pb];
+      launch_rev_E_lean(ra, st);
     }
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
-      launch_rev_H(g, F, A, PHb[pb], PHb[1 - pb], T, st);
+      ra.pin = PHb[pb];
+      ra.pout = PHb[1 - pb];
+      launch_rev_H_lean(ra, st);
     }
     launches += 2;
     pb = 1 - pb;
@@ -685,9 +702,15 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     // z-chunk of the fused kernels: enough blocks to fill every SM several times over
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
-    const int64_t want = 148 * 8;
+    // (8 planes per block at least: a shorter march pays its start-up plane too often; measured on
+    // the 96^3 workload, 8 beat 4, 6, 12, 16 and 24)
+    const int64_t want = 148 * 3;
     const int tz = (int)std::max<int64_t>(1, (int64_t)n[2] * nxy / want);
-    h->tz = std::max(4, std::min(tz, n[2]));
+    h->tz = std::max(8, std::min(tz, n[2]));
+    if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
+      const int v = std::atoi(e);
+      if (v >= 1) h->tz = std::min(v, n[2]);
+    }
   }
   if ((rc = dev_alloc(h, (void**)&h->fields, 2 * 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = dev_alloc(h, (void**)&h->a, g.vol * 4)) != FDTD_OK) return cleanup(rc);

@@ -45,6 +45,17 @@ __device__ __forceinline__ int zz_of(const Geo& g, int x, int y, int s) { return
 
 __device__ __forceinline__ float pick3(int c, float a, float b, float d) { return c == 0 ? a : (c == 1 ? b : d); }
 
+// Write this cell's H into face segment s of the record if (i, j, k) lies on it.
+__device__ __noinline__ void face_write(const FwdArgs& A, int s, int i, int j, int k, float hx, float hy, float hz) {
+  const FaceSeg& sg = A.faces.seg[s];
+  const int p[3] = {i, j, k};
+  const int a1 = (sg.axis + 1) % 3, a2 = (sg.axis + 2) % 3;
+  if (p[sg.axis] != sg.idx) return;
+  const int u = p[a1] - sg.lo1, v = p[a2] - sg.lo2;
+  if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) return;
+  A.rec[sg.off + (int64_t)v * sg.n1 + u] = sg.comp == 0 ? hx : (sg.comp == 1 ? hy : hz);
+}
+
 __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
 }
@@ -137,15 +148,29 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     const DetDev& d = A.det[s];
     if (own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1]) det_xy |= 1u << s;
   }
-  bool face_xy = false;
-  int fz0 = -1, fz1 = -1;
-  if (A.rec) {
+  // boundary-face record: a column on an x- or y-face writes its H there for the planes in range; a
+  // z-face plane is written by every column in range. Offsets into one step's record:
+  //   x-face (comp y, z): off + (k - lo2) * n1 + (j - lo1);   y-face (comp z, x): off + (i - lo2) * n1 + (k - lo1)
+  //   z-face (comp x, y): off + (j - lo2) * n1 + (i - lo1)
+  // (a column lies on at most one x- or y-face line, i.e. two segments; z-faces are at most two
+  // planes, each with an Hx and an Hy segment). Only segment numbers are kept; offsets are computed
+  // when a face value is written.
+  int fseg = -1;              // x/y face: segment numbers a | b << 8
+  int fz0 = -1, fz1 = -1;     // z-face planes through this column
+  int fzseg = 0;              // their segments: plane 0 (x, y), plane 1 (x, y), 8 bits each
+  if (A.rec && own) {
+    int na = 0;
     for (int s = 0; s < A.faces.nseg; ++s) {
       const FaceSeg& sg = A.faces.seg[s];
-      if (sg.axis == 0) face_xy |= own && i == sg.idx && j >= sg.lo1 && j < sg.lo1 + sg.n1;
-      else if (sg.axis == 1) face_xy |= own && j == sg.idx && i >= sg.lo2 && i < sg.lo2 + sg.n2;
-      else if (fz0 < 0 || fz0 == sg.idx) fz0 = sg.idx;
-      else fz1 = sg.idx;
+      if ((sg.axis == 0 && i == sg.idx && j >= sg.lo1 && j < sg.lo1 + sg.n1) ||
+          (sg.axis == 1 && j == sg.idx && i >= sg.lo2 && i < sg.lo2 + sg.n2)) {
+        fseg = (na == 0) ? s : ((fseg & 0xff) | (s << 8));
+        ++na;
+      } else if (sg.axis == 2 && i >= sg.lo1 && i < sg.lo1 + sg.n1 && j >= sg.lo2 && j < sg.lo2 + sg.n2) {
+        const int pl = (fz0 < 0 || fz0 == sg.idx) ? 0 : 1;
+        if (pl == 0) fz0 = sg.idx; else fz1 = sg.idx;
+        fzseg |= s << (8 * (2 * pl + sg.comp));
+      }
     }
   }
 
@@ -226,6 +251,9 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     }
     const float ikZh = T.ik[2][1][k], ikZe = T.ik[2][0][k];
     const int sZ = T.sidx[2][k];
+    unsigned src_k = 0, det_k = 0;  // sources and detectors whose z-range holds this plane
+    for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
+    for (int s = 0; s < A.ndet; ++s) det_k |= (k >= A.det[s].lo[2] && k < A.det[s].hi[2]) ? 1u << s : 0u;
     __syncthreads();
     const float(*ek)[SY][SX] = sE[cur];
     const float(*ek1)[SY][SX] = sE[cur ^ 1];
@@ -235,13 +263,20 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     const int zy = sY >= 0 ? zy_of(g, i, k, sY) : 0;
     const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
     float hx = 0.f, hy = 0.f, hz = 0.f;
-    if (own) {
+    const bool lay = (sX & sY & sZ) >= 0;  // some axis is in a layer (slab indices are -1 off them, all bits set)
+    if (own && !lay) {  // off the layers 1/kappa = 1 exactly: the plain Yee update
+      hx = hox - S * ((ek[2][ry + 1][rx] - ek[2][ry][rx]) - (ek1[1][ry][rx] - ek[1][ry][rx]));
+      hy = hoy - S * ((ek1[0][ry][rx] - ek[0][ry][rx]) - (ek[2][ry][rx + 1] - ek[2][ry][rx]));
+      hz = hoz - S * ((ek[1][ry][rx + 1] - ek[1][ry][rx]) - (ek[0][ry + 1][rx] - ek[0][ry][rx]));
+    } else if (own) {
       hx = hox - S * (cterm<true>(ek[2][ry + 1][rx] - ek[2][ry][rx], ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], PHo.p[0][1], zy) -
                       cterm<true>(ek1[1][ry][rx] - ek[1][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], PHo.p[0][2], zz));
       hy = hoy - S * (cterm<true>(ek1[0][ry][rx] - ek[0][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], PHo.p[1][2], zz) -
                       cterm<true>(ek[2][ry][rx + 1] - ek[2][ry][rx], ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], PHo.p[1][0], zx));
       hz = hoz - S * (cterm<true>(ek[1][ry][rx + 1] - ek[1][ry][rx], ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[2][0], PHo.p[2][0], zx) -
                       cterm<true>(ek[0][ry + 1][rx] - ek[0][ry][rx], ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[2][1], PHo.p[2][1], zy));
+    }
+    if (own) {
       sH[0][ry][rx] = hx;
       sH[1][ry][rx] = hy;
       sH[2][ry][rx] = hz;
@@ -267,16 +302,12 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       sH[2][r][0] = ho2 - S * (cterm<false>(ek[1][r][1] - ek[1][r][0], ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
                                cterm<false>(ek[0][r + 1][0] - ek[0][r][0], ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy));
     }
-    if (A.rec && (face_xy || k == fz0 || k == fz1) && own) {
-      for (int s = 0; s < A.faces.nseg; ++s) {
-        const FaceSeg& sg = A.faces.seg[s];
-        const int pa = sg.axis == 0 ? i : (sg.axis == 1 ? j : k);
-        if (pa != sg.idx) continue;
-        const int a1 = (sg.axis + 1) % 3, a2 = (sg.axis + 2) % 3;
-        const int u = (a1 == 0 ? i : (a1 == 1 ? j : k)) - sg.lo1, v = (a2 == 0 ? i : (a2 == 1 ? j : k)) - sg.lo2;
-        if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) continue;
-        A.rec[sg.off + (int64_t)v * sg.n1 + u] = pick3(sg.comp, hx, hy, hz);
-      }
+    if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
+    if (fseg >= 0) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
+    if (k == fz0 || k == fz1) {
+      const int sh = (k == fz0) ? 0 : 16;
+      face_write(A, (fzseg >> sh) & 0xff, i, j, k, hx, hy, hz);
+      face_write(A, (fzseg >> (sh + 8)) & 0xff, i, j, k, hx, hy, hz);
     }
     __syncthreads();
 
@@ -285,6 +316,11 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     if (own) {
       const float Sa = S * av;
       float ex = ek[0][ry][rx], ey = ek[1][ry][rx], ez = ek[2][ry][rx];
+      if (!lay && i > 0 && j > 0 && k > 0) {
+        ex += Sa * ((hz - sH[2][ry - 1][rx]) - (hy - hym));
+        ey += Sa * ((hx - hxm) - (hz - sH[2][ry][rx - 1]));
+        ez += Sa * ((hy - sH[1][ry][rx - 1]) - (hx - sH[0][ry - 1][rx]));
+      } else {
       if (j > 0 && k > 0)
         ex += Sa * (cterm<true>(hz - sH[2][ry - 1][rx], ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[0][1], PEo.p[0][1], zy) -
                     cterm<true>(hy - hym, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[0][2], PEo.p[0][2], zz));
@@ -294,10 +330,11 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       if (i > 0 && j > 0)
         ez += Sa * (cterm<true>(hy - sH[1][ry][rx - 1], ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[2][0], PEo.p[2][0], zx) -
                     cterm<true>(hx - sH[0][ry - 1][rx], ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[2][1], PEo.p[2][1], zy));
-      if (src_xy) {
+      }
+      if (src_xy & src_k) {
         for (int s = 0; s < A.nsrc; ++s) {
           const SrcDev& sd = A.src[s];
-          if (!((src_xy >> s) & 1u) || k < sd.lo[2] || k >= sd.hi[2]) continue;
+          if (!(((src_xy & src_k) >> s) & 1u)) continue;
           const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
           if (sd.comp == 0) ex += v;
           else if (sd.comp == 1) ey += v;
@@ -307,12 +344,12 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       N.f[0][q] = ex;
       N.f[1][q] = ey;
       N.f[2][q] = ez;
-      if (det_xy) {
+      if (det_xy & det_k) {
 #pragma unroll
         for (int s = 0; s < kMaxDet; ++s) {
           if (s >= A.ndet) break;
           const DetDev& d = A.det[s];
-          if (!((det_xy >> s) & 1u) || k < d.lo[2] || k >= d.hi[2]) continue;
+          if (!(((det_xy & det_k) >> s) & 1u)) continue;
           if (d.kind == 0) {
             A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, ex, ey, ez) : pick3(d.comp - 3, hx, hy, hz));
           } else if (d.kind == 1) {

@@ -139,7 +139,26 @@ void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& 
                   const Tables& T, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, cudaStream_t s);
+// Arguments of the reverse-step kernels (in place on the fields F and the adjoint fields B).
+struct RevArgs {
+  Geo g;
+  Tables T;
+  Fields F, B;
+  PsiSet pin, pout;        // psi-bar of E (rev_E) or of H (rev_H): read pin, write pout
+  const float* a;
+  int step;
+  int tz;
+  int dlo[3], dhi[3];      // design box
+  double* dLda;
+  const float* rec;        // face record of this step (rev_E), or nullptr
+  FaceSet faces;
+  int nsrc;
+  SrcDev src[kMaxSrc];
+};
+
 void launch_fwd_fused(const FwdArgs& a, cudaStream_t s);
+void launch_rev_E_lean(const RevArgs& a, cudaStream_t s);
+void launch_rev_H_lean(const RevArgs& a, cudaStream_t s);
 int fused_tile_x();
 int fused_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);

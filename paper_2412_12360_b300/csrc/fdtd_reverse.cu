@@ -1,0 +1,562 @@
+// Reverse step of arXiv 2412.12360 Sec. 2.2 as two z-marching kernels, in place:
+//
+//   rev_E(n): the inverse E update E^n = E^{n+1} - src - S a curl_b(H^{n+1/2}) on the PML-free region R,
+//             dL/da += S Ebar . curl_b(H^{n+1/2}) on the design box, and the transpose of the E update
+//             for the adjoint: Hbar += sum of the E-update coefficients P of the neighbouring E points
+//             (with the CPML memories psi-bar of E);
+//   rev_H(n): the inverse H update H^{n-1/2} = H^{n+1/2} + S curl_f(E^n) on R, and the transpose of the
+//             H update: Ebar += sum of the H-update coefficients Q of the neighbouring H points.
+//
+// Each kernel reads only fields it does not write (rev_E reads H and Ebar and writes E and Hbar;
+// rev_H reads E and Hbar and writes H and Ebar), so in-place updates are race-free. Blocks own a
+// TX x TY column tile and march their z-chunk downwards, so the coefficient of the plane above is
+// carried in registers. The tangential H recorded on the six boundary planes (Sec. 2.2) is
+// substituted while H is staged, which replays the face record without a separate kernel.
+//
+// The adjoint coefficients of one E point (component c, its transverse axes c1 = c+1, c2 = c+2):
+//   u = S a Ebar_c (zero where E_c is held by a PEC wall),
+//   P1 = u / kappa_c1 + c_c1 (psibar_c,c1 + u),   P2 = -u / kappa_c2 + c_c2 (psibar_c,c2 - u),
+//   psibar_c,c1 <- b_c1 (psibar_c,c1 + u),       psibar_c,c2 <- b_c2 (psibar_c,c2 - u),
+// and Hbar_h(p) += P1_{h+1}(p) - P1_{h+1}(p + e_{h+2}) + P2_{h+2}(p) - P2_{h+2}(p + e_{h+1}).
+// Those of one H point mirror them with w = -S Hbar_h and the H tables, giving
+//   Ebar_e(p) += Q1_{e+1}(p - e_{e+2}) - Q1_{e+1}(p) + Q2_{e+2}(p - e_{e+1}) - Q2_{e+2}(p).
+// Off the layers 1/kappa = 1 and c = 0, so P and Q reduce to +-u and +-w.
+#include "fdtd_internal.cuh"
+
+namespace fdtd {
+
+namespace {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int HX = TX + 1, HY = TY + 1;
+
+__device__ __forceinline__ int zx_of(const Geo& g, int y, int k, int s) { return (k * g.n[1] + y) * g.slab[0] + s; }
+__device__ __forceinline__ int zy_of(const Geo& g, int x, int k, int s) { return (k * g.slab[1] + s) * g.nxp + x; }
+__device__ __forceinline__ int zz_of(const Geo& g, int x, int y, int s) { return (s * g.n[1] + y) * g.nxp + x; }
+
+// psi index of (x, y, k) for the derivative along axis D with slab index s
+template <int D>
+__device__ __forceinline__ int zd_of(const Geo& g, int x, int y, int k, int s) {
+  return D == 0 ? zx_of(g, y, k, s) : (D == 1 ? zy_of(g, x, k, s) : zz_of(g, x, y, s));
+}
+
+// One adjoint coefficient: sgn * v * ik + c (psi_old + sgn * v) inside the layer (s >= 0).
+template <int D, int HALF>
+__device__ __forceinline__ float acoef(const Tables& T, float v, float sgn, float ik, int s, int pos,
+                                       const float* __restrict__ psi, int z) {
+  float r = sgn * v * ik;
+  if (s >= 0) r += T.c[D][HALF][pos] * (psi[z] + sgn * v);
+  return r;
+}
+
+// psi-bar update at the own point: psi_new = b (psi_old + sgn * v)
+template <int D, int HALF>
+__device__ __forceinline__ void apsi(const Tables& T, float v, float sgn, int s, int pos, const float* __restrict__ pin,
+                                     float* pout, int z) {
+  if (s >= 0) pout[z] = T.b[D][HALF][pos] * (pin[z] + sgn * v);
+}
+
+// Face segments (of the boundary record) through the column (x, y): x- and y-faces give at most two
+// segments, packed a | b << 8 (-1 if none); z-faces give at most two planes, each with an x and a
+// y segment, packed into zseg (plane 0 x, plane 0 y, plane 1 x, plane 1 y; 8 bits each).
+__device__ __forceinline__ void face_segments(const FaceSet& fs, int x, int y, int& seg, int& z0, int& z1, int& zseg) {
+  seg = -1;
+  z0 = z1 = -1;
+  zseg = 0;
+  int na = 0;
+  for (int s = 0; s < fs.nseg; ++s) {
+    const FaceSeg& sg = fs.seg[s];
+    if ((sg.axis == 0 && x == sg.idx && y >= sg.lo1 && y < sg.lo1 + sg.n1) ||
+        (sg.axis == 1 && y == sg.idx && x >= sg.lo2 && x < sg.lo2 + sg.n2)) {
+      seg = (na == 0) ? s : ((seg & 0xff) | (s << 8));
+      ++na;
+    } else if (sg.axis == 2 && x >= sg.lo1 && x < sg.lo1 + sg.n1 && y >= sg.lo2 && y < sg.lo2 + sg.n2) {
+      const int pl = (z0 < 0 || z0 == sg.idx) ? 0 : 1;
+      if (pl == 0) z0 = sg.idx; else z1 = sg.idx;
+      zseg |= s << (8 * (2 * pl + sg.comp));
+    }
+  }
+}
+
+// The recorded value at (x, y, k) if that point lies on face segment s (comp = -1 otherwise).
+struct FaceHit {
+  int comp;
+  float v;
+};
+
+__device__ __noinline__ FaceHit face_lookup(const RevArgs& A, int s, int x, int y, int k) {
+  const FaceSeg& sg = A.faces.seg[s];
+  FaceHit r = {-1, 0.f};
+  const int pa = sg.axis == 0 ? x : (sg.axis == 1 ? y : k);
+  if (pa != sg.idx) return r;
+  const int a1 = (sg.axis + 1) % 3, a2 = (sg.axis + 2) % 3;
+  const int u = (a1 == 0 ? x : (a1 == 1 ? y : k)) - sg.lo1, v = (a2 == 0 ? x : (a2 == 1 ? y : k)) - sg.lo2;
+  if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) return r;
+  r.comp = sg.comp;
+  r.v = A.rec[sg.off + (int64_t)v * sg.n1 + u];
+  return r;
+}
+
+__device__ __forceinline__ void face_take(const FaceHit& f, float& hx, float& hy, float& hz) {
+  if (f.comp == 0) hx = f.v;
+  else if (f.comp == 1) hy = f.v;
+  else if (f.comp == 2) hz = f.v;
+}
+
+// Apply every face segment through column (x, y) at plane k to (hx, hy, hz).
+__device__ __forceinline__ void face_fix(const RevArgs& A, int seg, int z0, int z1, int zseg, int x, int y, int k,
+                                         float& hx, float& hy, float& hz) {
+  if (seg >= 0) {
+    face_take(face_lookup(A, seg & 0xff, x, y, k), hx, hy, hz);
+    if (seg > 0xff) face_take(face_lookup(A, seg >> 8, x, y, k), hx, hy, hz);
+  }
+  if (k == z0 || k == z1) {
+    const int sh = (k == z0) ? 0 : 16;
+    face_take(face_lookup(A, (zseg >> sh) & 0xff, x, y, k), hx, hy, hz);
+    face_take(face_lookup(A, (zseg >> (sh + 8)) & 0xff, x, y, k), hx, hy, hz);
+  }
+}
+
+__device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
+  return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// rev_E
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
+  __shared__ float sH[3][HY][HX];  // H^{n+1/2}(k): x in [i0-1, i0+TX-1], y in [j0-1, j0+TY-1]
+  __shared__ float sU[3][HY][HX];  // u(k) = S a Ebar: x in [i0, i0+TX], y in [j0, j0+TY]
+
+  const Geo& g = A.g;
+  const Tables& T = A.T;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = blockIdx.z * A.tz;
+  const int k1 = min(g.n[2], k0 + A.tz);
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int plane = (int)g.plane;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < nx && j < ny;
+  const int q0 = j * g.nxp + i;
+  const float S = g.S;
+
+  // halo roles: H row (i, j0-1) and column (i0-1, j0+r); u row (i, j0+TY) and column (i0+TX, j0+r)
+  const int hh = tid % TX;
+  const int role = tid / TX;  // 0: H row, 1: H column (hh < TY), 2: u row, 3: u column (hh < TY)
+  int hx_ = 0, hy_ = 0;
+  bool hv = false;
+  if (role == 0) { hx_ = i0 + hh; hy_ = j0 - 1; hv = j0 > 0 && hx_ < nx; }
+  else if (role == 1) { hx_ = i0 - 1; hy_ = j0 + hh; hv = hh < TY && i0 > 0 && hy_ < ny; }
+  else if (role == 2) { hx_ = i0 + hh; hy_ = j0 + TY; hv = hy_ < ny && hx_ < nx; }
+  else if (role == 3) { hx_ = i0 + TX; hy_ = j0 + hh; hv = hh < TY && hx_ < nx && hy_ < ny; }
+  const int hq0 = hy_ * g.nxp + hx_;
+  int hseg = -1, hz0 = -1, hz1 = -1, hzseg = 0;  // face segments through the halo H column
+  if (hv && role < 2 && A.rec) face_segments(A.faces, hx_, hy_, hseg, hz0, hz1, hzseg);
+
+  // CPML data (integer positions, the E tables) along x and y
+  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
+  const float ikX0 = T.ik[0][0][ic], ikY0 = T.ik[1][0][jc];
+  const int sX0 = T.sidx[0][ic], sY0 = T.sidx[1][jc];
+  const bool hasX1 = i + 1 < nx, hasY1 = j + 1 < ny;
+  const float ikX1 = T.ik[0][0][min(i + 1, nx - 1)], ikY1 = T.ik[1][0][min(j + 1, ny - 1)];
+  const int sX1 = hasX1 ? T.sidx[0][i + 1] : -1, sY1 = hasY1 ? T.sidx[1][j + 1] : -1;
+
+  // R membership of the own E components along x and y (E_c: half along c, integer along the others)
+  const bool rxh = i >= g.rhalf_lo[0] && i <= g.rhalf_hi[0], rxi = i >= g.rint_lo[0] && i <= g.rint_hi[0];
+  const bool ryh = j >= g.rhalf_lo[1] && j <= g.rhalf_hi[1], ryi = j >= g.rint_lo[1] && j <= g.rint_hi[1];
+  const bool dxy = own && i >= A.dlo[0] && i < A.dhi[0] && j >= A.dlo[1] && j < A.dhi[1];
+  unsigned src_xy = 0;
+  for (int s = 0; s < A.nsrc; ++s)
+    if (own && i >= A.src[s].lo[0] && i < A.src[s].hi[0] && j >= A.src[s].lo[1] && j < A.src[s].hi[1]) src_xy |= 1u << s;
+  int fseg = -1, fz0 = -1, fz1 = -1, fzseg = 0;  // face segments through the own column
+  if (own && A.rec) face_segments(A.faces, i, j, fseg, fz0, fz1, fzseg);
+  const bool lay_xy = (sX0 & sX1 & sY0 & sY1) >= 0;  // this column or its +x/+y neighbour is in a layer
+
+  const PsiSet& Pi = A.pin;
+  const PsiSet& Po = A.pout;
+
+  // P1_y and P2_x of the own column at k1 (the plane above the chunk)
+  float p1y_up = 0.f, p2x_up = 0.f;
+  if (own && k1 < nz) {
+    const int q = k1 * plane + q0;
+    const float Sa = S * A.a[q];
+    const float ux = (j > 0) ? Sa * A.B.f[0][q] : 0.f;
+    const float uy = (i > 0) ? Sa * A.B.f[1][q] : 0.f;
+    const float ikZ = T.ik[2][0][k1];
+    const int sZ = T.sidx[2][k1];
+    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+    p1y_up = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k1, Pi.p[1][2], zz);
+    p2x_up = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k1, Pi.p[0][2], zz);
+  }
+
+  int sZ1 = (k1 < nz) ? T.sidx[2][k1] : -1;  // slab index of the plane above
+  for (int k = k1 - 1; k >= k0; --k) {
+    const int q = k * plane + q0;
+    // loads of the own cell
+    float hx = 0.f, hy = 0.f, hz = 0.f, hxm = 0.f, hym = 0.f, bx = 0.f, by = 0.f, bz = 0.f, av = 0.f;
+    float ex = 0.f, ey = 0.f, ez = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+    if (own) {
+      hx = A.F.f[3][q];
+      hy = A.F.f[4][q];
+      hz = A.F.f[5][q];
+      if (k > 0) {
+        hxm = A.F.f[3][q - plane];
+        hym = A.F.f[4][q - plane];
+      }
+      bx = A.B.f[0][q];
+      by = A.B.f[1][q];
+      bz = A.B.f[2][q];
+      av = A.a[q];
+      ex = A.F.f[0][q];
+      ey = A.F.f[1][q];
+      ez = A.F.f[2][q];
+      gx = A.B.f[3][q];
+      gy = A.B.f[4][q];
+      gz = A.B.f[5][q];
+      if (fseg >= 0 || k == fz0 || k == fz1) face_fix(A, fseg, fz0, fz1, fzseg, i, j, k, hx, hy, hz);
+      if (k > 0 && (fseg >= 0 || k - 1 == fz0 || k - 1 == fz1)) {
+        float dummy = 0.f;
+        face_fix(A, fseg, fz0, fz1, fzseg, i, j, k - 1, hxm, hym, dummy);
+      }
+    }
+    // halo loads
+    float h1 = 0.f, h2 = 0.f;
+    if (hv) {
+      const int hq = k * plane + hq0;
+      if (role == 0) {  // Hx, Hz at (i, j0-1)
+        h1 = A.F.f[3][hq];
+        h2 = A.F.f[5][hq];
+        if (hseg >= 0 || k == hz0 || k == hz1) {
+          float dummy = 0.f;
+          face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, k, h1, dummy, h2);
+        }
+      } else if (role == 1) {  // Hy, Hz at (i0-1, j0+r)
+        h1 = A.F.f[4][hq];
+        h2 = A.F.f[5][hq];
+        if (hseg >= 0 || k == hz0 || k == hz1) {
+          float dummy = 0.f;
+          face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, k, dummy, h1, h2);
+        }
+      } else {
+        const float Sa = S * A.a[hq];
+        if (role == 2) {  // u_z, u_x at (i, j0+TY)
+          h1 = (hx_ > 0 && hy_ > 0) ? Sa * A.B.f[2][hq] : 0.f;
+          h2 = (hy_ > 0 && k > 0) ? Sa * A.B.f[0][hq] : 0.f;
+        } else {  // u_y, u_z at (i0+TX, j0+r)
+          h1 = (hx_ > 0 && k > 0) ? Sa * A.B.f[1][hq] : 0.f;
+          h2 = (hx_ > 0 && hy_ > 0) ? Sa * A.B.f[2][hq] : 0.f;
+        }
+      }
+    }
+    const float Sa = S * av;
+    const float ux = (own && j > 0 && k > 0) ? Sa * bx : 0.f;
+    const float uy = (own && i > 0 && k > 0) ? Sa * by : 0.f;
+    const float uz = (own && i > 0 && j > 0) ? Sa * bz : 0.f;
+    __syncthreads();  // the previous plane's readers are done with the staging buffers
+    if (own) {
+      sH[0][ty + 1][tx + 1] = hx;
+      sH[1][ty + 1][tx + 1] = hy;
+      sH[2][ty + 1][tx + 1] = hz;
+      sU[0][ty][tx] = ux;
+      sU[1][ty][tx] = uy;
+      sU[2][ty][tx] = uz;
+    }
+    if (role == 0) {
+      sH[0][0][hh + 1] = h1;
+      sH[2][0][hh + 1] = h2;
+    } else if (role == 1 && hh < TY) {
+      sH[1][hh + 1][0] = h1;
+      sH[2][hh + 1][0] = h2;
+    } else if (role == 2) {
+      sU[2][TY][hh] = h1;
+      sU[0][TY][hh] = h2;
+    } else if (role == 3 && hh < TY) {
+      sU[1][hh][TX] = h1;
+      sU[2][hh][TX] = h2;
+    }
+    __syncthreads();
+    if (!own) continue;
+
+    const float ikZ = T.ik[2][0][k];
+    const int sZ = T.sidx[2][k];
+    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
+    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+
+    // adjoint coefficients of the own E point and of its +x, +y neighbours (off the layers they are
+    // +-u: 1/kappa = 1 and c = 0)
+    if (!lay_xy && sZ < 0 && sZ1 < 0) {
+      const float p1z_x = hasX1 ? sU[2][ty][tx + 1] : 0.f, p2y_x = hasX1 ? -sU[1][ty][tx + 1] : 0.f;
+      const float p2z_y = hasY1 ? -sU[2][ty + 1][tx] : 0.f, p1x_y = hasY1 ? sU[0][ty + 1][tx] : 0.f;
+      A.B.f[3][q] = gx + ((uy - p1y_up) + (-uz - p2z_y));
+      A.B.f[4][q] = gy + ((uz - p1z_x) + (-ux - p2x_up));
+      A.B.f[5][q] = gz + ((ux - p1x_y) + (-uy - p2y_x));
+      p1y_up = uy;
+      p2x_up = -ux;
+    } else {
+    const float p1x = acoef<1, 0>(T, ux, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
+    const float p2x = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
+    const float p1y = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
+    const float p2y = acoef<0, 0>(T, uy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
+    const float p1z = acoef<0, 0>(T, uz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
+    const float p2z = acoef<1, 0>(T, uz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
+    float p1z_x = 0.f, p2y_x = 0.f, p2z_y = 0.f, p1x_y = 0.f;
+    if (hasX1) {
+      const int zx1 = sX1 >= 0 ? zx_of(g, j, k, sX1) : 0;
+      p1z_x = acoef<0, 0>(T, sU[2][ty][tx + 1], 1.f, ikX1, sX1, i + 1, Pi.p[2][0], zx1);
+      p2y_x = acoef<0, 0>(T, sU[1][ty][tx + 1], -1.f, ikX1, sX1, i + 1, Pi.p[1][0], zx1);
+    }
+    if (hasY1) {
+      const int zy1 = sY1 >= 0 ? zy_of(g, i, k, sY1) : 0;
+      p2z_y = acoef<1, 0>(T, sU[2][ty + 1][tx], -1.f, ikY1, sY1, j + 1, Pi.p[2][1], zy1);
+      p1x_y = acoef<1, 0>(T, sU[0][ty + 1][tx], 1.f, ikY1, sY1, j + 1, Pi.p[0][1], zy1);
+    }
+    A.B.f[3][q] = gx + ((p1y - p1y_up) + (p2z - p2z_y));
+    A.B.f[4][q] = gy + ((p1z - p1z_x) + (p2x - p2x_up));
+    A.B.f[5][q] = gz + ((p1x - p1x_y) + (p2y - p2y_x));
+    apsi<1, 0>(T, ux, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
+    apsi<2, 0>(T, ux, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
+    apsi<2, 0>(T, uy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
+    apsi<0, 0>(T, uy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
+    apsi<0, 0>(T, uz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
+    apsi<1, 0>(T, uz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
+    p1y_up = p1y;
+    p2x_up = p2x;
+    }
+    sZ1 = sZ;
+
+    // inverse E update on R (mirrors the forward arithmetic: the curl difference times 1/kappa = 1)
+    const float dxa = hz - sH[2][ty][tx + 1], dxb = hy - hym;   // E_x: along y, along z
+    const float dya = hx - hxm, dyb = hz - sH[2][ty + 1][tx];   // E_y: along z, along x
+    const float dza = hy - sH[1][ty + 1][tx], dzb = hx - sH[0][ty][tx + 1];  // E_z: along x, along y
+    const bool rzh = k >= g.rhalf_lo[2] && k <= g.rhalf_hi[2], rzi = k >= g.rint_lo[2] && k <= g.rint_hi[2];
+    const bool inx = rxh && ryi && rzi && j > 0 && k > 0;
+    const bool iny = rxi && ryh && rzi && i > 0 && k > 0;
+    const bool inz = rxi && ryi && rzh && i > 0 && j > 0;
+    unsigned src_k = 0;
+    for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
+    if (src_xy & src_k) {
+      for (int s = 0; s < A.nsrc; ++s) {
+        const SrcDev& sd = A.src[s];
+        if (!(((src_xy & src_k) >> s) & 1u)) continue;
+        const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
+        if (sd.comp == 0 && inx) ex -= v;
+        else if (sd.comp == 1 && iny) ey -= v;
+        else if (sd.comp == 2 && inz) ez -= v;
+      }
+    }
+    if (inx) ex -= Sa * (dxa * ikY0 - dxb * ikZ);
+    if (iny) ey -= Sa * (dya * ikZ - dyb * ikX0);
+    if (inz) ez -= Sa * (dza * ikX0 - dzb * ikY0);
+    A.F.f[0][q] = ex;
+    A.F.f[1][q] = ey;
+    A.F.f[2][q] = ez;
+    // dL/da on the design box (inside R: kappa = 1, psi = 0)
+    if (dxy && k >= A.dlo[2] && k < A.dhi[2]) {
+      float gs = 0.f;
+      if (j > 0 && k > 0) gs += bx * (dxa - dxb);
+      if (i > 0 && k > 0) gs += by * (dya - dyb);
+      if (i > 0 && j > 0) gs += bz * (dza - dzb);
+      const int m = ((k - A.dlo[2]) * (A.dhi[1] - A.dlo[1]) + (j - A.dlo[1])) * (A.dhi[0] - A.dlo[0]) + (i - A.dlo[0]);
+      A.dLda[m] += (double)S * (double)gs;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// rev_H
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
+  __shared__ float sE[3][HY][HX];  // E^n(k): x in [i0, i0+TX], y in [j0, j0+TY]
+  __shared__ float sW[3][HY][HX];  // w(k) = -S Hbar: x in [i0-1, i0+TX-1], y in [j0-1, j0+TY-1]
+
+  const Geo& g = A.g;
+  const Tables& T = A.T;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = blockIdx.z * A.tz;
+  const int k1 = min(g.n[2], k0 + A.tz);
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const int plane = (int)g.plane;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < nx && j < ny;
+  const int q0 = j * g.nxp + i;
+  const float S = g.S;
+
+  // halo roles: E row (i, j0+TY) and column (i0+TX, j0+r); w row (i, j0-1) and column (i0-1, j0+r)
+  const int hh = tid % TX;
+  const int role = tid / TX;
+  int hx_ = 0, hy_ = 0;
+  bool hv = false;
+  if (role == 0) { hx_ = i0 + hh; hy_ = j0 + TY; hv = hy_ < ny && hx_ < nx; }
+  else if (role == 1) { hx_ = i0 + TX; hy_ = j0 + hh; hv = hh < TY && hx_ < nx && hy_ < ny; }
+  else if (role == 2) { hx_ = i0 + hh; hy_ = j0 - 1; hv = j0 > 0 && hx_ < nx; }
+  else if (role == 3) { hx_ = i0 - 1; hy_ = j0 + hh; hv = hh < TY && i0 > 0 && hy_ < ny; }
+  const int hq0 = hy_ * g.nxp + hx_;
+
+  // CPML data (half positions, the H tables) along x and y, at the own column and at -x, -y
+  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
+  const float ikX0 = T.ik[0][1][ic], ikY0 = T.ik[1][1][jc];
+  const int sX0 = T.sidx[0][ic], sY0 = T.sidx[1][jc];
+  const bool hasXm = i > 0, hasYm = j > 0;
+  const float ikXm = T.ik[0][1][max(i - 1, 0)], ikYm = T.ik[1][1][max(j - 1, 0)];
+  const int sXm = hasXm ? T.sidx[0][i - 1] : -1, sYm = hasYm ? T.sidx[1][j - 1] : -1;
+
+  // R membership of the own H components along x and y (H_c: integer along c, half along the others)
+  const bool rxh = i >= g.rhalf_lo[0] && i <= g.rhalf_hi[0], rxi = i >= g.rint_lo[0] && i <= g.rint_hi[0];
+  const bool ryh = j >= g.rhalf_lo[1] && j <= g.rhalf_hi[1], ryi = j >= g.rint_lo[1] && j <= g.rint_hi[1];
+
+  const PsiSet& Pi = A.pin;
+  const PsiSet& Po = A.pout;
+  const bool lay_xy = (sX0 & sXm & sY0 & sYm) >= 0;  // this column or its -x/-y neighbour is in a layer
+
+  // E_x, E_y of the own column at k1 (the plane above the chunk)
+  float ex_up = 0.f, ey_up = 0.f;
+  if (own && k1 < nz) {
+    ex_up = A.F.f[0][k1 * plane + q0];
+    ey_up = A.F.f[1][k1 * plane + q0];
+  }
+
+  for (int k = k1 - 1; k >= k0; --k) {
+    const int q = k * plane + q0;
+    float ex = 0.f, ey = 0.f, ez = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
+    float ebx = 0.f, eby = 0.f, ebz = 0.f, bxm = 0.f, bym = 0.f;
+    if (own) {
+      ex = A.F.f[0][q];
+      ey = A.F.f[1][q];
+      ez = A.F.f[2][q];
+      hx = A.F.f[3][q];
+      hy = A.F.f[4][q];
+      hz = A.F.f[5][q];
+      bx = A.B.f[3][q];
+      by = A.B.f[4][q];
+      bz = A.B.f[5][q];
+      ebx = A.B.f[0][q];
+      eby = A.B.f[1][q];
+      ebz = A.B.f[2][q];
+      if (k > 0) {
+        bxm = A.B.f[3][q - plane];
+        bym = A.B.f[4][q - plane];
+      }
+    }
+    float h1 = 0.f, h2 = 0.f;
+    if (hv) {
+      const int hq = k * plane + hq0;
+      if (role == 0) {  // E_z, E_x at (i, j0+TY)
+        h1 = A.F.f[2][hq];
+        h2 = A.F.f[0][hq];
+      } else if (role == 1) {  // E_y, E_z at (i0+TX, j0+r)
+        h1 = A.F.f[1][hq];
+        h2 = A.F.f[2][hq];
+      } else if (role == 2) {  // w_z, w_x at (i, j0-1)
+        h1 = -S * A.B.f[5][hq];
+        h2 = -S * A.B.f[3][hq];
+      } else {  // w_z, w_y at (i0-1, j0+r)
+        h1 = -S * A.B.f[5][hq];
+        h2 = -S * A.B.f[4][hq];
+      }
+    }
+    const float wx = -S * bx, wy = -S * by, wz = -S * bz;
+    __syncthreads();
+    if (own) {
+      sE[0][ty][tx] = ex;
+      sE[1][ty][tx] = ey;
+      sE[2][ty][tx] = ez;
+      sW[0][ty + 1][tx + 1] = wx;
+      sW[1][ty + 1][tx + 1] = wy;
+      sW[2][ty + 1][tx + 1] = wz;
+    }
+    if (role == 0) {
+      sE[2][TY][hh] = h1;
+      sE[0][TY][hh] = h2;
+    } else if (role == 1 && hh < TY) {
+      sE[1][hh][TX] = h1;
+      sE[2][hh][TX] = h2;
+    } else if (role == 2) {
+      sW[2][0][hh + 1] = h1;
+      sW[0][0][hh + 1] = h2;
+    } else if (role == 3 && hh < TY) {
+      sW[2][hh + 1][0] = h1;
+      sW[1][hh + 1][0] = h2;
+    }
+    __syncthreads();
+    if (!own) continue;
+
+    const float ikZ = T.ik[2][1][k];
+    const int sZ = T.sidx[2][k];
+    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
+    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+
+    // inverse H update on R (E beyond index N - 1 is the PEC wall: zero)
+    const float ez_y = (j + 1 < ny) ? sE[2][ty + 1][tx] : 0.f, ex_y = (j + 1 < ny) ? sE[0][ty + 1][tx] : 0.f;
+    const float ey_x = (i + 1 < nx) ? sE[1][ty][tx + 1] : 0.f, ez_x = (i + 1 < nx) ? sE[2][ty][tx + 1] : 0.f;
+    const bool rzh = k >= g.rhalf_lo[2] && k <= g.rhalf_hi[2], rzi = k >= g.rint_lo[2] && k <= g.rint_hi[2];
+    if (rxi && ryh && rzh) A.F.f[3][q] = hx + S * ((ez_y - ez) * ikY0 - (ey_up - ey) * ikZ);
+    if (rxh && ryi && rzh) A.F.f[4][q] = hy + S * ((ex_up - ex) * ikZ - (ez_x - ez) * ikX0);
+    if (rxh && ryh && rzi) A.F.f[5][q] = hz + S * ((ey_x - ey) * ikX0 - (ex_y - ex) * ikY0);
+    ex_up = ex;
+    ey_up = ey;
+
+    // adjoint: coefficients of the own H point and of its -x, -y, -z neighbours (off the layers +-w)
+    const int sZm = k > 0 ? T.sidx[2][k - 1] : -1;
+    if (!lay_xy && sZ < 0 && sZm < 0) {
+      const float q1z_x = hasXm ? sW[2][ty + 1][tx] : 0.f, q2y_x = hasXm ? -sW[1][ty + 1][tx] : 0.f;
+      const float q2z_y = hasYm ? -sW[2][ty][tx + 1] : 0.f, q1x_y = hasYm ? sW[0][ty][tx + 1] : 0.f;
+      const float q1y_z = k > 0 ? -S * bym : 0.f, q2x_z = k > 0 ? S * bxm : 0.f;
+      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - wy) + (q2z_y + wz));
+      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((q1z_x - wz) + (q2x_z + wx));
+      if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((q1x_y - wx) + (q2y_x + wy));
+      continue;
+    }
+    const float q1x = acoef<1, 1>(T, wx, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
+    const float q2x = acoef<2, 1>(T, wx, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
+    const float q1y = acoef<2, 1>(T, wy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
+    const float q2y = acoef<0, 1>(T, wy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
+    const float q1z = acoef<0, 1>(T, wz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
+    const float q2z = acoef<1, 1>(T, wz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
+    float q1z_x = 0.f, q2y_x = 0.f, q2z_y = 0.f, q1x_y = 0.f, q1y_z = 0.f, q2x_z = 0.f;
+    if (hasXm) {
+      const int zxm = sXm >= 0 ? zx_of(g, j, k, sXm) : 0;
+      q1z_x = acoef<0, 1>(T, sW[2][ty + 1][tx], 1.f, ikXm, sXm, i - 1, Pi.p[2][0], zxm);
+      q2y_x = acoef<0, 1>(T, sW[1][ty + 1][tx], -1.f, ikXm, sXm, i - 1, Pi.p[1][0], zxm);
+    }
+    if (hasYm) {
+      const int zym = sYm >= 0 ? zy_of(g, i, k, sYm) : 0;
+      q2z_y = acoef<1, 1>(T, sW[2][ty][tx + 1], -1.f, ikYm, sYm, j - 1, Pi.p[2][1], zym);
+      q1x_y = acoef<1, 1>(T, sW[0][ty][tx + 1], 1.f, ikYm, sYm, j - 1, Pi.p[0][1], zym);
+    }
+    if (k > 0) {
+      const float ikZm = T.ik[2][1][k - 1];
+      const int zzm = sZm >= 0 ? zz_of(g, i, j, sZm) : 0;
+      q1y_z = acoef<2, 1>(T, -S * bym, 1.f, ikZm, sZm, k - 1, Pi.p[1][2], zzm);
+      q2x_z = acoef<2, 1>(T, -S * bxm, -1.f, ikZm, sZm, k - 1, Pi.p[0][2], zzm);
+    }
+    if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - q1y) + (q2z_y - q2z));
+    if (i > 0 && k > 0) A.B.f[1][q] = eby + ((q1z_x - q1z) + (q2x_z - q2x));
+    if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((q1x_y - q1x) + (q2y_x - q2y));
+    apsi<1, 1>(T, wx, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
+    apsi<2, 1>(T, wx, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
+    apsi<2, 1>(T, wy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
+    apsi<0, 1>(T, wy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
+    apsi<0, 1>(T, wz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
+    apsi<1, 1>(T, wz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
+  }
+}
+
+}  // namespace
+
+void launch_rev_E_lean(const RevArgs& a, cudaStream_t s) {
+  const Geo& g = a.g;
+  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+  k_rev_E_lean<<<grid, NT, 0, s>>>(a);
+}
+
+void launch_rev_H_lean(const RevArgs& a, cudaStream_t s) {
+  const Geo& g = a.g;
+  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+  k_rev_H_lean<<<grid, NT, 0, s>>>(a);
+}
+
+}  // namespace fdtd
