@@ -191,6 +191,11 @@ struct LoopGraph {
 
 }  // namespace
 
+int fdtd::set_error(int code, const char* msg) {
+  g_last_error = msg;
+  return code;
+}
+
 struct fdtd_handle {
   Geo g{};
   fdtd_pml pml{};
@@ -702,11 +707,20 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     // z-chunk of the fused kernels: enough blocks to fill every SM several times over
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
-    // (8 planes per block at least: a shorter march pays its start-up plane too often; measured on
-    // the 96^3 workload, 8 beat 4, 6, 12, 16 and 24)
-    const int64_t want = 148 * 3;
-    const int tz = (int)std::max<int64_t>(1, (int64_t)n[2] * nxy / want);
-    h->tz = std::max(8, std::min(tz, n[2]));
+    // At least 8 planes per block (a shorter march pays its start-up plane too often; on the 96^3
+    // workload 8 beat 4, 6, 12, 16 and 24), and as few chunks as fill whole waves of resident blocks
+    // (3 per SM on 148 SMs) to within 90 %.
+    const int64_t slots = 148 * 3;
+    const int max_chunks = std::max(1, n[2] / 8);
+    int chunks = max_chunks;
+    for (int c = 1; c <= max_chunks; ++c) {
+      const double waves = double(nxy * c) / double(slots);
+      if (waves >= 1.0 && waves / std::ceil(waves) >= 0.9) {
+        chunks = c;
+        break;
+      }
+    }
+    h->tz = (n[2] + chunks - 1) / chunks;
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
       const int v = std::atoi(e);
       if (v >= 1) h->tz = std::min(v, n[2]);

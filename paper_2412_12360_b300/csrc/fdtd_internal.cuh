@@ -164,4 +164,7 @@ int fused_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);
 void launch_set_box(const Geo& g, float* a, const int* lo, const int* hi, const float* box, cudaStream_t s);
 
+// Record `msg` as the calling thread's last error (fdtd_last_error) and return `code`.
+int set_error(int code, const char* msg);
+
 }  // namespace fdtd

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("fdtd_launch_count", C.c_int64, [_VP]),
     ("fdtd_profile", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
+    ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
     ("fdtd_last_error", C.c_char_p, []),
     ("fdtd_version", C.c_char_p, []),
