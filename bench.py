@@ -96,6 +96,31 @@ def algorithmic_bytes(kind, sc):
     return None
 
 
+KERNEL_SOURCE = {"fused_fwd": "fdtd_fused.cu", "rev_E": "fdtd_reverse.cu", "rev_H": "fdtd_reverse.cu",
+                 "update_H": "fdtd_kernels.cu", "update_E": "fdtd_kernels.cu"}
+
+
+def kernel_source_hash(kind):
+    import hashlib
+    path = os.path.join(ROOT, "paper_2412_12360_b300", "csrc", KERNEL_SOURCE.get(kind, ""))
+    if not os.path.isfile(path):
+        return None
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()
+
+
+def recorded_traffic(kind, workload_name):
+    """DRAM bytes per launch of `kind` on this workload from a recorded ncu capture
+    (profiles/traffic.json), or None if there is none or the kernel source changed since."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(workload_name, {}).get(kind)
+    if not e or e.get("source_sha256") != kernel_source_hash(kind):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
 # ---- clocks during the timed region ------------------------------------------------------------------
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -172,13 +197,8 @@ def barrier(world):
 
 
 def max_over_ranks(x, world, device=None):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2412_12360_b300 import ranks
+    return ranks.reduce_time_and_work(x, 0.0, device)[0] if world > 1 else x
 
 
 # ---- CPU baseline (the oracle as it stands) ------------------------------------------------------------
@@ -293,7 +313,8 @@ def run_ours(args, world, rank, local):
             peak, src = 6400.0, "fallback"
         achieved = nbytes / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": src, "traffic": args.traffic,
+                "frac": round(achieved / peak, 4), "peak_source": src,
+                "traffic": args.traffic if args.traffic is not None else recorded_traffic(kname, args.workload),
                 "bytes_per_launch": nbytes, "avg_launch_ms": round(avg_ms, 5),
                 "kernel_ms_per_launch": {k: round(v, 5) for k, v in shares.items()}}
 
@@ -348,6 +369,55 @@ def run_ours(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ---- served stream (continuous batching) -----------------------------------------------------------------
+def run_serve(args, world, rank, local):
+    """Poisson arrivals of fwd+grad requests (grids from {64^3, 96^3, 128x128x256, 200^3}, 1000-3000
+    steps, random densities), served with continuous batching, against the same requests solved one
+    after another."""
+    import torch
+    from paper_2412_12360_b300 import ranks, serve
+
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(7)
+    ids = ranks.shard(args.serve_requests, world, rank)
+    all_scenes = [scenes.served_request(r, rng) for r in range(args.serve_requests)]
+    mine = [all_scenes[r] for r in ids]
+    cells = sum(sc.ncells * sc.nsteps for sc in mine)
+    serve.run_sequential(mine[:1])                     # warm-up: library load, first captures
+    t0 = time.perf_counter()
+    seq = serve.run_sequential(mine)
+    t_seq = time.perf_counter() - t0
+    mean_service = t_seq / max(1, len(mine))
+    arng = np.random.default_rng(8 + rank)
+    gaps = arng.exponential(mean_service / args.serve_load, size=len(mine))
+    with serve.Server(max_inflight=args.serve_slots) as srv:
+        t0 = time.perf_counter()
+        futs = []
+        for sc, gap in zip(mine, gaps):
+            time.sleep(float(gap))
+            futs.append(srv.submit(sc))
+        res = [f.result() for f in futs]
+        t_srv = time.perf_counter() - t0
+        peak = srv.peak_inflight
+    same = all(np.array_equal(a[0], r.detectors) and np.array_equal(a[1], r.dL_deps) for a, r in zip(seq, res))
+    lat = serve.latency_stats(res)
+    t_srv_max, cells_all = ranks.reduce_time_and_work(t_srv, cells)
+    t_seq_max, _ = ranks.reduce_time_and_work(t_seq, cells)
+    if rank != 0:
+        return
+    line = {"metric": "served fwd+grad solves: p50/p99 latency and Gcell-steps/s", "unit": "Gcell-steps/s",
+            "value": round(cells_all / t_srv_max / 1e9, 4), "n_gpus": world,
+            "sequential_value": round(cells_all / t_seq_max / 1e9, 4),
+            "p50_s": round(lat["p50_s"], 4), "p99_s": round(lat["p99_s"], 4), "requests": args.serve_requests,
+            "offered_load": args.serve_load, "slots": args.serve_slots, "peak_inflight": peak,
+            "results_equal_alone_and_in_mix": bool(same), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "served stream: Poisson arrivals, grids {64^3, 96^3, 128x128x256, 200^3}, "
+                                   "1000-3000 steps, 10-cell CPML, random rho per request (seed 10000+id), "
+                                   "arrival seed 8, %d requests" % args.serve_requests}}
+    print(json.dumps(line), flush=True)
+
+
 # ---- reference arm: the FP64 oracle on host cores -------------------------------------------------------
 def run_reference(args, world, rank):
     if rank != 0:
@@ -391,10 +461,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve", action="store_true", help="measure the continuous-batching server instead")
+    ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serve-load", type=float, default=1.5, help="offered load / sequential capacity")
+    ap.add_argument("--serve-slots", type=int, default=6)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.serve:
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -112,6 +112,15 @@ int fdtd_destroy(fdtd_handle* h);
 /* Replace the inverse permittivity on the design box (host or device, box-shaped, x fastest). */
 int fdtd_set_design_eps_inv(fdtd_handle* h, const float* eps_inv_box);
 
+/* Design parametrisation eps = eps_lo + (eps_hi - eps_lo) rho on the design box (the density form of
+ * the paper's design regions, Sec. 3.2-3.3): sets a = 1/eps from rho (host or device, box-shaped
+ * floats in [0, 1], x fastest), with eps rounded to float before the reciprocal. */
+int fdtd_set_design_density(fdtd_handle* h, const float* rho_box, double eps_lo, double eps_hi);
+
+/* As fdtd_backward, but writes dL/drho = (eps_hi - eps_lo) dL/deps for the parametrisation of the
+ * last fdtd_set_design_density (STATE if there was none). */
+int fdtd_backward_density(fdtd_handle* h, const double* dL_ddet, float* dL_drho);
+
 /* Set the initial state E^0, H^{-1/2} (host or device, 6*nx*ny*nz floats, field-major, x fastest);
  * NULL restores zero fields. Used for round-trip and eigenmode tests. */
 int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6);
@@ -161,8 +170,9 @@ int fdtd_set_byte_budget(int64_t bytes);
 int64_t fdtd_launch_count(fdtd_handle* h);
 
 /* With enable != 0, fdtd_forward and fdtd_backward bracket every `every`-th launch of each stencil
- * kernel with CUDA events on the handle's stream and synchronise that stream before returning, so
- * that fdtd_profile_read can report the device time of those launches. enable = 0 stops it and
+ * kernel with CUDA events on the handle's stream; the events are read (waiting for the stream) at
+ * the end of fdtd_backward, before a profiled time loop is replayed again, and by
+ * fdtd_profile_read, which reports the device time of those launches. enable = 0 stops it and
  * clears the totals. */
 int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every);
 

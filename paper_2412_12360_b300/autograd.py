@@ -1,0 +1,75 @@
+"""torch.autograd.Function over the FDTD solve and its time-reversal gradient (arXiv 2412.12360 Sec. 2.2).
+
+    det = FDTDSolve.apply(rho, solvers, eps_lo, eps_hi, nsteps, mode)
+
+rho is a CUDA float tensor [B, dz, dy, dx] of design densities in [0, 1] (eps = eps_lo + (eps_hi -
+eps_lo) rho on each solver's design box); det is [B, n_det] float64, the concatenated detector
+outputs of each design. Any torch loss of det can be back-propagated: the backward pass hands
+dL/d(det) to the library's reverse sweep and returns dL/drho. All field arithmetic, the density map
+and the dL/drho scaling run in the CUDA library; this module only moves pointers.
+
+mode "keep" records the boundary faces during the forward pass and reverses from them (one forward
+and one reversed sweep per design). mode "recompute" runs a plain forward first and, in backward,
+runs the recorded forward again immediately before the reverse sweep of each design, so only one
+face history at a time needs to fit in device memory (used for batches whose histories do not fit).
+"""
+from __future__ import annotations
+
+from typing import List, Sequence
+
+import torch
+
+from . import fdtd
+
+
+def _det_buffer(solver, device):
+    return torch.empty(solver.fdtd_detector_total(), dtype=torch.float64, device=device)
+
+
+class FDTDSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, rho: torch.Tensor, solvers: Sequence["fdtd.Solver"], eps_lo: float, eps_hi: float,
+                nsteps: int, mode: str = "keep"):
+        if not rho.is_cuda or rho.dtype != torch.float32:
+            raise TypeError("rho must be a CUDA float32 tensor [B, dz, dy, dx]")
+        if rho.shape[0] != len(solvers):
+            raise ValueError("one solver per design is needed")
+        if mode not in ("keep", "recompute"):
+            raise ValueError("mode is 'keep' or 'recompute'")
+        outs: List[torch.Tensor] = []
+        rho_c = rho.detach().contiguous()
+        for b, s in enumerate(solvers):
+            s.fdtd_set_design_density(rho_c[b], eps_lo, eps_hi)
+            s.fdtd_forward(nsteps, record_faces=(mode == "keep"))
+            d = _det_buffer(s, rho.device)
+            s.fdtd_read_detectors(d)
+            outs.append(d)
+        ctx.solvers = list(solvers)
+        ctx.eps = (float(eps_lo), float(eps_hi))
+        ctx.nsteps = int(nsteps)
+        ctx.mode = mode
+        ctx.save_for_backward(rho_c)
+        return torch.stack(outs)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        (rho_c,) = ctx.saved_tensors
+        grad = torch.empty_like(rho_c)
+        gd = g.detach().to(torch.float64).contiguous()
+        for b, s in enumerate(ctx.solvers):
+            if ctx.mode == "recompute":
+                s.fdtd_set_design_density(rho_c[b], *ctx.eps)
+                s.fdtd_forward(ctx.nsteps, record_faces=True)
+            s.fdtd_backward_density(gd[b], grad[b])
+        return grad, None, None, None, None, None
+
+
+def solve(rho: torch.Tensor, solvers: Sequence["fdtd.Solver"], eps_lo: float, eps_hi: float, nsteps: int,
+          mode: str = "keep") -> torch.Tensor:
+    """Differentiable detector outputs [B, n_det] for densities rho [B, dz, dy, dx]."""
+    return FDTDSolve.apply(rho, solvers, eps_lo, eps_hi, nsteps, mode)
+
+
+def fits_in_memory(scenes, nsteps: int, budget_bytes: int) -> bool:
+    """Whether every design's solver with its face history fits in `budget_bytes` at once."""
+    return sum(fdtd.footprint_bytes(sc, nsteps, record_faces=True) for sc in scenes) <= budget_bytes

@@ -176,6 +176,7 @@ struct LoopGraph {
   std::vector<Ev> ev;      // timing events recorded by the graph (profiling only)
   int64_t launches = 0;    // kernels per replay
   int cur_after = 0;       // field buffer holding the state after the loop
+  bool pending = false;    // a profiled replay whose events have not been read yet
   void reset() {
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -186,6 +187,7 @@ struct LoopGraph {
     ev.clear();
     nsteps = -1;
     key = -1;
+    pending = false;
   }
 };
 
@@ -240,6 +242,8 @@ struct fdtd_handle {
   int last_nsteps = -1;
   bool recorded = false;
   bool consumed = false;
+  bool density = false;        // the design box was last set from a density rho
+  double eps_lo = 0, eps_hi = 0;
 
   LoopGraph gfwd, gbwd;
 
@@ -330,12 +334,13 @@ int dev_alloc(fdtd_handle* h, void** p, int64_t bytes) {
   if (g_byte_budget >= 0 && h->bytes + bytes > g_byte_budget)
     return fail(FDTD_ERR_OOM, "byte budget %lld exceeded (%lld held, %lld requested)", (long long)g_byte_budget,
                 (long long)h->bytes, (long long)bytes);
-  cudaError_t e = cudaMalloc(p, (size_t)bytes);
+  // stream-ordered: no device-wide synchronisation, so handles can come and go while others run
+  cudaError_t e = cudaMallocAsync(p, (size_t)bytes, h->stream);
   if (e == cudaErrorMemoryAllocation) {
     cudaGetLastError();
-    return fail(FDTD_ERR_OOM, "cudaMalloc of %lld bytes failed", (long long)bytes);
+    return fail(FDTD_ERR_OOM, "cudaMallocAsync of %lld bytes failed", (long long)bytes);
   }
-  if (e != cudaSuccess) return fail(FDTD_ERR_CUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+  if (e != cudaSuccess) return fail(FDTD_ERR_CUDA, "cudaMallocAsync: %s", cudaGetErrorString(e));
   h->bytes += bytes;
   h->gen += 1;
   return FDTD_OK;
@@ -343,7 +348,7 @@ int dev_alloc(fdtd_handle* h, void** p, int64_t bytes) {
 
 void dev_free(fdtd_handle* h, void* p, int64_t bytes) {
   if (p) {
-    cudaFree(p);
+    cudaFreeAsync(p, h->stream);
     h->bytes -= bytes;
     h->gen += 1;
   }
@@ -389,7 +394,8 @@ int upload_tables(fdtd_handle* h) {
       host.push_back(f);
     }
   TRY(dev_alloc(h, (void**)&h->tables, (int64_t)host.size() * 4));
-  CK(cudaMemcpy(h->tables, host.data(), host.size() * 4, cudaMemcpyHostToDevice));
+  CK(cudaMemcpyAsync(h->tables, host.data(), host.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));  // `host` dies on return
   return FDTD_OK;
 }
 
@@ -405,7 +411,8 @@ int ensure_gtab(fdtd_handle* h, int nsteps) {
     std::vector<float> t((size_t)ns * nsteps);
     for (int q = 0; q < ns; ++q)
       for (int n = 0; n < nsteps; ++n) t[(size_t)q * nsteps + n] = (float)pulse(h->src_host[q], h->courant, n + 0.5);
-    CK(cudaMemcpy(h->gtab, t.data(), t.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(h->gtab, t.data(), t.size() * 4, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // `t` dies on return
     h->gtab_cap = nsteps;
   }
   for (int q = 0; q < ns; ++q) h->srcs[q].g = h->gtab + (size_t)q * h->gtab_cap;
@@ -573,14 +580,24 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   return launches;
 }
 
-int prof_collect(fdtd_handle* h, LoopGraph& lg) {
-  if (h->prof_every <= 0 || lg.ev.empty()) return FDTD_OK;
+// Read the timing events of every profiled replay still pending (waits for the stream). Called
+// before a pending graph is replayed again, after a backward, and by fdtd_profile_read, so a
+// forward followed by a backward costs one wait at the end instead of one between the two.
+int prof_collect(fdtd_handle* h) {
+  LoopGraph* gs[2] = {&h->gfwd, &h->gbwd};
+  bool any = false;
+  for (LoopGraph* lg : gs) any |= lg->pending;
+  if (!any) return FDTD_OK;
   CK(cudaStreamSynchronize(h->stream));
-  for (auto& e : lg.ev) {
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e.a, e.b));
-    h->prof_ms[e.kind] += ms;
-    h->prof_n[e.kind] += 1;
+  for (LoopGraph* lg : gs) {
+    if (!lg->pending) continue;
+    for (auto& e : lg->ev) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e.a, e.b));
+      h->prof_ms[e.kind] += ms;
+      h->prof_n[e.kind] += 1;
+    }
+    lg->pending = false;
   }
   return FDTD_OK;
 }
@@ -589,6 +606,7 @@ int prof_collect(fdtd_handle* h, LoopGraph& lg) {
 template <class Enqueue>
 int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int key, Enqueue enqueue) {
   if (nsteps == 0) return FDTD_OK;
+  if (lg.pending) TRY(prof_collect(h));  // its events are about to be recorded again
   const int cur0 = h->cur;
   if (!(lg.exec && lg.nsteps == nsteps && lg.key == key && lg.gen == h->gen)) {
     lg.reset();
@@ -616,7 +634,7 @@ int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int key, Enqueue enqueue
   CK(cudaGraphLaunch(lg.exec, h->stream));
   h->cur = lg.cur_after;
   h->launches += lg.launches;
-  TRY(prof_collect(h, lg));
+  lg.pending = h->prof_every > 0 && !lg.ev.empty();
   return FDTD_OK;
 }
 
@@ -737,11 +755,12 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     const int64_t N = (int64_t)n[0] * n[1] * n[2];
     float* tmp = nullptr;
     if ((rc = dev_alloc(h, (void**)&tmp, N * 4)) != FDTD_OK) return cleanup(rc);
-    cudaError_t e = cudaMemcpy(tmp, eps_inv, N * 4, cudaMemcpyDefault);
-    if (e == cudaSuccess) e = cudaMemset(h->a, 0, g.vol * 4);
+    cudaError_t e = cudaMemcpyAsync(tmp, eps_inv, N * 4, cudaMemcpyDefault, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->a, 0, g.vol * 4, h->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpy2D(h->a, (size_t)g.nxp * 4, tmp, (size_t)n[0] * 4, (size_t)n[0] * 4, (size_t)n[1] * n[2],
-                       cudaMemcpyDeviceToDevice);
+      e = cudaMemcpy2DAsync(h->a, (size_t)g.nxp * 4, tmp, (size_t)n[0] * 4, (size_t)n[0] * 4, (size_t)n[1] * n[2],
+                            cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // eps_inv may be a host buffer
     dev_free(h, tmp, N * 4);
     if (e != cudaSuccess) return cleanup(fail(FDTD_ERR_CUDA, "copy of eps_inv: %s", cudaGetErrorString(e)));
   }
@@ -762,7 +781,8 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     float* dw = nullptr;
     if ((rc = dev_alloc(h, (void**)&dw, m * 4)) != FDTD_OK) return cleanup(rc);
     h->src_w.push_back(dw);
-    if (cudaMemcpy(dw, w.data(), m * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpyAsync(dw, w.data(), m * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)  // `w` dies at the end of this iteration
       return cleanup(fail(FDTD_ERR_CUDA, "source upload failed"));
     SrcDev sd;
     sd.comp = s.component;
@@ -807,32 +827,23 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
 
 int fdtd_destroy(fdtd_handle* h) {
   if (!h) return FDTD_OK;
-  cudaStreamSynchronize(h->stream);
   h->gfwd.reset();
   h->gbwd.reset();
+  void* bufs[] = {h->fields, h->a, h->psiE, h->psiH, h->tables, h->init, h->gtab, h->det_out, h->partial,
+                  h->face_hist, h->adj, h->psibar, h->dLda, h->dLddet, h->staging};
+  for (void* p : bufs)
+    if (p) cudaFreeAsync(p, h->stream);
+  for (float* p : h->src_w) cudaFreeAsync(p, h->stream);
+  cudaStreamSynchronize(h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
-  cudaFree(h->fields);
-  cudaFree(h->a);
-  cudaFree(h->psiE);
-  cudaFree(h->psiH);
-  cudaFree(h->tables);
-  cudaFree(h->init);
-  for (float* p : h->src_w) cudaFree(p);
-  cudaFree(h->gtab);
-  cudaFree(h->det_out);
-  cudaFree(h->partial);
-  cudaFree(h->face_hist);
-  cudaFree(h->adj);
-  cudaFree(h->psibar);
-  cudaFree(h->dLda);
-  cudaFree(h->dLddet);
-  cudaFree(h->staging);
+  cudaGetLastError();
   delete h;
   return FDTD_OK;
 }
 
 int fdtd_set_design_eps_inv(fdtd_handle* h, const float* eps_inv_box) {
   if (!h || !eps_inv_box) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  h->density = false;
   const int64_t m = box_cells(h->design_lo, h->design_hi);
   if (m == 0) return FDTD_OK;
   TRY(ensure_staging(h));
@@ -896,7 +907,7 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   return FDTD_OK;
 }
 
-int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
+static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps, double scale) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (!h->recorded || h->consumed)
     return fail(FDTD_ERR_STATE, "backward needs a forward with FDTD_RECORD_FACES that no backward has consumed");
@@ -920,13 +931,41 @@ int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
   TRY(run_loop(h, h->gbwd, nsteps, key,
                [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
   if (M > 0) {
-    launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, h->stream);
+    launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, scale, h->stream);
     h->launches += 1;
     CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
   }
   CK(cudaGetLastError());
   h->consumed = true;
+  TRY(prof_collect(h));
   if (M > 0 && is_host_pointer(dL_deps)) CK(cudaStreamSynchronize(h->stream));
+  return FDTD_OK;
+}
+
+int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
+  return backward_scaled(h, dL_ddet, dL_deps, 1.0);
+}
+
+int fdtd_backward_density(fdtd_handle* h, const double* dL_ddet, float* dL_drho) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (!h->density) return fail(FDTD_ERR_STATE, "no design density was set");
+  return backward_scaled(h, dL_ddet, dL_drho, h->eps_hi - h->eps_lo);
+}
+
+int fdtd_set_design_density(fdtd_handle* h, const float* rho_box, double eps_lo, double eps_hi) {
+  if (!h || !rho_box) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  if (!(eps_lo > 0.0) || !(eps_hi > 0.0)) return fail(FDTD_ERR_INVALID_ARG, "eps_lo and eps_hi must be positive");
+  const int64_t m = box_cells(h->design_lo, h->design_hi);
+  h->density = true;
+  h->eps_lo = eps_lo;
+  h->eps_hi = eps_hi;
+  if (m == 0) return FDTD_OK;
+  TRY(ensure_staging(h));
+  CK(cudaMemcpyAsync(h->staging, rho_box, m * 4, cudaMemcpyDefault, h->stream));
+  launch_set_density(h->g, h->a, h->design_lo, h->design_hi, h->staging, (float)eps_lo, (float)(eps_hi - eps_lo),
+                     h->stream);
+  h->launches += 1;
+  CK(cudaGetLastError());
   return FDTD_OK;
 }
 
@@ -963,6 +1002,7 @@ int64_t fdtd_launch_count(fdtd_handle* h) { return h ? h->launches : -1; }
 int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (enable && every < 1) return fail(FDTD_ERR_INVALID_ARG, "every must be >= 1");
+  if (h->gfwd.pending || h->gbwd.pending) TRY(prof_collect(h));
   h->prof_every = enable ? every : 0;
   for (int k = 0; k < FDTD_KERNEL_KINDS; ++k) {
     h->prof_ms[k] = 0;
@@ -973,6 +1013,7 @@ int fdtd_profile(fdtd_handle* h, int32_t enable, int32_t every) {
 
 int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds) {
   if (!h || nkinds < 0) return fail(FDTD_ERR_INVALID_ARG, "bad argument");
+  TRY(prof_collect(h));
   for (int k = 0; k < nkinds && k < FDTD_KERNEL_KINDS; ++k) {
     if (ms) ms[k] = h->prof_ms[k];
     if (count) count[k] = h->prof_n[k];

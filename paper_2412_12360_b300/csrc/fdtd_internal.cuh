@@ -138,7 +138,9 @@ void launch_rev_E(const Geo& g, const Fields& F, const Fields& A, const PsiSet& 
 void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& psiH_old, const PsiSet& psiH_new,
                   const Tables& T, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
-                          float* dL_deps, cudaStream_t s);
+                          float* dL_deps, double scale, cudaStream_t s);
+void launch_set_density(const Geo& g, float* a, const int* lo, const int* hi, const float* rho, float eps_lo,
+                        float deps, cudaStream_t s);
 // Arguments of the reverse-step kernels (in place on the fields F and the adjoint fields B).
 struct RevArgs {
   Geo g;

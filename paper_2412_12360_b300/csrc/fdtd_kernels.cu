@@ -427,15 +427,25 @@ __global__ void k_rev_H(Geo g, Fields F, Fields A, PsiSet Pold, PsiSet Pnew, Tab
   h_psi_adjoint<2>(g, A, Pold, Pnew, T, p, q);
 }
 
+__global__ void k_set_density(Geo g, float* a, int lo0, int lo1, int lo2, int hi0, int hi1, int hi2,
+                              const float* rho, float eps_lo, float deps) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int bx = hi0 - lo0, by = hi1 - lo1;
+  if (m >= (int64_t)bx * by * (hi2 - lo2)) return;
+  const int i = lo0 + int(m % bx), j = lo1 + int((m / bx) % by), k = lo2 + int(m / ((int64_t)bx * by));
+  const float eps = eps_lo + deps * rho[m];          // float, as the scene inputs are built
+  a[cell_index(g, i, j, k)] = (float)(1.0 / (double)eps);
+}
+
 __global__ void k_grad_finalize(Geo g, const float* __restrict__ a, int dlo0, int dlo1, int dlo2, int dhi0,
-                                int dhi1, int dhi2, const double* dLda, float* out) {
+                                int dhi1, int dhi2, const double* dLda, float* out, double scale) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int bx = dhi0 - dlo0, by = dhi1 - dlo1;
   const int64_t M = (int64_t)bx * by * (dhi2 - dlo2);
   if (m >= M) return;
   const int i = dlo0 + int(m % bx), j = dlo1 + int((m / bx) % by), k = dlo2 + int(m / ((int64_t)bx * by));
   const double av = a[cell_index(g, i, j, k)];
-  out[m] = (float)(-av * av * dLda[m]);  // a = 1/eps, da/deps = -a^2
+  out[m] = (float)(-av * av * dLda[m] * scale);  // a = 1/eps, da/deps = -a^2; scale = deps/drho or 1
 }
 
 __global__ void k_pack(Geo g, Fields F, float* out6, int unpack) {
@@ -519,11 +529,18 @@ void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& 
 }
 
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
-                          float* dL_deps, cudaStream_t s) {
+                          float* dL_deps, double scale, cudaStream_t s) {
   const int64_t n = (int64_t)(dhi[0] - dlo[0]) * (dhi[1] - dlo[1]) * (dhi[2] - dlo[2]);
   if (n <= 0) return;
   k_grad_finalize<<<blocks_for(n, 256), 256, 0, s>>>(g, a, dlo[0], dlo[1], dlo[2], dhi[0], dhi[1], dhi[2], dLda,
-                                                     dL_deps);
+                                                     dL_deps, scale);
+}
+
+void launch_set_density(const Geo& g, float* a, const int* lo, const int* hi, const float* rho, float eps_lo,
+                        float deps, cudaStream_t s) {
+  const int64_t n = (int64_t)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+  if (n <= 0) return;
+  k_set_density<<<blocks_for(n, 256), 256, 0, s>>>(g, a, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], rho, eps_lo, deps);
 }
 
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s) {

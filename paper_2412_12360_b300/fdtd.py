@@ -67,6 +67,8 @@ SIGNATURES = [
     ("fdtd_destroy", C.c_int, [_VP]),
     ("fdtd_set_design_eps_inv", C.c_int, [_VP, _VP]),
     ("fdtd_set_initial_fields", C.c_int, [_VP, _VP]),
+    ("fdtd_set_design_density", C.c_int, [_VP, _VP, C.c_double, C.c_double]),
+    ("fdtd_backward_density", C.c_int, [_VP, _VP, _VP]),
     ("fdtd_forward", C.c_int, [_VP, C.c_int32, C.c_uint32]),
     ("fdtd_backward", C.c_int, [_VP, _VP, _VP]),
     ("fdtd_read_detectors", C.c_int, [_VP, _VP]),
@@ -238,6 +240,12 @@ class Solver:
 
     def fdtd_set_design_eps_inv(self, box):
         check(lib().fdtd_set_design_eps_inv(self.h, _ptr(box)))
+
+    def fdtd_set_design_density(self, rho_box, eps_lo: float, eps_hi: float):
+        check(lib().fdtd_set_design_density(self.h, _ptr(rho_box), float(eps_lo), float(eps_hi)))
+
+    def fdtd_backward_density(self, dL_ddet, dL_drho):
+        check(lib().fdtd_backward_density(self.h, _ptr(dL_ddet), _ptr(dL_drho)))
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))

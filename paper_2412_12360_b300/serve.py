@@ -1,0 +1,214 @@
+"""Continuous-batching server for forward + time-reversal-gradient solves of mixed sizes.
+
+Requests (a scene: grid, sources, detectors, design box and densities, step count) arrive at any
+time. A scheduler thread admits them in arrival order whenever a slot is free and the request's
+device footprint (fdtd_footprint_bytes: fields, CPML memories, adjoint state and the boundary-face
+history) fits in the memory budget still free; each admitted request gets its own CUDA stream and
+solver handle, so its forward and reversed sweeps overlap on the GPU with those of the requests
+already running. Completion is detected with CUDA events; finished requests return their detector
+outputs and dL/deps and free their memory (stream-ordered, so other requests keep running), which
+admits the next ones.
+
+The numerical work of every request is the library's (one captured graph per sweep); a request's
+result does not depend on what else is in flight, so it is the same alone and in the mix.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from concurrent.futures import Future
+from dataclasses import dataclass, field
+from typing import Deque, List, Optional
+
+import numpy as np
+
+
+def admit_count(queue_footprints, inflight: int, used: int, budget: int, max_inflight: int) -> int:
+    """How many requests at the head of the queue can be admitted now: first-come first-served, while a
+    slot is free and the next request's footprint fits in the memory still free (the head blocks the
+    ones behind it, so no request starves)."""
+    n = 0
+    for fp in queue_footprints:
+        if inflight + n >= max_inflight or used + fp > budget:
+            break
+        used += fp
+        n += 1
+    return n
+
+
+@dataclass
+class Result:
+    detectors: np.ndarray
+    dL_deps: np.ndarray
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class _Job:
+    scene: object
+    dL_ddet: Optional[np.ndarray]
+    future: Future
+    arrival: float
+    footprint: int
+    admitted: float = 0.0
+    solver: object = None
+    stream: object = None
+    done: object = None
+    det: object = None
+    grad: object = None
+    gvec: object = None
+
+
+class Server:
+    """Continuous-batching solver service on one GPU.
+
+    budget_bytes: device memory the server may give to requests (default: 85 % of the free memory).
+    max_inflight: requests running at once.
+    objective: dL/d(detector) used when a request gives none (default: ones, i.e. L = sum of outputs).
+    """
+
+    def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 8, device: int = 0,
+                 footprint=None):
+        import torch
+        from . import fdtd
+
+        self._torch = torch
+        self._fdtd = fdtd
+        self.device = torch.device("cuda", device)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            budget_bytes = int(0.85 * free)
+        self.budget = int(budget_bytes)
+        self.max_inflight = int(max_inflight)
+        self._footprint = footprint or (lambda sc: fdtd.footprint_bytes(sc, sc.nsteps, record_faces=True))
+        self._queue: Deque[_Job] = collections.deque()
+        self._inflight: List[_Job] = []
+        self._used = 0
+        self._lock = threading.Condition()
+        self._stop = False
+        self._streams: List[object] = []
+        self.peak_inflight = 0
+        self._thread = threading.Thread(target=self._loop, name="fdtd-server", daemon=True)
+        self._thread.start()
+
+    # ---- client side ---------------------------------------------------------------------------
+    def submit(self, scene, dL_ddet: Optional[np.ndarray] = None) -> Future:
+        fp = int(self._footprint(scene))
+        if fp > self.budget:
+            raise ValueError("request needs %d bytes, more than the server's budget of %d" % (fp, self.budget))
+        fut: Future = Future()
+        with self._lock:
+            self._queue.append(_Job(scene, dL_ddet, fut, time.perf_counter(), fp))
+            self._lock.notify()
+        return fut
+
+    def close(self):
+        with self._lock:
+            self._stop = True
+            self._lock.notify()
+        self._thread.join()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- scheduler ----------------------------------------------------------------------------
+    def _stream(self):
+        if self._streams:
+            return self._streams.pop()
+        return self._torch.cuda.Stream(device=self.device)
+
+    def _admit(self, job: _Job):
+        torch, fdtd = self._torch, self._fdtd
+        sc = job.scene
+        job.stream = self._stream()
+        job.admitted = time.perf_counter()
+        with torch.cuda.stream(job.stream):
+            job.solver = fdtd.Solver(sc, stream=job.stream)
+            job.solver.fdtd_forward(sc.nsteps, record_faces=True)
+            ndet = job.solver.fdtd_detector_total()
+            g = job.dL_ddet if job.dL_ddet is not None else np.ones(ndet)
+            job.gvec = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float64)).pin_memory().to(
+                self.device, non_blocking=True)
+            job.det = torch.empty(ndet, dtype=torch.float64, device=self.device)
+            job.grad = torch.empty(sc.design_shape(), dtype=torch.float32, device=self.device)
+            job.solver.fdtd_read_detectors(job.det)
+            job.solver.fdtd_backward(job.gvec, job.grad)
+            job.done = torch.cuda.Event()
+            job.done.record(job.stream)
+
+    def _retire(self, job: _Job):
+        det = job.det.cpu().numpy()
+        grad = job.grad.cpu().numpy()
+        job.solver.close()
+        self._streams.append(job.stream)
+        job.future.set_result(Result(det, grad, job.arrival, job.admitted, time.perf_counter()))
+
+    def _loop(self):
+        torch = self._torch
+        torch.cuda.set_device(self.device)
+        while True:
+            with self._lock:
+                if self._stop and not self._queue and not self._inflight:
+                    return
+                if not self._queue and not self._inflight:
+                    self._lock.wait(timeout=0.05)
+                    continue
+            progressed = False
+            for job in list(self._inflight):
+                if job.done.query():
+                    self._inflight.remove(job)
+                    self._used -= job.footprint
+                    try:
+                        self._retire(job)
+                    except Exception as e:  # noqa: BLE001 - report to the client
+                        job.future.set_exception(e)
+                    progressed = True
+            while True:
+                with self._lock:
+                    if not self._queue or admit_count([self._queue[0].footprint], len(self._inflight), self._used,
+                                                      self.budget, self.max_inflight) == 0:
+                        break
+                    job = self._queue.popleft()
+                self._used += job.footprint
+                try:
+                    self._admit(job)
+                    self._inflight.append(job)
+                    self.peak_inflight = max(self.peak_inflight, len(self._inflight))
+                except Exception as e:  # noqa: BLE001 - report to the client
+                    self._used -= job.footprint
+                    job.future.set_exception(e)
+                progressed = True
+            if not progressed:
+                time.sleep(0.0005)
+
+
+def run_sequential(scenes, device: int = 0):
+    """The same requests solved one after another on the default stream (the comparison baseline)."""
+    import torch
+    from . import fdtd
+
+    out = []
+    for sc in scenes:
+        with fdtd.Solver(sc) as s:
+            s.fdtd_forward(sc.nsteps, record_faces=True)
+            det = s.detectors()
+            grad = s.gradient(np.ones(s.fdtd_detector_total()))
+        out.append((det, grad))
+    torch.cuda.synchronize()
+    return out
+
+
+def latency_stats(results) -> dict:
+    lat = np.array([r.latency for r in results])
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "n": int(lat.size)}

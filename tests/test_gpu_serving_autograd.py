@@ -1,0 +1,74 @@
+"""Served (continuous-batching) solves and the autograd Function on the GPU.
+
+Each served request gives bitwise the same detectors and dL/deps alone and in the mix; the memory
+budget bounds what runs at once; FDTDSolve's dL/drho matches the FP64 oracle's dL/deps scaled by
+deps/drho, in both its keep and recompute modes.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2412_12360_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix(n=6):
+    rng = np.random.default_rng(5)
+    out = []
+    sizes = [(40, 40, 40), (48, 40, 56), (56, 56, 56), (40, 48, 40)]
+    for r in range(n):
+        nn = sizes[r % len(sizes)]
+        out.append(S.design_box_scene(nn, 6, 12, int(rng.integers(150, 260)), 900 + r, name="mix%d" % r))
+    return out
+
+
+def test_served_results_equal_alone_and_in_the_mix(cuda_ok):
+    from paper_2412_12360_b300 import serve
+    scenes = _mix(6)
+    alone = serve.run_sequential(scenes)
+    with serve.Server(max_inflight=4) as srv:
+        futs = [srv.submit(sc) for sc in scenes]
+        res = [f.result(timeout=600) for f in futs]
+        peak = srv.peak_inflight
+    assert peak >= 2
+    for (d0, g0), r in zip(alone, res):
+        assert np.array_equal(d0, r.detectors)
+        assert np.array_equal(g0, r.dL_deps)
+
+
+def test_served_admission_bounded_by_budget(cuda_ok):
+    from paper_2412_12360_b300 import fdtd, serve
+    scenes = _mix(5)
+    fps = [fdtd.footprint_bytes(sc, sc.nsteps) for sc in scenes]
+    budget = sum(sorted(fps)[-2:])  # room for the two largest at most
+    with serve.Server(budget_bytes=budget, max_inflight=8) as srv:
+        res = [f.result(timeout=600) for f in [srv.submit(sc) for sc in scenes]]
+        peak = srv.peak_inflight
+    assert len(res) == 5 and 1 <= peak <= 3
+    lat = serve.latency_stats(res)
+    assert lat["p99_s"] >= lat["p50_s"] > 0
+
+
+@pytest.mark.parametrize("mode", ["keep", "recompute"])
+def test_autograd_density_gradient_matches_oracle(cuda_ok, mode):
+    import torch
+    from paper_2412_12360_b300 import autograd, fdtd
+    scenes = [S.design_box_scene((40, 36, 44), 6, 12, 160, 31 + b, name="ad%d" % b) for b in range(2)]
+    eps_lo, eps_hi = scenes[0].extra["eps_lo"], scenes[0].extra["eps_hi"]
+    rho = torch.stack([torch.from_numpy(sc.extra["rho"]) for sc in scenes]).cuda().requires_grad_(True)
+    solvers = [fdtd.Solver(sc) for sc in scenes]
+    det = autograd.solve(rho, solvers, eps_lo, eps_hi, 160, mode)
+    w = torch.linspace(0.5, 1.5, det.shape[1], dtype=torch.float64, device="cuda")
+    loss = (det * w).sum()
+    loss.backward()
+    grad = rho.grad.cpu().numpy()
+    for b, sc in enumerate(scenes):
+        g = w.cpu().numpy()
+        grad_o, _, det_o = O.gradient(sc, 160, g, O.METHOD_TIME_REVERSAL)
+        ref = (eps_hi - eps_lo) * grad_o
+        e = np.linalg.norm(grad[b] - ref) / np.linalg.norm(ref)
+        assert e < 1e-3, e
+        assert np.linalg.norm(det[b].detach().cpu().numpy() - det_o) / np.linalg.norm(det_o) < 1e-4
+    for s in solvers:
+        s.close()
