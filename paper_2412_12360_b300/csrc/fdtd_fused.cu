@@ -12,8 +12,9 @@
 // The march is software-pipelined: while plane k is computed, the loads of E^n for plane k+2 and of
 // H^{n-1/2} and a for plane k+1 are already in flight. Everything that depends only on x and y (CPML
 // coefficients, slab indices, source, detector and face membership) is computed once per thread;
-// what depends on z once per plane. A cell off the layers pays a multiply by 1/kappa = 1 (exact) and
-// a few untaken branches for the CPML.
+// what depends on z once per plane. Every cell takes the plain Yee update; cells in a CPML layer add
+// the correction (1/kappa - 1) d + psi per curl term, which is exactly 0 off the layers and on their
+// inner edge, so the PML-free region R is updated by the plain formula the inverse step mirrors.
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -24,18 +25,17 @@ constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int SX = TX + 2, SY = TY + 2;  // staged E tile with a one-cell halo
 constexpr int HX = TX + 1, HY = TY + 1;  // new H with the low halo
 
-// One curl term: difference / kappa plus the updated CPML memory (b, c at table position `pos`, memory
-// read from pin[z], written to pout[z] when STORE). Off the layers (s < 0) it is d * 1 exactly.
+// CPML correction of one curl term inside a layer: the update uses d / kappa + psi_new where the plain
+// Yee update uses d, so the correction is (1/kappa - 1) d + psi_new with psi_new = b psi_old + c d
+// (read from pin[z], written to pout[z] when STORE). Off the layers (s < 0) it is 0; on the layer's
+// inner edge (depth 0) 1/kappa = 1, b = 1, c = 0 and psi stays 0, so it is 0 there too.
 template <bool STORE>
-__device__ __forceinline__ float cterm(float d, float ik, int s, const float* __restrict__ bt,
-                                       const float* __restrict__ ct, int pos, const float* pin, float* pout, int z) {
-  float t = d * ik;
-  if (s >= 0) {
-    const float v = bt[pos] * pin[z] + ct[pos] * d;
-    if (STORE) pout[z] = v;
-    t += v;
-  }
-  return t;
+__device__ __forceinline__ float corr(float d, float ik, int s, const float* __restrict__ bt,
+                                      const float* __restrict__ ct, int pos, const float* pin, float* pout, int z) {
+  if (s < 0) return 0.f;
+  const float v = bt[pos] * pin[z] + ct[pos] * d;
+  if (STORE) pout[z] = v;
+  return (ik - 1.f) * d + v;
 }
 
 // psi index of the point (x, y, k), slab index s, for the derivative along x, y or z
@@ -60,31 +60,31 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
 }
 
-// The four staging positions of a thread: rows ty and TY + ty (ty < 2), columns tx and TX + tx (tx < 2)
-// of the (TY + 2) x (TX + 2) tile whose corner is (i0 - 1, j0 - 1).
+// Staging of one E plane (tile plus a one-cell halo) into shared memory: every thread loads its own
+// cell (row ty+1, column tx+1: aligned, coalesced rows); warp 0 loads the halo row y = j0-1, warp 1 the
+// row y = j0+TY, and warp 2 the halo columns x = i0-1 (lanes 0..TY+1) and x = i0+TX (lanes 16..17+TY),
+// corners included.
 struct Stage {
-  int off[4];
-  bool ok[4];
+  int own_off, role_off;  // in-plane offsets of the own cell and of this thread's halo point
+  bool own_ok, role_ok;   // inside the grid
+  int role_ry, role_rx;   // where the halo point goes in the staged tile (role_ry < 0: no halo point)
 };
 
-__device__ __forceinline__ void load_plane(const Geo& g, const Fields& F, const Stage& st, int k, float r[3][4]) {
+__device__ __forceinline__ void load_stage(const Geo& g, const Fields& F, const Stage& st, int k, float r[2][3]) {
   const bool kin = k < g.n[2];
   const int base = k * (int)g.plane;
 #pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) r[c][u] = (kin && st.ok[u]) ? F.f[c][base + st.off[u]] : 0.f;
+  for (int c = 0; c < 3; ++c) {
+    r[0][c] = (kin && st.own_ok) ? F.f[c][base + st.own_off] : 0.f;
+    r[1][c] = (kin && st.role_ok) ? F.f[c][base + st.role_off] : 0.f;
+  }
 }
 
-__device__ __forceinline__ void store_plane(float (*dst)[SY][SX], const float r[3][4], int tx, int ty) {
+__device__ __forceinline__ void store_stage(float (*dst)[SY][SX], const Stage& st, const float r[2][3], int tx, int ty) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    dst[c][ty][tx] = r[c][0];
-    if (tx < 2) dst[c][ty][TX + tx] = r[c][1];
-    if (ty < 2) {
-      dst[c][TY + ty][tx] = r[c][2];
-      if (tx < 2) dst[c][TY + ty][TX + tx] = r[c][3];
-    }
+    dst[c][ty + 1][tx + 1] = r[0][c];
+    if (st.role_ry >= 0) dst[c][st.role_ry][st.role_rx] = r[1][c];
   }
 }
 
@@ -109,36 +109,43 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
   const int rx = tx + 1, ry = ty + 1;
 
   Stage st;
+  st.own_ok = own;
+  st.own_off = q0;
+  st.role_ry = -1;
+  st.role_rx = 0;
+  st.role_ok = false;
+  st.role_off = 0;
   {
-    const int xa = i0 - 1 + tx, xb = i0 + TX - 1 + tx, ya = j0 - 1 + ty, yb = j0 + TY - 1 + ty;
-    const bool oxa = xa >= 0 && xa < nx, oxb = tx < 2 && xb < nx;
-    const bool oya = ya >= 0 && ya < ny, oyb = ty < 2 && yb < ny;
-    st.ok[0] = oya && oxa;
-    st.ok[1] = oya && oxb;
-    st.ok[2] = oyb && oxa;
-    st.ok[3] = oyb && oxb;
-    st.off[0] = ya * g.nxp + xa;
-    st.off[1] = ya * g.nxp + xb;
-    st.off[2] = yb * g.nxp + xa;
-    st.off[3] = yb * g.nxp + xb;
+    int x = 0, y = 0;
+    if (ty == 0) {  // halo row y = j0 - 1
+      x = i0 + tx; y = j0 - 1; st.role_ry = 0; st.role_rx = tx + 1;
+    } else if (ty == 1) {  // halo row y = j0 + TY
+      x = i0 + tx; y = j0 + TY; st.role_ry = TY + 1; st.role_rx = tx + 1;
+    } else if (ty == 2 && tx < SY) {  // halo column x = i0 - 1, rows j0-1 .. j0+TY
+      x = i0 - 1; y = j0 - 1 + tx; st.role_ry = tx; st.role_rx = 0;
+    } else if (ty == 2 && tx >= 16 && tx < 16 + SY) {  // halo column x = i0 + TX
+      x = i0 + TX; y = j0 - 1 + (tx - 16); st.role_ry = tx - 16; st.role_rx = TX + 1;
+    }
+    st.role_ok = st.role_ry >= 0 && x >= 0 && x < nx && y >= 0 && y < ny;
+    st.role_off = y * g.nxp + x;
   }
 
-  // halo work: warp 0 takes the row y = j0-1 (Hx, Hz), threads TX .. TX+TY-1 the column x = i0-1 (Hy, Hz)
-  const bool hrow = tid < TX && j0 > 0 && i < nx;
-  const int hr = tid - TX;
-  const bool hcol = tid >= TX && tid < TX + TY && i0 > 0 && (j0 + hr) < ny;
-  const int xh = hcol ? i0 - 1 : min(i, nx - 1);            // x of this thread's halo point
-  const int yh = hcol ? j0 + hr : max(j0 - 1, 0);           // y of this thread's halo point
+  // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
+  const bool hrow = ty == 3 && j0 > 0 && i < nx;
+  const bool hcol = ty == 4 && tx < TY && i0 > 0 && (j0 + tx) < ny;
+  const int xh = hcol ? i0 - 1 : min(i, nx - 1);
+  const int yh = hcol ? j0 + tx : max(j0 - 1, 0);
+  const int hrx = hcol ? 0 : tx + 1, hry = hcol ? tx + 1 : 0;  // staged position of the halo point
   const int qh0 = yh * g.nxp + xh;
 
-  // CPML data along x and y, fixed for the whole march
+  // CPML data along x and y, fixed for the whole march (H tables at half, E tables at integer positions)
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   const float ikXh = T.ik[0][1][ic], ikXe = T.ik[0][0][ic], ikYh = T.ik[1][1][jc], ikYe = T.ik[1][0][jc];
   const int sX = T.sidx[0][ic], sY = T.sidx[1][jc];
   const float ikXhh = T.ik[0][1][xh], ikYhh = T.ik[1][1][yh];  // at the halo point
   const int sXh = T.sidx[0][xh], sYh = T.sidx[1][yh];
 
-  // membership of this column in the source and detector boxes (bit s), and in the x/y face planes
+  // membership of this column in the source and detector boxes (bit s), and face segments
   unsigned src_xy = 0, det_xy = 0;
   for (int s = 0; s < A.nsrc; ++s) {
     const SrcDev& sd = A.src[s];
@@ -148,10 +155,6 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     const DetDev& d = A.det[s];
     if (own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1]) det_xy |= 1u << s;
   }
-  // boundary-face record: a column on an x- or y-face writes its H there for the planes in range; a
-  // z-face plane is written by every column in range. Offsets into one step's record:
-  //   x-face (comp y, z): off + (k - lo2) * n1 + (j - lo1);   y-face (comp z, x): off + (i - lo2) * n1 + (k - lo1)
-  //   z-face (comp x, y): off + (j - lo2) * n1 + (i - lo1)
   // (a column lies on at most one x- or y-face line, i.e. two segments; z-faces are at most two
   // planes, each with an Hx and an Hy segment). Only segment numbers are kept; offsets are computed
   // when a face value is written.
@@ -185,16 +188,16 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
   const Fields& C = A.cur;
   const Fields& N = A.nxt;
 
-  float pe[3][4];
+  float pe[2][3];
   float hxm = 0.f, hym = 0.f;
   int cur = 0;
   if (k0 > 0) {
     // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
     const int km = k0 - 1;
-    load_plane(g, C, st, km, pe);
-    store_plane(sE[0], pe, tx, ty);
-    load_plane(g, C, st, k0, pe);
-    store_plane(sE[1], pe, tx, ty);
+    load_stage(g, C, st, km, pe);
+    store_stage(sE[0], st, pe, tx, ty);
+    load_stage(g, C, st, k0, pe);
+    store_stage(sE[1], st, pe, tx, ty);
     __syncthreads();
     if (own) {
       const int q = km * plane + q0;
@@ -202,21 +205,28 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       const float(*a1)[SY][SX] = sE[1];
       const float ikZh = T.ik[2][1][km];
       const int sZ = T.sidx[2][km];
-      const int zx = sX >= 0 ? zx_of(g, j, km, sX) : 0, zy = sY >= 0 ? zy_of(g, i, km, sY) : 0;
-      const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
-      hxm = C.f[3][q] - S * (cterm<false>(a0[2][ry + 1][rx] - a0[2][ry][rx], ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], nullptr, zy) -
-                             cterm<false>(a1[1][ry][rx] - a0[1][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[0][2], nullptr, zz));
-      hym = C.f[4][q] - S * (cterm<false>(a1[0][ry][rx] - a0[0][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[1][2], nullptr, zz) -
-                             cterm<false>(a0[2][ry][rx + 1] - a0[2][ry][rx], ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], nullptr, zx));
+      const float dzy = a0[2][ry + 1][rx] - a0[2][ry][rx], dyz = a1[1][ry][rx] - a0[1][ry][rx];
+      const float dxz = a1[0][ry][rx] - a0[0][ry][rx], dzx = a0[2][ry][rx + 1] - a0[2][ry][rx];
+      float cx = dzy - dyz, cy = dxz - dzx;
+      if ((sX & sY & sZ) >= 0) {
+        const int zx = sX >= 0 ? zx_of(g, j, km, sX) : 0, zy = sY >= 0 ? zy_of(g, i, km, sY) : 0;
+        const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+        cx += corr<false>(dzy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], nullptr, zy) -
+              corr<false>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[0][2], nullptr, zz);
+        cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[1][2], nullptr, zz) -
+              corr<false>(dzx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], nullptr, zx);
+      }
+      hxm = C.f[3][q] - S * cx;
+      hym = C.f[4][q] - S * cy;
     }
     cur = 1;
     __syncthreads();
   } else {
-    load_plane(g, C, st, k0, pe);
-    store_plane(sE[0], pe, tx, ty);
+    load_stage(g, C, st, k0, pe);
+    store_stage(sE[0], st, pe, tx, ty);
   }
   // prefetch: E^n of plane k0+1, and H^{n-1/2}, a of plane k0 (own and halo point)
-  load_plane(g, C, st, k0 + 1, pe);
+  load_stage(g, C, st, k0 + 1, pe);
   float nhx = 0.f, nhy = 0.f, nhz = 0.f, na = 0.f, nh1 = 0.f, nh2 = 0.f;
   if (own) {
     const int q = k0 * plane + q0;
@@ -233,10 +243,10 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
 
   for (int k = k0; k < k1; ++k) {
     const int q = k * plane + q0;
-    store_plane(sE[cur ^ 1], pe, tx, ty);
+    store_stage(sE[cur ^ 1], st, pe, tx, ty);
     const float hox = nhx, hoy = nhy, hoz = nhz, av = na, ho1 = nh1, ho2 = nh2;
     if (k + 1 < k1) {  // prefetch for the next plane
-      load_plane(g, C, st, k + 2, pe);
+      load_stage(g, C, st, k + 2, pe);
       if (own) {
         nhx = C.f[3][q + plane];
         nhy = C.f[4][q + plane];
@@ -257,26 +267,29 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     __syncthreads();
     const float(*ek)[SY][SX] = sE[cur];
     const float(*ek1)[SY][SX] = sE[cur ^ 1];
-
-    // (b) H^{n+1/2} on plane k: own cell and the low halo
+    const bool lay = (sX & sY & sZ) >= 0;  // some axis of this cell is in a layer (-1 = all bits set)
     const int zx = sX >= 0 ? zx_of(g, j, k, sX) : 0;
     const int zy = sY >= 0 ? zy_of(g, i, k, sY) : 0;
     const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+
+    // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
     float hx = 0.f, hy = 0.f, hz = 0.f;
-    const bool lay = (sX & sY & sZ) >= 0;  // some axis is in a layer (slab indices are -1 off them, all bits set)
-    if (own && !lay) {  // off the layers 1/kappa = 1 exactly: the plain Yee update
-      hx = hox - S * ((ek[2][ry + 1][rx] - ek[2][ry][rx]) - (ek1[1][ry][rx] - ek[1][ry][rx]));
-      hy = hoy - S * ((ek1[0][ry][rx] - ek[0][ry][rx]) - (ek[2][ry][rx + 1] - ek[2][ry][rx]));
-      hz = hoz - S * ((ek[1][ry][rx + 1] - ek[1][ry][rx]) - (ek[0][ry + 1][rx] - ek[0][ry][rx]));
-    } else if (own) {
-      hx = hox - S * (cterm<true>(ek[2][ry + 1][rx] - ek[2][ry][rx], ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], PHo.p[0][1], zy) -
-                      cterm<true>(ek1[1][ry][rx] - ek[1][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], PHo.p[0][2], zz));
-      hy = hoy - S * (cterm<true>(ek1[0][ry][rx] - ek[0][ry][rx], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], PHo.p[1][2], zz) -
-                      cterm<true>(ek[2][ry][rx + 1] - ek[2][ry][rx], ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], PHo.p[1][0], zx));
-      hz = hoz - S * (cterm<true>(ek[1][ry][rx + 1] - ek[1][ry][rx], ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[2][0], PHo.p[2][0], zx) -
-                      cterm<true>(ek[0][ry + 1][rx] - ek[0][ry][rx], ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[2][1], PHo.p[2][1], zy));
-    }
     if (own) {
+      const float dzy = ek[2][ry + 1][rx] - ek[2][ry][rx], dyz = ek1[1][ry][rx] - ek[1][ry][rx];
+      const float dxz = ek1[0][ry][rx] - ek[0][ry][rx], dzx = ek[2][ry][rx + 1] - ek[2][ry][rx];
+      const float dyx = ek[1][ry][rx + 1] - ek[1][ry][rx], dxy = ek[0][ry + 1][rx] - ek[0][ry][rx];
+      float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
+      if (lay) {
+        cx += corr<true>(dzy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], PHo.p[0][1], zy) -
+              corr<true>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], PHo.p[0][2], zz);
+        cy += corr<true>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], PHo.p[1][2], zz) -
+              corr<true>(dzx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], PHo.p[1][0], zx);
+        cz += corr<true>(dyx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[2][0], PHo.p[2][0], zx) -
+              corr<true>(dxy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[2][1], PHo.p[2][1], zy);
+      }
+      hx = hox - S * cx;
+      hy = hoy - S * cy;
+      hz = hoz - S * cz;
       sH[0][ry][rx] = hx;
       sH[1][ry][rx] = hy;
       sH[2][ry][rx] = hz;
@@ -284,26 +297,36 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       N.f[4][q] = hy;
       N.f[5][q] = hz;
     }
-    if (hrow) {  // (i, j0 - 1): staged at row 0, column tid + 1
-      const int c = tid + 1;
-      const int hzy = sYh >= 0 ? zy_of(g, xh, k, sYh) : 0, hzz = sZ >= 0 ? zz_of(g, xh, yh, sZ) : 0;
-      const int hzx = sXh >= 0 ? zx_of(g, yh, k, sXh) : 0;
-      sH[0][0][c] = ho1 - S * (cterm<false>(ek[2][1][c] - ek[2][0][c], ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[0][1], nullptr, hzy) -
-                               cterm<false>(ek1[1][0][c] - ek[1][0][c], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], nullptr, hzz));
-      sH[2][0][c] = ho2 - S * (cterm<false>(ek[1][0][c + 1] - ek[1][0][c], ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
-                               cterm<false>(ek[0][1][c] - ek[0][0][c], ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy));
-    }
-    if (hcol) {  // (i0 - 1, j0 + hr): staged at row hr + 1, column 0
-      const int r = hr + 1;
-      const int hzy = sYh >= 0 ? zy_of(g, xh, k, sYh) : 0, hzz = sZ >= 0 ? zz_of(g, xh, yh, sZ) : 0;
-      const int hzx = sXh >= 0 ? zx_of(g, yh, k, sXh) : 0;
-      sH[1][r][0] = ho1 - S * (cterm<false>(ek1[0][r][0] - ek[0][r][0], ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], nullptr, hzz) -
-                               cterm<false>(ek[2][r][1] - ek[2][r][0], ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[1][0], nullptr, hzx));
-      sH[2][r][0] = ho2 - S * (cterm<false>(ek[1][r][1] - ek[1][r][0], ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
-                               cterm<false>(ek[0][r + 1][0] - ek[0][r][0], ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy));
+    // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
+    if (hrow || hcol) {
+      const int r = hry, c = hrx;
+      const bool hl = (sXh & sYh & sZ) >= 0;
+      const int hzx = sXh >= 0 ? zx_of(g, yh, k, sXh) : 0, hzy = sYh >= 0 ? zy_of(g, xh, k, sYh) : 0;
+      const int hzz = sZ >= 0 ? zz_of(g, xh, yh, sZ) : 0;
+      const float dyx = ek[1][r][c + 1] - ek[1][r][c], dxy = ek[0][r + 1][c] - ek[0][r][c];
+      float cz = dyx - dxy;
+      if (hl)
+        cz += corr<false>(dyx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
+              corr<false>(dxy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy);
+      sH[2][r][c] = ho2 - S * cz;
+      if (hrow) {  // Hx
+        const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
+        float cx = dzy - dyz;
+        if (hl)
+          cx += corr<false>(dzy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[0][1], nullptr, hzy) -
+                corr<false>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], nullptr, hzz);
+        sH[0][r][c] = ho1 - S * cx;
+      } else {  // Hy
+        const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
+        float cy = dxz - dzx;
+        if (hl)
+          cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], nullptr, hzz) -
+                corr<false>(dzx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[1][0], nullptr, hzx);
+        sH[1][r][c] = ho1 - S * cy;
+      }
     }
     if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
-    if (fseg >= 0) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
+    if (fseg > 0xff) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
     if (k == fz0 || k == fz1) {
       const int sh = (k == fz0) ? 0 : 16;
       face_write(A, (fzseg >> sh) & 0xff, i, j, k, hx, hy, hz);
@@ -316,21 +339,24 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     if (own) {
       const float Sa = S * av;
       float ex = ek[0][ry][rx], ey = ek[1][ry][rx], ez = ek[2][ry][rx];
-      if (!lay && i > 0 && j > 0 && k > 0) {
-        ex += Sa * ((hz - sH[2][ry - 1][rx]) - (hy - hym));
-        ey += Sa * ((hx - hxm) - (hz - sH[2][ry][rx - 1]));
-        ez += Sa * ((hy - sH[1][ry][rx - 1]) - (hx - sH[0][ry - 1][rx]));
-      } else {
-      if (j > 0 && k > 0)
-        ex += Sa * (cterm<true>(hz - sH[2][ry - 1][rx], ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[0][1], PEo.p[0][1], zy) -
-                    cterm<true>(hy - hym, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[0][2], PEo.p[0][2], zz));
-      if (i > 0 && k > 0)
-        ey += Sa * (cterm<true>(hx - hxm, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[1][2], PEo.p[1][2], zz) -
-                    cterm<true>(hz - sH[2][ry][rx - 1], ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[1][0], PEo.p[1][0], zx));
-      if (i > 0 && j > 0)
-        ez += Sa * (cterm<true>(hy - sH[1][ry][rx - 1], ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[2][0], PEo.p[2][0], zx) -
-                    cterm<true>(hx - sH[0][ry - 1][rx], ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[2][1], PEo.p[2][1], zy));
+      const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
+      const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
+      const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
+      float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
+      if (lay) {
+        if (j > 0 && k > 0)
+          cx += corr<true>(d1x, ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[0][1], PEo.p[0][1], zy) -
+                corr<true>(d2x, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[0][2], PEo.p[0][2], zz);
+        if (i > 0 && k > 0)
+          cy += corr<true>(d1y, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[1][2], PEo.p[1][2], zz) -
+                corr<true>(d2y, ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[1][0], PEo.p[1][0], zx);
+        if (i > 0 && j > 0)
+          cz += corr<true>(d1z, ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[2][0], PEo.p[2][0], zx) -
+                corr<true>(d2z, ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[2][1], PEo.p[2][1], zy);
       }
+      if (j > 0 && k > 0) ex += Sa * cx;
+      if (i > 0 && k > 0) ey += Sa * cy;
+      if (i > 0 && j > 0) ez += Sa * cz;
       if (src_xy & src_k) {
         for (int s = 0; s < A.nsrc; ++s) {
           const SrcDev& sd = A.src[s];
