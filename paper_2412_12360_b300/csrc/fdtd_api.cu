@@ -15,8 +15,34 @@
 
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
+
+#include <cudaTypedefs.h>
+#include <mutex>
 
 using namespace fdtd;
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
+}
+
+namespace fdtd {
+
+int encode_field_map(CUtensorMap* m, const float* base, const Geo& g, int ncomp, MapBox box) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return set_error(FDTD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], (cuuint64_t)ncomp};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.nxp * 4, (cuuint64_t)g.plane * 4, (cuuint64_t)g.vol * 4};
+  const cuuint32_t boxd[4] = {(cuuint32_t)box.w, (cuuint32_t)box.h, 1, (cuuint32_t)ncomp};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(base), dims, strides, boxd, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(FDTD_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return FDTD_OK;
+}
+
+}  // namespace fdtd
 
 namespace {
 
@@ -46,6 +72,20 @@ int fail(int code, const char* fmt, ...) {
   } while (0)
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
 
 // CPML grading at one position (d = depth of the component's own position into the layer).
 void cpml_coef(double x, int N, int p0, int p1, const fdtd_pml& pm, double& b, double& c, double& ik) {
@@ -236,6 +276,8 @@ struct fdtd_handle {
   double* dLddet = nullptr;    // device copy of dL/d(detectors)
   int64_t dLddet_cap = 0;
   float* staging = nullptr;    // 6 x N, unpitched
+  int* status = nullptr;       // device status word written by the kernels (bounded waits)
+  FwdMaps fmaps[2];            // TMA maps of the forward kernel reading field buffer 0 or 1
   int64_t bytes = 0;
   uint64_t gen = 1;            // bumped whenever a buffer used by a captured loop is reallocated
 
@@ -498,6 +540,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.det_out = h->det_out;
   fa.partial = h->partial;
   fa.faces = h->faces;
+  fa.status = h->status;
   for (int n = 0; n < nsteps; ++n) {
     const int c = h->cur, x = 1 - c;
     fa.cur = h->F(c);
@@ -510,7 +553,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     fa.rec = faces ? h->face_hist + (int64_t)n * h->faces.per_step : nullptr;
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
-      launch_fwd_fused(fa, st);
+      launch_fwd_fused(fa, h->fmaps[c], st);
     }
     launches += 1;
     const Fields Fn = h->F(x);
@@ -723,12 +766,17 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   }
   {
     // z-chunk of the fused kernels: enough blocks to fill every SM several times over
+    int per_sm = 0, nsm = 0;
+    if ((rc = prepare_fwd_fused(&per_sm)) != FDTD_OK) return cleanup(rc);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
     // At least 8 planes per block (a shorter march pays its start-up plane too often; on the 96^3
     // workload 8 beat 4, 6, 12, 16 and 24), and as few chunks as fill whole waves of resident blocks
-    // (3 per SM on 148 SMs) to within 90 %.
-    const int64_t slots = 148 * 3;
+    // (per SM as many as the kernel's registers and shared memory allow) to within 90 %.
+    const int64_t slots = (int64_t)nsm * std::max(1, per_sm);
     const int max_chunks = std::max(1, n[2] / 8);
     int chunks = max_chunks;
     for (int c = 1; c <= max_chunks; ++c) {
@@ -746,6 +794,15 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   }
   if ((rc = dev_alloc(h, (void**)&h->fields, 2 * 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = dev_alloc(h, (void**)&h->a, g.vol * 4)) != FDTD_OK) return cleanup(rc);
+  if ((rc = dev_alloc(h, (void**)&h->status, 4)) != FDTD_OK) return cleanup(rc);
+  if (cudaMemsetAsync(h->status, 0, 4, h->stream) != cudaSuccess)
+    return cleanup(fail(FDTD_ERR_CUDA, "status reset: %s", cudaGetErrorString(cudaGetLastError())));
+  for (int b = 0; b < 2; ++b) {
+    const Fields Fb = h->F(b);
+    if ((rc = encode_field_map(&h->fmaps[b].e, Fb.f[0], g, 3, fwd_box_e())) != FDTD_OK) return cleanup(rc);
+    if ((rc = encode_field_map(&h->fmaps[b].h, Fb.f[3], g, 3, fwd_box_h())) != FDTD_OK) return cleanup(rc);
+    if ((rc = encode_field_map(&h->fmaps[b].a, h->a, g, 1, fwd_box_a())) != FDTD_OK) return cleanup(rc);
+  }
   const int64_t pf = h->psi_floats();
   if ((rc = dev_alloc(h, (void**)&h->psiE, 2 * pf * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = dev_alloc(h, (void**)&h->psiH, 2 * pf * 4)) != FDTD_OK) return cleanup(rc);
@@ -830,7 +887,7 @@ int fdtd_destroy(fdtd_handle* h) {
   h->gfwd.reset();
   h->gbwd.reset();
   void* bufs[] = {h->fields, h->a, h->psiE, h->psiH, h->tables, h->init, h->gtab, h->det_out, h->partial,
-                  h->face_hist, h->adj, h->psibar, h->dLda, h->dLddet, h->staging};
+                  h->face_hist, h->adj, h->psibar, h->dLda, h->dLddet, h->staging, h->status};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, h->stream);
   for (float* p : h->src_w) cudaFreeAsync(p, h->stream);
@@ -1024,6 +1081,12 @@ int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds
 int fdtd_synchronize(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   CK(cudaStreamSynchronize(h->stream));
+  int st = 0;
+  CK(cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CK(cudaMemset(h->status, 0, 4));
+    return fail(FDTD_ERR_TIMEOUT, "a device-side wait for a TMA copy gave up (status %d); results are invalid", st);
+  }
   return FDTD_OK;
 }
 

@@ -15,14 +15,15 @@
 // what depends on z once per plane. Every cell takes the plain Yee update; cells in a CPML layer add
 // the correction (1/kappa - 1) d + psi per curl term, which is exactly 0 off the layers and on their
 // inner edge, so the PML-free region R is updated by the plain formula the inverse step mirrors.
+#include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
 
 namespace fdtd {
 
 namespace {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int SX = TX + 2, SY = TY + 2;  // staged E tile with a one-cell halo
 constexpr int HX = TX + 1, HY = TY + 1;  // new H with the low halo
 
 // CPML correction of one curl term inside a layer: the update uses d / kappa + psi_new where the plain
@@ -60,38 +61,52 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
 }
 
-// Staging of one E plane (tile plus a one-cell halo) into shared memory: every thread loads its own
-// cell (row ty+1, column tx+1: aligned, coalesced rows); warp 0 loads the halo row y = j0-1, warp 1 the
-// row y = j0+TY, and warp 2 the halo columns x = i0-1 (lanes 0..TY+1) and x = i0+TX (lanes 16..17+TY),
-// corners included.
-struct Stage {
-  int own_off, role_off;  // in-plane offsets of the own cell and of this thread's halo point
-  bool own_ok, role_ok;   // inside the grid
-  int role_ry, role_rx;   // where the halo point goes in the staged tile (role_ry < 0: no halo point)
+// Shared-memory ring of z-planes filled by the TMA unit. One stage holds, for one plane k of the
+// tile, E^n with a halo (x in [i0-4, i0+TX+4), y in [j0-1, j0+TY+1)), H^{n-1/2} with the low halo
+// (x in [i0-4, i0+TX), y in [j0-1, j0+TY)) and a (the tile). Both boxes start 4 cells left of the
+// tile so that the x coordinate of every copy is 16-byte aligned; the extra columns are not used.
+constexpr int EW = TX + 8, EH = TY + 2;
+constexpr int HW = TX + 4, HH = TY + 1;
+constexpr int XO = 4;  // x offset of the tile inside the E and H boxes
+constexpr int NSTAGE = 4;
+constexpr uint32_t E_BYTES = 3 * EW * EH * 4, H_BYTES = 3 * HW * HH * 4, A_BYTES = TX * TY * 4;
+constexpr uint32_t STAGE_TX = E_BYTES + H_BYTES + A_BYTES;  // transaction bytes of one stage
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+constexpr int E_OFF = 0, H_OFF = round128(E_BYTES), A_OFF = H_OFF + round128(H_BYTES);
+constexpr int STAGE_BYTES = round128(A_OFF + A_BYTES);
+constexpr int SH_OFF = NSTAGE * STAGE_BYTES;                      // new H: [2][3][HY][HX] floats
+constexpr int BAR_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);  // NSTAGE mbarriers
+constexpr int SMEM_BYTES = BAR_OFF + NSTAGE * 8 + 128;             // + slack to align the base
+static_assert(NT * 8 <= STAGE_BYTES, "the flux reduction reuses the first stage");
+
+struct Ring {
+  unsigned char* base;
+  uint64_t* bar;
+  __device__ const float (*E(int b) const)[EH][EW] {
+    return reinterpret_cast<const float(*)[EH][EW]>(base + b * STAGE_BYTES + E_OFF);
+  }
+  __device__ const float (*H(int b) const)[HH][HW] {
+    return reinterpret_cast<const float(*)[HH][HW]>(base + b * STAGE_BYTES + H_OFF);
+  }
+  __device__ const float (*Av(int b) const)[TX] {
+    return reinterpret_cast<const float(*)[TX]>(base + b * STAGE_BYTES + A_OFF);
+  }
+  // one thread: fill stage b with plane k
+  __device__ void issue(const FwdMaps& M, int b, int i0, int j0, int k) const {
+    unsigned char* st = base + b * STAGE_BYTES;
+    mbar_arrive_expect(&bar[b], STAGE_TX);
+    tma_load_box(st + E_OFF, &M.e, i0 - XO, j0 - 1, k, 0, &bar[b]);
+    tma_load_box(st + H_OFF, &M.h, i0 - XO, j0 - 1, k, 0, &bar[b]);
+    tma_load_box(st + A_OFF, &M.a, i0, j0, k, 0, &bar[b]);
+  }
 };
 
-__device__ __forceinline__ void load_stage(const Geo& g, const Fields& F, const Stage& st, int k, float r[2][3]) {
-  const bool kin = k < g.n[2];
-  const int base = k * (int)g.plane;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    r[0][c] = (kin && st.own_ok) ? F.f[c][base + st.own_off] : 0.f;
-    r[1][c] = (kin && st.role_ok) ? F.f[c][base + st.role_off] : 0.f;
-  }
-}
-
-__device__ __forceinline__ void store_stage(float (*dst)[SY][SX], const Stage& st, const float r[2][3], int tx, int ty) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    dst[c][ty + 1][tx + 1] = r[0][c];
-    if (st.role_ry >= 0) dst[c][st.role_ry][st.role_rx] = r[1][c];
-  }
-}
-
-__global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
-  __shared__ float sE[2][3][SY][SX];
-  __shared__ float sH[3][HY][HX];
-  __shared__ double sred[NT];
+__global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
+  Ring R{sm, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
+  float(*sHb)[3][HY][HX] = reinterpret_cast<float(*)[3][HY][HX]>(sm + SH_OFF);
+  double* sred = reinterpret_cast<double*>(sm);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -100,43 +115,31 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
+  const int kb = k0 > 0 ? k0 - 1 : k0;  // first plane staged (k0-1 supplies H^{n+1/2} below the chunk)
   const int nx = g.n[0], ny = g.n[1];
   const int plane = (int)g.plane;
   const int i = i0 + tx, j = j0 + ty;
   const bool own = i < nx && j < ny;
   const int q0 = j * g.nxp + i;
   const float S = g.S;
-  const int rx = tx + 1, ry = ty + 1;
+  const int ex = tx + XO, ey = ty + 1;  // own cell in the staged boxes
+  const int rx = tx + 1, ry = ty + 1;   // own cell in the new-H tile
+  bool waited = true;
 
-  Stage st;
-  st.own_ok = own;
-  st.own_off = q0;
-  st.role_ry = -1;
-  st.role_rx = 0;
-  st.role_ok = false;
-  st.role_off = 0;
-  {
-    int x = 0, y = 0;
-    if (ty == 0) {  // halo row y = j0 - 1
-      x = i0 + tx; y = j0 - 1; st.role_ry = 0; st.role_rx = tx + 1;
-    } else if (ty == 1) {  // halo row y = j0 + TY
-      x = i0 + tx; y = j0 + TY; st.role_ry = TY + 1; st.role_rx = tx + 1;
-    } else if (ty == 2 && tx < SY) {  // halo column x = i0 - 1, rows j0-1 .. j0+TY
-      x = i0 - 1; y = j0 - 1 + tx; st.role_ry = tx; st.role_rx = 0;
-    } else if (ty == 2 && tx >= 16 && tx < 16 + SY) {  // halo column x = i0 + TX
-      x = i0 + TX; y = j0 - 1 + (tx - 16); st.role_ry = tx - 16; st.role_rx = TX + 1;
-    }
-    st.role_ok = st.role_ry >= 0 && x >= 0 && x < nx && y >= 0 && y < ny;
-    st.role_off = y * g.nxp + x;
+  if (tid == 0) {
+    for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
+    mbar_init_fence();
+    for (int p = kb; p <= min(kb + NSTAGE - 1, k1); ++p) R.issue(M, p - kb, i0, j0, p);
   }
+  __syncthreads();
 
   // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
   const bool hrow = ty == 3 && j0 > 0 && i < nx;
   const bool hcol = ty == 4 && tx < TY && i0 > 0 && (j0 + tx) < ny;
   const int xh = hcol ? i0 - 1 : min(i, nx - 1);
   const int yh = hcol ? j0 + tx : max(j0 - 1, 0);
-  const int hrx = hcol ? 0 : tx + 1, hry = hcol ? tx + 1 : 0;  // staged position of the halo point
-  const int qh0 = yh * g.nxp + xh;
+  const int hrx = hcol ? 0 : tx + 1, hry = hcol ? tx + 1 : 0;  // the halo point in the new-H tile
+  const int hex = hrx + XO - 1, hey = hry;                      // and in the staged boxes
 
   // CPML data along x and y, fixed for the whole march (H tables at half, E tables at integer positions)
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
@@ -185,28 +188,21 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
   const PsiSet& PHo = A.psiH_nxt;
   const PsiSet& PEi = A.psiE_cur;
   const PsiSet& PEo = A.psiE_nxt;
-  const Fields& C = A.cur;
   const Fields& N = A.nxt;
 
-  float pe[2][3];
+  waited &= mbar_wait(&R.bar[0], 0);
   float hxm = 0.f, hym = 0.f;
-  int cur = 0;
   if (k0 > 0) {
     // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
-    const int km = k0 - 1;
-    load_stage(g, C, st, km, pe);
-    store_stage(sE[0], st, pe, tx, ty);
-    load_stage(g, C, st, k0, pe);
-    store_stage(sE[1], st, pe, tx, ty);
-    __syncthreads();
+    waited &= mbar_wait(&R.bar[1], 0);
     if (own) {
-      const int q = km * plane + q0;
-      const float(*a0)[SY][SX] = sE[0];
-      const float(*a1)[SY][SX] = sE[1];
+      const int km = kb;
+      const float(*a0)[EH][EW] = R.E(0);
+      const float(*a1)[EH][EW] = R.E(1);
       const float ikZh = T.ik[2][1][km];
       const int sZ = T.sidx[2][km];
-      const float dzy = a0[2][ry + 1][rx] - a0[2][ry][rx], dyz = a1[1][ry][rx] - a0[1][ry][rx];
-      const float dxz = a1[0][ry][rx] - a0[0][ry][rx], dzx = a0[2][ry][rx + 1] - a0[2][ry][rx];
+      const float dzy = a0[2][ey + 1][ex] - a0[2][ey][ex], dyz = a1[1][ey][ex] - a0[1][ey][ex];
+      const float dxz = a1[0][ey][ex] - a0[0][ey][ex], dzx = a0[2][ey][ex + 1] - a0[2][ey][ex];
       float cx = dzy - dyz, cy = dxz - dzx;
       if ((sX & sY & sZ) >= 0) {
         const int zx = sX >= 0 ? zx_of(g, j, km, sX) : 0, zy = sY >= 0 ? zy_of(g, i, km, sY) : 0;
@@ -216,57 +212,25 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
         cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[1][2], nullptr, zz) -
               corr<false>(dzx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], nullptr, zx);
       }
-      hxm = C.f[3][q] - S * cx;
-      hym = C.f[4][q] - S * cy;
+      hxm = R.H(0)[0][ey][ex] - S * cx;
+      hym = R.H(0)[1][ey][ex] - S * cy;
     }
-    cur = 1;
-    __syncthreads();
-  } else {
-    load_stage(g, C, st, k0, pe);
-    store_stage(sE[0], st, pe, tx, ty);
-  }
-  // prefetch: E^n of plane k0+1, and H^{n-1/2}, a of plane k0 (own and halo point)
-  load_stage(g, C, st, k0 + 1, pe);
-  float nhx = 0.f, nhy = 0.f, nhz = 0.f, na = 0.f, nh1 = 0.f, nh2 = 0.f;
-  if (own) {
-    const int q = k0 * plane + q0;
-    nhx = C.f[3][q];
-    nhy = C.f[4][q];
-    nhz = C.f[5][q];
-    na = A.a[q];
-  }
-  if (hrow || hcol) {
-    const int q = k0 * plane + qh0;
-    nh1 = hrow ? C.f[3][q] : C.f[4][q];
-    nh2 = C.f[5][q];
   }
 
   for (int k = k0; k < k1; ++k) {
+    const int it = k - kb;  // stage use count of plane k
+    const int b0 = it % NSTAGE, b1 = (it + 1) % NSTAGE;
     const int q = k * plane + q0;
-    store_stage(sE[cur ^ 1], st, pe, tx, ty);
-    const float hox = nhx, hoy = nhy, hoz = nhz, av = na, ho1 = nh1, ho2 = nh2;
-    if (k + 1 < k1) {  // prefetch for the next plane
-      load_stage(g, C, st, k + 2, pe);
-      if (own) {
-        nhx = C.f[3][q + plane];
-        nhy = C.f[4][q + plane];
-        nhz = C.f[5][q + plane];
-        na = A.a[q + plane];
-      }
-      if (hrow || hcol) {
-        const int qn = (k + 1) * plane + qh0;
-        nh1 = hrow ? C.f[3][qn] : C.f[4][qn];
-        nh2 = C.f[5][qn];
-      }
-    }
     const float ikZh = T.ik[2][1][k], ikZe = T.ik[2][0][k];
     const int sZ = T.sidx[2][k];
     unsigned src_k = 0, det_k = 0;  // sources and detectors whose z-range holds this plane
     for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
     for (int s = 0; s < A.ndet; ++s) det_k |= (k >= A.det[s].lo[2] && k < A.det[s].hi[2]) ? 1u << s : 0u;
-    __syncthreads();
-    const float(*ek)[SY][SX] = sE[cur];
-    const float(*ek1)[SY][SX] = sE[cur ^ 1];
+    waited &= mbar_wait(&R.bar[b1], ((it + 1) / NSTAGE) & 1);  // plane k+1 (plane k was waited for before)
+    const float(*ek)[EH][EW] = R.E(b0);
+    const float(*ek1)[EH][EW] = R.E(b1);
+    const float(*hk)[HH][HW] = R.H(b0);
+    float(*sH)[HY][HX] = sHb[it & 1];
     const bool lay = (sX & sY & sZ) >= 0;  // some axis of this cell is in a layer (-1 = all bits set)
     const int zx = sX >= 0 ? zx_of(g, j, k, sX) : 0;
     const int zy = sY >= 0 ? zy_of(g, i, k, sY) : 0;
@@ -275,9 +239,9 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
     float hx = 0.f, hy = 0.f, hz = 0.f;
     if (own) {
-      const float dzy = ek[2][ry + 1][rx] - ek[2][ry][rx], dyz = ek1[1][ry][rx] - ek[1][ry][rx];
-      const float dxz = ek1[0][ry][rx] - ek[0][ry][rx], dzx = ek[2][ry][rx + 1] - ek[2][ry][rx];
-      const float dyx = ek[1][ry][rx + 1] - ek[1][ry][rx], dxy = ek[0][ry + 1][rx] - ek[0][ry][rx];
+      const float dzy = ek[2][ey + 1][ex] - ek[2][ey][ex], dyz = ek1[1][ey][ex] - ek[1][ey][ex];
+      const float dxz = ek1[0][ey][ex] - ek[0][ey][ex], dzx = ek[2][ey][ex + 1] - ek[2][ey][ex];
+      const float dyx = ek[1][ey][ex + 1] - ek[1][ey][ex], dxy = ek[0][ey + 1][ex] - ek[0][ey][ex];
       float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
       if (lay) {
         cx += corr<true>(dzy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], PHo.p[0][1], zy) -
@@ -287,9 +251,9 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
         cz += corr<true>(dyx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[2][0], PHo.p[2][0], zx) -
               corr<true>(dxy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[2][1], PHo.p[2][1], zy);
       }
-      hx = hox - S * cx;
-      hy = hoy - S * cy;
-      hz = hoz - S * cz;
+      hx = hk[0][ey][ex] - S * cx;
+      hy = hk[1][ey][ex] - S * cy;
+      hz = hk[2][ey][ex] - S * cz;
       sH[0][ry][rx] = hx;
       sH[1][ry][rx] = hy;
       sH[2][ry][rx] = hz;
@@ -299,7 +263,7 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
     }
     // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
     if (hrow || hcol) {
-      const int r = hry, c = hrx;
+      const int r = hey, c = hex;
       const bool hl = (sXh & sYh & sZ) >= 0;
       const int hzx = sXh >= 0 ? zx_of(g, yh, k, sXh) : 0, hzy = sYh >= 0 ? zy_of(g, xh, k, sYh) : 0;
       const int hzz = sZ >= 0 ? zz_of(g, xh, yh, sZ) : 0;
@@ -308,21 +272,21 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       if (hl)
         cz += corr<false>(dyx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
               corr<false>(dxy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy);
-      sH[2][r][c] = ho2 - S * cz;
+      sH[2][hry][hrx] = hk[2][r][c] - S * cz;
       if (hrow) {  // Hx
         const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
         float cx = dzy - dyz;
         if (hl)
           cx += corr<false>(dzy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[0][1], nullptr, hzy) -
                 corr<false>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], nullptr, hzz);
-        sH[0][r][c] = ho1 - S * cx;
+        sH[0][hry][hrx] = hk[0][r][c] - S * cx;
       } else {  // Hy
         const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
         float cy = dxz - dzx;
         if (hl)
           cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], nullptr, hzz) -
                 corr<false>(dzx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[1][0], nullptr, hzx);
-        sH[1][r][c] = ho1 - S * cy;
+        sH[1][hry][hrx] = hk[1][r][c] - S * cy;
       }
     }
     if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
@@ -333,12 +297,17 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
       face_write(A, (fzseg >> (sh + 8)) & 0xff, i, j, k, hx, hy, hz);
     }
     __syncthreads();
+    // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
+    if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {
+      async_proxy_fence();
+      R.issue(M, (it - 1) % NSTAGE, i0, j0, k - 1 + NSTAGE);
+    }
 
     // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
     // sources and detectors
     if (own) {
-      const float Sa = S * av;
-      float ex = ek[0][ry][rx], ey = ek[1][ry][rx], ez = ek[2][ry][rx];
+      const float Sa = S * R.Av(b0)[ty][tx];
+      float exv = ek[0][ey][ex], eyv = ek[1][ey][ex], ezv = ek[2][ey][ex];
       const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
       const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
       const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
@@ -354,22 +323,22 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
           cz += corr<true>(d1z, ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[2][0], PEo.p[2][0], zx) -
                 corr<true>(d2z, ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[2][1], PEo.p[2][1], zy);
       }
-      if (j > 0 && k > 0) ex += Sa * cx;
-      if (i > 0 && k > 0) ey += Sa * cy;
-      if (i > 0 && j > 0) ez += Sa * cz;
+      if (j > 0 && k > 0) exv += Sa * cx;
+      if (i > 0 && k > 0) eyv += Sa * cy;
+      if (i > 0 && j > 0) ezv += Sa * cz;
       if (src_xy & src_k) {
         for (int s = 0; s < A.nsrc; ++s) {
           const SrcDev& sd = A.src[s];
           if (!(((src_xy & src_k) >> s) & 1u)) continue;
           const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
-          if (sd.comp == 0) ex += v;
-          else if (sd.comp == 1) ey += v;
-          else ez += v;
+          if (sd.comp == 0) exv += v;
+          else if (sd.comp == 1) eyv += v;
+          else ezv += v;
         }
       }
-      N.f[0][q] = ex;
-      N.f[1][q] = ey;
-      N.f[2][q] = ez;
+      N.f[0][q] = exv;
+      N.f[1][q] = eyv;
+      N.f[2][q] = ezv;
       if (det_xy & det_k) {
 #pragma unroll
         for (int s = 0; s < kMaxDet; ++s) {
@@ -377,21 +346,22 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
           const DetDev& d = A.det[s];
           if (!(((det_xy & det_k) >> s) & 1u)) continue;
           if (d.kind == 0) {
-            A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, ex, ey, ez) : pick3(d.comp - 3, hx, hy, hz));
+            A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
           } else if (d.kind == 1) {
-            A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)ex * ex + (double)ey * ey + (double)ez * ez;
+            A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
           } else {
             const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
-            facc[s] += (double)pick3(a1, ex, ey, ez) * (double)pick3(a2, hx, hy, hz) -
-                       (double)pick3(a2, ex, ey, ez) * (double)pick3(a1, hx, hy, hz);
+            facc[s] += (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
+                       (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz);
           }
         }
       }
     }
     hxm = hx;
     hym = hy;
-    cur ^= 1;
   }
+  if (!waited) atomicOr(A.status, 1);
+  __syncthreads();  // the stages are free for the flux reduction
 
   // flux detectors: fixed-order block reduction into this block's slot
 #pragma unroll
@@ -423,10 +393,20 @@ __global__ void __launch_bounds__(NT, 3) k_fwd_fused(FwdArgs A) {
 int fused_tile_x() { return TX; }
 int fused_tile_y() { return TY; }
 
-void launch_fwd_fused(const FwdArgs& a, cudaStream_t s) {
+MapBox fwd_box_e() { return {EW, EH}; }
+MapBox fwd_box_h() { return {HW, HH}; }
+MapBox fwd_box_a() { return {TX, TY}; }
+
+int prepare_fwd_fused(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fwd_fused, NT, SMEM_BYTES);
+  return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+}
+
+void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_fwd_fused<<<grid, NT, 0, s>>>(a);
+  k_fwd_fused<<<grid, NT, SMEM_BYTES, s>>>(a, m);
 }
 
 }  // namespace fdtd

@@ -95,6 +95,7 @@ struct FwdArgs {
   double* partial;
   float* rec;              // this step's face record, or nullptr
   FaceSet faces;
+  int* status;             // device status word: bit 0 set when a bounded wait gave up
 };
 
 __host__ __device__ inline int64_t cell_index(const Geo& g, int i, int j, int k) {
@@ -158,7 +159,6 @@ struct RevArgs {
   SrcDev src[kMaxSrc];
 };
 
-void launch_fwd_fused(const FwdArgs& a, cudaStream_t s);
 void launch_rev_E_lean(const RevArgs& a, cudaStream_t s);
 void launch_rev_H_lean(const RevArgs& a, cudaStream_t s);
 int fused_tile_x();

@@ -1,0 +1,92 @@
+// Tensor-memory-accelerator (TMA) plumbing for the z-marching kernels: tensor maps over the field
+// arrays, and the inline-PTX wrappers for mbarriers and tiled bulk tensor loads (sm_90 and later;
+// built here for sm_103a).
+//
+// A field map describes `ncomp` consecutive arrays of a field buffer (components c = 0..ncomp-1, each
+// [nz][ny][nxp] float32 with pitch nxp and component stride vol) as a 4-d tensor (x, y, z, c) with the
+// logical extent (nx, ny, nz, ncomp): everything outside it, including the pitch padding x >= nx and
+// negative coordinates, reads as 0, which is the value the PEC walls give the tangential fields.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+#include "fdtd_internal.cuh"
+
+namespace fdtd {
+
+// Boxes the maps are encoded with; the kernels that use them rely on exactly these shapes.
+struct MapBox {
+  int w, h;  // x and y extent of one box (z extent 1, all components)
+};
+
+// Encode a field map (see above). Returns FDTD_OK or an FDTD_ERR_* code (with fdtd_last_error set).
+int encode_field_map(CUtensorMap* m, const float* base, const Geo& g, int ncomp, MapBox box);
+
+// The maps one forward step reads: E (3 components) and H (3) of the `cur` buffer, and a.
+struct FwdMaps {
+  CUtensorMap e, h, a;
+};
+
+// Box shapes of the forward kernel's maps, and its one-time set-up (dynamic shared memory limit).
+MapBox fwd_box_e();
+MapBox fwd_box_h();
+MapBox fwd_box_a();
+int prepare_fwd_fused(int* blocks_per_sm);
+void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s);
+
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Makes the barrier initialisation visible to the async proxy (the TMA unit) before first use.
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Orders this thread's earlier generic-proxy accesses to shared memory before later async-proxy ones.
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// One arrival that also announces `bytes` of transactions the next phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity to complete; false if it gave up (the caller
+// records a timeout status and carries on, so the block's barriers stay matched).
+constexpr int kWaitLimit = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it)
+    if (mbar_test(bar, parity)) return true;
+  return false;
+}
+
+// Tiled 4-d bulk tensor load of one box at (x, y, z, c) into shared memory, completing on `bar`.
+// x * 4 bytes must be a multiple of 16 (x a multiple of 4); the destination 128-byte aligned.
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int x, int y, int z, int c,
+                                             uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(c), "r"(smem_addr(bar))
+      : "memory");
+}
+
+#endif  // __CUDACC__
+
+}  // namespace fdtd
