@@ -278,6 +278,7 @@ struct fdtd_handle {
   float* staging = nullptr;    // 6 x N, unpitched
   int* status = nullptr;       // device status word written by the kernels (bounded waits)
   FwdMaps fmaps[2];            // TMA maps of the forward kernel reading field buffer 0 or 1
+  RevMaps rmaps[2];            // TMA maps of the reverse kernels on field buffer 0 or 1 (and adj)
   int64_t bytes = 0;
   uint64_t gen = 1;            // bumped whenever a buffer used by a captured loop is reallocated
 
@@ -519,6 +520,27 @@ bool is_host_pointer(const void* p) {
   return at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
 }
 
+// TMA maps of the reverse kernels (fdtd_reverse.cu): over each field buffer and the adjoint fields.
+int encode_rev_maps(fdtd_handle* h) {
+  const Geo& g = h->g;
+  const MapBox own = rev_box_own(), wide = rev_box_wide();
+  const Fields B = h->A();
+  for (int b = 0; b < 2; ++b) {
+    const Fields Fb = h->F(b);
+    RevMaps& m = h->rmaps[b];
+    TRY(encode_field_map(&m.e_own, Fb.f[0], g, 3, own));
+    TRY(encode_field_map(&m.e_high, Fb.f[0], g, 3, wide));
+    TRY(encode_field_map(&m.h_own, Fb.f[3], g, 3, own));
+    TRY(encode_field_map(&m.h_low, Fb.f[3], g, 3, wide));
+    TRY(encode_field_map(&m.eb_own, B.f[0], g, 3, own));
+    TRY(encode_field_map(&m.eb_high, B.f[0], g, 3, wide));
+    TRY(encode_field_map(&m.hb_own, B.f[3], g, 3, own));
+    TRY(encode_field_map(&m.hb_low, B.f[3], g, 3, wide));
+    TRY(encode_field_map(&m.a_high, h->a, g, 1, wide));
+  }
+  return FDTD_OK;
+}
+
 // ---- the time loops -------------------------------------------------------------------------------
 
 // Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
@@ -597,6 +619,8 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   ra.faces = h->faces;
   ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
+  ra.status = h->status;
+  const RevMaps& rm = h->rmaps[h->cur];
   int64_t launches = 0;
   int pb = 0;
   for (int n = nsteps - 1; n >= 0; --n) {
@@ -609,13 +633,13 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
       ra.pin = PEb[pb];
       ra.pout = PEb[1 - pb];
-      launch_rev_E_lean(ra, st);
+      launch_rev_E(ra, rm, st);
     }
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
       ra.pin = PHb[pb];
       ra.pout = PHb[1 - pb];
-      launch_rev_H_lean(ra, st);
+      launch_rev_H(ra, rm, st);
     }
     launches += 2;
     pb = 1 - pb;
@@ -768,6 +792,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     // z-chunk of the fused kernels: enough blocks to fill every SM several times over
     int per_sm = 0, nsm = 0;
     if ((rc = prepare_fwd_fused(&per_sm)) != FDTD_OK) return cleanup(rc);
+    if ((rc = prepare_rev()) != FDTD_OK) return cleanup(rc);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
@@ -975,7 +1000,10 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
-  if (!h->adj) TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
+  if (!h->adj) {
+    TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
+    TRY(encode_rev_maps(h));
+  }
   if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
   if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
   TRY(ensure_buf(h, &h->dLddet, &h->dLddet_cap, ndet, 8));

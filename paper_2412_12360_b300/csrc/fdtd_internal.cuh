@@ -122,22 +122,13 @@ __host__ __device__ inline int64_t psi_elems(const Geo& g, int d) {
 }
 
 // ---- launchers (fdtd_kernels.cu) --------------------------------------------------------------
-void launch_update_H(const Geo& g, const Fields& F, const PsiSet& psiH, const Tables& T, cudaStream_t s);
-void launch_update_E(const Geo& g, const Fields& F, const PsiSet& psiE, const Tables& T, const float* a,
-                     cudaStream_t s);
 void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, float sign, int only_R,
                    cudaStream_t s);
 void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,
                             double* partial, cudaStream_t s);
 void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s);
-void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record,
-                      cudaStream_t s);
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s);
-void launch_rev_E(const Geo& g, const Fields& F, const Fields& A, const PsiSet& psiE_old, const PsiSet& psiE_new,
-                  const Tables& T, const float* a, const int* dlo, const int* dhi, double* dLda, cudaStream_t s);
-void launch_rev_H(const Geo& g, const Fields& F, const Fields& A, const PsiSet& psiH_old, const PsiSet& psiH_new,
-                  const Tables& T, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, double scale, cudaStream_t s);
 void launch_set_density(const Geo& g, float* a, const int* lo, const int* hi, const float* rho, float eps_lo,
@@ -157,10 +148,9 @@ struct RevArgs {
   FaceSet faces;
   int nsrc;
   SrcDev src[kMaxSrc];
+  int* status;             // device status word: bit 0 set when a bounded wait gave up
 };
 
-void launch_rev_E_lean(const RevArgs& a, cudaStream_t s);
-void launch_rev_H_lean(const RevArgs& a, cudaStream_t s);
 int fused_tile_x();
 int fused_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);

@@ -21,14 +21,15 @@
 // Those of one H point mirror them with w = -S Hbar_h and the H tables, giving
 //   Ebar_e(p) += Q1_{e+1}(p - e_{e+2}) - Q1_{e+1}(p) + Q2_{e+2}(p - e_{e+1}) - Q2_{e+2}(p).
 // Off the layers 1/kappa = 1 and c = 0, so P and Q reduce to +-u and +-w.
+#include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
 
 namespace fdtd {
 
 namespace {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 1, HY = TY + 1;
 
 __device__ __forceinline__ int zx_of(const Geo& g, int y, int k, int s) { return (k * g.n[1] + y) * g.slab[0] + s; }
 __device__ __forceinline__ int zy_of(const Geo& g, int x, int k, int s) { return (k * g.slab[1] + s) * g.nxp + x; }
@@ -122,11 +123,77 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Plane staging. Both kernels march their z-chunk downwards and read every plane through a ring of
+// NSTAGE shared-memory stages filled by TMA bulk tensor copies (one elected thread issues them; the
+// block waits on one mbarrier per stage). Two box shapes are used: "own" boxes are the tile itself
+// (TX x TY at (i0, j0)); "wide" boxes add one cell on one side in x and y (BW x BH), either on the
+// high side (origin (i0, j0): the +x, +y neighbours) or on the low side (origin (i0-4, j0-1), 4 cells
+// to the left so the copy's x coordinate stays 16-byte aligned: the -x, -y neighbours). Outside the
+// grid the copies read 0, which is what the PEC walls and the zero adjoint give.
+// ---------------------------------------------------------------------------------------------
+constexpr int BW = TX + 4, BH = TY + 1;
+constexpr int NSTAGE = 4;
+constexpr int round128(int b) { return (b + 127) / 128 * 128; }
+constexpr uint32_t OWN3 = 3 * TX * TY * 4, WIDE3 = 3 * BW * BH * 4, WIDE1 = BW * BH * 4;
+
+// rev_E stage: H (wide, low side), E (own), Ebar (wide, high side), Hbar (own), a (wide, high side)
+constexpr int RE_H = 0, RE_E = RE_H + round128(WIDE3), RE_EB = RE_E + round128(OWN3),
+              RE_HB = RE_EB + round128(WIDE3), RE_A = RE_HB + round128(OWN3), RE_STAGE = RE_A + round128(WIDE1);
+constexpr uint32_t RE_TX = WIDE3 + OWN3 + WIDE3 + OWN3 + WIDE1;
+// rev_H stage: E (wide, high side), H (own), Hbar (wide, low side), Ebar (own)
+constexpr int RH_E = 0, RH_H = RH_E + round128(WIDE3), RH_HB = RH_H + round128(OWN3),
+              RH_EB = RH_HB + round128(WIDE3), RH_STAGE = RH_EB + round128(OWN3);
+constexpr uint32_t RH_TX = WIDE3 + OWN3 + WIDE3 + OWN3;
+
+constexpr int RE_SMEM = NSTAGE * RE_STAGE + NSTAGE * 8 + 128;
+constexpr int RH_SMEM = NSTAGE * RH_STAGE + NSTAGE * 8 + 128;
+
+typedef const float (*Own3)[TY][TX];
+typedef const float (*Wide3)[BH][BW];
+typedef const float (*Wide1)[BW];
+
+// Stage ring of a downward march over planes ktop, ktop-1, ..., kbot: plane p is use number
+// (ktop - p) / NSTAGE of stage (ktop - p) % NSTAGE.
+struct DownRing {
+  unsigned char* base;
+  uint64_t* bar;
+  int stage_bytes, ktop;
+  __device__ unsigned char* at(int p) const { return base + ((ktop - p) % NSTAGE) * stage_bytes; }
+  __device__ uint64_t* bar_of(int p) const { return &bar[(ktop - p) % NSTAGE]; }
+  __device__ bool wait(int p) const { return mbar_wait(bar_of(p), ((ktop - p) / NSTAGE) & 1); }
+};
+
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+  return p + ((128 - (smem_addr(p) & 127)) & 127);
+}
+
+__device__ __forceinline__ void issue_rev_E(const RevMaps& M, const DownRing& R, int i0, int j0, int p) {
+  unsigned char* st = R.at(p);
+  uint64_t* b = R.bar_of(p);
+  mbar_arrive_expect(b, RE_TX);
+  tma_load_box(st + RE_H, &M.h_low, i0 - 4, j0 - 1, p, 0, b);
+  tma_load_box(st + RE_E, &M.e_own, i0, j0, p, 0, b);
+  tma_load_box(st + RE_EB, &M.eb_high, i0, j0, p, 0, b);
+  tma_load_box(st + RE_HB, &M.hb_own, i0, j0, p, 0, b);
+  tma_load_box(st + RE_A, &M.a_high, i0, j0, p, 0, b);
+}
+
+__device__ __forceinline__ void issue_rev_H(const RevMaps& M, const DownRing& R, int i0, int j0, int p) {
+  unsigned char* st = R.at(p);
+  uint64_t* b = R.bar_of(p);
+  mbar_arrive_expect(b, RH_TX);
+  tma_load_box(st + RH_E, &M.e_high, i0, j0, p, 0, b);
+  tma_load_box(st + RH_H, &M.h_own, i0, j0, p, 0, b);
+  tma_load_box(st + RH_HB, &M.hb_low, i0 - 4, j0 - 1, p, 0, b);
+  tma_load_box(st + RH_EB, &M.eb_own, i0, j0, p, 0, b);
+}
+
+// ---------------------------------------------------------------------------------------------
 // rev_E
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
-  __shared__ float sH[3][HY][HX];  // H^{n+1/2}(k): x in [i0-1, i0+TX-1], y in [j0-1, j0+TY-1]
-  __shared__ float sU[3][HY][HX];  // u(k) = S a Ebar: x in [i0, i0+TX], y in [j0, j0+TY]
+__global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_constant__ RevMaps M) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = align128(smem_raw);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -141,19 +208,52 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
   const bool own = i < nx && j < ny;
   const int q0 = j * g.nxp + i;
   const float S = g.S;
+  const int ktop = k1 - 1, kbot = max(k0 - 1, 0);  // planes staged: H(k-1) is read below the chunk
+  const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RE_STAGE), RE_STAGE, ktop};
+  bool waited = true;
 
-  // halo roles: H row (i, j0-1) and column (i0-1, j0+r); u row (i, j0+TY) and column (i0+TX, j0+r)
+  if (tid == 0) {
+    for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
+    mbar_init_fence();
+    for (int p = ktop; p >= max(ktop - NSTAGE + 1, kbot); --p) issue_rev_E(M, R, i0, j0, p);
+  }
+  __syncthreads();
+
+  // face-record substitution of staged H: the own point, and the halo row (i, j0-1) (warp 0) and
+  // column (i0-1, j0+r) (warp 1, lanes 0..TY-1)
   const int hh = tid % TX;
-  const int role = tid / TX;  // 0: H row, 1: H column (hh < TY), 2: u row, 3: u column (hh < TY)
+  const int role = tid / TX;
   int hx_ = 0, hy_ = 0;
   bool hv = false;
   if (role == 0) { hx_ = i0 + hh; hy_ = j0 - 1; hv = j0 > 0 && hx_ < nx; }
   else if (role == 1) { hx_ = i0 - 1; hy_ = j0 + hh; hv = hh < TY && i0 > 0 && hy_ < ny; }
-  else if (role == 2) { hx_ = i0 + hh; hy_ = j0 + TY; hv = hy_ < ny && hx_ < nx; }
-  else if (role == 3) { hx_ = i0 + TX; hy_ = j0 + hh; hv = hh < TY && hx_ < nx && hy_ < ny; }
-  const int hq0 = hy_ * g.nxp + hx_;
-  int hseg = -1, hz0 = -1, hz1 = -1, hzseg = 0;  // face segments through the halo H column
-  if (hv && role < 2 && A.rec) face_segments(A.faces, hx_, hy_, hseg, hz0, hz1, hzseg);
+  const int hr = role == 0 ? 0 : hh + 1, hc = role == 0 ? hh + 4 : 3;  // the halo point in the H box
+  int hseg = -1, hz0 = -1, hz1 = -1, hzseg = 0;
+  if (hv && A.rec) face_segments(A.faces, hx_, hy_, hseg, hz0, hz1, hzseg);
+  int fseg = -1, fz0 = -1, fz1 = -1, fzseg = 0;  // face segments through the own column
+  if (own && A.rec) face_segments(A.faces, i, j, fseg, fz0, fz1, fzseg);
+  auto patch = [&](int p) {
+    float* hb = reinterpret_cast<float*>(R.at(p) + RE_H);
+    bool wrote = false;
+    if (own && (fseg >= 0 || p == fz0 || p == fz1)) {
+      float v0 = hb[(0 * BH + ty + 1) * BW + tx + 4], v1 = hb[(1 * BH + ty + 1) * BW + tx + 4],
+            v2 = hb[(2 * BH + ty + 1) * BW + tx + 4];
+      face_fix(A, fseg, fz0, fz1, fzseg, i, j, p, v0, v1, v2);
+      hb[(0 * BH + ty + 1) * BW + tx + 4] = v0;
+      hb[(1 * BH + ty + 1) * BW + tx + 4] = v1;
+      hb[(2 * BH + ty + 1) * BW + tx + 4] = v2;
+      wrote = true;
+    }
+    if (hv && (hseg >= 0 || p == hz0 || p == hz1)) {
+      float v0 = hb[(0 * BH + hr) * BW + hc], v1 = hb[(1 * BH + hr) * BW + hc], v2 = hb[(2 * BH + hr) * BW + hc];
+      face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, p, v0, v1, v2);
+      hb[(0 * BH + hr) * BW + hc] = v0;
+      hb[(1 * BH + hr) * BW + hc] = v1;
+      hb[(2 * BH + hr) * BW + hc] = v2;
+      wrote = true;
+    }
+    if (wrote) async_proxy_fence();  // these generic writes precede the stage's next TMA fill
+  };
 
   // CPML data (integer positions, the E tables) along x and y
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
@@ -170,8 +270,6 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
   unsigned src_xy = 0;
   for (int s = 0; s < A.nsrc; ++s)
     if (own && i >= A.src[s].lo[0] && i < A.src[s].hi[0] && j >= A.src[s].lo[1] && j < A.src[s].hi[1]) src_xy |= 1u << s;
-  int fseg = -1, fz0 = -1, fz1 = -1, fzseg = 0;  // face segments through the own column
-  if (own && A.rec) face_segments(A.faces, i, j, fseg, fz0, fz1, fzseg);
   const bool lay_xy = (sX0 & sX1 & sY0 & sY1) >= 0;  // this column or its +x/+y neighbour is in a layer
 
   const PsiSet& Pi = A.pin;
@@ -191,159 +289,111 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
     p2x_up = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k1, Pi.p[0][2], zz);
   }
 
+  waited &= R.wait(ktop);
+  patch(ktop);
   int sZ1 = (k1 < nz) ? T.sidx[2][k1] : -1;  // slab index of the plane above
-  for (int k = k1 - 1; k >= k0; --k) {
+  for (int k = ktop; k >= k0; --k) {
     const int q = k * plane + q0;
-    // loads of the own cell
-    float hx = 0.f, hy = 0.f, hz = 0.f, hxm = 0.f, hym = 0.f, bx = 0.f, by = 0.f, bz = 0.f, av = 0.f;
-    float ex = 0.f, ey = 0.f, ez = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-    if (own) {
-      hx = A.F.f[3][q];
-      hy = A.F.f[4][q];
-      hz = A.F.f[5][q];
-      if (k > 0) {
-        hxm = A.F.f[3][q - plane];
-        hym = A.F.f[4][q - plane];
-      }
-      bx = A.B.f[0][q];
-      by = A.B.f[1][q];
-      bz = A.B.f[2][q];
-      av = A.a[q];
-      ex = A.F.f[0][q];
-      ey = A.F.f[1][q];
-      ez = A.F.f[2][q];
-      gx = A.B.f[3][q];
-      gy = A.B.f[4][q];
-      gz = A.B.f[5][q];
-      if (fseg >= 0 || k == fz0 || k == fz1) face_fix(A, fseg, fz0, fz1, fzseg, i, j, k, hx, hy, hz);
-      if (k > 0 && (fseg >= 0 || k - 1 == fz0 || k - 1 == fz1)) {
-        float dummy = 0.f;
-        face_fix(A, fseg, fz0, fz1, fzseg, i, j, k - 1, hxm, hym, dummy);
-      }
+    if (k - 1 >= kbot) {
+      waited &= R.wait(k - 1);
+      patch(k - 1);
     }
-    // halo loads
-    float h1 = 0.f, h2 = 0.f;
-    if (hv) {
-      const int hq = k * plane + hq0;
-      if (role == 0) {  // Hx, Hz at (i, j0-1)
-        h1 = A.F.f[3][hq];
-        h2 = A.F.f[5][hq];
-        if (hseg >= 0 || k == hz0 || k == hz1) {
-          float dummy = 0.f;
-          face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, k, h1, dummy, h2);
-        }
-      } else if (role == 1) {  // Hy, Hz at (i0-1, j0+r)
-        h1 = A.F.f[4][hq];
-        h2 = A.F.f[5][hq];
-        if (hseg >= 0 || k == hz0 || k == hz1) {
-          float dummy = 0.f;
-          face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, k, dummy, h1, h2);
-        }
-      } else {
-        const float Sa = S * A.a[hq];
-        if (role == 2) {  // u_z, u_x at (i, j0+TY)
-          h1 = (hx_ > 0 && hy_ > 0) ? Sa * A.B.f[2][hq] : 0.f;
-          h2 = (hy_ > 0 && k > 0) ? Sa * A.B.f[0][hq] : 0.f;
-        } else {  // u_y, u_z at (i0+TX, j0+r)
-          h1 = (hx_ > 0 && k > 0) ? Sa * A.B.f[1][hq] : 0.f;
-          h2 = (hx_ > 0 && hy_ > 0) ? Sa * A.B.f[2][hq] : 0.f;
-        }
-      }
+    __syncthreads();  // plane k-1 patched everywhere; every thread is past plane k+1
+    if (tid == 0 && k + 1 <= ktop && k + 1 - NSTAGE >= kbot) {
+      async_proxy_fence();
+      issue_rev_E(M, R, i0, j0, k + 1 - NSTAGE);
     }
-    const float Sa = S * av;
-    const float ux = (own && j > 0 && k > 0) ? Sa * bx : 0.f;
-    const float uy = (own && i > 0 && k > 0) ? Sa * by : 0.f;
-    const float uz = (own && i > 0 && j > 0) ? Sa * bz : 0.f;
-    __syncthreads();  // the previous plane's readers are done with the staging buffers
-    if (own) {
-      sH[0][ty + 1][tx + 1] = hx;
-      sH[1][ty + 1][tx + 1] = hy;
-      sH[2][ty + 1][tx + 1] = hz;
-      sU[0][ty][tx] = ux;
-      sU[1][ty][tx] = uy;
-      sU[2][ty][tx] = uz;
-    }
-    if (role == 0) {
-      sH[0][0][hh + 1] = h1;
-      sH[2][0][hh + 1] = h2;
-    } else if (role == 1 && hh < TY) {
-      sH[1][hh + 1][0] = h1;
-      sH[2][hh + 1][0] = h2;
-    } else if (role == 2) {
-      sU[2][TY][hh] = h1;
-      sU[0][TY][hh] = h2;
-    } else if (role == 3 && hh < TY) {
-      sU[1][hh][TX] = h1;
-      sU[2][hh][TX] = h2;
-    }
-    __syncthreads();
     if (!own) continue;
+    const unsigned char* st = R.at(k);
+    const Wide3 Hs = reinterpret_cast<Wide3>(st + RE_H);
+    const Own3 Es = reinterpret_cast<Own3>(st + RE_E);
+    const Wide3 Bs = reinterpret_cast<Wide3>(st + RE_EB);
+    const Own3 Gs = reinterpret_cast<Own3>(st + RE_HB);
+    const Wide1 As = reinterpret_cast<Wide1>(st + RE_A);
+    const float hx = Hs[0][ty + 1][tx + 4], hy = Hs[1][ty + 1][tx + 4], hz = Hs[2][ty + 1][tx + 4];
+    float hxm = 0.f, hym = 0.f;
+    if (k > 0) {
+      const Wide3 Hm = reinterpret_cast<Wide3>(R.at(k - 1) + RE_H);
+      hxm = Hm[0][ty + 1][tx + 4];
+      hym = Hm[1][ty + 1][tx + 4];
+    }
+    const float bx = Bs[0][ty][tx], by = Bs[1][ty][tx], bz = Bs[2][ty][tx];
+    const float Sa = S * As[ty][tx];
+    const float ux = (j > 0 && k > 0) ? Sa * bx : 0.f;
+    const float uy = (i > 0 && k > 0) ? Sa * by : 0.f;
+    const float uz = (i > 0 && j > 0) ? Sa * bz : 0.f;
+    // u of the +x neighbour (z and y) and of the +y neighbour (z and x); 0 beyond the grid
+    const float Sax = S * As[ty][tx + 1], Say = S * As[ty + 1][tx];
+    const float uz_x = (j > 0) ? Sax * Bs[2][ty][tx + 1] : 0.f, uy_x = (k > 0) ? Sax * Bs[1][ty][tx + 1] : 0.f;
+    const float uz_y = (i > 0) ? Say * Bs[2][ty + 1][tx] : 0.f, ux_y = (k > 0) ? Say * Bs[0][ty + 1][tx] : 0.f;
+    const float gx = Gs[0][ty][tx], gy = Gs[1][ty][tx], gz = Gs[2][ty][tx];
+    float ex = Es[0][ty][tx], ey = Es[1][ty][tx], ez = Es[2][ty][tx];
 
     const float ikZ = T.ik[2][0][k];
     const int sZ = T.sidx[2][k];
-    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
-    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
 
     // adjoint coefficients of the own E point and of its +x, +y neighbours (off the layers they are
     // +-u: 1/kappa = 1 and c = 0)
     if (!lay_xy && sZ < 0 && sZ1 < 0) {
-      const float p1z_x = hasX1 ? sU[2][ty][tx + 1] : 0.f, p2y_x = hasX1 ? -sU[1][ty][tx + 1] : 0.f;
-      const float p2z_y = hasY1 ? -sU[2][ty + 1][tx] : 0.f, p1x_y = hasY1 ? sU[0][ty + 1][tx] : 0.f;
-      A.B.f[3][q] = gx + ((uy - p1y_up) + (-uz - p2z_y));
-      A.B.f[4][q] = gy + ((uz - p1z_x) + (-ux - p2x_up));
-      A.B.f[5][q] = gz + ((ux - p1x_y) + (-uy - p2y_x));
+      A.B.f[3][q] = gx + ((uy - p1y_up) + (-uz + uz_y));
+      A.B.f[4][q] = gy + ((uz - uz_x) + (-ux - p2x_up));
+      A.B.f[5][q] = gz + ((ux - ux_y) + (-uy + uy_x));
       p1y_up = uy;
       p2x_up = -ux;
     } else {
-    const float p1x = acoef<1, 0>(T, ux, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
-    const float p2x = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
-    const float p1y = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
-    const float p2y = acoef<0, 0>(T, uy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
-    const float p1z = acoef<0, 0>(T, uz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
-    const float p2z = acoef<1, 0>(T, uz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
-    float p1z_x = 0.f, p2y_x = 0.f, p2z_y = 0.f, p1x_y = 0.f;
-    if (hasX1) {
-      const int zx1 = sX1 >= 0 ? zx_of(g, j, k, sX1) : 0;
-      p1z_x = acoef<0, 0>(T, sU[2][ty][tx + 1], 1.f, ikX1, sX1, i + 1, Pi.p[2][0], zx1);
-      p2y_x = acoef<0, 0>(T, sU[1][ty][tx + 1], -1.f, ikX1, sX1, i + 1, Pi.p[1][0], zx1);
-    }
-    if (hasY1) {
-      const int zy1 = sY1 >= 0 ? zy_of(g, i, k, sY1) : 0;
-      p2z_y = acoef<1, 0>(T, sU[2][ty + 1][tx], -1.f, ikY1, sY1, j + 1, Pi.p[2][1], zy1);
-      p1x_y = acoef<1, 0>(T, sU[0][ty + 1][tx], 1.f, ikY1, sY1, j + 1, Pi.p[0][1], zy1);
-    }
-    A.B.f[3][q] = gx + ((p1y - p1y_up) + (p2z - p2z_y));
-    A.B.f[4][q] = gy + ((p1z - p1z_x) + (p2x - p2x_up));
-    A.B.f[5][q] = gz + ((p1x - p1x_y) + (p2y - p2y_x));
-    apsi<1, 0>(T, ux, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
-    apsi<2, 0>(T, ux, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
-    apsi<2, 0>(T, uy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
-    apsi<0, 0>(T, uy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
-    apsi<0, 0>(T, uz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
-    apsi<1, 0>(T, uz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
-    p1y_up = p1y;
-    p2x_up = p2x;
+      const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
+      const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
+      const float p1x = acoef<1, 0>(T, ux, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
+      const float p2x = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
+      const float p1y = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
+      const float p2y = acoef<0, 0>(T, uy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
+      const float p1z = acoef<0, 0>(T, uz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
+      const float p2z = acoef<1, 0>(T, uz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
+      float p1z_x = 0.f, p2y_x = 0.f, p2z_y = 0.f, p1x_y = 0.f;
+      if (hasX1) {
+        const int zx1 = sX1 >= 0 ? zx_of(g, j, k, sX1) : 0;
+        p1z_x = acoef<0, 0>(T, uz_x, 1.f, ikX1, sX1, i + 1, Pi.p[2][0], zx1);
+        p2y_x = acoef<0, 0>(T, uy_x, -1.f, ikX1, sX1, i + 1, Pi.p[1][0], zx1);
+      }
+      if (hasY1) {
+        const int zy1 = sY1 >= 0 ? zy_of(g, i, k, sY1) : 0;
+        p2z_y = acoef<1, 0>(T, uz_y, -1.f, ikY1, sY1, j + 1, Pi.p[2][1], zy1);
+        p1x_y = acoef<1, 0>(T, ux_y, 1.f, ikY1, sY1, j + 1, Pi.p[0][1], zy1);
+      }
+      A.B.f[3][q] = gx + ((p1y - p1y_up) + (p2z - p2z_y));
+      A.B.f[4][q] = gy + ((p1z - p1z_x) + (p2x - p2x_up));
+      A.B.f[5][q] = gz + ((p1x - p1x_y) + (p2y - p2y_x));
+      apsi<1, 0>(T, ux, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
+      apsi<2, 0>(T, ux, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
+      apsi<2, 0>(T, uy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
+      apsi<0, 0>(T, uy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
+      apsi<0, 0>(T, uz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
+      apsi<1, 0>(T, uz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
+      p1y_up = p1y;
+      p2x_up = p2x;
     }
     sZ1 = sZ;
 
     // inverse E update on R (mirrors the forward arithmetic: the curl difference times 1/kappa = 1)
-    const float dxa = hz - sH[2][ty][tx + 1], dxb = hy - hym;   // E_x: along y, along z
-    const float dya = hx - hxm, dyb = hz - sH[2][ty + 1][tx];   // E_y: along z, along x
-    const float dza = hy - sH[1][ty + 1][tx], dzb = hx - sH[0][ty][tx + 1];  // E_z: along x, along y
+    const float dxa = hz - Hs[2][ty][tx + 4], dxb = hy - hym;       // E_x: along y, along z
+    const float dya = hx - hxm, dyb = hz - Hs[2][ty + 1][tx + 3];   // E_y: along z, along x
+    const float dza = hy - Hs[1][ty + 1][tx + 3], dzb = hx - Hs[0][ty][tx + 4];  // E_z: along x, along y
     const bool rzh = k >= g.rhalf_lo[2] && k <= g.rhalf_hi[2], rzi = k >= g.rint_lo[2] && k <= g.rint_hi[2];
     const bool inx = rxh && ryi && rzi && j > 0 && k > 0;
     const bool iny = rxi && ryh && rzi && i > 0 && k > 0;
     const bool inz = rxi && ryi && rzh && i > 0 && j > 0;
-    unsigned src_k = 0;
-    for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
-    if (src_xy & src_k) {
-      for (int s = 0; s < A.nsrc; ++s) {
-        const SrcDev& sd = A.src[s];
-        if (!(((src_xy & src_k) >> s) & 1u)) continue;
-        const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
-        if (sd.comp == 0 && inx) ex -= v;
-        else if (sd.comp == 1 && iny) ey -= v;
-        else if (sd.comp == 2 && inz) ez -= v;
+    if (src_xy) {
+      unsigned src_k = 0;
+      for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
+      if (src_xy & src_k) {
+        for (int s = 0; s < A.nsrc; ++s) {
+          const SrcDev& sd = A.src[s];
+          if (!(((src_xy & src_k) >> s) & 1u)) continue;
+          const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
+          if (sd.comp == 0 && inx) ex -= v;
+          else if (sd.comp == 1 && iny) ey -= v;
+          else if (sd.comp == 2 && inz) ez -= v;
+        }
       }
     }
     if (inx) ex -= Sa * (dxa * ikY0 - dxb * ikZ);
@@ -362,14 +412,15 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E_lean(RevArgs A) {
       A.dLda[m] += (double)S * (double)gs;
     }
   }
+  if (!waited) atomicOr(A.status, 1);
 }
 
 // ---------------------------------------------------------------------------------------------
 // rev_H
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
-  __shared__ float sE[3][HY][HX];  // E^n(k): x in [i0, i0+TX], y in [j0, j0+TY]
-  __shared__ float sW[3][HY][HX];  // w(k) = -S Hbar: x in [i0-1, i0+TX-1], y in [j0-1, j0+TY-1]
+__global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_constant__ RevMaps M) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* sm = align128(smem_raw);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -384,17 +435,16 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
   const bool own = i < nx && j < ny;
   const int q0 = j * g.nxp + i;
   const float S = g.S;
+  const int ktop = k1 - 1, kbot = max(k0 - 1, 0);  // planes staged: Hbar(k-1) is read below the chunk
+  const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RH_STAGE), RH_STAGE, ktop};
+  bool waited = true;
 
-  // halo roles: E row (i, j0+TY) and column (i0+TX, j0+r); w row (i, j0-1) and column (i0-1, j0+r)
-  const int hh = tid % TX;
-  const int role = tid / TX;
-  int hx_ = 0, hy_ = 0;
-  bool hv = false;
-  if (role == 0) { hx_ = i0 + hh; hy_ = j0 + TY; hv = hy_ < ny && hx_ < nx; }
-  else if (role == 1) { hx_ = i0 + TX; hy_ = j0 + hh; hv = hh < TY && hx_ < nx && hy_ < ny; }
-  else if (role == 2) { hx_ = i0 + hh; hy_ = j0 - 1; hv = j0 > 0 && hx_ < nx; }
-  else if (role == 3) { hx_ = i0 - 1; hy_ = j0 + hh; hv = hh < TY && i0 > 0 && hy_ < ny; }
-  const int hq0 = hy_ * g.nxp + hx_;
+  if (tid == 0) {
+    for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
+    mbar_init_fence();
+    for (int p = ktop; p >= max(ktop - NSTAGE + 1, kbot); --p) issue_rev_H(M, R, i0, j0, p);
+  }
+  __syncthreads();
 
   // CPML data (half positions, the H tables) along x and y, at the own column and at -x, -y
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
@@ -419,79 +469,42 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
     ey_up = A.F.f[1][k1 * plane + q0];
   }
 
-  for (int k = k1 - 1; k >= k0; --k) {
+  waited &= R.wait(ktop);
+  for (int k = ktop; k >= k0; --k) {
     const int q = k * plane + q0;
-    float ex = 0.f, ey = 0.f, ez = 0.f, hx = 0.f, hy = 0.f, hz = 0.f, bx = 0.f, by = 0.f, bz = 0.f;
-    float ebx = 0.f, eby = 0.f, ebz = 0.f, bxm = 0.f, bym = 0.f;
-    if (own) {
-      ex = A.F.f[0][q];
-      ey = A.F.f[1][q];
-      ez = A.F.f[2][q];
-      hx = A.F.f[3][q];
-      hy = A.F.f[4][q];
-      hz = A.F.f[5][q];
-      bx = A.B.f[3][q];
-      by = A.B.f[4][q];
-      bz = A.B.f[5][q];
-      ebx = A.B.f[0][q];
-      eby = A.B.f[1][q];
-      ebz = A.B.f[2][q];
-      if (k > 0) {
-        bxm = A.B.f[3][q - plane];
-        bym = A.B.f[4][q - plane];
-      }
+    if (k - 1 >= kbot) waited &= R.wait(k - 1);
+    __syncthreads();  // every thread is past plane k+1
+    if (tid == 0 && k + 1 <= ktop && k + 1 - NSTAGE >= kbot) {
+      async_proxy_fence();
+      issue_rev_H(M, R, i0, j0, k + 1 - NSTAGE);
     }
-    float h1 = 0.f, h2 = 0.f;
-    if (hv) {
-      const int hq = k * plane + hq0;
-      if (role == 0) {  // E_z, E_x at (i, j0+TY)
-        h1 = A.F.f[2][hq];
-        h2 = A.F.f[0][hq];
-      } else if (role == 1) {  // E_y, E_z at (i0+TX, j0+r)
-        h1 = A.F.f[1][hq];
-        h2 = A.F.f[2][hq];
-      } else if (role == 2) {  // w_z, w_x at (i, j0-1)
-        h1 = -S * A.B.f[5][hq];
-        h2 = -S * A.B.f[3][hq];
-      } else {  // w_z, w_y at (i0-1, j0+r)
-        h1 = -S * A.B.f[5][hq];
-        h2 = -S * A.B.f[4][hq];
-      }
+    if (!own) continue;
+    const unsigned char* st = R.at(k);
+    const Wide3 Es = reinterpret_cast<Wide3>(st + RH_E);
+    const Own3 Hs = reinterpret_cast<Own3>(st + RH_H);
+    const Wide3 Bs = reinterpret_cast<Wide3>(st + RH_HB);
+    const Own3 Gs = reinterpret_cast<Own3>(st + RH_EB);
+    const float ex = Es[0][ty][tx], ey = Es[1][ty][tx], ez = Es[2][ty][tx];
+    const float hx = Hs[0][ty][tx], hy = Hs[1][ty][tx], hz = Hs[2][ty][tx];
+    const float bx = Bs[0][ty + 1][tx + 4], by = Bs[1][ty + 1][tx + 4], bz = Bs[2][ty + 1][tx + 4];
+    const float ebx = Gs[0][ty][tx], eby = Gs[1][ty][tx], ebz = Gs[2][ty][tx];
+    float bxm = 0.f, bym = 0.f;
+    if (k > 0) {
+      const Wide3 Bm = reinterpret_cast<Wide3>(R.at(k - 1) + RH_HB);
+      bxm = Bm[0][ty + 1][tx + 4];
+      bym = Bm[1][ty + 1][tx + 4];
     }
     const float wx = -S * bx, wy = -S * by, wz = -S * bz;
-    __syncthreads();
-    if (own) {
-      sE[0][ty][tx] = ex;
-      sE[1][ty][tx] = ey;
-      sE[2][ty][tx] = ez;
-      sW[0][ty + 1][tx + 1] = wx;
-      sW[1][ty + 1][tx + 1] = wy;
-      sW[2][ty + 1][tx + 1] = wz;
-    }
-    if (role == 0) {
-      sE[2][TY][hh] = h1;
-      sE[0][TY][hh] = h2;
-    } else if (role == 1 && hh < TY) {
-      sE[1][hh][TX] = h1;
-      sE[2][hh][TX] = h2;
-    } else if (role == 2) {
-      sW[2][0][hh + 1] = h1;
-      sW[0][0][hh + 1] = h2;
-    } else if (role == 3 && hh < TY) {
-      sW[2][hh + 1][0] = h1;
-      sW[1][hh + 1][0] = h2;
-    }
-    __syncthreads();
-    if (!own) continue;
+    // w of the -x neighbour (z and y) and of the -y neighbour (z and x); 0 beyond the grid
+    const float wz_x = -S * Bs[2][ty + 1][tx + 3], wy_x = -S * Bs[1][ty + 1][tx + 3];
+    const float wz_y = -S * Bs[2][ty][tx + 4], wx_y = -S * Bs[0][ty][tx + 4];
 
     const float ikZ = T.ik[2][1][k];
     const int sZ = T.sidx[2][k];
-    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
-    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
 
     // inverse H update on R (E beyond index N - 1 is the PEC wall: zero)
-    const float ez_y = (j + 1 < ny) ? sE[2][ty + 1][tx] : 0.f, ex_y = (j + 1 < ny) ? sE[0][ty + 1][tx] : 0.f;
-    const float ey_x = (i + 1 < nx) ? sE[1][ty][tx + 1] : 0.f, ez_x = (i + 1 < nx) ? sE[2][ty][tx + 1] : 0.f;
+    const float ez_y = Es[2][ty + 1][tx], ex_y = Es[0][ty + 1][tx];
+    const float ey_x = Es[1][ty][tx + 1], ez_x = Es[2][ty][tx + 1];
     const bool rzh = k >= g.rhalf_lo[2] && k <= g.rhalf_hi[2], rzi = k >= g.rint_lo[2] && k <= g.rint_hi[2];
     if (rxi && ryh && rzh) A.F.f[3][q] = hx + S * ((ez_y - ez) * ikY0 - (ey_up - ey) * ikZ);
     if (rxh && ryi && rzh) A.F.f[4][q] = hy + S * ((ex_up - ex) * ikZ - (ez_x - ez) * ikX0);
@@ -502,14 +515,14 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
     // adjoint: coefficients of the own H point and of its -x, -y, -z neighbours (off the layers +-w)
     const int sZm = k > 0 ? T.sidx[2][k - 1] : -1;
     if (!lay_xy && sZ < 0 && sZm < 0) {
-      const float q1z_x = hasXm ? sW[2][ty + 1][tx] : 0.f, q2y_x = hasXm ? -sW[1][ty + 1][tx] : 0.f;
-      const float q2z_y = hasYm ? -sW[2][ty][tx + 1] : 0.f, q1x_y = hasYm ? sW[0][ty][tx + 1] : 0.f;
       const float q1y_z = k > 0 ? -S * bym : 0.f, q2x_z = k > 0 ? S * bxm : 0.f;
-      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - wy) + (q2z_y + wz));
-      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((q1z_x - wz) + (q2x_z + wx));
-      if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((q1x_y - wx) + (q2y_x + wy));
+      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - wy) + (-wz_y + wz));
+      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((wz_x - wz) + (q2x_z + wx));
+      if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((wx_y - wx) + (-wy_x + wy));
       continue;
     }
+    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
+    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
     const float q1x = acoef<1, 1>(T, wx, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
     const float q2x = acoef<2, 1>(T, wx, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
     const float q1y = acoef<2, 1>(T, wy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
@@ -519,13 +532,13 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
     float q1z_x = 0.f, q2y_x = 0.f, q2z_y = 0.f, q1x_y = 0.f, q1y_z = 0.f, q2x_z = 0.f;
     if (hasXm) {
       const int zxm = sXm >= 0 ? zx_of(g, j, k, sXm) : 0;
-      q1z_x = acoef<0, 1>(T, sW[2][ty + 1][tx], 1.f, ikXm, sXm, i - 1, Pi.p[2][0], zxm);
-      q2y_x = acoef<0, 1>(T, sW[1][ty + 1][tx], -1.f, ikXm, sXm, i - 1, Pi.p[1][0], zxm);
+      q1z_x = acoef<0, 1>(T, wz_x, 1.f, ikXm, sXm, i - 1, Pi.p[2][0], zxm);
+      q2y_x = acoef<0, 1>(T, wy_x, -1.f, ikXm, sXm, i - 1, Pi.p[1][0], zxm);
     }
     if (hasYm) {
       const int zym = sYm >= 0 ? zy_of(g, i, k, sYm) : 0;
-      q2z_y = acoef<1, 1>(T, sW[2][ty][tx + 1], -1.f, ikYm, sYm, j - 1, Pi.p[2][1], zym);
-      q1x_y = acoef<1, 1>(T, sW[0][ty][tx + 1], 1.f, ikYm, sYm, j - 1, Pi.p[0][1], zym);
+      q2z_y = acoef<1, 1>(T, wz_y, -1.f, ikYm, sYm, j - 1, Pi.p[2][1], zym);
+      q1x_y = acoef<1, 1>(T, wx_y, 1.f, ikYm, sYm, j - 1, Pi.p[0][1], zym);
     }
     if (k > 0) {
       const float ikZm = T.ik[2][1][k - 1];
@@ -543,20 +556,30 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H_lean(RevArgs A) {
     apsi<0, 1>(T, wz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
     apsi<1, 1>(T, wz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
   }
+  if (!waited) atomicOr(A.status, 1);
 }
 
 }  // namespace
 
-void launch_rev_E_lean(const RevArgs& a, cudaStream_t s) {
-  const Geo& g = a.g;
-  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_rev_E_lean<<<grid, NT, 0, s>>>(a);
+MapBox rev_box_own() { return {TX, TY}; }
+MapBox rev_box_wide() { return {BW, BH}; }
+
+int prepare_rev() {
+  cudaError_t e = cudaFuncSetAttribute(k_rev_E, cudaFuncAttributeMaxDynamicSharedMemorySize, RE_SMEM);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rev_H, cudaFuncAttributeMaxDynamicSharedMemorySize, RH_SMEM);
+  return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }
 
-void launch_rev_H_lean(const RevArgs& a, cudaStream_t s) {
+void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_rev_H_lean<<<grid, NT, 0, s>>>(a);
+  k_rev_E<<<grid, NT, RE_SMEM, s>>>(a, m);
+}
+
+void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
+  const Geo& g = a.g;
+  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+  k_rev_H<<<grid, NT, RH_SMEM, s>>>(a, m);
 }
 
 }  // namespace fdtd

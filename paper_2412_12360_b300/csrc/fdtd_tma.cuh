@@ -35,6 +35,19 @@ MapBox fwd_box_a();
 int prepare_fwd_fused(int* blocks_per_sm);
 void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s);
 
+// The maps the reverse-step kernels read (F = fields, B = adjoint fields): "own" boxes cover the
+// TX x TY tile, "high" boxes the tile plus one cell at +x and +y, "low" boxes the tile plus one cell
+// at -x and -y (origin 4 cells left of the tile).
+struct RevMaps {
+  CUtensorMap e_own, e_high, h_own, h_low, eb_own, eb_high, hb_own, hb_low, a_high;
+};
+
+MapBox rev_box_own();
+MapBox rev_box_wide();
+int prepare_rev();
+void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s);
+void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s);
+
 #if defined(__CUDACC__)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
