@@ -28,16 +28,31 @@ constexpr int HX = TX + 1, HY = TY + 1;  // new H with the low halo
 
 // CPML correction of one curl term inside a layer: the update uses d / kappa + psi_new where the plain
 // Yee update uses d, so the correction is (1/kappa - 1) d + psi_new with psi_new = b psi_old + c d
-// (read from pin[z], written to pout[z] when STORE). Off the layers (s < 0) it is 0; on the layer's
-// inner edge (depth 0) 1/kappa = 1, b = 1, c = 0 and psi stays 0, so it is 0 there too.
+// (written to pout[z] when STORE). On the layer's inner edge (depth 0) 1/kappa = 1, b = 1, c = 0 and
+// psi stays 0, so the correction is 0 there, as it is off the layers (where the caller skips it).
 template <bool STORE>
-__device__ __forceinline__ float corr(float d, float ik, int s, const float* __restrict__ bt,
-                                      const float* __restrict__ ct, int pos, const float* pin, float* pout, int z) {
-  if (s < 0) return 0.f;
-  const float v = bt[pos] * pin[z] + ct[pos] * d;
+__device__ __forceinline__ float corr(float d, float ik, float b, float c, float psi_old, float* pout, int z) {
+  const float v = b * psi_old + c * d;
   if (STORE) pout[z] = v;
   return (ik - 1.f) * d + v;
 }
+
+// CPML coefficients at one position along one axis: integer-position (E) and half-position (H) sets
+struct Coef {
+  float b, c, ik;
+};
+
+// slab index of position x along an axis with n cells and layers p0, p1 (-1 off the layers)
+__device__ __forceinline__ int slab_of(int x, int n, int p0, int p1) {
+  return x < p0 ? x : (x >= n - p1 ? p0 + x - (n - p1) : -1);
+}
+
+// 4-byte asynchronous copy global -> shared (completion tracked per thread with commit groups)
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // psi index of the point (x, y, k), slab index s, for the derivative along x, y or z
 __device__ __forceinline__ int zx_of(const Geo& g, int y, int k, int s) { return (k * g.n[1] + y) * g.slab[0] + s; }
@@ -68,14 +83,24 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
 constexpr int EW = TX + 8, EH = TY + 2;
 constexpr int HW = TX + 4, HH = TY + 1;
 constexpr int XO = 4;  // x offset of the tile inside the E and H boxes
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 3;
 constexpr uint32_t E_BYTES = 3 * EW * EH * 4, H_BYTES = 3 * HW * HH * 4, A_BYTES = TX * TY * 4;
 constexpr uint32_t STAGE_TX = E_BYTES + H_BYTES + A_BYTES;  // transaction bytes of one stage
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 constexpr int E_OFF = 0, H_OFF = round128(E_BYTES), A_OFF = H_OFF + round128(H_BYTES);
 constexpr int STAGE_BYTES = round128(A_OFF + A_BYTES);
+// CPML memories of the plane being computed, copied ahead by each thread for itself (cp.async):
+// H slots 0..5 own point (Hy_x, Hz_x, Hx_y, Hz_y, Hx_z, Hy_z), 6..9 the halo point; E slots 0..5.
+constexpr int NPH = 10, NPE = 6;
+// CPML tables of the tile's x and y positions (from i0-1 and j0-1): b, c, 1/kappa at integer then
+// half positions
+constexpr int TABX = TX + 1, TABY = TY + 1;
 constexpr int SH_OFF = NSTAGE * STAGE_BYTES;                      // new H: [2][3][HY][HX] floats
-constexpr int BAR_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);  // NSTAGE mbarriers
+constexpr int PH_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);    // [NPH][NT]
+constexpr int PE_OFF = PH_OFF + NPH * NT * 4;                     // [NPE][NT]
+constexpr int TX_OFF = PE_OFF + NPE * NT * 4;                     // [6][TABX]
+constexpr int TY_OFF = TX_OFF + 6 * TABX * 4;                     // [6][TABY]
+constexpr int BAR_OFF = round128(TY_OFF + 6 * TABY * 4);          // NSTAGE mbarriers
 constexpr int SMEM_BYTES = BAR_OFF + NSTAGE * 8 + 128;             // + slack to align the base
 static_assert(NT * 8 <= STAGE_BYTES, "the flux reduction reuses the first stage");
 
@@ -101,11 +126,21 @@ struct Ring {
   }
 };
 
+// the coefficients of table column idx: row0 = 0 for integer (E) positions, 3 for half (H) positions
+template <int W>
+__device__ __forceinline__ Coef coef_at(const float (*tab)[W], int row0, int idx) {
+  return Coef{tab[row0][idx], tab[row0 + 1][idx], tab[row0 + 2][idx]};
+}
+
 __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
   Ring R{sm, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
   float(*sHb)[3][HY][HX] = reinterpret_cast<float(*)[3][HY][HX]>(sm + SH_OFF);
+  float(*sPH)[NT] = reinterpret_cast<float(*)[NT]>(sm + PH_OFF);
+  float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PE_OFF);
+  float(*tabX)[TABX] = reinterpret_cast<float(*)[TABX]>(sm + TX_OFF);
+  float(*tabY)[TABY] = reinterpret_cast<float(*)[TABY]>(sm + TY_OFF);
   double* sred = reinterpret_cast<double*>(sm);
 
   const Geo& g = A.g;
@@ -116,7 +151,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int k0 = blockIdx.z * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int kb = k0 > 0 ? k0 - 1 : k0;  // first plane staged (k0-1 supplies H^{n+1/2} below the chunk)
-  const int nx = g.n[0], ny = g.n[1];
+  const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
   const int i = i0 + tx, j = j0 + ty;
   const bool own = i < nx && j < ny;
@@ -131,6 +166,17 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     mbar_init_fence();
     for (int p = kb; p <= min(kb + NSTAGE - 1, k1); ++p) R.issue(M, p - kb, i0, j0, p);
   }
+  // CPML tables of the tile's positions (clamped into the grid; out-of-grid entries are not used)
+  for (int t = tid; t < 6 * (TABX + TABY); t += NT) {
+    const bool isx = t < 6 * TABX;
+    const int u = isx ? t : t - 6 * TABX;
+    const int row = isx ? u / TABX : u / TABY, col = isx ? u % TABX : u % TABY;
+    const int ax = isx ? 0 : 1;
+    const int pos = min(max((isx ? i0 : j0) - 1 + col, 0), g.n[ax] - 1);
+    const int hf = row / 3, w = row % 3;
+    const float* src = w == 0 ? T.b[ax][hf] : (w == 1 ? T.c[ax][hf] : T.ik[ax][hf]);
+    (isx ? tabX[row] : tabY[row])[col] = src[pos];
+  }
   __syncthreads();
 
   // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
@@ -141,12 +187,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int hrx = hcol ? 0 : tx + 1, hry = hcol ? tx + 1 : 0;  // the halo point in the new-H tile
   const int hex = hrx + XO - 1, hey = hry;                      // and in the staged boxes
 
-  // CPML data along x and y, fixed for the whole march (H tables at half, E tables at integer positions)
-  const int ic = min(i, nx - 1), jc = min(j, ny - 1);
-  const float ikXh = T.ik[0][1][ic], ikXe = T.ik[0][0][ic], ikYh = T.ik[1][1][jc], ikYe = T.ik[1][0][jc];
-  const int sX = T.sidx[0][ic], sY = T.sidx[1][jc];
-  const float ikXhh = T.ik[0][1][xh], ikYhh = T.ik[1][1][yh];  // at the halo point
-  const int sXh = T.sidx[0][xh], sYh = T.sidx[1][yh];
+  // slab indices along x and y of the own and the halo point (-1 off the layers)
+  const int sX = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
+  const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
+  const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
 
   // membership of this column in the source and detector boxes (bit s), and face segments
   unsigned src_xy = 0, det_xy = 0;
@@ -190,51 +234,114 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const PsiSet& PEo = A.psiE_nxt;
   const Fields& N = A.nxt;
 
+  // copies of psi_old of plane kk into this thread's slots (one commit group each)
+  auto fetch_psiH = [&](int kk) {
+    const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+    if (own) {
+      if (sX >= 0) {
+        const int z = zx_of(g, j, kk, sX);
+        cp4(&sPH[0][tid], PHi.p[1][0] + z);
+        cp4(&sPH[1][tid], PHi.p[2][0] + z);
+      }
+      if (sY >= 0) {
+        const int z = zy_of(g, i, kk, sY);
+        cp4(&sPH[2][tid], PHi.p[0][1] + z);
+        cp4(&sPH[3][tid], PHi.p[2][1] + z);
+      }
+      if (sZk >= 0) {
+        const int z = zz_of(g, i, j, sZk);
+        cp4(&sPH[4][tid], PHi.p[0][2] + z);
+        cp4(&sPH[5][tid], PHi.p[1][2] + z);
+      }
+    }
+    if (hrow || hcol) {
+      if (sXh >= 0) cp4(&sPH[6][tid], PHi.p[2][0] + zx_of(g, yh, kk, sXh));  // Hz along x
+      if (sYh >= 0) cp4(&sPH[7][tid], PHi.p[2][1] + zy_of(g, xh, kk, sYh));  // Hz along y
+      if (hrow) {
+        if (sYh >= 0) cp4(&sPH[8][tid], PHi.p[0][1] + zy_of(g, xh, kk, sYh));  // Hx along y
+        if (sZk >= 0) cp4(&sPH[9][tid], PHi.p[0][2] + zz_of(g, xh, yh, sZk));  // Hx along z
+      } else {
+        if (sZk >= 0) cp4(&sPH[8][tid], PHi.p[1][2] + zz_of(g, xh, yh, sZk));  // Hy along z
+        if (sXh >= 0) cp4(&sPH[9][tid], PHi.p[1][0] + zx_of(g, yh, kk, sXh));  // Hy along x
+      }
+    }
+    cp_commit();
+  };
+  auto fetch_psiE = [&](int kk) {
+    const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+    if (own) {
+      if (sX >= 0) {
+        const int z = zx_of(g, j, kk, sX);
+        cp4(&sPE[0][tid], PEi.p[1][0] + z);
+        cp4(&sPE[1][tid], PEi.p[2][0] + z);
+      }
+      if (sY >= 0) {
+        const int z = zy_of(g, i, kk, sY);
+        cp4(&sPE[2][tid], PEi.p[0][1] + z);
+        cp4(&sPE[3][tid], PEi.p[2][1] + z);
+      }
+      if (sZk >= 0) {
+        const int z = zz_of(g, i, j, sZk);
+        cp4(&sPE[4][tid], PEi.p[0][2] + z);
+        cp4(&sPE[5][tid], PEi.p[1][2] + z);
+      }
+    }
+    cp_commit();
+  };
+
   waited &= mbar_wait(&R.bar[0], 0);
   float hxm = 0.f, hym = 0.f;
   if (k0 > 0) {
     // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
     waited &= mbar_wait(&R.bar[1], 0);
+    const int km = kb;
+    const int sZ = slab_of(km, nz, g.pml[4], g.pml[5]);
     if (own) {
-      const int km = kb;
       const float(*a0)[EH][EW] = R.E(0);
       const float(*a1)[EH][EW] = R.E(1);
-      const float ikZh = T.ik[2][1][km];
-      const int sZ = T.sidx[2][km];
       const float dzy = a0[2][ey + 1][ex] - a0[2][ey][ex], dyz = a1[1][ey][ex] - a0[1][ey][ex];
       const float dxz = a1[0][ey][ex] - a0[0][ey][ex], dzx = a0[2][ey][ex + 1] - a0[2][ey][ex];
       float cx = dzy - dyz, cy = dxz - dzx;
       if ((sX & sY & sZ) >= 0) {
-        const int zx = sX >= 0 ? zx_of(g, j, km, sX) : 0, zy = sY >= 0 ? zy_of(g, i, km, sY) : 0;
-        const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
-        cx += corr<false>(dzy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], nullptr, zy) -
-              corr<false>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[0][2], nullptr, zz);
-        cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], km, PHi.p[1][2], nullptr, zz) -
-              corr<false>(dzx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], nullptr, zx);
+        const Coef cz{T.b[2][1][km], T.c[2][1][km], T.ik[2][1][km]};
+        const Coef cxh = coef_at(tabX, 3, rx), cyh = coef_at(tabY, 3, ry);
+        if (sY >= 0) cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, i, km, sY)], nullptr, 0);
+        if (sZ >= 0) {
+          const int zz = zz_of(g, i, j, sZ);
+          cx -= corr<false>(dyz, cz.ik, cz.b, cz.c, PHi.p[0][2][zz], nullptr, 0);
+          cy += corr<false>(dxz, cz.ik, cz.b, cz.c, PHi.p[1][2][zz], nullptr, 0);
+        }
+        if (sX >= 0) cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
       }
       hxm = R.H(0)[0][ey][ex] - S * cx;
       hym = R.H(0)[1][ey][ex] - S * cy;
     }
   }
+  fetch_psiH(k0);
+  fetch_psiE(k0);
 
   for (int k = k0; k < k1; ++k) {
     const int it = k - kb;  // stage use count of plane k
     const int b0 = it % NSTAGE, b1 = (it + 1) % NSTAGE;
     const int q = k * plane + q0;
-    const float ikZh = T.ik[2][1][k], ikZe = T.ik[2][0][k];
-    const int sZ = T.sidx[2][k];
+    const int sZ = slab_of(k, nz, g.pml[4], g.pml[5]);
+    Coef czh{0.f, 0.f, 1.f}, cze{0.f, 0.f, 1.f};
+    if (sZ >= 0) {  // uniform over the block
+      czh = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
+      cze = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
+    }
     unsigned src_k = 0, det_k = 0;  // sources and detectors whose z-range holds this plane
-    for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
-    for (int s = 0; s < A.ndet; ++s) det_k |= (k >= A.det[s].lo[2] && k < A.det[s].hi[2]) ? 1u << s : 0u;
+    if (src_xy)
+      for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
+    if (det_xy)
+      for (int s = 0; s < A.ndet; ++s) det_k |= (k >= A.det[s].lo[2] && k < A.det[s].hi[2]) ? 1u << s : 0u;
     waited &= mbar_wait(&R.bar[b1], ((it + 1) / NSTAGE) & 1);  // plane k+1 (plane k was waited for before)
+    cp_wait_all_but_one();                                      // psi_old of H at plane k
     const float(*ek)[EH][EW] = R.E(b0);
     const float(*ek1)[EH][EW] = R.E(b1);
     const float(*hk)[HH][HW] = R.H(b0);
     float(*sH)[HY][HX] = sHb[it & 1];
     const bool lay = (sX & sY & sZ) >= 0;  // some axis of this cell is in a layer (-1 = all bits set)
-    const int zx = sX >= 0 ? zx_of(g, j, k, sX) : 0;
-    const int zy = sY >= 0 ? zy_of(g, i, k, sY) : 0;
-    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
 
     // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
     float hx = 0.f, hy = 0.f, hz = 0.f;
@@ -244,12 +351,23 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       const float dyx = ek[1][ey][ex + 1] - ek[1][ey][ex], dxy = ek[0][ey + 1][ex] - ek[0][ey][ex];
       float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
       if (lay) {
-        cx += corr<true>(dzy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[0][1], PHo.p[0][1], zy) -
-              corr<true>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], PHo.p[0][2], zz);
-        cy += corr<true>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], PHo.p[1][2], zz) -
-              corr<true>(dzx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[1][0], PHo.p[1][0], zx);
-        cz += corr<true>(dyx, ikXh, sX, T.b[0][1], T.c[0][1], i, PHi.p[2][0], PHo.p[2][0], zx) -
-              corr<true>(dxy, ikYh, sY, T.b[1][1], T.c[1][1], j, PHi.p[2][1], PHo.p[2][1], zy);
+        if (sX >= 0) {
+          const Coef c = coef_at(tabX, 3, rx);
+          const int z = zx_of(g, j, k, sX);
+          cy -= corr<true>(dzx, c.ik, c.b, c.c, sPH[0][tid], PHo.p[1][0], z);
+          cz += corr<true>(dyx, c.ik, c.b, c.c, sPH[1][tid], PHo.p[2][0], z);
+        }
+        if (sY >= 0) {
+          const Coef c = coef_at(tabY, 3, ry);
+          const int z = zy_of(g, i, k, sY);
+          cx += corr<true>(dzy, c.ik, c.b, c.c, sPH[2][tid], PHo.p[0][1], z);
+          cz -= corr<true>(dxy, c.ik, c.b, c.c, sPH[3][tid], PHo.p[2][1], z);
+        }
+        if (sZ >= 0) {
+          const int z = zz_of(g, i, j, sZ);
+          cx -= corr<true>(dyz, czh.ik, czh.b, czh.c, sPH[4][tid], PHo.p[0][2], z);
+          cy += corr<true>(dxz, czh.ik, czh.b, czh.c, sPH[5][tid], PHo.p[1][2], z);
+        }
       }
       hx = hk[0][ey][ex] - S * cx;
       hy = hk[1][ey][ex] - S * cy;
@@ -264,31 +382,28 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
     if (hrow || hcol) {
       const int r = hey, c = hex;
-      const bool hl = (sXh & sYh & sZ) >= 0;
-      const int hzx = sXh >= 0 ? zx_of(g, yh, k, sXh) : 0, hzy = sYh >= 0 ? zy_of(g, xh, k, sYh) : 0;
-      const int hzz = sZ >= 0 ? zz_of(g, xh, yh, sZ) : 0;
       const float dyx = ek[1][r][c + 1] - ek[1][r][c], dxy = ek[0][r + 1][c] - ek[0][r][c];
+      const Coef chx = coef_at(tabX, 3, hrx), chy = coef_at(tabY, 3, hry);
       float cz = dyx - dxy;
-      if (hl)
-        cz += corr<false>(dyx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[2][0], nullptr, hzx) -
-              corr<false>(dxy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[2][1], nullptr, hzy);
+      if (sXh >= 0) cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sPH[6][tid], nullptr, 0);
+      if (sYh >= 0) cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sPH[7][tid], nullptr, 0);
       sH[2][hry][hrx] = hk[2][r][c] - S * cz;
       if (hrow) {  // Hx
         const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
         float cx = dzy - dyz;
-        if (hl)
-          cx += corr<false>(dzy, ikYhh, sYh, T.b[1][1], T.c[1][1], yh, PHi.p[0][1], nullptr, hzy) -
-                corr<false>(dyz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[0][2], nullptr, hzz);
+        if (sYh >= 0) cx += corr<false>(dzy, chy.ik, chy.b, chy.c, sPH[8][tid], nullptr, 0);
+        if (sZ >= 0) cx -= corr<false>(dyz, czh.ik, czh.b, czh.c, sPH[9][tid], nullptr, 0);
         sH[0][hry][hrx] = hk[0][r][c] - S * cx;
       } else {  // Hy
         const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
         float cy = dxz - dzx;
-        if (hl)
-          cy += corr<false>(dxz, ikZh, sZ, T.b[2][1], T.c[2][1], k, PHi.p[1][2], nullptr, hzz) -
-                corr<false>(dzx, ikXhh, sXh, T.b[0][1], T.c[0][1], xh, PHi.p[1][0], nullptr, hzx);
+        if (sZ >= 0) cy += corr<false>(dxz, czh.ik, czh.b, czh.c, sPH[8][tid], nullptr, 0);
+        if (sXh >= 0) cy -= corr<false>(dzx, chx.ik, chx.b, chx.c, sPH[9][tid], nullptr, 0);
         sH[1][hry][hrx] = hk[1][r][c] - S * cy;
       }
     }
+    if (k + 1 < k1) fetch_psiH(k + 1);
+    else cp_commit();
     if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
     if (fseg > 0xff) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
     if (k == fz0 || k == fz1) {
@@ -302,6 +417,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       async_proxy_fence();
       R.issue(M, (it - 1) % NSTAGE, i0, j0, k - 1 + NSTAGE);
     }
+    cp_wait_all_but_one();  // psi_old of E at plane k
 
     // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
     // sources and detectors
@@ -313,15 +429,25 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
       float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
       if (lay) {
-        if (j > 0 && k > 0)
-          cx += corr<true>(d1x, ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[0][1], PEo.p[0][1], zy) -
-                corr<true>(d2x, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[0][2], PEo.p[0][2], zz);
-        if (i > 0 && k > 0)
-          cy += corr<true>(d1y, ikZe, sZ, T.b[2][0], T.c[2][0], k, PEi.p[1][2], PEo.p[1][2], zz) -
-                corr<true>(d2y, ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[1][0], PEo.p[1][0], zx);
-        if (i > 0 && j > 0)
-          cz += corr<true>(d1z, ikXe, sX, T.b[0][0], T.c[0][0], i, PEi.p[2][0], PEo.p[2][0], zx) -
-                corr<true>(d2z, ikYe, sY, T.b[1][0], T.c[1][0], j, PEi.p[2][1], PEo.p[2][1], zy);
+        // (a component held by a PEC wall keeps psi = 0: its memory is neither updated nor used)
+        const bool ux = j > 0 && k > 0, uy = i > 0 && k > 0, uz = i > 0 && j > 0;
+        if (sX >= 0) {
+          const Coef c = coef_at(tabX, 0, rx);
+          const int z = zx_of(g, j, k, sX);
+          if (uy) cy -= corr<true>(d2y, c.ik, c.b, c.c, sPE[0][tid], PEo.p[1][0], z);
+          if (uz) cz += corr<true>(d1z, c.ik, c.b, c.c, sPE[1][tid], PEo.p[2][0], z);
+        }
+        if (sY >= 0) {
+          const Coef c = coef_at(tabY, 0, ry);
+          const int z = zy_of(g, i, k, sY);
+          if (ux) cx += corr<true>(d1x, c.ik, c.b, c.c, sPE[2][tid], PEo.p[0][1], z);
+          if (uz) cz -= corr<true>(d2z, c.ik, c.b, c.c, sPE[3][tid], PEo.p[2][1], z);
+        }
+        if (sZ >= 0) {
+          const int z = zz_of(g, i, j, sZ);
+          if (ux) cx -= corr<true>(d2x, cze.ik, cze.b, cze.c, sPE[4][tid], PEo.p[0][2], z);
+          if (uy) cy += corr<true>(d1y, cze.ik, cze.b, cze.c, sPE[5][tid], PEo.p[1][2], z);
+        }
       }
       if (j > 0 && k > 0) exv += Sa * cx;
       if (i > 0 && k > 0) eyv += Sa * cy;
@@ -357,9 +483,12 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
         }
       }
     }
+    if (k + 1 < k1) fetch_psiE(k + 1);
+    else cp_commit();
     hxm = hx;
     hym = hy;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   if (!waited) atomicOr(A.status, 1);
   __syncthreads();  // the stages are free for the flux reduction
 
