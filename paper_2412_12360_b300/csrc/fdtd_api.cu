@@ -816,6 +816,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       const int v = std::atoi(e);
       if (v >= 1) h->tz = std::min(v, n[2]);
     }
+    h->tz = std::min(h->tz, fused_max_tz());
   }
   if ((rc = dev_alloc(h, (void**)&h->fields, 2 * 6 * g.vol * 4)) != FDTD_OK) return cleanup(rc);
   if ((rc = dev_alloc(h, (void**)&h->a, g.vol * 4)) != FDTD_OK) return cleanup(rc);

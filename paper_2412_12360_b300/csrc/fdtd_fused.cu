@@ -100,9 +100,13 @@ constexpr int PH_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);    // [NPH][NT]
 constexpr int PE_OFF = PH_OFF + NPH * NT * 4;                     // [NPE][NT]
 constexpr int TX_OFF = PE_OFF + NPE * NT * 4;                     // [6][TABX]
 constexpr int TY_OFF = TX_OFF + 6 * TABX * 4;                     // [6][TABY]
-constexpr int BAR_OFF = round128(TY_OFF + 6 * TABY * 4);          // NSTAGE mbarriers
+// per-plane flags of the block's z-chunk: bit 0 a source, bit 1 a detector, bit 2 a z-face of the
+// record meets the tile at that plane (uniform over the block, so planes without any cost one load)
+constexpr int MAXTZ = 1024;
+constexpr int PF_OFF = TY_OFF + 6 * TABY * 4;                     // [MAXTZ] bytes
+constexpr int WF_OFF = round128(PF_OFF + MAXTZ);                  // flux sums per warp: [kMaxDet][NT/32]
+constexpr int BAR_OFF = round128(WF_OFF + kMaxDet * (NT / 32) * 8);  // NSTAGE mbarriers
 constexpr int SMEM_BYTES = BAR_OFF + NSTAGE * 8 + 128;             // + slack to align the base
-static_assert(NT * 8 <= STAGE_BYTES, "the flux reduction reuses the first stage");
 
 struct Ring {
   unsigned char* base;
@@ -141,7 +145,8 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PE_OFF);
   float(*tabX)[TABX] = reinterpret_cast<float(*)[TABX]>(sm + TX_OFF);
   float(*tabY)[TABY] = reinterpret_cast<float(*)[TABY]>(sm + TY_OFF);
-  double* sred = reinterpret_cast<double*>(sm);
+  unsigned char* pflag = sm + PF_OFF;
+  double(*wflux)[NT / 32] = reinterpret_cast<double(*)[NT / 32]>(sm + WF_OFF);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -177,6 +182,30 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     const float* src = w == 0 ? T.b[ax][hf] : (w == 1 ? T.c[ax][hf] : T.ik[ax][hf]);
     (isx ? tabX[row] : tabY[row])[col] = src[pos];
   }
+  {
+    // epilogue flags of the chunk's planes for this tile
+    const int xa = i0, xb = min(i0 + TX, nx), ya = j0, yb = min(j0 + TY, ny);
+    for (int p = tid; p < k1 - k0; p += NT) {
+      const int k = k0 + p;
+      int f = 0;
+      for (int s = 0; s < A.nsrc; ++s) {
+        const SrcDev& sd = A.src[s];
+        if (k >= sd.lo[2] && k < sd.hi[2] && sd.lo[0] < xb && sd.hi[0] > xa && sd.lo[1] < yb && sd.hi[1] > ya) f |= 1;
+      }
+      for (int s = 0; s < A.ndet; ++s) {
+        const DetDev& d = A.det[s];
+        if (k >= d.lo[2] && k < d.hi[2] && d.lo[0] < xb && d.hi[0] > xa && d.lo[1] < yb && d.hi[1] > ya) f |= 2;
+      }
+      if (A.rec)
+        for (int s = 0; s < A.faces.nseg; ++s) {
+          const FaceSeg& sg = A.faces.seg[s];
+          if (sg.axis == 2 && sg.idx == k && sg.lo1 < xb && sg.lo1 + sg.n1 > xa && sg.lo2 < yb && sg.lo2 + sg.n2 > ya)
+            f |= 4;
+        }
+      pflag[p] = (unsigned char)f;
+    }
+    if (tid < kMaxDet * (NT / 32)) wflux[tid / (NT / 32)][tid % (NT / 32)] = 0.0;
+  }
   __syncthreads();
 
   // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
@@ -192,22 +221,9 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
   const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
 
-  // membership of this column in the source and detector boxes (bit s), and face segments
-  unsigned src_xy = 0, det_xy = 0;
-  for (int s = 0; s < A.nsrc; ++s) {
-    const SrcDev& sd = A.src[s];
-    if (own && i >= sd.lo[0] && i < sd.hi[0] && j >= sd.lo[1] && j < sd.hi[1]) src_xy |= 1u << s;
-  }
-  for (int s = 0; s < A.ndet; ++s) {
-    const DetDev& d = A.det[s];
-    if (own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1]) det_xy |= 1u << s;
-  }
-  // (a column lies on at most one x- or y-face line, i.e. two segments; z-faces are at most two
-  // planes, each with an Hx and an Hy segment). Only segment numbers are kept; offsets are computed
-  // when a face value is written.
-  int fseg = -1;              // x/y face: segment numbers a | b << 8
-  int fz0 = -1, fz1 = -1;     // z-face planes through this column
-  int fzseg = 0;              // their segments: plane 0 (x, y), plane 1 (x, y), 8 bits each
+  // x- and y-face segments of the record through this column (a column lies on at most one x- or
+  // y-face line, i.e. two segments: a | b << 8, -1 if none); z-faces are found per flagged plane
+  int fseg = -1;
   if (A.rec && own) {
     int na = 0;
     for (int s = 0; s < A.faces.nseg; ++s) {
@@ -216,17 +232,9 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
           (sg.axis == 1 && j == sg.idx && i >= sg.lo2 && i < sg.lo2 + sg.n2)) {
         fseg = (na == 0) ? s : ((fseg & 0xff) | (s << 8));
         ++na;
-      } else if (sg.axis == 2 && i >= sg.lo1 && i < sg.lo1 + sg.n1 && j >= sg.lo2 && j < sg.lo2 + sg.n2) {
-        const int pl = (fz0 < 0 || fz0 == sg.idx) ? 0 : 1;
-        if (pl == 0) fz0 = sg.idx; else fz1 = sg.idx;
-        fzseg |= s << (8 * (2 * pl + sg.comp));
       }
     }
   }
-
-  double facc[kMaxDet];
-#pragma unroll
-  for (int q = 0; q < kMaxDet; ++q) facc[q] = 0.0;
 
   const PsiSet& PHi = A.psiH_cur;
   const PsiSet& PHo = A.psiH_nxt;
@@ -330,11 +338,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       czh = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
       cze = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
     }
-    unsigned src_k = 0, det_k = 0;  // sources and detectors whose z-range holds this plane
-    if (src_xy)
-      for (int s = 0; s < A.nsrc; ++s) src_k |= (k >= A.src[s].lo[2] && k < A.src[s].hi[2]) ? 1u << s : 0u;
-    if (det_xy)
-      for (int s = 0; s < A.ndet; ++s) det_k |= (k >= A.det[s].lo[2] && k < A.det[s].hi[2]) ? 1u << s : 0u;
+    const int pf = pflag[k - k0];
     waited &= mbar_wait(&R.bar[b1], ((it + 1) / NSTAGE) & 1);  // plane k+1 (plane k was waited for before)
     cp_wait_all_but_one();                                      // psi_old of H at plane k
     const float(*ek)[EH][EW] = R.E(b0);
@@ -406,10 +410,9 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     else cp_commit();
     if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
     if (fseg > 0xff) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
-    if (k == fz0 || k == fz1) {
-      const int sh = (k == fz0) ? 0 : 16;
-      face_write(A, (fzseg >> sh) & 0xff, i, j, k, hx, hy, hz);
-      face_write(A, (fzseg >> (sh + 8)) & 0xff, i, j, k, hx, hy, hz);
+    if (pf & 4) {
+      for (int s = 0; s < A.faces.nseg; ++s)
+        if (own && A.faces.seg[s].axis == 2 && A.faces.seg[s].idx == k) face_write(A, s, i, j, k, hx, hy, hz);
     }
     __syncthreads();
     // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
@@ -421,9 +424,12 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
 
     // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
     // sources and detectors
+    float exv = 0.f, eyv = 0.f, ezv = 0.f;
     if (own) {
       const float Sa = S * R.Av(b0)[ty][tx];
-      float exv = ek[0][ey][ex], eyv = ek[1][ey][ex], ezv = ek[2][ey][ex];
+      exv = ek[0][ey][ex];
+      eyv = ek[1][ey][ex];
+      ezv = ek[2][ey][ex];
       const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
       const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
       const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
@@ -452,10 +458,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       if (j > 0 && k > 0) exv += Sa * cx;
       if (i > 0 && k > 0) eyv += Sa * cy;
       if (i > 0 && j > 0) ezv += Sa * cz;
-      if (src_xy & src_k) {
+      if (pf & 1) {
         for (int s = 0; s < A.nsrc; ++s) {
           const SrcDev& sd = A.src[s];
-          if (!(((src_xy & src_k) >> s) & 1u)) continue;
+          if (i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2]) continue;
           const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
           if (sd.comp == 0) exv += v;
           else if (sd.comp == 1) eyv += v;
@@ -465,21 +471,27 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       N.f[0][q] = exv;
       N.f[1][q] = eyv;
       N.f[2][q] = ezv;
-      if (det_xy & det_k) {
+    }
+    // detectors (block-uniform branch; flux partials are reduced over the warp in a fixed order and
+    // summed per warp over the planes)
+    if (pf & 2) {
 #pragma unroll
-        for (int s = 0; s < kMaxDet; ++s) {
-          if (s >= A.ndet) break;
-          const DetDev& d = A.det[s];
-          if (!(((det_xy & det_k) >> s) & 1u)) continue;
-          if (d.kind == 0) {
-            A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
-          } else if (d.kind == 1) {
-            A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
-          } else {
-            const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
-            facc[s] += (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
-                       (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz);
-          }
+      for (int s = 0; s < kMaxDet; ++s) {
+        if (s >= A.ndet) break;
+        const DetDev& d = A.det[s];
+        const bool in = own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1] && k >= d.lo[2] && k < d.hi[2];
+        if (d.kind == 0) {
+          if (in) A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
+        } else if (d.kind == 1) {
+          if (in) A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
+        } else if (k >= d.lo[2] && k < d.hi[2]) {
+          const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
+          double f = in ? (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
+                              (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz)
+                        : 0.0;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+          if (tx == 0) wflux[s][ty] += f;
         }
       }
     }
@@ -490,29 +502,24 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (!waited) atomicOr(A.status, 1);
-  __syncthreads();  // the stages are free for the flux reduction
+  __syncthreads();  // every warp's flux sums are in place
 
-  // flux detectors: fixed-order block reduction into this block's slot
+  // flux detectors: this block's partial sum (warp sums in warp order) into its slot
+  if (tid == 0) {
 #pragma unroll
-  for (int s = 0; s < kMaxDet; ++s) {
-    if (s >= A.ndet) break;
-    const DetDev& d = A.det[s];
-    if (d.kind != 2) continue;
-    const int bx0 = d.lo[0] / TX, bx1 = (d.hi[0] - 1) / TX;
-    const int by0 = d.lo[1] / TY, by1 = (d.hi[1] - 1) / TY;
-    const int bz0 = d.lo[2] / A.tz, bz1 = (d.hi[2] - 1) / A.tz;
-    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
-    if (bx < bx0 || bx > bx1 || by < by0 || by > by1 || bz < bz0 || bz > bz1) continue;
-    __syncthreads();
-    sred[tid] = facc[s];
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-      if (tid < w) sred[tid] += sred[tid + w];
-      __syncthreads();
-    }
-    if (tid == 0) {
+    for (int s = 0; s < kMaxDet; ++s) {
+      if (s >= A.ndet) break;
+      const DetDev& d = A.det[s];
+      if (d.kind != 2) continue;
+      const int bx0 = d.lo[0] / TX, bx1 = (d.hi[0] - 1) / TX;
+      const int by0 = d.lo[1] / TY, by1 = (d.hi[1] - 1) / TY;
+      const int bz0 = d.lo[2] / A.tz, bz1 = (d.hi[2] - 1) / A.tz;
+      const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+      if (bx < bx0 || bx > bx1 || by < by0 || by > by1 || bz < bz0 || bz > bz1) continue;
+      double sum = 0.0;
+      for (int w = 0; w < NT / 32; ++w) sum += wflux[s][w];
       const int64_t slotid = ((int64_t)(bz - bz0) * (by1 - by0 + 1) + (by - by0)) * (bx1 - bx0 + 1) + (bx - bx0);
-      A.partial[d.poff + (int64_t)A.step * d.nblk + slotid] = sred[0];
+      A.partial[d.poff + (int64_t)A.step * d.nblk + slotid] = sum;
     }
   }
 }
@@ -520,6 +527,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
 }  // namespace
 
 int fused_tile_x() { return TX; }
+int fused_max_tz() { return MAXTZ; }
 int fused_tile_y() { return TY; }
 
 MapBox fwd_box_e() { return {EW, EH}; }
