@@ -62,12 +62,14 @@ __device__ __forceinline__ int zz_of(const Geo& g, int x, int y, int s) { return
 __device__ __forceinline__ float pick3(int c, float a, float b, float d) { return c == 0 ? a : (c == 1 ? b : d); }
 
 // Write this cell's H into face segment s of the record if (i, j, k) lies on it.
-__device__ __noinline__ void face_write(const FwdArgs& A, int s, int i, int j, int k, float hx, float hy, float hz) {
+__device__ __forceinline__ void face_write(const FwdArgs& A, int s, int i, int j, int k, float hx, float hy, float hz) {
   const FaceSeg& sg = A.faces.seg[s];
-  const int p[3] = {i, j, k};
-  const int a1 = (sg.axis + 1) % 3, a2 = (sg.axis + 2) % 3;
-  if (p[sg.axis] != sg.idx) return;
-  const int u = p[a1] - sg.lo1, v = p[a2] - sg.lo2;
+  const int ax = sg.axis;
+  const int pa = ax == 0 ? i : (ax == 1 ? j : k);
+  const int p1 = ax == 0 ? j : (ax == 1 ? k : i);  // along e1 = axis + 1
+  const int p2 = ax == 0 ? k : (ax == 1 ? i : j);  // along e2 = axis + 2
+  if (pa != sg.idx) return;
+  const int u = p1 - sg.lo1, v = p2 - sg.lo2;
   if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) return;
   A.rec[sg.off + (int64_t)v * sg.n1 + u] = sg.comp == 0 ? hx : (sg.comp == 1 ? hy : hz);
 }
