@@ -164,6 +164,8 @@ int fdtd_set_byte_budget(int64_t bytes);
 #define FDTD_KERNEL_REV_H 3        /* reverse: inverse H, adjoint into E-bar */
 #define FDTD_KERNEL_FUSED_FWD 4    /* forward H and E of one step in one sweep */
 #define FDTD_KERNEL_FUSED_REV 5    /* reverse step in one sweep */
+#define FDTD_KERNEL_FACE_COPY 6    /* boundary-face record (forward) or replay (reverse) of one step */
+#define FDTD_KERNEL_DET_ADJ 7      /* detector adjoints of one reverse step */
 #define FDTD_KERNEL_KINDS 8
 
 /* Number of kernels this handle has launched since creation (or -1). */

@@ -561,7 +561,6 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   for (int q = 0; q < fa.ndet; ++q) fa.det[q] = h->dets[q];
   fa.det_out = h->det_out;
   fa.partial = h->partial;
-  fa.faces = h->faces;
   fa.status = h->status;
   for (int n = 0; n < nsteps; ++n) {
     const int c = h->cur, x = 1 - c;
@@ -572,13 +571,17 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     fa.psiH_cur = h->psi_set(h->psiH + c * pf);
     fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
     fa.step = n;
-    fa.rec = faces ? h->face_hist + (int64_t)n * h->faces.per_step : nullptr;
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
       launch_fwd_fused(fa, h->fmaps[c], st);
     }
     launches += 1;
     const Fields Fn = h->F(x);
+    if (faces) {  // H^{n+1/2} on the boundary faces
+      ProfScope ps(h, evs, st, FDTD_KERNEL_FACE_COPY, n);
+      launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, st);
+      launches += 1;
+    }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
     for (size_t q = kMaxDet; q < h->dets.size(); ++q, ++launches)
       launch_detector_sample(g, Fn, h->dets[q], n, h->det_out, h->partial, st);
@@ -592,9 +595,9 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   return launches;
 }
 
-// Reverse (Sec. 2.2): per step, the detector adjoints, then the inverse-E / adjoint-H kernel (which also
-// replays the face record and removes the sources) and the inverse-H / adjoint-E kernel, in place on
-// the current field buffer.
+// Reverse (Sec. 2.2): per step, the detector adjoints, the face record of the step written back into H,
+// the inverse-E / adjoint-H kernel (which also removes the sources) and the inverse-H / adjoint-E
+// kernel, in place on the current field buffer.
 int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
@@ -616,7 +619,6 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     ra.dhi[d] = h->design_hi[d];
   }
   ra.dLda = h->dLda;
-  ra.faces = h->faces;
   ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
   ra.status = h->status;
@@ -624,11 +626,18 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   int64_t launches = 0;
   int pb = 0;
   for (int n = nsteps - 1; n >= 0; --n) {
-    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
-    launches += (int64_t)h->dets.size();
+    if (!h->dets.empty()) {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
+      for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
+      launches += (int64_t)h->dets.size();
+    }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
     ra.step = n;
-    ra.rec = h->faces.per_step > 0 ? h->face_hist + (int64_t)n * h->faces.per_step : nullptr;
+    if (h->faces.per_step > 0) {  // H^{n+1/2} on the boundary faces, from the record
+      ProfScope ps(h, evs, st, FDTD_KERNEL_FACE_COPY, n);
+      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, st);
+      launches += 1;
+    }
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
       ra.pin = PEb[pb];

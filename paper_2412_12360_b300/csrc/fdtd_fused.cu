@@ -1,20 +1,21 @@
 // Fused forward step of arXiv 2412.12360 Sec. 2.1: the H update (Eq. 1) and the E update (Eq. 2) of
-// one time step in a single sweep over the grid, with the CPML memories, the soft sources, the
-// detectors and the boundary-face record (Sec. 2.2) as epilogues of the same sweep.
+// one time step in a single sweep over the grid, with the CPML memories, the soft sources and the
+// detectors as epilogues of the same sweep.
 //
-// Each block owns a TX x TY column tile and marches a chunk of TZ z-planes. Per plane it stages
-// E^n of the tile plus a one-cell halo in shared memory (planes k and k+1 in flight), computes
-// H^{n+1/2} for its cells and, redundantly, for the halo column x = i0-1 and row y = j0-1 that its
-// E update reads, then computes E^{n+1}. Fields are double-buffered (read `cur`, write `nxt`) so
-// neighbouring tiles never see a half-updated field; every cell is read and written once per step
-// from HBM (52 bytes per cell) and the halos come from L1/L2.
+// Each block owns a TX x TY column tile and marches a chunk of z-planes upwards. The planes arrive
+// through a ring of shared-memory stages that the TMA unit fills (one thread issues the bulk tensor
+// copies of E^n with a one-cell halo, H^{n-1/2} with the low halo, and a; the block waits on one
+// mbarrier per stage), so the loads of the next planes are in flight while a plane is computed.
+// Per plane the block computes H^{n+1/2} for its cells and, redundantly, for the halo column
+// x = i0-1 and row y = j0-1 that its E update reads, then E^{n+1}. Fields are double-buffered (read
+// `cur`, write `nxt`) so neighbouring tiles never see a half-updated field; every cell is read and
+// written once per step from HBM (52 bytes per cell) and the halos come from L2.
 //
-// The march is software-pipelined: while plane k is computed, the loads of E^n for plane k+2 and of
-// H^{n-1/2} and a for plane k+1 are already in flight. Everything that depends only on x and y (CPML
-// coefficients, slab indices, source, detector and face membership) is computed once per thread;
-// what depends on z once per plane. Every cell takes the plain Yee update; cells in a CPML layer add
-// the correction (1/kappa - 1) d + psi per curl term, which is exactly 0 off the layers and on their
-// inner edge, so the PML-free region R is updated by the plain formula the inverse step mirrors.
+// Every cell takes the plain Yee update; cells in a CPML layer add the correction
+// (1/kappa - 1) d + psi per curl term, which is exactly 0 off the layers and on their inner edge, so
+// the PML-free region R is updated by the plain formula the inverse step mirrors. The CPML memories a
+// cell needs are copied ahead by its thread (cp.async into private shared-memory slots) one phase
+// before use. Sources and detectors are decided per plane from flags the block computes once.
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 #include "fdtd_tma.cuh"
@@ -61,19 +62,6 @@ __device__ __forceinline__ int zz_of(const Geo& g, int x, int y, int s) { return
 
 __device__ __forceinline__ float pick3(int c, float a, float b, float d) { return c == 0 ? a : (c == 1 ? b : d); }
 
-// Write this cell's H into face segment s of the record if (i, j, k) lies on it.
-__device__ __forceinline__ void face_write(const FwdArgs& A, int s, int i, int j, int k, float hx, float hy, float hz) {
-  const FaceSeg& sg = A.faces.seg[s];
-  const int ax = sg.axis;
-  const int pa = ax == 0 ? i : (ax == 1 ? j : k);
-  const int p1 = ax == 0 ? j : (ax == 1 ? k : i);  // along e1 = axis + 1
-  const int p2 = ax == 0 ? k : (ax == 1 ? i : j);  // along e2 = axis + 2
-  if (pa != sg.idx) return;
-  const int u = p1 - sg.lo1, v = p2 - sg.lo2;
-  if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) return;
-  A.rec[sg.off + (int64_t)v * sg.n1 + u] = sg.comp == 0 ? hx : (sg.comp == 1 ? hy : hz);
-}
-
 __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
 }
@@ -102,8 +90,8 @@ constexpr int PH_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);    // [NPH][NT]
 constexpr int PE_OFF = PH_OFF + NPH * NT * 4;                     // [NPE][NT]
 constexpr int TX_OFF = PE_OFF + NPE * NT * 4;                     // [6][TABX]
 constexpr int TY_OFF = TX_OFF + 6 * TABX * 4;                     // [6][TABY]
-// per-plane flags of the block's z-chunk: bit 0 a source, bit 1 a detector, bit 2 a z-face of the
-// record meets the tile at that plane (uniform over the block, so planes without any cost one load)
+// per-plane flags of the block's z-chunk: bit 0 a source, bit 1 a detector meets the tile at that
+// plane (uniform over the block, so planes without either cost one load)
 constexpr int MAXTZ = 1024;
 constexpr int PF_OFF = TY_OFF + 6 * TABY * 4;                     // [MAXTZ] bytes
 constexpr int WF_OFF = round128(PF_OFF + MAXTZ);                  // flux sums per warp: [kMaxDet][NT/32]
@@ -198,12 +186,6 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
         const DetDev& d = A.det[s];
         if (k >= d.lo[2] && k < d.hi[2] && d.lo[0] < xb && d.hi[0] > xa && d.lo[1] < yb && d.hi[1] > ya) f |= 2;
       }
-      if (A.rec)
-        for (int s = 0; s < A.faces.nseg; ++s) {
-          const FaceSeg& sg = A.faces.seg[s];
-          if (sg.axis == 2 && sg.idx == k && sg.lo1 < xb && sg.lo1 + sg.n1 > xa && sg.lo2 < yb && sg.lo2 + sg.n2 > ya)
-            f |= 4;
-        }
       pflag[p] = (unsigned char)f;
     }
     if (tid < kMaxDet * (NT / 32)) wflux[tid / (NT / 32)][tid % (NT / 32)] = 0.0;
@@ -222,21 +204,6 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int sX = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
   const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
   const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
-
-  // x- and y-face segments of the record through this column (a column lies on at most one x- or
-  // y-face line, i.e. two segments: a | b << 8, -1 if none); z-faces are found per flagged plane
-  int fseg = -1;
-  if (A.rec && own) {
-    int na = 0;
-    for (int s = 0; s < A.faces.nseg; ++s) {
-      const FaceSeg& sg = A.faces.seg[s];
-      if ((sg.axis == 0 && i == sg.idx && j >= sg.lo1 && j < sg.lo1 + sg.n1) ||
-          (sg.axis == 1 && j == sg.idx && i >= sg.lo2 && i < sg.lo2 + sg.n2)) {
-        fseg = (na == 0) ? s : ((fseg & 0xff) | (s << 8));
-        ++na;
-      }
-    }
-  }
 
   const PsiSet& PHi = A.psiH_cur;
   const PsiSet& PHo = A.psiH_nxt;
@@ -410,12 +377,6 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     }
     if (k + 1 < k1) fetch_psiH(k + 1);
     else cp_commit();
-    if (fseg >= 0) face_write(A, fseg & 0xff, i, j, k, hx, hy, hz);
-    if (fseg > 0xff) face_write(A, fseg >> 8, i, j, k, hx, hy, hz);
-    if (pf & 4) {
-      for (int s = 0; s < A.faces.nseg; ++s)
-        if (own && A.faces.seg[s].axis == 2 && A.faces.seg[s].idx == k) face_write(A, s, i, j, k, hx, hy, hz);
-    }
     __syncthreads();
     // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
     if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {

@@ -93,8 +93,6 @@ struct FwdArgs {
   DetDev det[kMaxDet];
   double* det_out;
   double* partial;
-  float* rec;              // this step's face record, or nullptr
-  FaceSet faces;
   int* status;             // device status word: bit 0 set when a bounded wait gave up
 };
 
@@ -127,6 +125,7 @@ void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, f
 void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,
                             double* partial, cudaStream_t s);
 void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s);
+void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record, cudaStream_t s);
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
@@ -144,8 +143,6 @@ struct RevArgs {
   int tz;
   int dlo[3], dhi[3];      // design box
   double* dLda;
-  const float* rec;        // face record of this step (rev_E), or nullptr
-  FaceSet faces;
   int nsrc;
   SrcDev src[kMaxSrc];
   int* status;             // device status word: bit 0 set when a bounded wait gave up

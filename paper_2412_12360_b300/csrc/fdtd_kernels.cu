@@ -2,6 +2,8 @@
 // detectors beyond the fused kernels' slots, the fixed-order flux sums, the detector adjoints of the
 // reverse sweep (the transpose of each sampling, Sec. 2.2 of arXiv 2412.12360), the density map
 // eps = eps_lo + (eps_hi - eps_lo) rho, the dL/deps finalisation and field packing.
+#include <algorithm>
+
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -33,12 +35,14 @@ __device__ __forceinline__ bool cell_of(const Geo& g, int p[3]) {
   return p[0] < g.n[0] && p[1] < g.n[1];
 }
 
-__device__ __forceinline__ bool box_cell(const int lo[3], const int hi[3], int64_t m, int p[3]) {
+__device__ __forceinline__ bool box_cell(const int lo[3], const int hi[3], int64_t m64, int p[3]) {
+  // 32-bit arithmetic: a box holds fewer than 2^31 cells (it lies inside a grid that does)
+  const int m = (int)m64;
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1];
-  p[0] = lo[0] + int(m % bx);
-  const int64_t r = m / bx;
-  p[1] = lo[1] + int(r % by);
-  p[2] = lo[2] + int(r / by);
+  p[0] = lo[0] + m % bx;
+  const int r = m / bx;
+  p[1] = lo[1] + r % by;
+  p[2] = lo[2] + r / by;
   return p[2] < hi[2];
 }
 
@@ -103,6 +107,24 @@ __global__ void k_flux_finalize(DetDev d, int nsteps, const double* partial, dou
   double s = 0.0;
   for (int b = 0; b < d.nblk; ++b) s += partial[d.poff + (int64_t)n * d.nblk + b];
   out[d.off + n] = s;
+}
+
+// Boundary-face record of one step (Sec. 2.2): the tangential H on the planes just outside the PML-free
+// region, segment by segment. Within a segment the elements run along x where the segment spans x
+// (y- and z-faces), else along y, so that the field side of the copy is coalesced wherever it can be.
+__global__ void k_face_copy(Geo g, Fields F, FaceSet fs, float* __restrict__ rec, int to_record) {
+  const FaceSeg& sg = fs.seg[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // a face segment holds fewer than 2^31 cells
+  if (t >= sg.n1 * sg.n2) return;
+  const int nf = sg.axis == 1 ? sg.n2 : sg.n1;  // extent along the fast axis
+  const int f = t % nf, sl = t / nf;
+  int x, y, z;
+  if (sg.axis == 0) { x = sg.idx; y = sg.lo1 + f; z = sg.lo2 + sl; }
+  else if (sg.axis == 1) { y = sg.idx; x = sg.lo2 + f; z = sg.lo1 + sl; }
+  else { z = sg.idx; x = sg.lo1 + f; y = sg.lo2 + sl; }
+  float* h = F.f[3 + sg.comp] + cell_index(g, x, y, z);
+  if (to_record) rec[sg.off + t] = *h;
+  else *h = rec[sg.off + t];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -200,6 +222,14 @@ void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int 
 void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s) {
   if (nsteps <= 0) return;
   k_flux_finalize<<<blocks_for(nsteps, 128), 128, 0, s>>>(d, nsteps, partial, out);
+}
+
+void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record, cudaStream_t s) {
+  int64_t mx = 0;
+  for (int q = 0; q < fs.nseg; ++q) mx = std::max<int64_t>(mx, (int64_t)fs.seg[q].n1 * fs.seg[q].n2);
+  if (fs.nseg == 0 || mx == 0) return;
+  dim3 grid((unsigned)((mx + 255) / 256), fs.nseg);
+  k_face_copy<<<grid, 256, 0, s>>>(g, F, fs, rec, to_record);
 }
 
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,

@@ -10,8 +10,8 @@
 // Each kernel reads only fields it does not write (rev_E reads H and Ebar and writes E and Hbar;
 // rev_H reads E and Hbar and writes H and Ebar), so in-place updates are race-free. Blocks own a
 // TX x TY column tile and march their z-chunk downwards, so the coefficient of the plane above is
-// carried in registers. The tangential H recorded on the six boundary planes (Sec. 2.2) is
-// substituted while H is staged, which replays the face record without a separate kernel.
+// carried in registers. The tangential H recorded on the six boundary planes (Sec. 2.2) is written
+// back into H by a copy kernel before each rev_E.
 //
 // The adjoint coefficients of one E point (component c, its transverse axes c1 = c+1, c2 = c+2):
 //   u = S a Ebar_c (zero where E_c is held by a PEC wall),
@@ -20,7 +20,10 @@
 // and Hbar_h(p) += P1_{h+1}(p) - P1_{h+1}(p + e_{h+2}) + P2_{h+2}(p) - P2_{h+2}(p + e_{h+1}).
 // Those of one H point mirror them with w = -S Hbar_h and the H tables, giving
 //   Ebar_e(p) += Q1_{e+1}(p - e_{e+2}) - Q1_{e+1}(p) + Q2_{e+2}(p - e_{e+1}) - Q2_{e+2}(p).
-// Off the layers 1/kappa = 1 and c = 0, so P and Q reduce to +-u and +-w.
+// Off the layers 1/kappa = 1 and c = 0, so P and Q reduce to +-u and +-w: the kernels gather those
+// plain values for every point and add, for each axis d whose layer holds the point or the
+// neighbour along d, the correction sgn v (1/kappa_d - 1) + c_d (psibar + sgn v) of the coefficients
+// along d (exactly 0 on the layer's inner edge).
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 #include "fdtd_tma.cuh"
@@ -41,82 +44,9 @@ __device__ __forceinline__ int zd_of(const Geo& g, int x, int y, int k, int s) {
   return D == 0 ? zx_of(g, y, k, s) : (D == 1 ? zy_of(g, x, k, s) : zz_of(g, x, y, s));
 }
 
-// One adjoint coefficient: sgn * v * ik + c (psi_old + sgn * v) inside the layer (s >= 0).
-template <int D, int HALF>
-__device__ __forceinline__ float acoef(const Tables& T, float v, float sgn, float ik, int s, int pos,
-                                       const float* __restrict__ psi, int z) {
-  float r = sgn * v * ik;
-  if (s >= 0) r += T.c[D][HALF][pos] * (psi[z] + sgn * v);
-  return r;
-}
-
-// psi-bar update at the own point: psi_new = b (psi_old + sgn * v)
-template <int D, int HALF>
-__device__ __forceinline__ void apsi(const Tables& T, float v, float sgn, int s, int pos, const float* __restrict__ pin,
-                                     float* pout, int z) {
-  if (s >= 0) pout[z] = T.b[D][HALF][pos] * (pin[z] + sgn * v);
-}
-
-// Face segments (of the boundary record) through the column (x, y): x- and y-faces give at most two
-// segments, packed a | b << 8 (-1 if none); z-faces give at most two planes, each with an x and a
-// y segment, packed into zseg (plane 0 x, plane 0 y, plane 1 x, plane 1 y; 8 bits each).
-__device__ __forceinline__ void face_segments(const FaceSet& fs, int x, int y, int& seg, int& z0, int& z1, int& zseg) {
-  seg = -1;
-  z0 = z1 = -1;
-  zseg = 0;
-  int na = 0;
-  for (int s = 0; s < fs.nseg; ++s) {
-    const FaceSeg& sg = fs.seg[s];
-    if ((sg.axis == 0 && x == sg.idx && y >= sg.lo1 && y < sg.lo1 + sg.n1) ||
-        (sg.axis == 1 && y == sg.idx && x >= sg.lo2 && x < sg.lo2 + sg.n2)) {
-      seg = (na == 0) ? s : ((seg & 0xff) | (s << 8));
-      ++na;
-    } else if (sg.axis == 2 && x >= sg.lo1 && x < sg.lo1 + sg.n1 && y >= sg.lo2 && y < sg.lo2 + sg.n2) {
-      const int pl = (z0 < 0 || z0 == sg.idx) ? 0 : 1;
-      if (pl == 0) z0 = sg.idx; else z1 = sg.idx;
-      zseg |= s << (8 * (2 * pl + sg.comp));
-    }
-  }
-}
-
-// The recorded value at (x, y, k) if that point lies on face segment s (comp = -1 otherwise).
-struct FaceHit {
-  int comp;
-  float v;
-};
-
-__device__ __noinline__ FaceHit face_lookup(const RevArgs& A, int s, int x, int y, int k) {
-  const FaceSeg& sg = A.faces.seg[s];
-  FaceHit r = {-1, 0.f};
-  const int pa = sg.axis == 0 ? x : (sg.axis == 1 ? y : k);
-  if (pa != sg.idx) return r;
-  const int a1 = (sg.axis + 1) % 3, a2 = (sg.axis + 2) % 3;
-  const int u = (a1 == 0 ? x : (a1 == 1 ? y : k)) - sg.lo1, v = (a2 == 0 ? x : (a2 == 1 ? y : k)) - sg.lo2;
-  if (u < 0 || u >= sg.n1 || v < 0 || v >= sg.n2) return r;
-  r.comp = sg.comp;
-  r.v = A.rec[sg.off + (int64_t)v * sg.n1 + u];
-  return r;
-}
-
-__device__ __forceinline__ void face_take(const FaceHit& f, float& hx, float& hy, float& hz) {
-  if (f.comp == 0) hx = f.v;
-  else if (f.comp == 1) hy = f.v;
-  else if (f.comp == 2) hz = f.v;
-}
-
-// Apply every face segment through column (x, y) at plane k to (hx, hy, hz).
-__device__ __forceinline__ void face_fix(const RevArgs& A, int seg, int z0, int z1, int zseg, int x, int y, int k,
-                                         float& hx, float& hy, float& hz) {
-  if (seg >= 0) {
-    face_take(face_lookup(A, seg & 0xff, x, y, k), hx, hy, hz);
-    if (seg > 0xff) face_take(face_lookup(A, seg >> 8, x, y, k), hx, hy, hz);
-  }
-  if (k == z0 || k == z1) {
-    const int sh = (k == z0) ? 0 : 16;
-    face_take(face_lookup(A, (zseg >> sh) & 0xff, x, y, k), hx, hy, hz);
-    face_take(face_lookup(A, (zseg >> (sh + 8)) & 0xff, x, y, k), hx, hy, hz);
-  }
-}
+// CPML part of one adjoint coefficient inside a layer: the coefficient is sv / kappa + c (psi + sv)
+// (sv = sgn v), its plain value off the layers sv.
+__device__ __forceinline__ float acorr(float sv, float ik, float c, float psi) { return sv * (ik - 1.f) + c * (psi + sv); }
 
 __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
@@ -219,42 +149,6 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
   }
   __syncthreads();
 
-  // face-record substitution of staged H: the own point, and the halo row (i, j0-1) (warp 0) and
-  // column (i0-1, j0+r) (warp 1, lanes 0..TY-1)
-  const int hh = tid % TX;
-  const int role = tid / TX;
-  int hx_ = 0, hy_ = 0;
-  bool hv = false;
-  if (role == 0) { hx_ = i0 + hh; hy_ = j0 - 1; hv = j0 > 0 && hx_ < nx; }
-  else if (role == 1) { hx_ = i0 - 1; hy_ = j0 + hh; hv = hh < TY && i0 > 0 && hy_ < ny; }
-  const int hr = role == 0 ? 0 : hh + 1, hc = role == 0 ? hh + 4 : 3;  // the halo point in the H box
-  int hseg = -1, hz0 = -1, hz1 = -1, hzseg = 0;
-  if (hv && A.rec) face_segments(A.faces, hx_, hy_, hseg, hz0, hz1, hzseg);
-  int fseg = -1, fz0 = -1, fz1 = -1, fzseg = 0;  // face segments through the own column
-  if (own && A.rec) face_segments(A.faces, i, j, fseg, fz0, fz1, fzseg);
-  auto patch = [&](int p) {
-    float* hb = reinterpret_cast<float*>(R.at(p) + RE_H);
-    bool wrote = false;
-    if (own && (fseg >= 0 || p == fz0 || p == fz1)) {
-      float v0 = hb[(0 * BH + ty + 1) * BW + tx + 4], v1 = hb[(1 * BH + ty + 1) * BW + tx + 4],
-            v2 = hb[(2 * BH + ty + 1) * BW + tx + 4];
-      face_fix(A, fseg, fz0, fz1, fzseg, i, j, p, v0, v1, v2);
-      hb[(0 * BH + ty + 1) * BW + tx + 4] = v0;
-      hb[(1 * BH + ty + 1) * BW + tx + 4] = v1;
-      hb[(2 * BH + ty + 1) * BW + tx + 4] = v2;
-      wrote = true;
-    }
-    if (hv && (hseg >= 0 || p == hz0 || p == hz1)) {
-      float v0 = hb[(0 * BH + hr) * BW + hc], v1 = hb[(1 * BH + hr) * BW + hc], v2 = hb[(2 * BH + hr) * BW + hc];
-      face_fix(A, hseg, hz0, hz1, hzseg, hx_, hy_, p, v0, v1, v2);
-      hb[(0 * BH + hr) * BW + hc] = v0;
-      hb[(1 * BH + hr) * BW + hc] = v1;
-      hb[(2 * BH + hr) * BW + hc] = v2;
-      wrote = true;
-    }
-    if (wrote) async_proxy_fence();  // these generic writes precede the stage's next TMA fill
-  };
-
   // CPML data (integer positions, the E tables) along x and y
   const int ic = min(i, nx - 1), jc = min(j, ny - 1);
   const float ikX0 = T.ik[0][0][ic], ikY0 = T.ik[1][0][jc];
@@ -270,35 +164,33 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
   unsigned src_xy = 0;
   for (int s = 0; s < A.nsrc; ++s)
     if (own && i >= A.src[s].lo[0] && i < A.src[s].hi[0] && j >= A.src[s].lo[1] && j < A.src[s].hi[1]) src_xy |= 1u << s;
-  const bool lay_xy = (sX0 & sX1 & sY0 & sY1) >= 0;  // this column or its +x/+y neighbour is in a layer
 
   const PsiSet& Pi = A.pin;
   const PsiSet& Po = A.pout;
 
-  // P1_y and P2_x of the own column at k1 (the plane above the chunk)
-  float p1y_up = 0.f, p2x_up = 0.f;
+  // u_y, u_x of the own column at k1 (the plane above the chunk) and the z-layer corrections of
+  // P1 of E_y and P2 of E_x there
+  float uy_up = 0.f, ux_up = 0.f, d1y_up = 0.f, d2x_up = 0.f;
   if (own && k1 < nz) {
     const int q = k1 * plane + q0;
     const float Sa = S * A.a[q];
-    const float ux = (j > 0) ? Sa * A.B.f[0][q] : 0.f;
-    const float uy = (i > 0) ? Sa * A.B.f[1][q] : 0.f;
-    const float ikZ = T.ik[2][0][k1];
+    ux_up = (j > 0) ? Sa * A.B.f[0][q] : 0.f;
+    uy_up = (i > 0) ? Sa * A.B.f[1][q] : 0.f;
     const int sZ = T.sidx[2][k1];
-    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
-    p1y_up = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k1, Pi.p[1][2], zz);
-    p2x_up = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k1, Pi.p[0][2], zz);
+    if (sZ >= 0) {
+      const int zz = zz_of(g, i, j, sZ);
+      const float ikZ = T.ik[2][0][k1], cZ = T.c[2][0][k1];
+      d1y_up = acorr(uy_up, ikZ, cZ, Pi.p[1][2][zz]);
+      d2x_up = acorr(-ux_up, ikZ, cZ, Pi.p[0][2][zz]);
+    }
   }
 
   waited &= R.wait(ktop);
-  patch(ktop);
   int sZ1 = (k1 < nz) ? T.sidx[2][k1] : -1;  // slab index of the plane above
   for (int k = ktop; k >= k0; --k) {
     const int q = k * plane + q0;
-    if (k - 1 >= kbot) {
-      waited &= R.wait(k - 1);
-      patch(k - 1);
-    }
-    __syncthreads();  // plane k-1 patched everywhere; every thread is past plane k+1
+    if (k - 1 >= kbot) waited &= R.wait(k - 1);
+    __syncthreads();  // every thread is past plane k+1
     if (tid == 0 && k + 1 <= ktop && k + 1 - NSTAGE >= kbot) {
       async_proxy_fence();
       issue_rev_E(M, R, i0, j0, k + 1 - NSTAGE);
@@ -332,46 +224,73 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
     const float ikZ = T.ik[2][0][k];
     const int sZ = T.sidx[2][k];
 
-    // adjoint coefficients of the own E point and of its +x, +y neighbours (off the layers they are
-    // +-u: 1/kappa = 1 and c = 0)
-    if (!lay_xy && sZ < 0 && sZ1 < 0) {
-      A.B.f[3][q] = gx + ((uy - p1y_up) + (-uz + uz_y));
-      A.B.f[4][q] = gy + ((uz - uz_x) + (-ux - p2x_up));
-      A.B.f[5][q] = gz + ((ux - ux_y) + (-uy + uy_x));
-      p1y_up = uy;
-      p2x_up = -ux;
-    } else {
-      const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
-      const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
-      const float p1x = acoef<1, 0>(T, ux, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
-      const float p2x = acoef<2, 0>(T, ux, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
-      const float p1y = acoef<2, 0>(T, uy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
-      const float p2y = acoef<0, 0>(T, uy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
-      const float p1z = acoef<0, 0>(T, uz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
-      const float p2z = acoef<1, 0>(T, uz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
-      float p1z_x = 0.f, p2y_x = 0.f, p2z_y = 0.f, p1x_y = 0.f;
-      if (hasX1) {
-        const int zx1 = sX1 >= 0 ? zx_of(g, j, k, sX1) : 0;
-        p1z_x = acoef<0, 0>(T, uz_x, 1.f, ikX1, sX1, i + 1, Pi.p[2][0], zx1);
-        p2y_x = acoef<0, 0>(T, uy_x, -1.f, ikX1, sX1, i + 1, Pi.p[1][0], zx1);
+    // adjoint gather into H-bar: the plain coefficients +-u of the own E point and of its +x, +y, +z
+    // neighbours, then the CPML corrections axis by axis
+    float hbx = (uy - uy_up) + (-uz + uz_y);
+    float hby = (uz - uz_x) + (-ux + ux_up);
+    float hbz = (ux - ux_y) + (-uy + uy_x);
+    float cbx = 0.f, cby = 0.f, cbz = 0.f;
+    if (sX0 >= 0 || sX1 >= 0) {  // along x: P1 of E_z (2,0) and P2 of E_y (1,0), own and +x
+      float c1z = 0.f, c2y = 0.f, n1z = 0.f, n2y = 0.f;
+      if (sX0 >= 0) {
+        const int z = zx_of(g, j, k, sX0);
+        const float cX = T.c[0][0][i], bX = T.b[0][0][i];
+        const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
+        c1z = acorr(uz, ikX0, cX, p20);
+        c2y = acorr(-uy, ikX0, cX, p10);
+        Po.p[2][0][z] = bX * (p20 + uz);
+        Po.p[1][0][z] = bX * (p10 - uy);
       }
-      if (hasY1) {
-        const int zy1 = sY1 >= 0 ? zy_of(g, i, k, sY1) : 0;
-        p2z_y = acoef<1, 0>(T, uz_y, -1.f, ikY1, sY1, j + 1, Pi.p[2][1], zy1);
-        p1x_y = acoef<1, 0>(T, ux_y, 1.f, ikY1, sY1, j + 1, Pi.p[0][1], zy1);
+      if (sX1 >= 0) {
+        const int z = zx_of(g, j, k, sX1);
+        const float cX = T.c[0][0][i + 1];
+        n1z = acorr(uz_x, ikX1, cX, Pi.p[2][0][z]);
+        n2y = acorr(-uy_x, ikX1, cX, Pi.p[1][0][z]);
       }
-      A.B.f[3][q] = gx + ((p1y - p1y_up) + (p2z - p2z_y));
-      A.B.f[4][q] = gy + ((p1z - p1z_x) + (p2x - p2x_up));
-      A.B.f[5][q] = gz + ((p1x - p1x_y) + (p2y - p2y_x));
-      apsi<1, 0>(T, ux, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
-      apsi<2, 0>(T, ux, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
-      apsi<2, 0>(T, uy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
-      apsi<0, 0>(T, uy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
-      apsi<0, 0>(T, uz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
-      apsi<1, 0>(T, uz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
-      p1y_up = p1y;
-      p2x_up = p2x;
+      cby += c1z - n1z;
+      cbz += c2y - n2y;
     }
+    if (sY0 >= 0 || sY1 >= 0) {  // along y: P1 of E_x (0,1) and P2 of E_z (2,1), own and +y
+      float c1x = 0.f, c2z = 0.f, n1x = 0.f, n2z = 0.f;
+      if (sY0 >= 0) {
+        const int z = zy_of(g, i, k, sY0);
+        const float cY = T.c[1][0][j], bY = T.b[1][0][j];
+        const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
+        c1x = acorr(ux, ikY0, cY, p01);
+        c2z = acorr(-uz, ikY0, cY, p21);
+        Po.p[0][1][z] = bY * (p01 + ux);
+        Po.p[2][1][z] = bY * (p21 - uz);
+      }
+      if (sY1 >= 0) {
+        const int z = zy_of(g, i, k, sY1);
+        const float cY = T.c[1][0][j + 1];
+        n1x = acorr(ux_y, ikY1, cY, Pi.p[0][1][z]);
+        n2z = acorr(-uz_y, ikY1, cY, Pi.p[2][1][z]);
+      }
+      cbx += c2z - n2z;
+      cbz += c1x - n1x;
+    }
+    float d1y = 0.f, d2x = 0.f;  // along z: P1 of E_y (1,2) and P2 of E_x (0,2), own (below: carried)
+    if (sZ >= 0 || sZ1 >= 0) {
+      if (sZ >= 0) {
+        const int z = zz_of(g, i, j, sZ);
+        const float cZ = T.c[2][0][k], bZ = T.b[2][0][k];
+        const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
+        d1y = acorr(uy, ikZ, cZ, p12);
+        d2x = acorr(-ux, ikZ, cZ, p02);
+        Po.p[1][2][z] = bZ * (p12 + uy);
+        Po.p[0][2][z] = bZ * (p02 - ux);
+      }
+      cbx += d1y - d1y_up;
+      cby += d2x - d2x_up;
+    }
+    A.B.f[3][q] = gx + (hbx + cbx);
+    A.B.f[4][q] = gy + (hby + cby);
+    A.B.f[5][q] = gz + (hbz + cbz);
+    uy_up = uy;
+    ux_up = ux;
+    d1y_up = d1y;
+    d2x_up = d2x;
     sZ1 = sZ;
 
     // inverse E update on R (mirrors the forward arithmetic: the curl difference times 1/kappa = 1)
@@ -512,49 +431,80 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
     ex_up = ex;
     ey_up = ey;
 
-    // adjoint: coefficients of the own H point and of its -x, -y, -z neighbours (off the layers +-w)
+    // adjoint gather into E-bar: the plain coefficients +-w of the own H point and of its -x, -y, -z
+    // neighbours, then the CPML corrections axis by axis
+    const float wy_m = k > 0 ? -S * bym : 0.f, wx_m = k > 0 ? -S * bxm : 0.f;  // w at (i, j, k-1)
     const int sZm = k > 0 ? T.sidx[2][k - 1] : -1;
-    if (!lay_xy && sZ < 0 && sZm < 0) {
-      const float q1y_z = k > 0 ? -S * bym : 0.f, q2x_z = k > 0 ? S * bxm : 0.f;
-      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - wy) + (-wz_y + wz));
-      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((wz_x - wz) + (q2x_z + wx));
+    if (!lay_xy && sZ < 0 && sZm < 0) {  // no layer along any axis at this point or its neighbours
+      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((wy_m - wy) + (-wz_y + wz));
+      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((wz_x - wz) + (-wx_m + wx));
       if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((wx_y - wx) + (-wy_x + wy));
       continue;
     }
-    const int zx = sX0 >= 0 ? zx_of(g, j, k, sX0) : 0, zy = sY0 >= 0 ? zy_of(g, i, k, sY0) : 0;
-    const int zz = sZ >= 0 ? zz_of(g, i, j, sZ) : 0;
-    const float q1x = acoef<1, 1>(T, wx, 1.f, ikY0, sY0, j, Pi.p[0][1], zy);
-    const float q2x = acoef<2, 1>(T, wx, -1.f, ikZ, sZ, k, Pi.p[0][2], zz);
-    const float q1y = acoef<2, 1>(T, wy, 1.f, ikZ, sZ, k, Pi.p[1][2], zz);
-    const float q2y = acoef<0, 1>(T, wy, -1.f, ikX0, sX0, i, Pi.p[1][0], zx);
-    const float q1z = acoef<0, 1>(T, wz, 1.f, ikX0, sX0, i, Pi.p[2][0], zx);
-    const float q2z = acoef<1, 1>(T, wz, -1.f, ikY0, sY0, j, Pi.p[2][1], zy);
-    float q1z_x = 0.f, q2y_x = 0.f, q2z_y = 0.f, q1x_y = 0.f, q1y_z = 0.f, q2x_z = 0.f;
-    if (hasXm) {
-      const int zxm = sXm >= 0 ? zx_of(g, j, k, sXm) : 0;
-      q1z_x = acoef<0, 1>(T, wz_x, 1.f, ikXm, sXm, i - 1, Pi.p[2][0], zxm);
-      q2y_x = acoef<0, 1>(T, wy_x, -1.f, ikXm, sXm, i - 1, Pi.p[1][0], zxm);
+    float cex = 0.f, cey = 0.f, cez = 0.f;
+    if (sX0 >= 0 || sXm >= 0) {  // along x: Q1 of H_z (2,0) and Q2 of H_y (1,0), own and -x
+      float e1z = 0.f, e2y = 0.f, n1z = 0.f, n2y = 0.f;
+      if (sX0 >= 0) {
+        const int z = zx_of(g, j, k, sX0);
+        const float cX = T.c[0][1][i], bX = T.b[0][1][i];
+        const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
+        e1z = acorr(wz, ikX0, cX, p20);
+        e2y = acorr(-wy, ikX0, cX, p10);
+        Po.p[2][0][z] = bX * (p20 + wz);
+        Po.p[1][0][z] = bX * (p10 - wy);
+      }
+      if (sXm >= 0) {
+        const int z = zx_of(g, j, k, sXm);
+        const float cX = T.c[0][1][i - 1];
+        n1z = acorr(wz_x, ikXm, cX, Pi.p[2][0][z]);
+        n2y = acorr(-wy_x, ikXm, cX, Pi.p[1][0][z]);
+      }
+      cey += n1z - e1z;
+      cez += n2y - e2y;
     }
-    if (hasYm) {
-      const int zym = sYm >= 0 ? zy_of(g, i, k, sYm) : 0;
-      q2z_y = acoef<1, 1>(T, wz_y, -1.f, ikYm, sYm, j - 1, Pi.p[2][1], zym);
-      q1x_y = acoef<1, 1>(T, wx_y, 1.f, ikYm, sYm, j - 1, Pi.p[0][1], zym);
+    if (sY0 >= 0 || sYm >= 0) {  // along y: Q1 of H_x (0,1) and Q2 of H_z (2,1), own and -y
+      float e1x = 0.f, e2z = 0.f, n1x = 0.f, n2z = 0.f;
+      if (sY0 >= 0) {
+        const int z = zy_of(g, i, k, sY0);
+        const float cY = T.c[1][1][j], bY = T.b[1][1][j];
+        const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
+        e1x = acorr(wx, ikY0, cY, p01);
+        e2z = acorr(-wz, ikY0, cY, p21);
+        Po.p[0][1][z] = bY * (p01 + wx);
+        Po.p[2][1][z] = bY * (p21 - wz);
+      }
+      if (sYm >= 0) {
+        const int z = zy_of(g, i, k, sYm);
+        const float cY = T.c[1][1][j - 1];
+        n1x = acorr(wx_y, ikYm, cY, Pi.p[0][1][z]);
+        n2z = acorr(-wz_y, ikYm, cY, Pi.p[2][1][z]);
+      }
+      cex += n2z - e2z;
+      cez += n1x - e1x;
     }
-    if (k > 0) {
-      const float ikZm = T.ik[2][1][k - 1];
-      const int zzm = sZm >= 0 ? zz_of(g, i, j, sZm) : 0;
-      q1y_z = acoef<2, 1>(T, -S * bym, 1.f, ikZm, sZm, k - 1, Pi.p[1][2], zzm);
-      q2x_z = acoef<2, 1>(T, -S * bxm, -1.f, ikZm, sZm, k - 1, Pi.p[0][2], zzm);
+    if (sZ >= 0 || sZm >= 0) {  // along z: Q1 of H_y (1,2) and Q2 of H_x (0,2), own and -z
+      float e1y = 0.f, e2x = 0.f, m1y = 0.f, m2x = 0.f;
+      if (sZ >= 0) {
+        const int z = zz_of(g, i, j, sZ);
+        const float cZ = T.c[2][1][k], bZ = T.b[2][1][k];
+        const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
+        e1y = acorr(wy, ikZ, cZ, p12);
+        e2x = acorr(-wx, ikZ, cZ, p02);
+        Po.p[1][2][z] = bZ * (p12 + wy);
+        Po.p[0][2][z] = bZ * (p02 - wx);
+      }
+      if (sZm >= 0) {
+        const int z = zz_of(g, i, j, sZm);
+        const float ikZm = T.ik[2][1][k - 1], cZ = T.c[2][1][k - 1];
+        m1y = acorr(wy_m, ikZm, cZ, Pi.p[1][2][z]);
+        m2x = acorr(-wx_m, ikZm, cZ, Pi.p[0][2][z]);
+      }
+      cex += m1y - e1y;
+      cey += m2x - e2x;
     }
-    if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((q1y_z - q1y) + (q2z_y - q2z));
-    if (i > 0 && k > 0) A.B.f[1][q] = eby + ((q1z_x - q1z) + (q2x_z - q2x));
-    if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((q1x_y - q1x) + (q2y_x - q2y));
-    apsi<1, 1>(T, wx, 1.f, sY0, j, Pi.p[0][1], Po.p[0][1], zy);
-    apsi<2, 1>(T, wx, -1.f, sZ, k, Pi.p[0][2], Po.p[0][2], zz);
-    apsi<2, 1>(T, wy, 1.f, sZ, k, Pi.p[1][2], Po.p[1][2], zz);
-    apsi<0, 1>(T, wy, -1.f, sX0, i, Pi.p[1][0], Po.p[1][0], zx);
-    apsi<0, 1>(T, wz, 1.f, sX0, i, Pi.p[2][0], Po.p[2][0], zx);
-    apsi<1, 1>(T, wz, -1.f, sY0, j, Pi.p[2][1], Po.p[2][1], zy);
+    if (j > 0 && k > 0) A.B.f[0][q] = ebx + (((wy_m - wy) + (-wz_y + wz)) + cex);
+    if (i > 0 && k > 0) A.B.f[1][q] = eby + (((wz_x - wz) + (-wx_m + wx)) + cey);
+    if (i > 0 && j > 0) A.B.f[2][q] = ebz + (((wx_y - wx) + (-wy_x + wy)) + cez);
   }
   if (!waited) atomicOr(A.status, 1);
 }

@@ -24,7 +24,7 @@ FDTD_ERR_STATE = -5
 FDTD_ERR_NONFINITE = -6
 FDTD_ERR_TIMEOUT = -7
 FDTD_RECORD_FACES = 1
-KERNEL_NAMES = ["update_H", "update_E", "rev_E", "rev_H", "fused_fwd", "fused_rev", "k6", "k7"]
+KERNEL_NAMES = ["update_H", "update_E", "rev_E", "rev_H", "fused_fwd", "fused_rev", "face_copy", "det_adj"]
 
 ERROR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSTABLE", -3: "OOM", -4: "CUDA", -5: "STATE",
                -6: "NONFINITE", -7: "TIMEOUT"}
