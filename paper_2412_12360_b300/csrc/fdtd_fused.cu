@@ -308,6 +308,19 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       cze = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
     }
     const int pf = pflag[k - k0];
+    // soft-source terms of this plane, loaded before the H phase so that their latency overlaps it
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (pf & 1) {
+      for (int s = 0; s < A.nsrc; ++s) {
+        const SrcDev& sd = A.src[s];
+        if (!own || i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2])
+          continue;
+        const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
+        if (sd.comp == 0) sx += v;
+        else if (sd.comp == 1) sy += v;
+        else sz += v;
+      }
+    }
     waited &= mbar_wait(&R.bar[b1], ((it + 1) / NSTAGE) & 1);  // plane k+1 (plane k was waited for before)
     cp_wait_all_but_one();                                      // psi_old of H at plane k
     const float(*ek)[EH][EW] = R.E(b0);
@@ -421,16 +434,9 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       if (j > 0 && k > 0) exv += Sa * cx;
       if (i > 0 && k > 0) eyv += Sa * cy;
       if (i > 0 && j > 0) ezv += Sa * cz;
-      if (pf & 1) {
-        for (int s = 0; s < A.nsrc; ++s) {
-          const SrcDev& sd = A.src[s];
-          if (i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2]) continue;
-          const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
-          if (sd.comp == 0) exv += v;
-          else if (sd.comp == 1) eyv += v;
-          else ezv += v;
-        }
-      }
+      exv += sx;
+      eyv += sy;
+      ezv += sz;
       N.f[0][q] = exv;
       N.f[1][q] = eyv;
       N.f[2][q] = ezv;
@@ -452,9 +458,13 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
           double f = in ? (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
                               (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz)
                         : 0.0;
+          if (d.axis == 0) {  // an x-normal plane holds at most one lane of each warp
+            if (in) wflux[s][ty] += f;
+          } else {
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-          if (tx == 0) wflux[s][ty] += f;
+            for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+            if (tx == 0) wflux[s][ty] += f;
+          }
         }
       }
     }
