@@ -159,7 +159,6 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   if (tid == 0) {
     for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
     mbar_init_fence();
-    for (int p = kb; p <= min(kb + NSTAGE - 1, k1); ++p) R.issue(M, p - kb, i0, j0, p);
   }
   // CPML tables of the tile's positions (clamped into the grid; out-of-grid entries are not used)
   for (int t = tid; t < 6 * (TABX + TABY); t += NT) {
@@ -190,6 +189,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     }
     if (tid < kMaxDet * (NT / 32)) wflux[tid / (NT / 32)][tid % (NT / 32)] = 0.0;
   }
+  // everything above reads only constant tables and arguments; the fields come after the previous step
+  pdl_wait();
+  if (tid == 0)
+    for (int p = kb; p <= min(kb + NSTAGE - 1, k1); ++p) R.issue(M, p - kb, i0, j0, p);
   __syncthreads();
 
   // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
@@ -204,6 +207,9 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int sX = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
   const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
   const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
+  // whether the tile or its low halo reaches into an x or y layer (uniform over the block): if not,
+  // only planes in a z layer have CPML work
+  const bool tile_xy = i0 - 1 < g.pml[0] || i0 + TX > nx - g.pml[1] || j0 - 1 < g.pml[2] || j0 + TY > ny - g.pml[3];
 
   const PsiSet& PHi = A.psiH_cur;
   const PsiSet& PHo = A.psiH_nxt;
@@ -214,6 +220,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   // copies of psi_old of plane kk into this thread's slots (one commit group each)
   auto fetch_psiH = [&](int kk) {
     const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+    if (!tile_xy && sZk < 0) {
+      cp_commit();
+      return;
+    }
     if (own) {
       if (sX >= 0) {
         const int z = zx_of(g, j, kk, sX);
@@ -246,6 +256,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   };
   auto fetch_psiE = [&](int kk) {
     const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+    if (!tile_xy && sZk < 0) {
+      cp_commit();
+      return;
+    }
     if (own) {
       if (sX >= 0) {
         const int z = zx_of(g, j, kk, sX);
@@ -516,7 +530,7 @@ int prepare_fwd_fused(int* blocks_per_sm) {
 void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_fwd_fused<<<grid, NT, SMEM_BYTES, s>>>(a, m);
+  launch_pdl(k_fwd_fused, grid, dim3(NT), SMEM_BYTES, s, a, m);
 }
 
 }  // namespace fdtd

@@ -154,6 +154,29 @@ int fused_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);
 void launch_set_box(const Geo& g, float* a, const int* lo, const int* hi, const float* box, cudaStream_t s);
 
+// Launch with programmatic dependent launch allowed: the kernel may be scheduled while the previous
+// kernel in the stream finishes, and must call pdl_wait() before it touches memory that kernel
+// reads or writes. Inside a captured graph this becomes a programmatic dependency edge.
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
+#if defined(__CUDACC__)
+// Wait until the previous kernel of the stream has completed and its memory operations are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // Record `msg` as the calling thread's last error (fdtd_last_error) and return `code`.
 int set_error(int code, const char* msg);
 

@@ -113,6 +113,7 @@ __global__ void k_flux_finalize(DetDev d, int nsteps, const double* partial, dou
 // region, segment by segment. Within a segment the elements run along x where the segment spans x
 // (y- and z-faces), else along y, so that the field side of the copy is coalesced wherever it can be.
 __global__ void k_face_copy(Geo g, Fields F, FaceSet fs, float* __restrict__ rec, int to_record) {
+  pdl_wait();
   const FaceSeg& sg = fs.seg[blockIdx.y];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // a face segment holds fewer than 2^31 cells
   if (t >= sg.n1 * sg.n2) return;
@@ -131,6 +132,7 @@ __global__ void k_face_copy(Geo g, Fields F, FaceSet fs, float* __restrict__ rec
 // reverse: detector adjoint (the transpose of the sampling at step n)
 // ---------------------------------------------------------------------------------------------
 __global__ void k_det_adjoint(Geo g, Fields F, Fields A, DetDev d, int step, const double* __restrict__ gy) {
+  pdl_wait();
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (d.kind == 0) {
     if (m != 0) return;
@@ -229,13 +231,13 @@ void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* r
   for (int q = 0; q < fs.nseg; ++q) mx = std::max<int64_t>(mx, (int64_t)fs.seg[q].n1 * fs.seg[q].n2);
   if (fs.nseg == 0 || mx == 0) return;
   dim3 grid((unsigned)((mx + 255) / 256), fs.nseg);
-  k_face_copy<<<grid, 256, 0, s>>>(g, F, fs, rec, to_record);
+  launch_pdl(k_face_copy, grid, dim3(256), 0, s, g, F, fs, rec, to_record);
 }
 
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s) {
   const int64_t n = d.kind == 0 ? 1 : (int64_t)(d.hi[0] - d.lo[0]) * (d.hi[1] - d.lo[1]) * (d.hi[2] - d.lo[2]);
-  k_det_adjoint<<<blocks_for(n, 256), 256, 0, s>>>(g, F, A, d, step, dL_ddet);
+  launch_pdl(k_det_adjoint, dim3(blocks_for(n, 256)), dim3(256), 0, s, g, F, A, d, step, dL_ddet);
 }
 
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,

@@ -24,6 +24,8 @@
 // plain values for every point and add, for each axis d whose layer holds the point or the
 // neighbour along d, the correction sgn v (1/kappa_d - 1) + c_d (psibar + sgn v) of the coefficients
 // along d (exactly 0 on the layer's inner edge).
+#include <algorithm>
+
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 #include "fdtd_tma.cuh"
@@ -142,6 +144,7 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
   const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RE_STAGE), RE_STAGE, ktop};
   bool waited = true;
 
+  pdl_wait();  // the fields come after the previous kernel of the stream
   if (tid == 0) {
     for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
     mbar_init_fence();
@@ -358,6 +361,7 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
   const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RH_STAGE), RH_STAGE, ktop};
   bool waited = true;
 
+  pdl_wait();  // the fields come after the previous kernel of the stream
   if (tid == 0) {
     for (int b = 0; b < NSTAGE; ++b) mbar_init(&R.bar[b], 1);
     mbar_init_fence();
@@ -514,22 +518,26 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
 MapBox rev_box_own() { return {TX, TY}; }
 MapBox rev_box_wide() { return {BW, BH}; }
 
-int prepare_rev() {
+int prepare_rev(int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_rev_E, cudaFuncAttributeMaxDynamicSharedMemorySize, RE_SMEM);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rev_H, cudaFuncAttributeMaxDynamicSharedMemorySize, RH_SMEM);
+  int be = 0, bh = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_rev_E, NT, RE_SMEM);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, k_rev_H, NT, RH_SMEM);
+  *blocks_per_sm = std::min(be, bh);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }
 
 void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_rev_E<<<grid, NT, RE_SMEM, s>>>(a, m);
+  launch_pdl(k_rev_E, grid, dim3(NT), RE_SMEM, s, a, m);
 }
 
 void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  k_rev_H<<<grid, NT, RH_SMEM, s>>>(a, m);
+  launch_pdl(k_rev_H, grid, dim3(NT), RH_SMEM, s, a, m);
 }
 
 }  // namespace fdtd
