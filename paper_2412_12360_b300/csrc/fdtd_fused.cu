@@ -218,8 +218,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const Fields& N = A.nxt;
 
   // copies of psi_old of plane kk into this thread's slots (one commit group each)
-  auto fetch_psiH = [&](int kk) {
-    const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+  auto fetch_psiH = [&](int kk, int sZk) {
     if (!tile_xy && sZk < 0) {
       cp_commit();
       return;
@@ -254,8 +253,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
     }
     cp_commit();
   };
-  auto fetch_psiE = [&](int kk) {
-    const int sZk = slab_of(kk, nz, g.pml[4], g.pml[5]);
+  auto fetch_psiE = [&](int kk, int sZk) {
     if (!tile_xy && sZk < 0) {
       cp_commit();
       return;
@@ -308,14 +306,19 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
       hym = R.H(0)[1][ey][ex] - S * cy;
     }
   }
-  fetch_psiH(k0);
-  fetch_psiE(k0);
+  int sZ = slab_of(k0, nz, g.pml[4], g.pml[5]);  // z slab index of the current plane (-1 off the layers)
+  fetch_psiH(k0, sZ);
+  fetch_psiE(k0, sZ);
+  // stage of the current plane, of the next one and the mbarrier phase of the next one's fill,
+  // advanced by one stage per plane (plane p of the chunk sits in stage (p - kb) % NSTAGE)
+  int b0 = (k0 - kb) % NSTAGE;
+  int b1 = b0 + 1 == NSTAGE ? 0 : b0 + 1;
+  uint32_t ph1 = ((k0 - kb + 1) / NSTAGE) & 1;
 
   for (int k = k0; k < k1; ++k) {
     const int it = k - kb;  // stage use count of plane k
-    const int b0 = it % NSTAGE, b1 = (it + 1) % NSTAGE;
     const int q = k * plane + q0;
-    const int sZ = slab_of(k, nz, g.pml[4], g.pml[5]);
+    const int sZn = k + 1 < nz ? slab_of(k + 1, nz, g.pml[4], g.pml[5]) : -1;  // of the next plane
     Coef czh{0.f, 0.f, 1.f}, cze{0.f, 0.f, 1.f};
     if (sZ >= 0) {  // uniform over the block
       czh = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
@@ -335,7 +338,7 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
         else sz += v;
       }
     }
-    waited &= mbar_wait(&R.bar[b1], ((it + 1) / NSTAGE) & 1);  // plane k+1 (plane k was waited for before)
+    waited &= mbar_wait(&R.bar[b1], ph1);  // plane k+1 (plane k was waited for before)
     cp_wait_all_but_one();                                      // psi_old of H at plane k
     const float(*ek)[EH][EW] = R.E(b0);
     const float(*ek1)[EH][EW] = R.E(b1);
@@ -402,13 +405,13 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
         sH[1][hry][hrx] = hk[1][r][c] - S * cy;
       }
     }
-    if (k + 1 < k1) fetch_psiH(k + 1);
+    if (k + 1 < k1) fetch_psiH(k + 1, sZn);
     else cp_commit();
     __syncthreads();
     // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
     if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {
       async_proxy_fence();
-      R.issue(M, (it - 1) % NSTAGE, i0, j0, k - 1 + NSTAGE);
+      R.issue(M, b0 == 0 ? NSTAGE - 1 : b0 - 1, i0, j0, k - 1 + NSTAGE);  // the stage of plane k-1
     }
     cp_wait_all_but_one();  // psi_old of E at plane k
 
@@ -482,10 +485,14 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
         }
       }
     }
-    if (k + 1 < k1) fetch_psiE(k + 1);
+    if (k + 1 < k1) fetch_psiE(k + 1, sZn);
     else cp_commit();
     hxm = hx;
     hym = hy;
+    sZ = sZn;
+    b0 = b1;
+    b1 = b1 + 1 == NSTAGE ? 0 : b1 + 1;
+    if (b1 == 0) ph1 ^= 1u;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (!waited) atomicOr(A.status, 1);
