@@ -413,6 +413,89 @@ def run_serve(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, world, rank, local):
+    """A batch of designs of one scene (default: 16 designs of a 240x240x960 waveguide, 12-cell CPML,
+    120^3 design box each, rho seeds 500..515, flux objective, 3000 steps) through the
+    torch.autograd.Function: forward of every design, then the backward. Recompute mode (forward
+    again per design before its reverse sweep, one face history held at a time) when the histories of
+    all designs do not fit in device memory. Beside the throughput, a central finite-difference check
+    of dL/drho of design 0 on 4 voxels (indices from seed 99) with delta rho 1e-2 and 1e-3."""
+    import torch
+    from paper_2412_12360_b300 import autograd, fdtd, ranks
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T = args.time_steps or 3000
+    ids = ranks.shard(args.batch, world, rank)
+    scs = [scenes.waveguide_batch_member(b, T) for b in ids]
+    free, _ = torch.cuda.mem_get_info(dev)
+    base = sum(fdtd.footprint_bytes(sc, T, record_faces=False) for sc in scs)
+    hist = max(fdtd.footprint_bytes(sc, T, record_faces=True) - fdtd.footprint_bytes(sc, T, record_faces=False)
+               for sc in scs)
+    mode = "keep" if autograd.fits_in_memory(scs, T, int(0.85 * free)) else "recompute"
+    if mode == "recompute" and base + hist > 0.85 * free:
+        raise SystemExit("batch does not fit even one design at a time: %d + %d bytes" % (base, hist))
+    eps_lo, eps_hi = scs[0].extra["eps_lo"], scs[0].extra["eps_hi"]
+    solvers = [fdtd.Solver(sc) for sc in scs]
+    rho = torch.stack([torch.from_numpy(sc.extra["rho"]) for sc in scs]).to(dev).requires_grad_(True)
+
+    def batch_step():
+        rho.grad = None
+        det = autograd.solve(rho, solvers, eps_lo, eps_hi, T, mode)
+        loss = det.sum()          # L = sum over steps of the flux through the detector plane, per design
+        loss.backward()
+        return det
+
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    det = batch_step()
+    b.record()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t = a.elapsed_time(b) * 1e-3
+    cells = sum(sc.ncells * T for sc in scs)
+    t_max, cells_all = ranks.reduce_time_and_work(t, cells)
+    grad0 = rho.grad[0].detach().cpu().numpy() if rank == 0 else None
+
+    fd = None
+    if rank == 0 and not args.no_fd:
+        sc0, s0 = scs[0], solvers[0]
+        rng = np.random.default_rng(99)
+        shape = sc0.design_shape()
+        vox = [tuple(int(rng.integers(d)) for d in shape) for _ in range(4)]
+        rho0 = rho[0].detach().clone()
+
+        def loss_at(r):
+            s0.fdtd_set_design_density(r, eps_lo, eps_hi)
+            s0.fdtd_forward(T)
+            return float(np.sum(s0.detectors()))
+
+        fd = []
+        for v in vox:
+            row = {"voxel": list(v), "autograd": float(grad0[v])}
+            for h in (1e-2, 1e-3):
+                rp, rm = rho0.clone(), rho0.clone()
+                rp[v] += h
+                rm[v] -= h
+                row["fd_%g" % h] = (loss_at(rp) - loss_at(rm)) / (2 * h)
+            fd.append(row)
+        s0.fdtd_set_design_density(rho0, eps_lo, eps_hi)
+    for s in solvers:
+        s.close()
+    if rank != 0:
+        return
+    line = {"metric": "Gcell-steps/s fwd+grad (batched autograd)", "unit": "Gcell-steps/s",
+            "value": round(cells_all / t_max / 1e9, 4), "n_gpus": world, "higher_is_better": True,
+            "seconds": round(t_max, 3), "designs": args.batch, "mode": mode, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "fd_check": fd,
+            "config": {"workload": "%d designs of a 240x240x960 waveguide (along z), 12-cell CPML, 120^3 design box "
+                                   "each, rho~U[0,1) seeds 500.., flux objective, %d steps; recompute mode re-runs "
+                                   "each forward with the face record before its reverse sweep" % (args.batch, T)}}
+    print(json.dumps(line), flush=True)
+
+
 # ---- reference arm: the FP64 oracle on host cores -------------------------------------------------------
 def run_reference(args, world, rank):
     if rank != 0:
@@ -460,12 +543,17 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-load", type=float, default=1.5, help="offered load / sequential capacity")
     ap.add_argument("--serve-slots", type=int, default=6)
+    ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference check of --batched")
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.serve:
         run_serve(args, world, rank, local)
+    elif args.batched:
+        run_batched(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -185,6 +185,12 @@ int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds
 /* Device bytes currently held by the handle (or -1). */
 int64_t fdtd_bytes_allocated(fdtd_handle* h);
 
+/* Free the boundary-face history of the last recorded forward (stream-ordered on the handle's
+ * stream), for callers that solve many designs one after another and cannot keep every history
+ * (batched gradients in recompute mode). A later fdtd_backward then fails with FDTD_ERR_STATE until
+ * a new fdtd_forward with FDTD_RECORD_FACES. Returns FDTD_OK, or FDTD_ERR_INVALID_ARG for NULL. */
+int fdtd_release_history(fdtd_handle* h);
+
 /* Allocation-free Poynting flux: out = sum over the cell box [lo, hi) of (E x H)[axis] for the fields
  * the caller passes. The paper has no counterpart; this is a library utility for callers that cannot
  * call cudaMalloc (code running while a CUDA graph is captured, hosts that give the library a fixed

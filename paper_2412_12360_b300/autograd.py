@@ -10,8 +10,9 @@ and the dL/drho scaling run in the CUDA library; this module only moves pointers
 
 mode "keep" records the boundary faces during the forward pass and reverses from them (one forward
 and one reversed sweep per design). mode "recompute" runs a plain forward first and, in backward,
-runs the recorded forward again immediately before the reverse sweep of each design, so only one
-face history at a time needs to fit in device memory (used for batches whose histories do not fit).
+runs the recorded forward again immediately before the reverse sweep of each design and frees that
+history afterwards, so only one face history at a time is held in device memory (used for batches
+whose histories do not fit).
 """
 from __future__ import annotations
 
@@ -61,6 +62,8 @@ class FDTDSolve(torch.autograd.Function):
                 s.fdtd_set_design_density(rho_c[b], *ctx.eps)
                 s.fdtd_forward(ctx.nsteps, record_faces=True)
             s.fdtd_backward_density(gd[b], grad[b])
+            if ctx.mode == "recompute":
+                s.fdtd_release_history()  # only one design's history is held at a time
         return grad, None, None, None, None, None
 
 

@@ -1130,6 +1130,15 @@ int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds
   return FDTD_OK;
 }
 
+int fdtd_release_history(fdtd_handle* h) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  dev_free(h, h->face_hist, h->face_cap_steps * h->faces.per_step * 4);
+  h->face_hist = nullptr;
+  h->face_cap_steps = 0;
+  h->recorded = false;
+  return FDTD_OK;
+}
+
 int fdtd_synchronize(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   CK(cudaStreamSynchronize(h->stream));

@@ -78,6 +78,7 @@ SIGNATURES = [
                                          _I3, _I3]),
     ("fdtd_set_byte_budget", C.c_int, [C.c_int64]),
     ("fdtd_bytes_allocated", C.c_int64, [_VP]),
+    ("fdtd_release_history", C.c_int, [_VP]),
     ("fdtd_launch_count", C.c_int64, [_VP]),
     ("fdtd_profile", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
@@ -252,6 +253,9 @@ class Solver:
 
     def fdtd_bytes_allocated(self) -> int:
         return int(lib().fdtd_bytes_allocated(self.h))
+
+    def fdtd_release_history(self):
+        check(lib().fdtd_release_history(self.h))
 
     def fdtd_launch_count(self) -> int:
         return int(lib().fdtd_launch_count(self.h))
