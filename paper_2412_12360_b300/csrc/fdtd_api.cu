@@ -269,6 +269,7 @@ struct fdtd_handle {
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
   int tz_rev = 8;                 // z-planes per block of the reverse kernels
+  int fwd_nstage = 3;             // stages of the forward kernel's plane ring
 
   std::vector<fdtd_source> src_host;
   std::vector<SrcDev> srcs;
@@ -577,6 +578,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.T = h->tab();
   fa.a = h->a;
   fa.tz = h->tz;
+  fa.nstage = h->fwd_nstage;
   fa.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < fa.nsrc; ++q) fa.src[q] = h->srcs[q];
   fa.ndet = (int)std::min<size_t>(h->dets.size(), kMaxDet);
@@ -821,8 +823,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   }
   {
     // z-chunks of the marching kernels, each for its own number of resident blocks per SM
-    int per_sm = 0, nsm = 0;
-    if ((rc = prepare_fwd_fused(&per_sm)) != FDTD_OK) return cleanup(rc);
+    int per_sm3 = 0, per_sm4 = 0, nsm = 0;
+    if ((rc = prepare_fwd_fused(3, &per_sm3)) != FDTD_OK) return cleanup(rc);
+    if ((rc = prepare_fwd_fused(4, &per_sm4)) != FDTD_OK) return cleanup(rc);
     int per_sm_rev = 0;
     if ((rc = prepare_rev(&per_sm_rev)) != FDTD_OK) return cleanup(rc);
     int dev = 0;
@@ -830,7 +833,14 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
-    const int64_t slots_f = (int64_t)nsm * std::max(1, per_sm);
+    // forward: a 4-stage ring (fewer resident blocks, more planes in flight each) when the sweep
+    // fills at least four waves of them, else 3 stages (on one B300: 600^3 and 256^3 run faster with
+    // 4, 96^3 with 3)
+    const int64_t slots4 = (int64_t)nsm * std::max(1, per_sm4), slots3 = (int64_t)nsm * std::max(1, per_sm3);
+    const int tz4 = choose_tz(nxy, n[2], slots4);
+    const bool ring4 = nxy * ((n[2] + tz4 - 1) / tz4) >= 4 * slots4;
+    h->fwd_nstage = ring4 ? 4 : 3;
+    const int64_t slots_f = ring4 ? slots4 : slots3;
     const int64_t slots_r = (int64_t)nsm * std::max(1, per_sm_rev);
     h->tz = choose_tz(nxy, n[2], slots_f);
     h->tz_rev = choose_tz(nxy, n[2], slots_r);

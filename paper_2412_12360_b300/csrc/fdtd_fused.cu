@@ -43,6 +43,12 @@ struct Coef {
   float b, c, ik;
 };
 
+// compile-time flag for the specialised plane loops
+template <bool B>
+struct Flag {
+  static constexpr bool value = B;
+};
+
 // slab index of position x along an axis with n cells and layers p0, p1 (-1 off the layers)
 __device__ __forceinline__ int slab_of(int x, int n, int p0, int p1) {
   return x < p0 ? x : (x >= n - p1 ? p0 + x - (n - p1) : -1);
@@ -73,7 +79,6 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
 constexpr int EW = TX + 8, EH = TY + 2;
 constexpr int HW = TX + 4, HH = TY + 1;
 constexpr int XO = 4;  // x offset of the tile inside the E and H boxes
-constexpr int NSTAGE = 3;
 constexpr uint32_t E_BYTES = 3 * EW * EH * 4, H_BYTES = 3 * HW * HH * 4, A_BYTES = TX * TY * 4;
 constexpr uint32_t STAGE_TX = E_BYTES + H_BYTES + A_BYTES;  // transaction bytes of one stage
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
@@ -85,7 +90,10 @@ constexpr int NPH = 10, NPE = 6;
 // CPML tables of the tile's x and y positions (from i0-1 and j0-1): b, c, 1/kappa at integer then
 // half positions
 constexpr int TABX = TX + 1, TABY = TY + 1;
-constexpr int SH_OFF = NSTAGE * STAGE_BYTES;                      // new H: [2][3][HY][HX] floats
+// shared memory: the new-H tiles, the psi slots, tables, flags and flux sums, the mbarriers, then
+// the ring of NS stages (3 or 4: more stages keep more planes in flight per block, fewer let more
+// blocks reside per SM)
+constexpr int SH_OFF = 0;                                         // new H: [2][3][HY][HX] floats
 constexpr int PH_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);    // [NPH][NT]
 constexpr int PE_OFF = PH_OFF + NPH * NT * 4;                     // [NPE][NT]
 constexpr int TX_OFF = PE_OFF + NPE * NT * 4;                     // [6][TABX]
@@ -95,8 +103,9 @@ constexpr int TY_OFF = TX_OFF + 6 * TABX * 4;                     // [6][TABY]
 constexpr int MAXTZ = 1024;
 constexpr int PF_OFF = TY_OFF + 6 * TABY * 4;                     // [MAXTZ] bytes
 constexpr int WF_OFF = round128(PF_OFF + MAXTZ);                  // flux sums per warp: [kMaxDet][NT/32]
-constexpr int BAR_OFF = round128(WF_OFF + kMaxDet * (NT / 32) * 8);  // NSTAGE mbarriers
-constexpr int SMEM_BYTES = BAR_OFF + NSTAGE * 8 + 128;             // + slack to align the base
+constexpr int BAR_OFF = round128(WF_OFF + kMaxDet * (NT / 32) * 8);  // up to 4 mbarriers
+constexpr int RING_OFF = round128(BAR_OFF + 4 * 8);
+constexpr int smem_bytes(int ns) { return RING_OFF + ns * STAGE_BYTES + 128; }  // + slack to align the base
 
 struct Ring {
   unsigned char* base;
@@ -126,10 +135,11 @@ __device__ __forceinline__ Coef coef_at(const float (*tab)[W], int row0, int idx
   return Coef{tab[row0][idx], tab[row0 + 1][idx], tab[row0 + 2][idx]};
 }
 
-__global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
-  Ring R{sm, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
+  Ring R{sm + RING_OFF, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
   float(*sHb)[3][HY][HX] = reinterpret_cast<float(*)[3][HY][HX]>(sm + SH_OFF);
   float(*sPH)[NT] = reinterpret_cast<float(*)[NT]>(sm + PH_OFF);
   float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PE_OFF);
@@ -207,6 +217,10 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const int sX = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
   const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
   const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
+  // whether some lane of this warp has its own cell in an x or a y layer (uniform over the warp, so
+  // the per-axis CPML code below is branched over, not predicated, by the warps that have none)
+  const bool wx = __any_sync(0xffffffffu, own && sX >= 0);
+  const bool wy = __any_sync(0xffffffffu, own && sY >= 0);
   // whether the tile or its low halo reaches into an x or y layer (uniform over the block): if not,
   // only planes in a z layer have CPML work
   const bool tile_xy = i0 - 1 < g.pml[0] || i0 + TX > nx - g.pml[1] || j0 - 1 < g.pml[2] || j0 + TY > ny - g.pml[3];
@@ -217,283 +231,313 @@ __global__ void __launch_bounds__(NT, 4) k_fwd_fused(const FwdArgs A, const __gr
   const PsiSet& PEo = A.psiE_nxt;
   const Fields& N = A.nxt;
 
-  // copies of psi_old of plane kk into this thread's slots (one commit group each)
-  auto fetch_psiH = [&](int kk, int sZk) {
-    if (!tile_xy && sZk < 0) {
-      cp_commit();
-      return;
-    }
-    if (own) {
-      if (sX >= 0) {
-        const int z = zx_of(g, j, kk, sX);
-        cp4(&sPH[0][tid], PHi.p[1][0] + z);
-        cp4(&sPH[1][tid], PHi.p[2][0] + z);
+  // The plane loop, compiled twice: with or without CPML along x and y in the tile (XY). Each block
+  // runs the one it needs, so the common interior path carries none of the code (nor the register
+  // pressure) of the x/y layers.
+  auto march = [&](auto xy_tag) {
+    constexpr bool XY = decltype(xy_tag)::value;
+    // copies of psi_old of plane kk into this thread's slots (one commit group each)
+    auto fetch_psiH = [&](int kk, int sZk) {
+      if (!XY && sZk < 0) {
+        cp_commit();
+        return;
       }
-      if (sY >= 0) {
-        const int z = zy_of(g, i, kk, sY);
-        cp4(&sPH[2][tid], PHi.p[0][1] + z);
-        cp4(&sPH[3][tid], PHi.p[2][1] + z);
+      if constexpr (XY) {
+        if (wx && own && sX >= 0) {
+          const int z = zx_of(g, j, kk, sX);
+          cp4(&sPH[0][tid], PHi.p[1][0] + z);
+          cp4(&sPH[1][tid], PHi.p[2][0] + z);
+        }
+        if (wy && own && sY >= 0) {
+          const int z = zy_of(g, i, kk, sY);
+          cp4(&sPH[2][tid], PHi.p[0][1] + z);
+          cp4(&sPH[3][tid], PHi.p[2][1] + z);
+        }
       }
-      if (sZk >= 0) {
+      if (sZk >= 0 && own) {
         const int z = zz_of(g, i, j, sZk);
         cp4(&sPH[4][tid], PHi.p[0][2] + z);
         cp4(&sPH[5][tid], PHi.p[1][2] + z);
       }
-    }
-    if (hrow || hcol) {
-      if (sXh >= 0) cp4(&sPH[6][tid], PHi.p[2][0] + zx_of(g, yh, kk, sXh));  // Hz along x
-      if (sYh >= 0) cp4(&sPH[7][tid], PHi.p[2][1] + zy_of(g, xh, kk, sYh));  // Hz along y
-      if (hrow) {
-        if (sYh >= 0) cp4(&sPH[8][tid], PHi.p[0][1] + zy_of(g, xh, kk, sYh));  // Hx along y
-        if (sZk >= 0) cp4(&sPH[9][tid], PHi.p[0][2] + zz_of(g, xh, yh, sZk));  // Hx along z
-      } else {
-        if (sZk >= 0) cp4(&sPH[8][tid], PHi.p[1][2] + zz_of(g, xh, yh, sZk));  // Hy along z
-        if (sXh >= 0) cp4(&sPH[9][tid], PHi.p[1][0] + zx_of(g, yh, kk, sXh));  // Hy along x
+      if ((ty == 3 || ty == 4) && (hrow || hcol)) {
+        if constexpr (XY) {
+          if (sXh >= 0) cp4(&sPH[6][tid], PHi.p[2][0] + zx_of(g, yh, kk, sXh));  // Hz along x
+          if (sYh >= 0) cp4(&sPH[7][tid], PHi.p[2][1] + zy_of(g, xh, kk, sYh));  // Hz along y
+          if (hrow && sYh >= 0) cp4(&sPH[8][tid], PHi.p[0][1] + zy_of(g, xh, kk, sYh));  // Hx along y
+          if (hcol && sXh >= 0) cp4(&sPH[9][tid], PHi.p[1][0] + zx_of(g, yh, kk, sXh));  // Hy along x
+        }
+        if (hrow && sZk >= 0) cp4(&sPH[9][tid], PHi.p[0][2] + zz_of(g, xh, yh, sZk));  // Hx along z
+        if (hcol && sZk >= 0) cp4(&sPH[8][tid], PHi.p[1][2] + zz_of(g, xh, yh, sZk));  // Hy along z
       }
-    }
-    cp_commit();
-  };
-  auto fetch_psiE = [&](int kk, int sZk) {
-    if (!tile_xy && sZk < 0) {
       cp_commit();
-      return;
-    }
-    if (own) {
-      if (sX >= 0) {
-        const int z = zx_of(g, j, kk, sX);
-        cp4(&sPE[0][tid], PEi.p[1][0] + z);
-        cp4(&sPE[1][tid], PEi.p[2][0] + z);
+    };
+    auto fetch_psiE = [&](int kk, int sZk) {
+      if (!XY && sZk < 0) {
+        cp_commit();
+        return;
       }
-      if (sY >= 0) {
-        const int z = zy_of(g, i, kk, sY);
-        cp4(&sPE[2][tid], PEi.p[0][1] + z);
-        cp4(&sPE[3][tid], PEi.p[2][1] + z);
+      if constexpr (XY) {
+        if (wx && own && sX >= 0) {
+          const int z = zx_of(g, j, kk, sX);
+          cp4(&sPE[0][tid], PEi.p[1][0] + z);
+          cp4(&sPE[1][tid], PEi.p[2][0] + z);
+        }
+        if (wy && own && sY >= 0) {
+          const int z = zy_of(g, i, kk, sY);
+          cp4(&sPE[2][tid], PEi.p[0][1] + z);
+          cp4(&sPE[3][tid], PEi.p[2][1] + z);
+        }
       }
-      if (sZk >= 0) {
+      if (sZk >= 0 && own) {
         const int z = zz_of(g, i, j, sZk);
         cp4(&sPE[4][tid], PEi.p[0][2] + z);
         cp4(&sPE[5][tid], PEi.p[1][2] + z);
       }
-    }
-    cp_commit();
-  };
+      cp_commit();
+    };
 
-  waited &= mbar_wait(&R.bar[0], 0);
-  float hxm = 0.f, hym = 0.f;
-  if (k0 > 0) {
-    // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
-    waited &= mbar_wait(&R.bar[1], 0);
-    const int km = kb;
-    const int sZ = slab_of(km, nz, g.pml[4], g.pml[5]);
-    if (own) {
-      const float(*a0)[EH][EW] = R.E(0);
-      const float(*a1)[EH][EW] = R.E(1);
-      const float dzy = a0[2][ey + 1][ex] - a0[2][ey][ex], dyz = a1[1][ey][ex] - a0[1][ey][ex];
-      const float dxz = a1[0][ey][ex] - a0[0][ey][ex], dzx = a0[2][ey][ex + 1] - a0[2][ey][ex];
-      float cx = dzy - dyz, cy = dxz - dzx;
-      if ((sX & sY & sZ) >= 0) {
-        const Coef cz{T.b[2][1][km], T.c[2][1][km], T.ik[2][1][km]};
-        const Coef cxh = coef_at(tabX, 3, rx), cyh = coef_at(tabY, 3, ry);
-        if (sY >= 0) cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, i, km, sY)], nullptr, 0);
+    waited &= mbar_wait(&R.bar[0], 0);
+    float hxm = 0.f, hym = 0.f;
+    if (k0 > 0) {
+      // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
+      waited &= mbar_wait(&R.bar[1], 0);
+      const int km = kb;
+      const int sZ = slab_of(km, nz, g.pml[4], g.pml[5]);
+      if (own) {
+        const float(*a0)[EH][EW] = R.E(0);
+        const float(*a1)[EH][EW] = R.E(1);
+        const float dzy = a0[2][ey + 1][ex] - a0[2][ey][ex], dyz = a1[1][ey][ex] - a0[1][ey][ex];
+        const float dxz = a1[0][ey][ex] - a0[0][ey][ex], dzx = a0[2][ey][ex + 1] - a0[2][ey][ex];
+        float cx = dzy - dyz, cy = dxz - dzx;
+        if constexpr (XY) {
+          if (sY >= 0) {
+            const Coef cyh = coef_at(tabY, 3, ry);
+            cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, i, km, sY)], nullptr, 0);
+          }
+        }
         if (sZ >= 0) {
+          const Coef cz{T.b[2][1][km], T.c[2][1][km], T.ik[2][1][km]};
           const int zz = zz_of(g, i, j, sZ);
           cx -= corr<false>(dyz, cz.ik, cz.b, cz.c, PHi.p[0][2][zz], nullptr, 0);
           cy += corr<false>(dxz, cz.ik, cz.b, cz.c, PHi.p[1][2][zz], nullptr, 0);
         }
-        if (sX >= 0) cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
-      }
-      hxm = R.H(0)[0][ey][ex] - S * cx;
-      hym = R.H(0)[1][ey][ex] - S * cy;
-    }
-  }
-  int sZ = slab_of(k0, nz, g.pml[4], g.pml[5]);  // z slab index of the current plane (-1 off the layers)
-  fetch_psiH(k0, sZ);
-  fetch_psiE(k0, sZ);
-  // stage of the current plane, of the next one and the mbarrier phase of the next one's fill,
-  // advanced by one stage per plane (plane p of the chunk sits in stage (p - kb) % NSTAGE)
-  int b0 = (k0 - kb) % NSTAGE;
-  int b1 = b0 + 1 == NSTAGE ? 0 : b0 + 1;
-  uint32_t ph1 = ((k0 - kb + 1) / NSTAGE) & 1;
-
-  for (int k = k0; k < k1; ++k) {
-    const int it = k - kb;  // stage use count of plane k
-    const int q = k * plane + q0;
-    const int sZn = k + 1 < nz ? slab_of(k + 1, nz, g.pml[4], g.pml[5]) : -1;  // of the next plane
-    Coef czh{0.f, 0.f, 1.f}, cze{0.f, 0.f, 1.f};
-    if (sZ >= 0) {  // uniform over the block
-      czh = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
-      cze = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
-    }
-    const int pf = pflag[k - k0];
-    // soft-source terms of this plane, loaded before the H phase so that their latency overlaps it
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    if (pf & 1) {
-      for (int s = 0; s < A.nsrc; ++s) {
-        const SrcDev& sd = A.src[s];
-        if (!own || i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2])
-          continue;
-        const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
-        if (sd.comp == 0) sx += v;
-        else if (sd.comp == 1) sy += v;
-        else sz += v;
-      }
-    }
-    waited &= mbar_wait(&R.bar[b1], ph1);  // plane k+1 (plane k was waited for before)
-    cp_wait_all_but_one();                                      // psi_old of H at plane k
-    const float(*ek)[EH][EW] = R.E(b0);
-    const float(*ek1)[EH][EW] = R.E(b1);
-    const float(*hk)[HH][HW] = R.H(b0);
-    float(*sH)[HY][HX] = sHb[it & 1];
-    const bool lay = (sX & sY & sZ) >= 0;  // some axis of this cell is in a layer (-1 = all bits set)
-
-    // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
-    float hx = 0.f, hy = 0.f, hz = 0.f;
-    if (own) {
-      const float dzy = ek[2][ey + 1][ex] - ek[2][ey][ex], dyz = ek1[1][ey][ex] - ek[1][ey][ex];
-      const float dxz = ek1[0][ey][ex] - ek[0][ey][ex], dzx = ek[2][ey][ex + 1] - ek[2][ey][ex];
-      const float dyx = ek[1][ey][ex + 1] - ek[1][ey][ex], dxy = ek[0][ey + 1][ex] - ek[0][ey][ex];
-      float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
-      if (lay) {
-        if (sX >= 0) {
-          const Coef c = coef_at(tabX, 3, rx);
-          const int z = zx_of(g, j, k, sX);
-          cy -= corr<true>(dzx, c.ik, c.b, c.c, sPH[0][tid], PHo.p[1][0], z);
-          cz += corr<true>(dyx, c.ik, c.b, c.c, sPH[1][tid], PHo.p[2][0], z);
+        if constexpr (XY) {
+          if (sX >= 0) {
+            const Coef cxh = coef_at(tabX, 3, rx);
+            cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
+          }
         }
-        if (sY >= 0) {
-          const Coef c = coef_at(tabY, 3, ry);
-          const int z = zy_of(g, i, k, sY);
-          cx += corr<true>(dzy, c.ik, c.b, c.c, sPH[2][tid], PHo.p[0][1], z);
-          cz -= corr<true>(dxy, c.ik, c.b, c.c, sPH[3][tid], PHo.p[2][1], z);
+        hxm = R.H(0)[0][ey][ex] - S * cx;
+        hym = R.H(0)[1][ey][ex] - S * cy;
+      }
+    }
+    int sZ = slab_of(k0, nz, g.pml[4], g.pml[5]);  // z slab index of the current plane (-1 off the layers)
+    fetch_psiH(k0, sZ);
+    fetch_psiE(k0, sZ);
+    // stage of the current plane, of the next one and the mbarrier phase of the next one's fill,
+    // advanced by one stage per plane (plane p of the chunk sits in stage (p - kb) % NSTAGE)
+    int b0 = (k0 - kb) % NSTAGE;
+    int b1 = b0 + 1 == NSTAGE ? 0 : b0 + 1;
+    uint32_t ph1 = ((k0 - kb + 1) / NSTAGE) & 1;
+
+    for (int k = k0; k < k1; ++k) {
+      const int it = k - kb;  // stage use count of plane k
+      const int q = k * plane + q0;
+      const int sZn = k + 1 < nz ? slab_of(k + 1, nz, g.pml[4], g.pml[5]) : -1;  // of the next plane
+      Coef czh{0.f, 0.f, 1.f}, cze{0.f, 0.f, 1.f};
+      if (sZ >= 0) {  // uniform over the block
+        czh = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
+        cze = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
+      }
+      const int pf = pflag[k - k0];
+      // soft-source terms of this plane, loaded before the H phase so that their latency overlaps it
+      float sx = 0.f, sy = 0.f, sz = 0.f;
+      if (pf & 1) {
+        for (int s = 0; s < A.nsrc; ++s) {
+          const SrcDev& sd = A.src[s];
+          if (!own || i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2])
+            continue;
+          const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
+          if (sd.comp == 0) sx += v;
+          else if (sd.comp == 1) sy += v;
+          else sz += v;
+        }
+      }
+      waited &= mbar_wait(&R.bar[b1], ph1);  // plane k+1 (plane k was waited for before)
+      cp_wait_all_but_one();                                      // psi_old of H at plane k
+      const float(*ek)[EH][EW] = R.E(b0);
+      const float(*ek1)[EH][EW] = R.E(b1);
+      const float(*hk)[HH][HW] = R.H(b0);
+      float(*sH)[HY][HX] = sHb[it & 1];
+
+      // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
+      float hx = 0.f, hy = 0.f, hz = 0.f;
+      if (own) {
+        const float dzy = ek[2][ey + 1][ex] - ek[2][ey][ex], dyz = ek1[1][ey][ex] - ek[1][ey][ex];
+        const float dxz = ek1[0][ey][ex] - ek[0][ey][ex], dzx = ek[2][ey][ex + 1] - ek[2][ey][ex];
+        const float dyx = ek[1][ey][ex + 1] - ek[1][ey][ex], dxy = ek[0][ey + 1][ex] - ek[0][ey][ex];
+        float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
+        if constexpr (XY) {
+          if (wx && sX >= 0) {
+            const Coef c = coef_at(tabX, 3, rx);
+            const int z = zx_of(g, j, k, sX);
+            cy -= corr<true>(dzx, c.ik, c.b, c.c, sPH[0][tid], PHo.p[1][0], z);
+            cz += corr<true>(dyx, c.ik, c.b, c.c, sPH[1][tid], PHo.p[2][0], z);
+          }
+          if (wy && sY >= 0) {
+            const Coef c = coef_at(tabY, 3, ry);
+            const int z = zy_of(g, i, k, sY);
+            cx += corr<true>(dzy, c.ik, c.b, c.c, sPH[2][tid], PHo.p[0][1], z);
+            cz -= corr<true>(dxy, c.ik, c.b, c.c, sPH[3][tid], PHo.p[2][1], z);
+          }
         }
         if (sZ >= 0) {
           const int z = zz_of(g, i, j, sZ);
           cx -= corr<true>(dyz, czh.ik, czh.b, czh.c, sPH[4][tid], PHo.p[0][2], z);
           cy += corr<true>(dxz, czh.ik, czh.b, czh.c, sPH[5][tid], PHo.p[1][2], z);
         }
+        hx = hk[0][ey][ex] - S * cx;
+        hy = hk[1][ey][ex] - S * cy;
+        hz = hk[2][ey][ex] - S * cz;
+        sH[0][ry][rx] = hx;
+        sH[1][ry][rx] = hy;
+        sH[2][ry][rx] = hz;
+        N.f[3][q] = hx;
+        N.f[4][q] = hy;
+        N.f[5][q] = hz;
       }
-      hx = hk[0][ey][ex] - S * cx;
-      hy = hk[1][ey][ex] - S * cy;
-      hz = hk[2][ey][ex] - S * cz;
-      sH[0][ry][rx] = hx;
-      sH[1][ry][rx] = hy;
-      sH[2][ry][rx] = hz;
-      N.f[3][q] = hx;
-      N.f[4][q] = hy;
-      N.f[5][q] = hz;
-    }
-    // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
-    if (hrow || hcol) {
-      const int r = hey, c = hex;
-      const float dyx = ek[1][r][c + 1] - ek[1][r][c], dxy = ek[0][r + 1][c] - ek[0][r][c];
-      const Coef chx = coef_at(tabX, 3, hrx), chy = coef_at(tabY, 3, hry);
-      float cz = dyx - dxy;
-      if (sXh >= 0) cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sPH[6][tid], nullptr, 0);
-      if (sYh >= 0) cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sPH[7][tid], nullptr, 0);
-      sH[2][hry][hrx] = hk[2][r][c] - S * cz;
-      if (hrow) {  // Hx
-        const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
-        float cx = dzy - dyz;
-        if (sYh >= 0) cx += corr<false>(dzy, chy.ik, chy.b, chy.c, sPH[8][tid], nullptr, 0);
-        if (sZ >= 0) cx -= corr<false>(dyz, czh.ik, czh.b, czh.c, sPH[9][tid], nullptr, 0);
-        sH[0][hry][hrx] = hk[0][r][c] - S * cx;
-      } else {  // Hy
-        const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
-        float cy = dxz - dzx;
-        if (sZ >= 0) cy += corr<false>(dxz, czh.ik, czh.b, czh.c, sPH[8][tid], nullptr, 0);
-        if (sXh >= 0) cy -= corr<false>(dzx, chx.ik, chx.b, chx.c, sPH[9][tid], nullptr, 0);
-        sH[1][hry][hrx] = hk[1][r][c] - S * cy;
+      // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
+      if ((ty == 3 || ty == 4) && (hrow || hcol)) {
+        const int r = hey, c = hex;
+        const float dyx = ek[1][r][c + 1] - ek[1][r][c], dxy = ek[0][r + 1][c] - ek[0][r][c];
+        float cz = dyx - dxy;
+        if constexpr (XY) {
+          if (sXh >= 0) {
+            const Coef chx = coef_at(tabX, 3, hrx);
+            cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sPH[6][tid], nullptr, 0);
+          }
+          if (sYh >= 0) {
+            const Coef chy = coef_at(tabY, 3, hry);
+            cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sPH[7][tid], nullptr, 0);
+          }
+        }
+        sH[2][hry][hrx] = hk[2][r][c] - S * cz;
+        if (hrow) {  // Hx
+          const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
+          float cx = dzy - dyz;
+          if constexpr (XY) {
+            if (sYh >= 0) {
+              const Coef chy = coef_at(tabY, 3, hry);
+              cx += corr<false>(dzy, chy.ik, chy.b, chy.c, sPH[8][tid], nullptr, 0);
+            }
+          }
+          if (sZ >= 0) cx -= corr<false>(dyz, czh.ik, czh.b, czh.c, sPH[9][tid], nullptr, 0);
+          sH[0][hry][hrx] = hk[0][r][c] - S * cx;
+        } else {  // Hy
+          const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
+          float cy = dxz - dzx;
+          if (sZ >= 0) cy += corr<false>(dxz, czh.ik, czh.b, czh.c, sPH[8][tid], nullptr, 0);
+          if constexpr (XY) {
+            if (sXh >= 0) {
+              const Coef chx = coef_at(tabX, 3, hrx);
+              cy -= corr<false>(dzx, chx.ik, chx.b, chx.c, sPH[9][tid], nullptr, 0);
+            }
+          }
+          sH[1][hry][hrx] = hk[1][r][c] - S * cy;
+        }
       }
-    }
-    if (k + 1 < k1) fetch_psiH(k + 1, sZn);
-    else cp_commit();
-    __syncthreads();
-    // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
-    if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {
-      async_proxy_fence();
-      R.issue(M, b0 == 0 ? NSTAGE - 1 : b0 - 1, i0, j0, k - 1 + NSTAGE);  // the stage of plane k-1
-    }
-    cp_wait_all_but_one();  // psi_old of E at plane k
+      if (k + 1 < k1) fetch_psiH(k + 1, sZn);
+      else cp_commit();
+      __syncthreads();
+      // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
+      if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {
+        async_proxy_fence();
+        R.issue(M, b0 == 0 ? NSTAGE - 1 : b0 - 1, i0, j0, k - 1 + NSTAGE);  // the stage of plane k-1
+      }
+      cp_wait_all_but_one();  // psi_old of E at plane k
 
-    // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
-    // sources and detectors
-    float exv = 0.f, eyv = 0.f, ezv = 0.f;
-    if (own) {
-      const float Sa = S * R.Av(b0)[ty][tx];
-      exv = ek[0][ey][ex];
-      eyv = ek[1][ey][ex];
-      ezv = ek[2][ey][ex];
-      const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
-      const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
-      const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
-      float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
-      if (lay) {
+      // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
+      // sources and detectors
+      float exv = 0.f, eyv = 0.f, ezv = 0.f;
+      if (own) {
+        const float Sa = S * R.Av(b0)[ty][tx];
+        exv = ek[0][ey][ex];
+        eyv = ek[1][ey][ex];
+        ezv = ek[2][ey][ex];
+        const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
+        const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
+        const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
+        float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
         // (a component held by a PEC wall keeps psi = 0: its memory is neither updated nor used)
         const bool ux = j > 0 && k > 0, uy = i > 0 && k > 0, uz = i > 0 && j > 0;
-        if (sX >= 0) {
-          const Coef c = coef_at(tabX, 0, rx);
-          const int z = zx_of(g, j, k, sX);
-          if (uy) cy -= corr<true>(d2y, c.ik, c.b, c.c, sPE[0][tid], PEo.p[1][0], z);
-          if (uz) cz += corr<true>(d1z, c.ik, c.b, c.c, sPE[1][tid], PEo.p[2][0], z);
-        }
-        if (sY >= 0) {
-          const Coef c = coef_at(tabY, 0, ry);
-          const int z = zy_of(g, i, k, sY);
-          if (ux) cx += corr<true>(d1x, c.ik, c.b, c.c, sPE[2][tid], PEo.p[0][1], z);
-          if (uz) cz -= corr<true>(d2z, c.ik, c.b, c.c, sPE[3][tid], PEo.p[2][1], z);
+        if constexpr (XY) {
+          if (wx && sX >= 0) {
+            const Coef c = coef_at(tabX, 0, rx);
+            const int z = zx_of(g, j, k, sX);
+            if (uy) cy -= corr<true>(d2y, c.ik, c.b, c.c, sPE[0][tid], PEo.p[1][0], z);
+            if (uz) cz += corr<true>(d1z, c.ik, c.b, c.c, sPE[1][tid], PEo.p[2][0], z);
+          }
+          if (wy && sY >= 0) {
+            const Coef c = coef_at(tabY, 0, ry);
+            const int z = zy_of(g, i, k, sY);
+            if (ux) cx += corr<true>(d1x, c.ik, c.b, c.c, sPE[2][tid], PEo.p[0][1], z);
+            if (uz) cz -= corr<true>(d2z, c.ik, c.b, c.c, sPE[3][tid], PEo.p[2][1], z);
+          }
         }
         if (sZ >= 0) {
           const int z = zz_of(g, i, j, sZ);
           if (ux) cx -= corr<true>(d2x, cze.ik, cze.b, cze.c, sPE[4][tid], PEo.p[0][2], z);
           if (uy) cy += corr<true>(d1y, cze.ik, cze.b, cze.c, sPE[5][tid], PEo.p[1][2], z);
         }
+        if (j > 0 && k > 0) exv += Sa * cx;
+        if (i > 0 && k > 0) eyv += Sa * cy;
+        if (i > 0 && j > 0) ezv += Sa * cz;
+        exv += sx;
+        eyv += sy;
+        ezv += sz;
+        N.f[0][q] = exv;
+        N.f[1][q] = eyv;
+        N.f[2][q] = ezv;
       }
-      if (j > 0 && k > 0) exv += Sa * cx;
-      if (i > 0 && k > 0) eyv += Sa * cy;
-      if (i > 0 && j > 0) ezv += Sa * cz;
-      exv += sx;
-      eyv += sy;
-      ezv += sz;
-      N.f[0][q] = exv;
-      N.f[1][q] = eyv;
-      N.f[2][q] = ezv;
-    }
-    // detectors (block-uniform branch; flux partials are reduced over the warp in a fixed order and
-    // summed per warp over the planes)
-    if (pf & 2) {
-#pragma unroll
-      for (int s = 0; s < kMaxDet; ++s) {
-        if (s >= A.ndet) break;
-        const DetDev& d = A.det[s];
-        const bool in = own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1] && k >= d.lo[2] && k < d.hi[2];
-        if (d.kind == 0) {
-          if (in) A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
-        } else if (d.kind == 1) {
-          if (in) A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
-        } else if (k >= d.lo[2] && k < d.hi[2]) {
-          const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
-          double f = in ? (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
-                              (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz)
-                        : 0.0;
-          if (d.axis == 0) {  // an x-normal plane holds at most one lane of each warp
-            if (in) wflux[s][ty] += f;
-          } else {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-            if (tx == 0) wflux[s][ty] += f;
+      // detectors (block-uniform branch; flux partials are reduced over the warp in a fixed order and
+      // summed per warp over the planes)
+      if (pf & 2) {
+  #pragma unroll
+        for (int s = 0; s < kMaxDet; ++s) {
+          if (s >= A.ndet) break;
+          const DetDev& d = A.det[s];
+          const bool in = own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1] && k >= d.lo[2] && k < d.hi[2];
+          if (d.kind == 0) {
+            if (in) A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
+          } else if (d.kind == 1) {
+            if (in) A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
+          } else if (k >= d.lo[2] && k < d.hi[2]) {
+            const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
+            double f = in ? (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
+                                (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz)
+                          : 0.0;
+            if (d.axis == 0) {  // an x-normal plane holds at most one lane of each warp
+              if (in) wflux[s][ty] += f;
+            } else {
+  #pragma unroll
+              for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
+              if (tx == 0) wflux[s][ty] += f;
+            }
           }
         }
       }
+      if (k + 1 < k1) fetch_psiE(k + 1, sZn);
+      else cp_commit();
+      hxm = hx;
+      hym = hy;
+      sZ = sZn;
+      b0 = b1;
+      b1 = b1 + 1 == NSTAGE ? 0 : b1 + 1;
+      if (b1 == 0) ph1 ^= 1u;
     }
-    if (k + 1 < k1) fetch_psiE(k + 1, sZn);
-    else cp_commit();
-    hxm = hx;
-    hym = hy;
-    sZ = sZn;
-    b0 = b1;
-    b1 = b1 + 1 == NSTAGE ? 0 : b1 + 1;
-    if (b1 == 0) ph1 ^= 1u;
-  }
+  };
+  if (tile_xy) march(Flag<true>{});
+  else march(Flag<false>{});
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (!waited) atomicOr(A.status, 1);
   __syncthreads();  // every warp's flux sums are in place
@@ -528,16 +572,19 @@ MapBox fwd_box_e() { return {EW, EH}; }
 MapBox fwd_box_h() { return {HW, HH}; }
 MapBox fwd_box_a() { return {TX, TY}; }
 
-int prepare_fwd_fused(int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_fwd_fused, NT, SMEM_BYTES);
+int prepare_fwd_fused(int nstage, int* blocks_per_sm) {
+  auto k = nstage == 4 ? k_fwd_fused<4> : k_fwd_fused<3>;
+  const int smem = smem_bytes(nstage);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }
 
 void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  launch_pdl(k_fwd_fused, grid, dim3(NT), SMEM_BYTES, s, a, m);
+  if (a.nstage == 4) launch_pdl(k_fwd_fused<4>, grid, dim3(NT), smem_bytes(4), s, a, m);
+  else launch_pdl(k_fwd_fused<3>, grid, dim3(NT), smem_bytes(3), s, a, m);
 }
 
 }  // namespace fdtd

@@ -87,6 +87,7 @@ struct FwdArgs {
   const float* a;
   int step;
   int tz;                  // z-planes per block
+  int nstage;              // stages of the plane ring (3 or 4)
   int nsrc;
   SrcDev src[kMaxSrc];
   int ndet;

@@ -32,7 +32,7 @@ struct FwdMaps {
 MapBox fwd_box_e();
 MapBox fwd_box_h();
 MapBox fwd_box_a();
-int prepare_fwd_fused(int* blocks_per_sm);
+int prepare_fwd_fused(int nstage, int* blocks_per_sm);
 void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s);
 
 // The maps the reverse-step kernels read (F = fields, B = adjoint fields): "own" boxes cover the
