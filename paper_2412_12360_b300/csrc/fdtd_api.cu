@@ -831,19 +831,20 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
+    // column tiles of the forward and of the reverse kernels
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
-    // forward: a 4-stage ring (fewer resident blocks, more planes in flight each) when the sweep
-    // fills at least four waves of them, else 3 stages (on one B300: 600^3 and 256^3 run faster with
-    // 4, 96^3 with 3)
+    const int64_t nxy_rev = (int64_t)((n[0] + rev_tile_x() - 1) / rev_tile_x()) *
+                            ((n[1] + rev_tile_y() - 1) / rev_tile_y());
+    // forward: a 4-stage ring (more planes in flight per block) when it keeps as many blocks
+    // resident per SM as 3 stages do (two, on one B300), else 3 stages
     const int64_t slots4 = (int64_t)nsm * std::max(1, per_sm4), slots3 = (int64_t)nsm * std::max(1, per_sm3);
-    const int tz4 = choose_tz(nxy, n[2], slots4);
-    const bool ring4 = nxy * ((n[2] + tz4 - 1) / tz4) >= 4 * slots4;
+    const bool ring4 = per_sm4 >= per_sm3;
     h->fwd_nstage = ring4 ? 4 : 3;
     const int64_t slots_f = ring4 ? slots4 : slots3;
     const int64_t slots_r = (int64_t)nsm * std::max(1, per_sm_rev);
     h->tz = choose_tz(nxy, n[2], slots_f);
-    h->tz_rev = choose_tz(nxy, n[2], slots_r);
+    h->tz_rev = choose_tz(nxy_rev, n[2], slots_r);
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
       const int v = std::atoi(e);
       if (v >= 1) h->tz = h->tz_rev = std::min(v, n[2]);

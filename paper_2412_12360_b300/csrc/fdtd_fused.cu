@@ -11,6 +11,11 @@
 // `cur`, write `nxt`) so neighbouring tiles never see a half-updated field; every cell is read and
 // written once per step from HBM (52 bytes per cell) and the halos come from L2.
 //
+// Each thread updates two x-adjacent cells (x0 = i0 + 2 lx and x0 + 1): the staged planes are read
+// and the results written as float2 pairs, the x-neighbour one cell needs is the other cell's value
+// already in registers, and the per-plane bookkeeping (waits, flags, indices) is shared by two
+// cells. A warp covers two rows of the tile (lanes 0..15 and 16..31).
+//
 // Every cell takes the plain Yee update; cells in a CPML layer add the correction
 // (1/kappa - 1) d + psi per curl term, which is exactly 0 off the layers and on their inner edge, so
 // the PML-free region R is updated by the plain formula the inverse step mirrors. The CPML memories a
@@ -24,8 +29,12 @@ namespace fdtd {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 1, HY = TY + 1;  // new H with the low halo
+constexpr int TX = 32, TY = 16, NT = 256;  // tile of TX x TY cells, two x-adjacent cells per thread
+constexpr int LX = TX / 2;                 // threads per tile row
+static_assert(NT == LX * TY && LX == 16, "one thread per cell pair, two tile rows per warp");
+// new H with the low halo: row r = y - (j0 - 1), column c = x - i0 + 2 (column 1 is the halo
+// x = i0 - 1, column 0 is padding so that every pair of own cells starts at an even column)
+constexpr int HX = TX + 2, HY = TY + 1;
 
 // CPML correction of one curl term inside a layer: the update uses d / kappa + psi_new where the plain
 // Yee update uses d, so the correction is (1/kappa - 1) d + psi_new with psi_new = b psi_old + c d
@@ -61,6 +70,10 @@ __device__ __forceinline__ void cp4(float* dst, const float* src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// 8-byte (two x-adjacent floats) shared or global accesses; the address must be 8-byte aligned
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+
 // psi index of the point (x, y, k), slab index s, for the derivative along x, y or z
 __device__ __forceinline__ int zx_of(const Geo& g, int y, int k, int s) { return (k * g.n[1] + y) * g.slab[0] + s; }
 __device__ __forceinline__ int zy_of(const Geo& g, int x, int k, int s) { return (k * g.slab[1] + s) * g.nxp + x; }
@@ -84,26 +97,33 @@ constexpr uint32_t STAGE_TX = E_BYTES + H_BYTES + A_BYTES;  // transaction bytes
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 constexpr int E_OFF = 0, H_OFF = round128(E_BYTES), A_OFF = H_OFF + round128(H_BYTES);
 constexpr int STAGE_BYTES = round128(A_OFF + A_BYTES);
-// CPML memories of the plane being computed, copied ahead by each thread for itself (cp.async):
-// H slots 0..5 own point (Hy_x, Hz_x, Hx_y, Hz_y, Hx_z, Hy_z), 6..9 the halo point; E slots 0..5.
-constexpr int NPH = 10, NPE = 6;
+// float2 accesses to the staged boxes and the new-H tile need even row pitches, even component
+// planes and an even column for every pair's first cell
+static_assert(EW % 2 == 0 && HW % 2 == 0 && HX % 2 == 0 && XO % 2 == 0, "float2 pairs");
+static_assert((EW * EH) % 2 == 0 && (HW * HH) % 2 == 0 && (HX * HY) % 2 == 0, "float2 pairs");
+// CPML memories of the plane being computed, copied ahead by each thread for itself (cp.async).
+// H slots: 6 c + m for own cell c (m: Hy_x, Hz_x, Hx_y, Hz_y, Hx_z, Hy_z). E slots: 6 c + m
+// (m: Ey_x, Ez_x, Ex_y, Ez_y, Ex_z, Ey_z). Halo slots, one column per halo thread (hid 0..15 the
+// row-halo lanes, 16..31 the column-halo lanes): the row-halo cell c at 4 c + (Hz_x, Hz_y, Hx_y,
+// Hx_z), the column-halo point at (Hz_x, Hz_y, Hy_z, Hy_x).
+constexpr int NPH = 12, NPE = 12, NHAL = 8, NHT = 32;
 // CPML tables of the tile's x and y positions (from i0-1 and j0-1): b, c, 1/kappa at integer then
 // half positions
 constexpr int TABX = TX + 1, TABY = TY + 1;
 // shared memory: the new-H tiles, the psi slots, tables, flags and flux sums, the mbarriers, then
-// the ring of NS stages (3 or 4: more stages keep more planes in flight per block, fewer let more
-// blocks reside per SM)
+// the ring of NS stages
 constexpr int SH_OFF = 0;                                         // new H: [2][3][HY][HX] floats
 constexpr int PH_OFF = SH_OFF + round128(2 * 3 * HY * HX * 4);    // [NPH][NT]
 constexpr int PE_OFF = PH_OFF + NPH * NT * 4;                     // [NPE][NT]
-constexpr int TX_OFF = PE_OFF + NPE * NT * 4;                     // [6][TABX]
+constexpr int HA_OFF = PE_OFF + NPE * NT * 4;                     // [NHAL][NHT]
+constexpr int TX_OFF = HA_OFF + NHAL * NHT * 4;                   // [6][TABX]
 constexpr int TY_OFF = TX_OFF + 6 * TABX * 4;                     // [6][TABY]
 // per-plane flags of the block's z-chunk: bit 0 a source, bit 1 a detector meets the tile at that
 // plane (uniform over the block, so planes without either cost one load)
-constexpr int MAXTZ = 1024;
+constexpr int MAXTZ = 256;
 constexpr int PF_OFF = TY_OFF + 6 * TABY * 4;                     // [MAXTZ] bytes
-constexpr int WF_OFF = round128(PF_OFF + MAXTZ);                  // flux sums per warp: [kMaxDet][NT/32]
-constexpr int BAR_OFF = round128(WF_OFF + kMaxDet * (NT / 32) * 8);  // up to 4 mbarriers
+constexpr int WF_OFF = round128(PF_OFF + MAXTZ);                  // flux sums per tile row: [kMaxDet][TY]
+constexpr int BAR_OFF = round128(WF_OFF + kMaxDet * TY * 8);      // up to 4 mbarriers
 constexpr int RING_OFF = round128(BAR_OFF + 4 * 8);
 constexpr int smem_bytes(int ns) { return RING_OFF + ns * STAGE_BYTES + 128; }  // + slack to align the base
 
@@ -136,34 +156,37 @@ __device__ __forceinline__ Coef coef_at(const float (*tab)[W], int row0, int idx
 }
 
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
+__global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
   Ring R{sm + RING_OFF, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
   float(*sHb)[3][HY][HX] = reinterpret_cast<float(*)[3][HY][HX]>(sm + SH_OFF);
   float(*sPH)[NT] = reinterpret_cast<float(*)[NT]>(sm + PH_OFF);
   float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PE_OFF);
+  float(*sHal)[NHT] = reinterpret_cast<float(*)[NHT]>(sm + HA_OFF);
   float(*tabX)[TABX] = reinterpret_cast<float(*)[TABX]>(sm + TX_OFF);
   float(*tabY)[TABY] = reinterpret_cast<float(*)[TABY]>(sm + TY_OFF);
   unsigned char* pflag = sm + PF_OFF;
-  double(*wflux)[NT / 32] = reinterpret_cast<double(*)[NT / 32]>(sm + WF_OFF);
+  double(*wflux)[TY] = reinterpret_cast<double(*)[TY]>(sm + WF_OFF);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int lx = lane & (LX - 1), ty = 2 * warp + (lane >> 4);
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = blockIdx.z * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int kb = k0 > 0 ? k0 - 1 : k0;  // first plane staged (k0-1 supplies H^{n+1/2} below the chunk)
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
-  const int i = i0 + tx, j = j0 + ty;
-  const bool own = i < nx && j < ny;
+  const int i = i0 + 2 * lx, j = j0 + ty;  // the thread's cells (i, j) and (i + 1, j)
+  const bool own0 = i < nx && j < ny, own1 = i + 1 < nx && j < ny;
   const int q0 = j * g.nxp + i;
   const float S = g.S;
-  const int ex = tx + XO, ey = ty + 1;  // own cell in the staged boxes
-  const int rx = tx + 1, ry = ty + 1;   // own cell in the new-H tile
+  const int ex = 2 * lx + XO, ey = ty + 1;  // cell 0 in the staged boxes
+  const int rx = 2 * lx + 2, ry = ty + 1;   // cell 0 in the new-H tile
+  const int cx0 = 2 * lx + 1;               // cell 0 in the x table
   bool waited = true;
 
   if (tid == 0) {
@@ -197,7 +220,7 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
       }
       pflag[p] = (unsigned char)f;
     }
-    if (tid < kMaxDet * (NT / 32)) wflux[tid / (NT / 32)][tid % (NT / 32)] = 0.0;
+    if (tid < kMaxDet * TY) wflux[tid / TY][tid % TY] = 0.0;
   }
   // everything above reads only constant tables and arguments; the fields come after the previous step
   pdl_wait();
@@ -205,22 +228,25 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
     for (int p = kb; p <= min(kb + NSTAGE - 1, k1); ++p) R.issue(M, p - kb, i0, j0, p);
   __syncthreads();
 
-  // halo H: warp 3 computes the row y = j0-1 (Hx, Hz), warp 4 lanes 0..TY-1 the column x = i0-1 (Hy, Hz)
-  const bool hrow = ty == 3 && j0 > 0 && i < nx;
-  const bool hcol = ty == 4 && tx < TY && i0 > 0 && (j0 + tx) < ny;
-  const int xh = hcol ? i0 - 1 : min(i, nx - 1);
-  const int yh = hcol ? j0 + tx : max(j0 - 1, 0);
-  const int hrx = hcol ? 0 : tx + 1, hry = hcol ? tx + 1 : 0;  // the halo point in the new-H tile
-  const int hex = hrx + XO - 1, hey = hry;                      // and in the staged boxes
+  // halo H: warp 3 lanes 0..15 compute the row y = j0-1 (Hx, Hz) at the pair (i, i+1); warp 4 lanes
+  // 0..15 the column x = i0-1 (Hy, Hz) at y = j0 + lx
+  const bool hrow = warp == 3 && lane < LX && j0 > 0 && i < nx;
+  const bool hrow1 = hrow && i + 1 < nx;
+  const int yc = j0 + lx;
+  const bool hcol = warp == 4 && lane < LX && i0 > 0 && yc < ny;
+  const int hid = (warp == 4 ? LX : 0) + lx;  // the halo thread's slot column
 
-  // slab indices along x and y of the own and the halo point (-1 off the layers)
-  const int sX = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
+  // slab indices along x and y of the own cells and the halo points (-1 off the layers)
+  const int sX0 = slab_of(min(i, nx - 1), nx, g.pml[0], g.pml[1]);
+  const int sX1 = slab_of(min(i + 1, nx - 1), nx, g.pml[0], g.pml[1]);
   const int sY = slab_of(min(j, ny - 1), ny, g.pml[2], g.pml[3]);
-  const int sXh = slab_of(xh, nx, g.pml[0], g.pml[1]), sYh = slab_of(yh, ny, g.pml[2], g.pml[3]);
-  // whether some lane of this warp has its own cell in an x or a y layer (uniform over the warp, so
+  const int sYh = slab_of(max(j0 - 1, 0), ny, g.pml[2], g.pml[3]);  // the row halo (block uniform)
+  const int sXc = slab_of(max(i0 - 1, 0), nx, g.pml[0], g.pml[1]);  // the column halo (block uniform)
+  const int sYc = slab_of(min(yc, ny - 1), ny, g.pml[2], g.pml[3]);
+  // whether some lane of this warp has an own cell in an x or a y layer (uniform over the warp, so
   // the per-axis CPML code below is branched over, not predicated, by the warps that have none)
-  const bool wx = __any_sync(0xffffffffu, own && sX >= 0);
-  const bool wy = __any_sync(0xffffffffu, own && sY >= 0);
+  const bool wx = __any_sync(0xffffffffu, (own0 && sX0 >= 0) || (own1 && sX1 >= 0));
+  const bool wy = __any_sync(0xffffffffu, own0 && sY >= 0);
   // whether the tile or its low halo reaches into an x or y layer (uniform over the block): if not,
   // only planes in a z layer have CPML work
   const bool tile_xy = i0 - 1 < g.pml[0] || i0 + TX > nx - g.pml[1] || j0 - 1 < g.pml[2] || j0 + TY > ny - g.pml[3];
@@ -242,32 +268,54 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
         cp_commit();
         return;
       }
-      if constexpr (XY) {
-        if (wx && own && sX >= 0) {
-          const int z = zx_of(g, j, kk, sX);
-          cp4(&sPH[0][tid], PHi.p[1][0] + z);
-          cp4(&sPH[1][tid], PHi.p[2][0] + z);
-        }
-        if (wy && own && sY >= 0) {
-          const int z = zy_of(g, i, kk, sY);
-          cp4(&sPH[2][tid], PHi.p[0][1] + z);
-          cp4(&sPH[3][tid], PHi.p[2][1] + z);
-        }
-      }
-      if (sZk >= 0 && own) {
-        const int z = zz_of(g, i, j, sZk);
-        cp4(&sPH[4][tid], PHi.p[0][2] + z);
-        cp4(&sPH[5][tid], PHi.p[1][2] + z);
-      }
-      if ((ty == 3 || ty == 4) && (hrow || hcol)) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!(c == 0 ? own0 : own1)) continue;
+        const int sX = c == 0 ? sX0 : sX1, x = i + c;
         if constexpr (XY) {
-          if (sXh >= 0) cp4(&sPH[6][tid], PHi.p[2][0] + zx_of(g, yh, kk, sXh));  // Hz along x
-          if (sYh >= 0) cp4(&sPH[7][tid], PHi.p[2][1] + zy_of(g, xh, kk, sYh));  // Hz along y
-          if (hrow && sYh >= 0) cp4(&sPH[8][tid], PHi.p[0][1] + zy_of(g, xh, kk, sYh));  // Hx along y
-          if (hcol && sXh >= 0) cp4(&sPH[9][tid], PHi.p[1][0] + zx_of(g, yh, kk, sXh));  // Hy along x
+          if (wx && sX >= 0) {
+            const int z = zx_of(g, j, kk, sX);
+            cp4(&sPH[6 * c + 0][tid], PHi.p[1][0] + z);
+            cp4(&sPH[6 * c + 1][tid], PHi.p[2][0] + z);
+          }
+          if (wy && sY >= 0) {
+            const int z = zy_of(g, x, kk, sY);
+            cp4(&sPH[6 * c + 2][tid], PHi.p[0][1] + z);
+            cp4(&sPH[6 * c + 3][tid], PHi.p[2][1] + z);
+          }
         }
-        if (hrow && sZk >= 0) cp4(&sPH[9][tid], PHi.p[0][2] + zz_of(g, xh, yh, sZk));  // Hx along z
-        if (hcol && sZk >= 0) cp4(&sPH[8][tid], PHi.p[1][2] + zz_of(g, xh, yh, sZk));  // Hy along z
+        if (sZk >= 0) {
+          const int z = zz_of(g, x, j, sZk);
+          cp4(&sPH[6 * c + 4][tid], PHi.p[0][2] + z);
+          cp4(&sPH[6 * c + 5][tid], PHi.p[1][2] + z);
+        }
+      }
+      if (hrow) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (c == 1 && !hrow1) continue;
+          const int sX = c == 0 ? sX0 : sX1, x = i + c;
+          if constexpr (XY) {
+            if (sX >= 0) cp4(&sHal[4 * c][hid], PHi.p[2][0] + zx_of(g, j0 - 1, kk, sX));  // Hz along x
+            if (sYh >= 0) {
+              const int z = zy_of(g, x, kk, sYh);
+              cp4(&sHal[4 * c + 1][hid], PHi.p[2][1] + z);  // Hz along y
+              cp4(&sHal[4 * c + 2][hid], PHi.p[0][1] + z);  // Hx along y
+            }
+          }
+          if (sZk >= 0) cp4(&sHal[4 * c + 3][hid], PHi.p[0][2] + zz_of(g, x, j0 - 1, sZk));  // Hx along z
+        }
+      }
+      if (hcol) {
+        if constexpr (XY) {
+          if (sXc >= 0) {
+            const int z = zx_of(g, yc, kk, sXc);
+            cp4(&sHal[0][hid], PHi.p[2][0] + z);  // Hz along x
+            cp4(&sHal[3][hid], PHi.p[1][0] + z);  // Hy along x
+          }
+          if (sYc >= 0) cp4(&sHal[1][hid], PHi.p[2][1] + zy_of(g, i0 - 1, kk, sYc));  // Hz along y
+        }
+        if (sZk >= 0) cp4(&sHal[2][hid], PHi.p[1][2] + zz_of(g, i0 - 1, yc, sZk));  // Hy along z
       }
       cp_commit();
     };
@@ -276,59 +324,69 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
         cp_commit();
         return;
       }
-      if constexpr (XY) {
-        if (wx && own && sX >= 0) {
-          const int z = zx_of(g, j, kk, sX);
-          cp4(&sPE[0][tid], PEi.p[1][0] + z);
-          cp4(&sPE[1][tid], PEi.p[2][0] + z);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!(c == 0 ? own0 : own1)) continue;
+        const int sX = c == 0 ? sX0 : sX1, x = i + c;
+        if constexpr (XY) {
+          if (wx && sX >= 0) {
+            const int z = zx_of(g, j, kk, sX);
+            cp4(&sPE[6 * c + 0][tid], PEi.p[1][0] + z);
+            cp4(&sPE[6 * c + 1][tid], PEi.p[2][0] + z);
+          }
+          if (wy && sY >= 0) {
+            const int z = zy_of(g, x, kk, sY);
+            cp4(&sPE[6 * c + 2][tid], PEi.p[0][1] + z);
+            cp4(&sPE[6 * c + 3][tid], PEi.p[2][1] + z);
+          }
         }
-        if (wy && own && sY >= 0) {
-          const int z = zy_of(g, i, kk, sY);
-          cp4(&sPE[2][tid], PEi.p[0][1] + z);
-          cp4(&sPE[3][tid], PEi.p[2][1] + z);
+        if (sZk >= 0) {
+          const int z = zz_of(g, x, j, sZk);
+          cp4(&sPE[6 * c + 4][tid], PEi.p[0][2] + z);
+          cp4(&sPE[6 * c + 5][tid], PEi.p[1][2] + z);
         }
-      }
-      if (sZk >= 0 && own) {
-        const int z = zz_of(g, i, j, sZk);
-        cp4(&sPE[4][tid], PEi.p[0][2] + z);
-        cp4(&sPE[5][tid], PEi.p[1][2] + z);
       }
       cp_commit();
     };
 
     waited &= mbar_wait(&R.bar[0], 0);
-    float hxm = 0.f, hym = 0.f;
+    // H^{n+1/2} (x and y components) at the own cells of plane k-1, read by the E update of plane k
+    float hxm[2] = {0.f, 0.f}, hym[2] = {0.f, 0.f};
     if (k0 > 0) {
-      // H^{n+1/2} at (i, j, k0-1), read by the first plane's E update (its owner stores it)
+      // plane k0-1 (its owner stores it; this block recomputes it from the staged planes)
       waited &= mbar_wait(&R.bar[1], 0);
       const int km = kb;
       const int sZ = slab_of(km, nz, g.pml[4], g.pml[5]);
-      if (own) {
-        const float(*a0)[EH][EW] = R.E(0);
-        const float(*a1)[EH][EW] = R.E(1);
-        const float dzy = a0[2][ey + 1][ex] - a0[2][ey][ex], dyz = a1[1][ey][ex] - a0[1][ey][ex];
-        const float dxz = a1[0][ey][ex] - a0[0][ey][ex], dzx = a0[2][ey][ex + 1] - a0[2][ey][ex];
+      const float(*a0)[EH][EW] = R.E(0);
+      const float(*a1)[EH][EW] = R.E(1);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!(c == 0 ? own0 : own1)) continue;
+        const int x = i + c, e = ex + c;
+        const float dzy = a0[2][ey + 1][e] - a0[2][ey][e], dyz = a1[1][ey][e] - a0[1][ey][e];
+        const float dxz = a1[0][ey][e] - a0[0][ey][e], dzx = a0[2][ey][e + 1] - a0[2][ey][e];
         float cx = dzy - dyz, cy = dxz - dzx;
         if constexpr (XY) {
           if (sY >= 0) {
             const Coef cyh = coef_at(tabY, 3, ry);
-            cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, i, km, sY)], nullptr, 0);
+            cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, x, km, sY)], nullptr, 0);
           }
         }
         if (sZ >= 0) {
           const Coef cz{T.b[2][1][km], T.c[2][1][km], T.ik[2][1][km]};
-          const int zz = zz_of(g, i, j, sZ);
+          const int zz = zz_of(g, x, j, sZ);
           cx -= corr<false>(dyz, cz.ik, cz.b, cz.c, PHi.p[0][2][zz], nullptr, 0);
           cy += corr<false>(dxz, cz.ik, cz.b, cz.c, PHi.p[1][2][zz], nullptr, 0);
         }
         if constexpr (XY) {
+          const int sX = c == 0 ? sX0 : sX1;
           if (sX >= 0) {
-            const Coef cxh = coef_at(tabX, 3, rx);
+            const Coef cxh = coef_at(tabX, 3, cx0 + c);
             cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
           }
         }
-        hxm = R.H(0)[0][ey][ex] - S * cx;
-        hym = R.H(0)[1][ey][ex] - S * cy;
+        hxm[c] = R.H(0)[0][ey][e] - S * cx;
+        hym[c] = R.H(0)[1][ey][e] - S * cy;
       }
     }
     int sZ = slab_of(k0, nz, g.pml[4], g.pml[5]);  // z slab index of the current plane (-1 off the layers)
@@ -351,185 +409,236 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
       }
       const int pf = pflag[k - k0];
       // soft-source terms of this plane, loaded before the H phase so that their latency overlaps it
-      float sx = 0.f, sy = 0.f, sz = 0.f;
+      float srcv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       if (pf & 1) {
         for (int s = 0; s < A.nsrc; ++s) {
           const SrcDev& sd = A.src[s];
-          if (!own || i < sd.lo[0] || i >= sd.hi[0] || j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2])
-            continue;
-          const float v = sd.w[box_offset(sd.lo, sd.hi, i, j, k)] * sd.g[A.step];
-          if (sd.comp == 0) sx += v;
-          else if (sd.comp == 1) sy += v;
-          else sz += v;
+          if (j < sd.lo[1] || j >= sd.hi[1] || k < sd.lo[2] || k >= sd.hi[2]) continue;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int x = i + c;
+            if (!(c == 0 ? own0 : own1) || x < sd.lo[0] || x >= sd.hi[0]) continue;
+            const float v = sd.w[box_offset(sd.lo, sd.hi, x, j, k)] * sd.g[A.step];
+            if (sd.comp == 0) srcv[c][0] += v;
+            else if (sd.comp == 1) srcv[c][1] += v;
+            else srcv[c][2] += v;
+          }
         }
       }
       waited &= mbar_wait(&R.bar[b1], ph1);  // plane k+1 (plane k was waited for before)
-      cp_wait_all_but_one();                                      // psi_old of H at plane k
+      cp_wait_all_but_one();                 // psi_old of H at plane k
       const float(*ek)[EH][EW] = R.E(b0);
       const float(*ek1)[EH][EW] = R.E(b1);
       const float(*hk)[HH][HW] = R.H(b0);
       float(*sH)[HY][HX] = sHb[it & 1];
 
-      // (b) H^{n+1/2} on plane k: own cell (plain Yee update plus the CPML correction in the layers)
-      float hx = 0.f, hy = 0.f, hz = 0.f;
-      if (own) {
-        const float dzy = ek[2][ey + 1][ex] - ek[2][ey][ex], dyz = ek1[1][ey][ex] - ek[1][ey][ex];
-        const float dxz = ek1[0][ey][ex] - ek[0][ey][ex], dzx = ek[2][ey][ex + 1] - ek[2][ey][ex];
-        const float dyx = ek[1][ey][ex + 1] - ek[1][ey][ex], dxy = ek[0][ey + 1][ex] - ek[0][ey][ex];
-        float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
-        if constexpr (XY) {
-          if (wx && sX >= 0) {
-            const Coef c = coef_at(tabX, 3, rx);
-            const int z = zx_of(g, j, k, sX);
-            cy -= corr<true>(dzx, c.ik, c.b, c.c, sPH[0][tid], PHo.p[1][0], z);
-            cz += corr<true>(dyx, c.ik, c.b, c.c, sPH[1][tid], PHo.p[2][0], z);
+      // (b) H^{n+1/2} on plane k at the own pair (plain Yee update plus the CPML correction in the
+      // layers); E^n and a of the pair stay in registers for the E update
+      const float2 exa = ld2(&ek[0][ey][ex]), eya = ld2(&ek[1][ey][ex]), eza = ld2(&ek[2][ey][ex]);
+      const float2 av = ld2(&R.Av(b0)[ty][2 * lx]);
+      float hx[2] = {0.f, 0.f}, hy[2] = {0.f, 0.f}, hz[2] = {0.f, 0.f};
+      if (own0) {
+        const float2 exb = ld2(&ek[0][ey + 1][ex]), ezb = ld2(&ek[2][ey + 1][ex]);
+        const float2 exc = ld2(&ek1[0][ey][ex]), eyc = ld2(&ek1[1][ey][ex]);
+        const float ey2 = ek[1][ey][ex + 2], ez2 = ek[2][ey][ex + 2];
+        const float2 hxo = ld2(&hk[0][ey][ex]), hyo = ld2(&hk[1][ey][ex]), hzo = ld2(&hk[2][ey][ex]);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float ex_ = c ? exa.y : exa.x, ey_ = c ? eya.y : eya.x, ez_ = c ? eza.y : eza.x;
+          const float dzy = (c ? ezb.y : ezb.x) - ez_, dyz = (c ? eyc.y : eyc.x) - ey_;
+          const float dxz = (c ? exc.y : exc.x) - ex_, dzx = (c ? ez2 : eza.y) - ez_;
+          const float dyx = (c ? ey2 : eya.y) - ey_, dxy = (c ? exb.y : exb.x) - ex_;
+          float cx = dzy - dyz, cy = dxz - dzx, cz = dyx - dxy;
+          const int x = i + c;
+          const bool ok = c == 0 || own1;  // the cell is in the grid (psi is written only then)
+          if constexpr (XY) {
+            const int sX = c == 0 ? sX0 : sX1;
+            if (wx && sX >= 0 && ok) {
+              const Coef cc = coef_at(tabX, 3, cx0 + c);
+              const int z = zx_of(g, j, k, sX);
+              cy -= corr<true>(dzx, cc.ik, cc.b, cc.c, sPH[6 * c + 0][tid], PHo.p[1][0], z);
+              cz += corr<true>(dyx, cc.ik, cc.b, cc.c, sPH[6 * c + 1][tid], PHo.p[2][0], z);
+            }
+            if (wy && sY >= 0 && ok) {
+              const Coef cc = coef_at(tabY, 3, ry);
+              const int z = zy_of(g, x, k, sY);
+              cx += corr<true>(dzy, cc.ik, cc.b, cc.c, sPH[6 * c + 2][tid], PHo.p[0][1], z);
+              cz -= corr<true>(dxy, cc.ik, cc.b, cc.c, sPH[6 * c + 3][tid], PHo.p[2][1], z);
+            }
           }
-          if (wy && sY >= 0) {
-            const Coef c = coef_at(tabY, 3, ry);
-            const int z = zy_of(g, i, k, sY);
-            cx += corr<true>(dzy, c.ik, c.b, c.c, sPH[2][tid], PHo.p[0][1], z);
-            cz -= corr<true>(dxy, c.ik, c.b, c.c, sPH[3][tid], PHo.p[2][1], z);
+          if (sZ >= 0 && ok) {
+            const int z = zz_of(g, x, j, sZ);
+            cx -= corr<true>(dyz, czh.ik, czh.b, czh.c, sPH[6 * c + 4][tid], PHo.p[0][2], z);
+            cy += corr<true>(dxz, czh.ik, czh.b, czh.c, sPH[6 * c + 5][tid], PHo.p[1][2], z);
           }
+          hx[c] = (c ? hxo.y : hxo.x) - S * cx;
+          hy[c] = (c ? hyo.y : hyo.x) - S * cy;
+          hz[c] = (c ? hzo.y : hzo.x) - S * cz;
         }
-        if (sZ >= 0) {
-          const int z = zz_of(g, i, j, sZ);
-          cx -= corr<true>(dyz, czh.ik, czh.b, czh.c, sPH[4][tid], PHo.p[0][2], z);
-          cy += corr<true>(dxz, czh.ik, czh.b, czh.c, sPH[5][tid], PHo.p[1][2], z);
-        }
-        hx = hk[0][ey][ex] - S * cx;
-        hy = hk[1][ey][ex] - S * cy;
-        hz = hk[2][ey][ex] - S * cz;
-        sH[0][ry][rx] = hx;
-        sH[1][ry][rx] = hy;
-        sH[2][ry][rx] = hz;
-        N.f[3][q] = hx;
-        N.f[4][q] = hy;
-        N.f[5][q] = hz;
+        if (!own1) hx[1] = hy[1] = hz[1] = 0.f;  // the pitch padding x >= nx holds zeros
+        st2(&sH[0][ry][rx], hx[0], hx[1]);
+        st2(&sH[1][ry][rx], hy[0], hy[1]);
+        st2(&sH[2][ry][rx], hz[0], hz[1]);
+        st2(&N.f[3][q], hx[0], hx[1]);
+        st2(&N.f[4][q], hy[0], hy[1]);
+        st2(&N.f[5][q], hz[0], hz[1]);
       }
-      // the low halo: (i, j0-1) gives Hx, Hz; (i0-1, j0+r) gives Hy, Hz
-      if ((ty == 3 || ty == 4) && (hrow || hcol)) {
-        const int r = hey, c = hex;
+      // the low halo row (i, j0-1), (i+1, j0-1): Hx, Hz
+      if (hrow) {
+        const float2 exr = ld2(&ek[0][0][ex]), exr1 = ld2(&ek[0][1][ex]);
+        const float2 eyr = ld2(&ek[1][0][ex]), eyrk = ld2(&ek1[1][0][ex]);
+        const float2 ezr = ld2(&ek[2][0][ex]), ezr1 = ld2(&ek[2][1][ex]);
+        const float eyr2 = ek[1][0][ex + 2];
+        const float2 hxo = ld2(&hk[0][0][ex]), hzo = ld2(&hk[2][0][ex]);
+        float hxr[2], hzr[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float eyv = c ? eyr.y : eyr.x;
+          const float dyx = (c ? eyr2 : eyr.y) - eyv, dxy = (c ? exr1.y : exr1.x) - (c ? exr.y : exr.x);
+          const float dzy = (c ? ezr1.y : ezr1.x) - (c ? ezr.y : ezr.x), dyz = (c ? eyrk.y : eyrk.x) - eyv;
+          float cz = dyx - dxy, cx = dzy - dyz;
+          const bool ok = c == 0 || hrow1;  // the halo cell is in the grid (its slots were filled)
+          if constexpr (XY) {
+            const int sX = c == 0 ? sX0 : sX1;
+            if (sX >= 0 && ok) {
+              const Coef chx = coef_at(tabX, 3, cx0 + c);
+              cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sHal[4 * c][hid], nullptr, 0);
+            }
+            if (sYh >= 0 && ok) {
+              const Coef chy = coef_at(tabY, 3, 0);
+              cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sHal[4 * c + 1][hid], nullptr, 0);
+              cx += corr<false>(dzy, chy.ik, chy.b, chy.c, sHal[4 * c + 2][hid], nullptr, 0);
+            }
+          }
+          if (sZ >= 0 && ok) cx -= corr<false>(dyz, czh.ik, czh.b, czh.c, sHal[4 * c + 3][hid], nullptr, 0);
+          hzr[c] = (c ? hzo.y : hzo.x) - S * cz;
+          hxr[c] = (c ? hxo.y : hxo.x) - S * cx;
+        }
+        st2(&sH[2][0][rx], hzr[0], hzr[1]);
+        st2(&sH[0][0][rx], hxr[0], hxr[1]);
+      }
+      // the low halo column (i0-1, j0+lx): Hy, Hz
+      if (hcol) {
+        const int r = lx + 1, c = XO - 1;
         const float dyx = ek[1][r][c + 1] - ek[1][r][c], dxy = ek[0][r + 1][c] - ek[0][r][c];
-        float cz = dyx - dxy;
+        const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
+        float cz = dyx - dxy, cy = dxz - dzx;
         if constexpr (XY) {
-          if (sXh >= 0) {
-            const Coef chx = coef_at(tabX, 3, hrx);
-            cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sPH[6][tid], nullptr, 0);
+          if (sXc >= 0) {
+            const Coef chx = coef_at(tabX, 3, 0);
+            cz += corr<false>(dyx, chx.ik, chx.b, chx.c, sHal[0][hid], nullptr, 0);
+            cy -= corr<false>(dzx, chx.ik, chx.b, chx.c, sHal[3][hid], nullptr, 0);
           }
-          if (sYh >= 0) {
-            const Coef chy = coef_at(tabY, 3, hry);
-            cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sPH[7][tid], nullptr, 0);
+          if (sYc >= 0) {
+            const Coef chy = coef_at(tabY, 3, r);
+            cz -= corr<false>(dxy, chy.ik, chy.b, chy.c, sHal[1][hid], nullptr, 0);
           }
         }
-        sH[2][hry][hrx] = hk[2][r][c] - S * cz;
-        if (hrow) {  // Hx
-          const float dzy = ek[2][r + 1][c] - ek[2][r][c], dyz = ek1[1][r][c] - ek[1][r][c];
-          float cx = dzy - dyz;
-          if constexpr (XY) {
-            if (sYh >= 0) {
-              const Coef chy = coef_at(tabY, 3, hry);
-              cx += corr<false>(dzy, chy.ik, chy.b, chy.c, sPH[8][tid], nullptr, 0);
-            }
-          }
-          if (sZ >= 0) cx -= corr<false>(dyz, czh.ik, czh.b, czh.c, sPH[9][tid], nullptr, 0);
-          sH[0][hry][hrx] = hk[0][r][c] - S * cx;
-        } else {  // Hy
-          const float dxz = ek1[0][r][c] - ek[0][r][c], dzx = ek[2][r][c + 1] - ek[2][r][c];
-          float cy = dxz - dzx;
-          if (sZ >= 0) cy += corr<false>(dxz, czh.ik, czh.b, czh.c, sPH[8][tid], nullptr, 0);
-          if constexpr (XY) {
-            if (sXh >= 0) {
-              const Coef chx = coef_at(tabX, 3, hrx);
-              cy -= corr<false>(dzx, chx.ik, chx.b, chx.c, sPH[9][tid], nullptr, 0);
-            }
-          }
-          sH[1][hry][hrx] = hk[1][r][c] - S * cy;
-        }
+        if (sZ >= 0) cy += corr<false>(dxz, czh.ik, czh.b, czh.c, sHal[2][hid], nullptr, 0);
+        sH[2][r][1] = hk[2][r][c] - S * cz;
+        sH[1][r][1] = hk[1][r][c] - S * cy;
       }
       if (k + 1 < k1) fetch_psiH(k + 1, sZn);
       else cp_commit();
       __syncthreads();
-      // every thread is past plane k-1, so its stage can take plane k-1+NSTAGE
-      if (tid == 0 && it >= 1 && k - 1 + NSTAGE <= k1) {
+      // the H phase is the last reader of plane k's stage (the E phase works from registers and the
+      // new-H tile), so every thread being past it frees the stage for plane k+NSTAGE; on the first
+      // plane of a chunk that starts above 0 the stage of plane k0-1 (read by the prologue only) is
+      // refilled too
+      if (tid == 0) {
         async_proxy_fence();
-        R.issue(M, b0 == 0 ? NSTAGE - 1 : b0 - 1, i0, j0, k - 1 + NSTAGE);  // the stage of plane k-1
+        if (k == k0 && kb < k0 && kb + NSTAGE <= k1) R.issue(M, 0, i0, j0, kb + NSTAGE);
+        if (k + NSTAGE <= k1) R.issue(M, b0, i0, j0, k + NSTAGE);
       }
       cp_wait_all_but_one();  // psi_old of E at plane k
 
-      // (c) E^{n+1} on plane k at the own cell (tangential E on a PEC wall at index 0 is held), then
+      // (c) E^{n+1} on plane k at the own pair (tangential E on a PEC wall at index 0 is held), then
       // sources and detectors
-      float exv = 0.f, eyv = 0.f, ezv = 0.f;
-      if (own) {
-        const float Sa = S * R.Av(b0)[ty][tx];
-        exv = ek[0][ey][ex];
-        eyv = ek[1][ey][ex];
-        ezv = ek[2][ey][ex];
-        const float d1x = hz - sH[2][ry - 1][rx], d2x = hy - hym;   // E_x: along y, along z
-        const float d1y = hx - hxm, d2y = hz - sH[2][ry][rx - 1];   // E_y: along z, along x
-        const float d1z = hy - sH[1][ry][rx - 1], d2z = hx - sH[0][ry - 1][rx];  // E_z: along x, along y
-        float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
-        // (a component held by a PEC wall keeps psi = 0: its memory is neither updated nor used)
-        const bool ux = j > 0 && k > 0, uy = i > 0 && k > 0, uz = i > 0 && j > 0;
-        if constexpr (XY) {
-          if (wx && sX >= 0) {
-            const Coef c = coef_at(tabX, 0, rx);
-            const int z = zx_of(g, j, k, sX);
-            if (uy) cy -= corr<true>(d2y, c.ik, c.b, c.c, sPE[0][tid], PEo.p[1][0], z);
-            if (uz) cz += corr<true>(d1z, c.ik, c.b, c.c, sPE[1][tid], PEo.p[2][0], z);
+      float ev[2][3] = {{exa.x, eya.x, eza.x}, {exa.y, eya.y, eza.y}};
+      if (own0) {
+        const float2 hzs = ld2(&sH[2][ry - 1][rx]), hxs = ld2(&sH[0][ry - 1][rx]);  // at y-1
+        const float hyl = sH[1][ry][rx - 1], hzl = sH[2][ry][rx - 1];             // at x-1 of cell 0
+        const bool ux = j > 0 && k > 0;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float d1x = hz[c] - (c ? hzs.y : hzs.x), d2x = hy[c] - hym[c];              // E_x: along y, z
+          const float d1y = hx[c] - hxm[c], d2y = hz[c] - (c ? hz[0] : hzl);                 // E_y: along z, x
+          const float d1z = hy[c] - (c ? hy[0] : hyl), d2z = hx[c] - (c ? hxs.y : hxs.x);  // E_z: along x, y
+          float cx = d1x - d2x, cy = d1y - d2y, cz = d1z - d2z;
+          const int x = i + c;
+          // (a component held by a PEC wall keeps psi = 0: its memory is neither updated nor used)
+          const bool uy = x > 0 && k > 0, uz = x > 0 && j > 0;
+          const bool ok = c == 0 || own1;
+          if constexpr (XY) {
+            const int sX = c == 0 ? sX0 : sX1;
+            if (wx && sX >= 0 && ok) {
+              const Coef cc = coef_at(tabX, 0, cx0 + c);
+              const int z = zx_of(g, j, k, sX);
+              if (uy) cy -= corr<true>(d2y, cc.ik, cc.b, cc.c, sPE[6 * c + 0][tid], PEo.p[1][0], z);
+              if (uz) cz += corr<true>(d1z, cc.ik, cc.b, cc.c, sPE[6 * c + 1][tid], PEo.p[2][0], z);
+            }
+            if (wy && sY >= 0 && ok) {
+              const Coef cc = coef_at(tabY, 0, ry);
+              const int z = zy_of(g, x, k, sY);
+              if (ux) cx += corr<true>(d1x, cc.ik, cc.b, cc.c, sPE[6 * c + 2][tid], PEo.p[0][1], z);
+              if (uz) cz -= corr<true>(d2z, cc.ik, cc.b, cc.c, sPE[6 * c + 3][tid], PEo.p[2][1], z);
+            }
           }
-          if (wy && sY >= 0) {
-            const Coef c = coef_at(tabY, 0, ry);
-            const int z = zy_of(g, i, k, sY);
-            if (ux) cx += corr<true>(d1x, c.ik, c.b, c.c, sPE[2][tid], PEo.p[0][1], z);
-            if (uz) cz -= corr<true>(d2z, c.ik, c.b, c.c, sPE[3][tid], PEo.p[2][1], z);
+          if (sZ >= 0 && ok) {
+            const int z = zz_of(g, x, j, sZ);
+            if (ux) cx -= corr<true>(d2x, cze.ik, cze.b, cze.c, sPE[6 * c + 4][tid], PEo.p[0][2], z);
+            if (uy) cy += corr<true>(d1y, cze.ik, cze.b, cze.c, sPE[6 * c + 5][tid], PEo.p[1][2], z);
           }
+          const float Sa = S * (c ? av.y : av.x);
+          if (ux) ev[c][0] += Sa * cx;
+          if (uy) ev[c][1] += Sa * cy;
+          if (uz) ev[c][2] += Sa * cz;
+          ev[c][0] += srcv[c][0];
+          ev[c][1] += srcv[c][1];
+          ev[c][2] += srcv[c][2];
         }
-        if (sZ >= 0) {
-          const int z = zz_of(g, i, j, sZ);
-          if (ux) cx -= corr<true>(d2x, cze.ik, cze.b, cze.c, sPE[4][tid], PEo.p[0][2], z);
-          if (uy) cy += corr<true>(d1y, cze.ik, cze.b, cze.c, sPE[5][tid], PEo.p[1][2], z);
-        }
-        if (j > 0 && k > 0) exv += Sa * cx;
-        if (i > 0 && k > 0) eyv += Sa * cy;
-        if (i > 0 && j > 0) ezv += Sa * cz;
-        exv += sx;
-        eyv += sy;
-        ezv += sz;
-        N.f[0][q] = exv;
-        N.f[1][q] = eyv;
-        N.f[2][q] = ezv;
+        if (!own1) ev[1][0] = ev[1][1] = ev[1][2] = 0.f;  // the pitch padding x >= nx holds zeros
+        st2(&N.f[0][q], ev[0][0], ev[1][0]);
+        st2(&N.f[1][q], ev[0][1], ev[1][1]);
+        st2(&N.f[2][q], ev[0][2], ev[1][2]);
       }
-      // detectors (block-uniform branch; flux partials are reduced over the warp in a fixed order and
-      // summed per warp over the planes)
+      // detectors (block-uniform branch; flux partials are reduced over each tile row in a fixed
+      // order and summed per row over the planes)
       if (pf & 2) {
-  #pragma unroll
+#pragma unroll
         for (int s = 0; s < kMaxDet; ++s) {
           if (s >= A.ndet) break;
           const DetDev& d = A.det[s];
-          const bool in = own && i >= d.lo[0] && i < d.hi[0] && j >= d.lo[1] && j < d.hi[1] && k >= d.lo[2] && k < d.hi[2];
-          if (d.kind == 0) {
-            if (in) A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, exv, eyv, ezv) : pick3(d.comp - 3, hx, hy, hz));
-          } else if (d.kind == 1) {
-            if (in) A.det_out[d.off + box_offset(d.lo, d.hi, i, j, k)] += (double)exv * exv + (double)eyv * eyv + (double)ezv * ezv;
-          } else if (k >= d.lo[2] && k < d.hi[2]) {
-            const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
-            double f = in ? (double)pick3(a1, exv, eyv, ezv) * (double)pick3(a2, hx, hy, hz) -
-                                (double)pick3(a2, exv, eyv, ezv) * (double)pick3(a1, hx, hy, hz)
-                          : 0.0;
-            if (d.axis == 0) {  // an x-normal plane holds at most one lane of each warp
-              if (in) wflux[s][ty] += f;
-            } else {
-  #pragma unroll
-              for (int o = 16; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o);
-              if (tx == 0) wflux[s][ty] += f;
+          const bool iny = j >= d.lo[1] && j < d.hi[1] && k >= d.lo[2] && k < d.hi[2];
+          double f = 0.0;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const int x = i + c;
+            const bool in = (c == 0 ? own0 : own1) && iny && x >= d.lo[0] && x < d.hi[0];
+            const float e0 = ev[c][0], e1 = ev[c][1], e2 = ev[c][2];
+            if (d.kind == 0) {
+              if (in) A.det_out[d.off + A.step] = (double)(d.comp < 3 ? pick3(d.comp, e0, e1, e2) : pick3(d.comp - 3, hx[c], hy[c], hz[c]));
+            } else if (d.kind == 1) {
+              if (in) A.det_out[d.off + box_offset(d.lo, d.hi, x, j, k)] += (double)e0 * e0 + (double)e1 * e1 + (double)e2 * e2;
+            } else if (in) {
+              const int a1 = (d.axis + 1) % 3, a2 = (d.axis + 2) % 3;
+              f += (double)pick3(a1, e0, e1, e2) * (double)pick3(a2, hx[c], hy[c], hz[c]) -
+                   (double)pick3(a2, e0, e1, e2) * (double)pick3(a1, hx[c], hy[c], hz[c]);
             }
+          }
+          if (d.kind == 2 && k >= d.lo[2] && k < d.hi[2]) {  // sum over the row's 16 lanes, then one add
+#pragma unroll
+            for (int o = LX / 2; o > 0; o >>= 1) f += __shfl_down_sync(0xffffffffu, f, o, LX);
+            if (lx == 0) wflux[s][ty] += f;
           }
         }
       }
       if (k + 1 < k1) fetch_psiE(k + 1, sZn);
       else cp_commit();
-      hxm = hx;
-      hym = hy;
+      hxm[0] = hx[0];
+      hxm[1] = hx[1];
+      hym[0] = hy[0];
+      hym[1] = hy[1];
       sZ = sZn;
       b0 = b1;
       b1 = b1 + 1 == NSTAGE ? 0 : b1 + 1;
@@ -540,9 +649,9 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
   else march(Flag<false>{});
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (!waited) atomicOr(A.status, 1);
-  __syncthreads();  // every warp's flux sums are in place
+  __syncthreads();  // every row's flux sums are in place
 
-  // flux detectors: this block's partial sum (warp sums in warp order) into its slot
+  // flux detectors: this block's partial sum (row sums in row order) into its slot
   if (tid == 0) {
 #pragma unroll
     for (int s = 0; s < kMaxDet; ++s) {
@@ -555,7 +664,7 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_fwd_fused(const Fwd
       const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
       if (bx < bx0 || bx > bx1 || by < by0 || by > by1 || bz < bz0 || bz > bz1) continue;
       double sum = 0.0;
-      for (int w = 0; w < NT / 32; ++w) sum += wflux[s][w];
+      for (int r = 0; r < TY; ++r) sum += wflux[s][r];
       const int64_t slotid = ((int64_t)(bz - bz0) * (by1 - by0 + 1) + (by - by0)) * (bx1 - bx0 + 1) + (bx - bx0);
       A.partial[d.poff + (int64_t)A.step * d.nblk + slotid] = sum;
     }

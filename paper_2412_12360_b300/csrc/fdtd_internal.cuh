@@ -152,6 +152,8 @@ struct RevArgs {
 int fused_tile_x();
 int fused_max_tz();   // z-planes one block of the forward kernel may march at most
 int fused_tile_y();
+int rev_tile_x();     // column tile of the reverse kernels
+int rev_tile_y();
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s);
 void launch_set_box(const Geo& g, float* a, const int* lo, const int* hi, const float* box, cudaStream_t s);
 

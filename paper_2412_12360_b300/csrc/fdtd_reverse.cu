@@ -515,6 +515,9 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
 
 }  // namespace
 
+int rev_tile_x() { return TX; }
+int rev_tile_y() { return TY; }
+
 MapBox rev_box_own() { return {TX, TY}; }
 MapBox rev_box_wide() { return {BW, BH}; }
 
