@@ -2,7 +2,9 @@
 
 Bars: fields after the run within 1e-4 relative L2; detector outputs within 1e-4 relative; dL/deps
 within 1e-3 relative L2 over the design box (and the max error is reported). Grids span several
-32 x 8 thread tiles with ragged tails; layers differ per face.
+column tiles of both the forward (32 x 16) and the reverse (32 x 8) kernels with ragged tails, one
+with an odd x extent (the forward kernel's last cell pair then has one cell in the grid); layers
+differ per face.
 """
 import numpy as np
 import pytest
@@ -47,6 +49,27 @@ def ragged_scene(nsteps=600, seed=41):
                        nsteps=nsteps, name="ragged")
 
 
+def odd_scene(nsteps=400, seed=43, pml=(5, 7, 4, 6, 6, 3)):
+    """Odd nx, sources, detectors and the design box reaching the last x column, and a two-cell-thick
+    x-normal flux box whose cells fall in two different cell pairs."""
+    n = (67, 37, 29)
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    eps_inv = np.ones((nz, ny, nx), dtype=np.float32)
+    dlo, dhi = (41, 9, 8), (67, 30, 22)
+    eps_inv[dlo[2]:dhi[2], dlo[1]:dhi[1], dlo[0]:dhi[0]] = S.inv(
+        1.0 + 11.1 * rng.random((dhi[2] - dlo[2], dhi[1] - dlo[1], dhi[0] - dlo[0])))
+    prof = S.gaussian_sheet((ny - 10, nx - 5), 10.0)[None]
+    sheet = S.default_pulse(S.Source(S.EY, (5, 5, 8), (nx, ny - 5, 9), prof, 1.0, 12.0), S.courant_from_factor())
+    pt = H.point_source(S.EZ, (66, 20, 14), wavelength=9.0, amplitude=0.5)
+    dets = [H.point_probe(S.EZ, (66, 18, 16)),
+            S.Detector(S.DET_PLANE_E2_SUM, (50, 6, 20), (67, 31, 21)),
+            S.Detector(S.DET_PLANE_FLUX, (41, 6, 6), (43, 31, 23), axis=0),
+            S.Detector(S.DET_PLANE_FLUX, (5, 6, 23), (66, 31, 24), axis=2)]
+    return H.box_scene(n, pml=pml, eps_inv=eps_inv, sources=[sheet, pt], detectors=dets, design=(dlo, dhi),
+                       nsteps=nsteps, name="odd_x")
+
+
 def test_forward_pec_cavity_1000_steps(F):
     sc = S.cavity_32(1000)
     f_o, d_o = O.forward(sc, 1000)
@@ -77,6 +100,35 @@ def test_forward_cpml_ragged_grid(F):
         print("  detector kind %d rel %.3e" % (d.kind, ed))
         assert ed < 1e-4
         off += m
+
+
+def test_forward_and_gradient_odd_x_extent(F):
+    sc = odd_scene(400)
+    f_o, d_o = O.forward(sc, 400)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(400)
+        f_g = s.fields()
+        d_g = s.detectors()
+    e = rel_l2(f_g, f_o)
+    print("odd_x 400 steps: fields rel L2 %.3e" % e)
+    assert e < 1e-4
+    off = 0
+    for d in sc.detectors:
+        m = 400 if d.kind != S.DET_PLANE_E2_SUM else int(np.prod([d.hi[k] - d.lo[k] for k in range(3)]))
+        ed = rel_l2(d_g[off:off + m], d_o[off:off + m])
+        print("  detector kind %d rel %.3e" % (d.kind, ed))
+        assert ed < 1e-4
+        off += m
+    # the gradient needs its detectors off the layers: no layer on the high x face (a PEC wall there)
+    sc = odd_scene(300, pml=(5, 0, 4, 6, 6, 3))
+    g = np.random.default_rng(9).standard_normal(O.detector_total(sc, 300))
+    grad_o, _, _ = O.gradient(sc, 300, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(300, record_faces=True)
+        grad_g = s.gradient(g)
+    e = rel_l2(grad_g, grad_o)
+    print("odd_x 300 steps: dL/deps rel L2 %.3e" % e)
+    assert e < 1e-3
 
 
 def test_forward_from_initial_state_and_zero_steps(F):
