@@ -529,6 +529,60 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_design(args, world, rank, local):
+    """The inverse-design loop (design.DesignLoop) on the workload's design box: per iteration the
+    projection, the density map, the recorded forward, the objective (the negated sum of the
+    workload's detector outputs: maximise the |E|^2 plane or the flux), the reverse sweep for dL/drho
+    and the Adam step. beta = 0 for the first half of the iterations, then 8 (binarisation)."""
+    import torch
+    from paper_2412_12360_b300 import design, fdtd
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sc, desc = workload(args.workload)
+    if args.time_steps:
+        sc.nsteps = args.time_steps
+        desc += " [time steps overridden: %d]" % args.time_steps
+    T = sc.nsteps
+    eps_lo, eps_hi = sc.extra.get("eps_lo", 1.0), sc.extra.get("eps_hi", 12.1)
+    stream = torch.cuda.Stream(device=dev)
+    iters = args.design_iters
+    theta0 = torch.full(sc.design_shape(), 0.5, dtype=torch.float32, device=dev)
+    beta_of = lambda it: 0.0 if it < iters // 2 else 8.0
+    with torch.cuda.stream(stream):
+        solver = fdtd.Solver(sc, stream=stream)
+        loop = design.DesignLoop(solver, theta0, eps_lo, eps_hi, T, lambda det: (-det.sum(), -torch.ones_like(det)),
+                                 lr=0.02, beta_of=beta_of)
+        for _ in range(args.warmup):       # warm-up iterations (graph captures), then a fresh loop
+            loop.step()
+        stream.synchronize()
+        loop = design.DesignLoop(solver, theta0, eps_lo, eps_hi, T, lambda det: (-det.sum(), -torch.ones_like(det)),
+                                 lr=0.02, beta_of=beta_of)
+        barrier(world)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        losses = [loop.step() for _ in range(iters)]
+        b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b)
+        losses = [float(x) for x in losses]
+        rho = loop.rho.float()
+        binary = float(((rho < 0.05) | (rho > 0.95)).float().mean())
+        solver.close()
+    ms_max = max_over_ranks(ms, world, dev)
+    if rank != 0:
+        return
+    line = {"metric": "inverse-design iterations (fwd+grad+Adam) in Gcell-steps/s", "unit": UNIT,
+            "value": round(world * sc.ncells * T * iters / (ms_max * 1e-3) / 1e9, 4), "n_gpus": world,
+            "iterations": iters, "ms_per_iteration": round(ms_max / iters, 3), "higher_is_better": True,
+            "loss_first": losses[0], "loss_last": losses[-1], "binary_fraction_last": round(binary, 4),
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc + "; design loop: theta0 = 0.5, Adam lr 0.02, projection beta 0 then 8",
+                       "grid": list(sc.n), "time_steps": T, "design": list(sc.design_shape())}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -551,6 +605,8 @@ def main():
     ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference check of --batched")
+    ap.add_argument("--design-loop", action="store_true", help="measure the inverse-design loop instead")
+    ap.add_argument("--design-iters", type=int, default=10)
     args = ap.parse_args()
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
@@ -559,6 +615,8 @@ def main():
         run_serve(args, world, rank, local)
     elif args.batched:
         run_batched(args, world, rank, local)
+    elif args.design_loop:
+        run_design(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -121,6 +121,29 @@ int fdtd_set_design_density(fdtd_handle* h, const float* rho_box, double eps_lo,
  * last fdtd_set_design_density (STATE if there was none). */
 int fdtd_backward_density(fdtd_handle* h, const double* dL_ddet, float* dL_drho);
 
+/* One step of the inverse-design loop that drives the forward and gradient solves (Sec. 3.2-3.3:
+ * gradient-based optimisation of a design quantised to two materials). The design densities are
+ * rho = P(theta), the smoothed Heaviside projection of latent variables theta in [0, 1] that pushes
+ * rho towards 0 or 1 as proj_beta grows (binarisation; proj_beta = 0 is the identity):
+ *   P(theta) = (tanh(beta eta) + tanh(beta (theta - eta))) / (tanh(beta eta) + tanh(beta (1 - eta))).
+ * Given dL/drho at rho = P(theta) (from fdtd_backward_density), the step is Adam (Kingma and Ba):
+ *   g = dL/drho P'(theta); m = beta1 m + (1 - beta1) g; v = beta2 v + (1 - beta2) g^2;
+ *   theta -= lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps), then clamped to [0, 1];
+ *   rho_out = P(theta).
+ * All five arrays are DEVICE pointers of design-box cells (x fastest, fp32): dL_drho is read,
+ * theta, m and v are updated in place, rho_out is written (it may alias nothing else). The work is
+ * enqueued on the solver's stream; t >= 1 is the step count. INVALID_ARG on a NULL or host pointer,
+ * t < 1, lr <= 0, beta1 or beta2 outside [0, 1), eps <= 0, proj_beta < 0 or proj_eta outside (0, 1). */
+int fdtd_design_adam_step(fdtd_handle* h, const float* dL_drho, float* theta, float* m, float* v, float* rho_out,
+                          int32_t t, double lr, double beta1, double beta2, double eps, double proj_beta,
+                          double proj_eta);
+
+/* rho_out = P(theta) with the projection of fdtd_design_adam_step (used when proj_beta changes between
+ * steps, and for the first densities). theta and rho_out: DEVICE pointers of design-box cells, fp32,
+ * enqueued on the solver's stream. INVALID_ARG on a NULL or host pointer, proj_beta < 0 or proj_eta
+ * outside (0, 1). */
+int fdtd_design_project(fdtd_handle* h, const float* theta, float* rho_out, double proj_beta, double proj_eta);
+
 /* Set the initial state E^0, H^{-1/2} (host or device, 6*nx*ny*nz floats, field-major, x fastest);
  * NULL restores zero fields. Used for round-trip and eigenmode tests. */
 int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6);

@@ -1089,6 +1089,37 @@ int fdtd_set_design_density(fdtd_handle* h, const float* rho_box, double eps_lo,
   return FDTD_OK;
 }
 
+int fdtd_design_adam_step(fdtd_handle* h, const float* dL_drho, float* theta, float* m, float* v, float* rho_out,
+                          int32_t t, double lr, double beta1, double beta2, double eps, double proj_beta,
+                          double proj_eta) {
+  if (!h || !dL_drho || !theta || !m || !v || !rho_out) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  if (is_host_pointer(dL_drho) || is_host_pointer(theta) || is_host_pointer(m) || is_host_pointer(v) ||
+      is_host_pointer(rho_out))
+    return fail(FDTD_ERR_INVALID_ARG, "the design-loop arrays must be device memory");
+  if (t < 1 || !(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps > 0.0) ||
+      !(proj_beta >= 0.0) || !(proj_eta > 0.0 && proj_eta < 1.0))
+    return fail(FDTD_ERR_INVALID_ARG, "design step: need t >= 1, lr > 0, beta1/beta2 in [0, 1), eps > 0, "
+                                      "proj_beta >= 0, proj_eta in (0, 1)");
+  const int64_t n = box_cells(h->design_lo, h->design_hi);
+  launch_design_adam(dL_drho, theta, m, v, rho_out, n, t, lr, beta1, beta2, eps, proj_beta, proj_eta, h->stream);
+  if (n > 0) h->launches += 1;
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int fdtd_design_project(fdtd_handle* h, const float* theta, float* rho_out, double proj_beta, double proj_eta) {
+  if (!h || !theta || !rho_out) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  if (is_host_pointer(theta) || is_host_pointer(rho_out))
+    return fail(FDTD_ERR_INVALID_ARG, "the design-loop arrays must be device memory");
+  if (!(proj_beta >= 0.0) || !(proj_eta > 0.0 && proj_eta < 1.0))
+    return fail(FDTD_ERR_INVALID_ARG, "projection: need proj_beta >= 0 and proj_eta in (0, 1)");
+  const int64_t n = box_cells(h->design_lo, h->design_hi);
+  launch_design_project(theta, rho_out, n, proj_beta, proj_eta, h->stream);
+  if (n > 0) h->launches += 1;
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
 int fdtd_read_detectors(fdtd_handle* h, double* out) {
   if (!h || !out) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
   if (h->last_nsteps < 0) return fail(FDTD_ERR_STATE, "no forward has run");

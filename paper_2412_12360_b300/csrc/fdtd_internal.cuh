@@ -131,6 +131,9 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
                              const double* dL_ddet, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, double scale, cudaStream_t s);
+void launch_design_adam(const float* g_rho, float* theta, float* m, float* v, float* rho, int64_t n, int t, double lr,
+                        double b1, double b2, double eps, double beta, double eta, cudaStream_t s);
+void launch_design_project(const float* theta, float* rho, int64_t n, double beta, double eta, cudaStream_t s);
 void launch_set_density(const Geo& g, float* a, const int* lo, const int* hi, const float* rho, float eps_lo,
                         float deps, cudaStream_t s);
 // Arguments of the reverse-step kernels (in place on the fields F and the adjoint fields B).

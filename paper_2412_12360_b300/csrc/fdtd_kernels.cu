@@ -4,6 +4,8 @@
 // eps = eps_lo + (eps_hi - eps_lo) rho, the dL/deps finalisation and field packing.
 #include <algorithm>
 
+#include <cmath>
+
 #include "fdtd_internal.cuh"
 
 namespace fdtd {
@@ -180,6 +182,39 @@ __global__ void k_grad_finalize(Geo g, const float* __restrict__ a, int dlo0, in
   out[m] = (float)(-av * av * dLda[m] * scale);  // a = 1/eps, da/deps = -a^2; scale = deps/drho or 1
 }
 
+// One Adam step of the design loop on the latent variables theta, with the smoothed Heaviside
+// projection rho = P(theta) (see fdtd_design_adam_step). P's constants tbe = tanh(beta eta) and
+// tden = tanh(beta eta) + tanh(beta (1 - eta)) and the bias corrections bc1 = 1 - beta1^t,
+// bc2 = 1 - beta2^t come from the host; beta = 0 selects the identity projection.
+__global__ void k_design_adam(const float* __restrict__ g_rho, float* theta, float* m, float* v, float* rho,
+                              int64_t n, float lr, float b1, float b2, float eps, float bc1, float bc2,
+                              float beta, float eta, float tbe, float tden) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float th = theta[i];
+  float dp = 1.f;  // P'(theta)
+  if (beta > 0.f) {
+    const float t = tanhf(beta * (th - eta));
+    dp = beta * (1.f - t * t) / tden;
+  }
+  const float gr = g_rho[i] * dp;
+  const float mm = b1 * m[i] + (1.f - b1) * gr;
+  const float vv = b2 * v[i] + (1.f - b2) * gr * gr;
+  th -= lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
+  th = fminf(fmaxf(th, 0.f), 1.f);
+  m[i] = mm;
+  v[i] = vv;
+  theta[i] = th;
+  rho[i] = beta > 0.f ? (tbe + tanhf(beta * (th - eta))) / tden : th;
+}
+
+__global__ void k_design_project(const float* __restrict__ theta, float* rho, int64_t n, float beta, float eta,
+                                 float tbe, float tden) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  rho[i] = beta > 0.f ? (tbe + tanhf(beta * (theta[i] - eta))) / tden : theta[i];
+}
+
 __global__ void k_pack(Geo g, Fields F, float* out6, int unpack) {
   int p[3];
   if (!cell_of(g, p)) return;
@@ -253,6 +288,24 @@ void launch_set_density(const Geo& g, float* a, const int* lo, const int* hi, co
   const int64_t n = (int64_t)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
   if (n <= 0) return;
   k_set_density<<<blocks_for(n, 256), 256, 0, s>>>(g, a, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], rho, eps_lo, deps);
+}
+
+void launch_design_adam(const float* g_rho, float* theta, float* m, float* v, float* rho, int64_t n, int t, double lr,
+                        double b1, double b2, double eps, double beta, double eta, cudaStream_t s) {
+  if (n <= 0) return;
+  const double tbe = beta > 0 ? std::tanh(beta * eta) : 0.0;
+  const double tden = beta > 0 ? tbe + std::tanh(beta * (1.0 - eta)) : 1.0;
+  const double bc1 = 1.0 - std::pow(b1, t), bc2 = 1.0 - std::pow(b2, t);
+  k_design_adam<<<blocks_for(n, 256), 256, 0, s>>>(g_rho, theta, m, v, rho, n, (float)lr, (float)b1, (float)b2, (float)eps,
+                                                   (float)bc1, (float)bc2, (float)beta, (float)eta, (float)tbe,
+                                                   (float)tden);
+}
+
+void launch_design_project(const float* theta, float* rho, int64_t n, double beta, double eta, cudaStream_t s) {
+  if (n <= 0) return;
+  const double tbe = beta > 0 ? std::tanh(beta * eta) : 0.0;
+  const double tden = beta > 0 ? tbe + std::tanh(beta * (1.0 - eta)) : 1.0;
+  k_design_project<<<blocks_for(n, 256), 256, 0, s>>>(theta, rho, n, (float)beta, (float)eta, (float)tbe, (float)tden);
 }
 
 void launch_pack_fields(const Geo& g, const Fields& F, float* out6, int unpack, cudaStream_t s) {

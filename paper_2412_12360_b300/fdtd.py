@@ -69,6 +69,9 @@ SIGNATURES = [
     ("fdtd_set_initial_fields", C.c_int, [_VP, _VP]),
     ("fdtd_set_design_density", C.c_int, [_VP, _VP, C.c_double, C.c_double]),
     ("fdtd_backward_density", C.c_int, [_VP, _VP, _VP]),
+    ("fdtd_design_project", C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double]),
+    ("fdtd_design_adam_step", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_double]),
     ("fdtd_forward", C.c_int, [_VP, C.c_int32, C.c_uint32]),
     ("fdtd_backward", C.c_int, [_VP, _VP, _VP]),
     ("fdtd_read_detectors", C.c_int, [_VP, _VP]),
@@ -201,6 +204,7 @@ class Solver:
                             _I3(*scene.design_lo), _I3(*scene.design_hi), stream_ptr))
         self.h = h
         self.nsteps = None
+        self.stream = stream  # the stream given at creation (None: the legacy default stream)
 
     def close(self):
         if getattr(self, "h", None):
@@ -247,6 +251,16 @@ class Solver:
 
     def fdtd_backward_density(self, dL_ddet, dL_drho):
         check(lib().fdtd_backward_density(self.h, _ptr(dL_ddet), _ptr(dL_drho)))
+
+    def fdtd_design_adam_step(self, dL_drho, theta, m, v, rho_out, t: int, lr: float, beta1: float = 0.9,
+                              beta2: float = 0.999, eps: float = 1e-8, proj_beta: float = 0.0,
+                              proj_eta: float = 0.5):
+        check(lib().fdtd_design_adam_step(self.h, _ptr(dL_drho), _ptr(theta), _ptr(m), _ptr(v), _ptr(rho_out),
+                                          int(t), float(lr), float(beta1), float(beta2), float(eps),
+                                          float(proj_beta), float(proj_eta)))
+
+    def fdtd_design_project(self, theta, rho_out, proj_beta: float = 0.0, proj_eta: float = 0.5):
+        check(lib().fdtd_design_project(self.h, _ptr(theta), _ptr(rho_out), float(proj_beta), float(proj_eta)))
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))
