@@ -73,8 +73,22 @@ typedef struct {
   int32_t grading_m;               /* polynomial grading order, >= 1 */
 } fdtd_pml;
 
-/* Soft source on an E component over the cell box [lo, hi) (Sec. 2.1 names sources; this library
- * implements additive soft sources). */
+/* Source on an E component over the cell box [lo, hi) (Sec. 2.1). Two kinds:
+ *   tfsf = 0: additive soft source, E_c += amplitude * profile * g(n + 1/2) after the E update of
+ *     step n, g the Gaussian-modulated sine below.
+ *   tfsf = +-(d + 1): the plane of a total-field / scattered-field source (Sec. 2.1: the incident
+ *     field enters on one side only), a plane wave travelling along axis d in the direction of the
+ *     sign. The box must be one cell thick along d (plane index k) and `component` transverse to d.
+ *     The incident field is that of a one-dimensional Yee line along d (same Courant number,
+ *     permittivity eps_background) driven by a soft source amplitude * g(n + 1/2) on its E four
+ *     cells upstream of the plane. E_c on plane k is total field; the H component h (the third
+ *     axis) on the adjacent half plane (k - 1/2 for +, k + 1/2 for -) is scattered field, and each
+ *     gets the incident value of the other side as a correction, weighted by the profile:
+ *       H_h += dir S sH Einc^n(k)  after the H update,  E_c += -dir S a sE Hinc^{n+1/2}  after the E
+ *     update, with sE, sH = +-1 the signs of the axis-d derivatives in (curl H)_c and (curl E)_h.
+ *     Requires k >= 1 (+) or k <= n_d - 2 (-), and the plane and its H half plane outside the design
+ *     box (the E correction uses a there, taken at creation).
+ * g(s) = sin(2 pi (s - t0) S / lambda) exp(-((s - t0) / tau)^2), s in steps. */
 typedef struct {
   int32_t component;               /* 0, 1, 2 = Ex, Ey, Ez */
   int32_t lo[3], hi[3];            /* cell box, hi exclusive */
@@ -83,6 +97,8 @@ typedef struct {
   double wavelength_cells;         /* vacuum wavelength in cells */
   double tau_steps;                /* width of the Gaussian envelope, steps (> 0) */
   double t0_steps;                 /* centre of the envelope, steps */
+  int32_t tfsf;                    /* 0 = soft source; +-(axis + 1) = TFSF plane, direction of travel */
+  double eps_background;           /* TFSF: permittivity of the incident-field line (> 0) */
 } fdtd_source;
 
 /* Detector (Sec. 2.1: detectors record field values at intermediate time steps; composite values

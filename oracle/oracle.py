@@ -19,7 +19,8 @@ from . import build as _build
 class _Source(C.Structure):
     _fields_ = [("component", C.c_int32), ("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3),
                 ("profile", C.POINTER(C.c_double)), ("amplitude", C.c_double),
-                ("wavelength_cells", C.c_double), ("tau_steps", C.c_double), ("t0_steps", C.c_double)]
+                ("wavelength_cells", C.c_double), ("tau_steps", C.c_double), ("t0_steps", C.c_double),
+                ("tfsf", C.c_int32), ("eps_background", C.c_double)]
 
 
 class _Detector(C.Structure):
@@ -69,7 +70,8 @@ class _SceneArgs:
 
     Expected attributes: n (nx, ny, nz), courant, pml (6 ints), sigma_max, kappa_max, alpha_max,
     grading_m, eps_inv (array (nz, ny, nx)), sources (component, lo, hi, profile or None, amplitude,
-    wavelength_cells, tau_steps, t0_steps), detectors (kind, component, axis, lo, hi),
+    wavelength_cells, tau_steps, t0_steps, and optionally tfsf and eps_background), detectors (kind,
+    component, axis, lo, hi),
     design_lo, design_hi.
     """
 
@@ -93,6 +95,8 @@ class _SceneArgs:
             srcs[q].wavelength_cells = float(s.wavelength_cells)
             srcs[q].tau_steps = float(s.tau_steps)
             srcs[q].t0_steps = float(s.t0_steps)
+            srcs[q].tfsf = int(getattr(s, "tfsf", 0))
+            srcs[q].eps_background = float(getattr(s, "eps_background", 1.0))
         dets = (_Detector * max(1, len(scene.detectors)))()
         for q, dt in enumerate(scene.detectors):
             dets[q].kind = int(dt.kind)

@@ -37,7 +37,9 @@
 
 extern "C" {
 
-// A soft source on an E component over a box of cells [lo, hi).
+// A source on an E component over a box of cells [lo, hi): a soft source (tfsf = 0), or the plane of
+// a one-sided total-field / scattered-field source (tfsf = +-(axis + 1), the sign giving the direction
+// of travel; the box is one cell thick along the axis).
 typedef struct {
   int32_t component;      // 0, 1, 2 = Ex, Ey, Ez
   int32_t lo[3], hi[3];   // cell box, x fastest
@@ -46,6 +48,8 @@ typedef struct {
   double wavelength_cells;
   double tau_steps;       // width of the Gaussian envelope, in steps
   double t0_steps;        // centre of the envelope, in steps
+  int32_t tfsf;
+  double eps_background;  // TFSF: permittivity of the one-dimensional incident-field line
 } orc_source;
 
 // Detector kinds. Outputs are concatenated in detector order.
@@ -132,6 +136,47 @@ double waveform(const orc_source& src, double S, double s) {
   return std::sin(2.0 * M_PI * u / P) * std::exp(-(u / src.tau_steps) * (u / src.tau_steps));
 }
 
+// Total-field / scattered-field plane source (Sec. 2.1: the incident field enters on one side only).
+// The incident plane wave (E component c, H component h, travelling along `axis` in direction dir)
+// comes from a one-dimensional Yee line along the axis with the same S and a = 1/eps_background,
+// driven by a soft source amplitude * g(n + 1/2) on its E a few cells upstream of the plane. Its
+// equations are the 3-D ones restricted to the axis: (curl H)_c holds sE dH_h/d(axis) and
+// (curl E)_h holds sH dE_c/d(axis), with sE, sH = +-1 from the cyclic order of the components.
+// The plane's E_c (index k) is total field, the adjacent H_h (index k-1 when dir > 0, k when dir < 0)
+// scattered field; each side's update reads one value of the other side, so it gets the incident
+// value as a correction:
+//   H_h += dir S sH Einc^n(k)                 after the H update of step n,
+//   E_c += -dir S a sE Hinc^{n+1/2}(k -+ 1/2)  after the E update of step n.
+struct Tfsf {
+  int axis = 0, dir = 0, c = 0, h = 0, hidx = 0;
+  double sE = 0, sH = 0;
+  std::vector<double> einc, hinc;  // Einc^n at the plane, Hinc^{n+1/2} at the adjacent H plane
+};
+
+Tfsf make_tfsf(const orc_source& s, double S, int nsteps) {
+  Tfsf t;
+  t.axis = std::abs(s.tfsf) - 1;
+  t.dir = s.tfsf > 0 ? 1 : -1;
+  t.c = s.component;
+  t.h = 3 - t.axis - t.c;
+  t.sE = (t.axis == m3(t.c + 1)) ? 1.0 : -1.0;  // (curl H)_c = dH_{c+2}/dx_{c+1} - dH_{c+1}/dx_{c+2}
+  t.sH = (t.axis == m3(t.h + 1)) ? 1.0 : -1.0;  // (curl E)_h = dE_{h+2}/dx_{h+1} - dE_{h+1}/dx_{h+2}
+  t.hidx = s.lo[t.axis] - (t.dir > 0 ? 1 : 0);
+  const int L = 2 * nsteps + 16, K = nsteps + 8, ksrc = K - 4 * t.dir;
+  const double ab = 1.0 / s.eps_background;
+  std::vector<double> E(L, 0.0), H(L, 0.0);  // H[k] sits at k + 1/2; E[0] is a PEC end
+  t.einc.resize(nsteps);
+  t.hinc.resize(nsteps);
+  for (int n = 0; n < nsteps; ++n) {
+    t.einc[n] = E[K];
+    for (int k = 0; k + 1 < L; ++k) H[k] -= S * t.sH * (E[k + 1] - E[k]);
+    t.hinc[n] = t.dir > 0 ? H[K - 1] : H[K];
+    for (int k = 1; k < L; ++k) E[k] += S * ab * t.sE * (H[k] - H[k - 1]);
+    E[ksrc] += s.amplitude * waveform(s, S, n + 0.5);
+  }
+  return t;
+}
+
 template <class T>
 struct State {
   std::vector<T> F[6];           // Ex, Ey, Ez, Hx, Hy, Hz
@@ -159,10 +204,14 @@ struct Sim {
   std::vector<size_t> det_offset;   // start of each detector's output in the concatenated vector
   size_t det_total = 0;
   int nsteps;
+  std::vector<Tfsf> tfsf;           // per source (used where the source has tfsf != 0)
 
   Sim(const orc_scene& s, int nsteps_) : sc(s), g(s), S(s.courant), cf(make_coefs(s)), nsteps(nsteps_) {
     a.resize(g.N);
     for (size_t p = 0; p < g.N; ++p) a[p] = T(s.eps_inv[p]);
+    tfsf.resize(s.nsrc);
+    for (int q = 0; q < s.nsrc; ++q)
+      if (s.src[q].tfsf != 0) tfsf[q] = make_tfsf(s.src[q], S, nsteps);
     for (int q = 0; q < s.ndet; ++q) {
       det_offset.push_back(det_total);
       det_total += det_size(s.det[q]);
@@ -236,21 +285,48 @@ struct Sim {
     }
   }
 
-  // Soft sources: E_c += amplitude * profile * g(n + 1/2), after the E update of step n.
-  void add_sources(State<T>& st, int n, double sign) const {
+  // E sources after the E update of step n: soft sources E_c += amplitude * profile * g(n + 1/2);
+  // the E correction of a TFSF plane, -dir S a sE profile Hinc^{n+1/2} (a of the cell, held constant:
+  // the plane lies outside the design box). With only_R, cells outside R are skipped.
+  void add_sources(State<T>& st, int n, double sign, bool only_R = false) const {
     for (int q = 0; q < sc.nsrc; ++q) {
       const orc_source& s = sc.src[q];
-      const double gn = s.amplitude * waveform(s, S, n + 0.5);
+      const Tfsf& t = tfsf[q];
+      const double gn = s.tfsf ? -t.dir * S * t.sE * t.hinc[n] : s.amplitude * waveform(s, S, n + 0.5);
       const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
       for (int k = s.lo[2]; k < s.hi[2]; ++k)
         for (int j = s.lo[1]; j < s.hi[1]; ++j)
           for (int i = s.lo[0]; i < s.hi[0]; ++i) {
             int p[3] = {i, j, k};
             if (!e_updated(s.component, p)) continue;
+            if (only_R && !e_in_R(s.component, p)) continue;
+            double w = s.profile ? s.profile[(size_t(k - s.lo[2]) * by + (j - s.lo[1])) * bx + (i - s.lo[0])]
+                                 : 1.0;
+            if (s.tfsf) w *= sc.eps_inv[g.at(p)];
+            st.F[s.component][g.at(p)] += sign * (w * gn);
+          }
+    }
+  }
+
+  // H corrections of the TFSF planes after the H update of step n: H_h += dir S sH profile Einc^n on
+  // the scattered-side H plane next to the source plane. With only_R, cells outside R are skipped.
+  void add_h_sources(State<T>& st, int n, double sign, bool only_R = false) const {
+    for (int q = 0; q < sc.nsrc; ++q) {
+      const orc_source& s = sc.src[q];
+      if (!s.tfsf) continue;
+      const Tfsf& t = tfsf[q];
+      const double gn = t.dir * S * t.sH * t.einc[n];
+      const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
+      for (int k = s.lo[2]; k < s.hi[2]; ++k)
+        for (int j = s.lo[1]; j < s.hi[1]; ++j)
+          for (int i = s.lo[0]; i < s.hi[0]; ++i) {
+            int p[3] = {i, j, k};
+            p[t.axis] = t.hidx;
+            if (only_R && !h_in_R(t.h, p)) continue;
             const double w = s.profile
                                  ? s.profile[(size_t(k - s.lo[2]) * by + (j - s.lo[1])) * bx + (i - s.lo[0])]
                                  : 1.0;
-            st.F[s.component][g.at(p)] += sign * (w * gn);
+            st.F[3 + t.h][g.at(p)] += sign * (w * gn);
           }
     }
   }
@@ -286,6 +362,7 @@ struct Sim {
 
   void step(State<T>& st, int n, std::vector<T>* det) const {
     update_H(st);
+    add_h_sources(st, n, +1.0);
     update_E(st);
     add_sources(st, n, +1.0);
     if (det) sample(st, n, *det);
@@ -455,7 +532,7 @@ struct Sim {
 
   // (E^{n+1}, H^{n+1/2}) -> (E^n, H^{n-1/2}) on R; H outside R at the face set must hold step n's record.
   void inverse_step(State<T>& st, int n) const {
-    add_sources_in_R(st, n, -1.0);
+    add_sources(st, n, -1.0, true);
     for (int c = 0; c < 3; ++c) {
       const int c1 = m3(c + 1), c2 = m3(c + 2);
       std::vector<T>& E = st.F[c];
@@ -506,6 +583,16 @@ struct Sim {
             H[q] += S * (d1 / 1.0 + T(0) - d2 / 1.0 - T(0));
           }
     }
+    add_h_sources(st, n, -1.0, true);
+  }
+
+  bool h_in_R(int c, const int* p) const {
+    for (int d = 0; d < 3; ++d) {
+      const int lo = (d == c) ? int_lo(d) : half_lo(d);
+      const int hi = (d == c) ? int_hi(d) : half_hi(d);
+      if (p[d] < lo || p[d] > hi) return false;
+    }
+    return true;
   }
 
   bool e_in_R(int c, const int* p) const {
@@ -515,24 +602,6 @@ struct Sim {
       if (p[d] < lo || p[d] > hi) return false;
     }
     return true;
-  }
-
-  void add_sources_in_R(State<T>& st, int n, double sign) const {
-    for (int q = 0; q < sc.nsrc; ++q) {
-      const orc_source& s = sc.src[q];
-      const double gn = s.amplitude * waveform(s, S, n + 0.5);
-      const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
-      for (int k = s.lo[2]; k < s.hi[2]; ++k)
-        for (int j = s.lo[1]; j < s.hi[1]; ++j)
-          for (int i = s.lo[0]; i < s.hi[0]; ++i) {
-            int p[3] = {i, j, k};
-            if (!e_updated(s.component, p) || !e_in_R(s.component, p)) continue;
-            const double w = s.profile
-                                 ? s.profile[(size_t(k - s.lo[2]) * by + (j - s.lo[1])) * bx + (i - s.lo[0])]
-                                 : 1.0;
-            st.F[s.component][g.at(p)] += sign * (w * gn);
-          }
-    }
   }
 
   void load_initial(State<T>& st, const double* init6) const {
@@ -599,6 +668,7 @@ int orc_roundtrip(const orc_scene* s, int32_t nsteps, const double* init6, doubl
   std::vector<std::vector<double>> rec(nsteps);
   for (int n = 0; n < nsteps; ++n) {
     sim.update_H(st);
+    sim.add_h_sources(st, n, +1.0);
     sim.record_faces(st, fs, rec[n]);
     sim.update_E(st);
     sim.add_sources(st, n, +1.0);
@@ -659,6 +729,7 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
     std::vector<std::vector<double>> rec(nsteps);
     for (int n = 0; n < nsteps; ++n) {
       sim.update_H(st);
+      sim.add_h_sources(st, n, +1.0);
       sim.record_faces(st, fs, rec[n]);
       sim.update_E(st);
       sim.add_sources(st, n, +1.0);

@@ -134,6 +134,48 @@ double pulse(const fdtd_source& s, double S, double t) {
   return std::sin(2.0 * M_PI * u / P) * std::exp(-(u / s.tau_steps) * (u / s.tau_steps));
 }
 
+// A one-sided TFSF plane source (see fdtd_source): travel axis and direction, its E and H components
+// c and h, and sE, sH = +-1, the signs of the axis derivatives in (curl H)_c and (curl E)_h.
+struct Tfsf {
+  fdtd_source s;
+  int axis, dir, c, h;
+  double sE, sH;
+};
+
+Tfsf make_tfsf(const fdtd_source& s) {
+  Tfsf t;
+  t.s = s;
+  t.s.profile = nullptr;
+  t.axis = std::abs(s.tfsf) - 1;
+  t.dir = s.tfsf > 0 ? 1 : -1;
+  t.c = s.component;
+  t.h = 3 - t.axis - t.c;
+  t.sE = t.axis == (t.c + 1) % 3 ? 1.0 : -1.0;  // (curl H)_c = dH_{c+2}/dx_{c+1} - dH_{c+1}/dx_{c+2}
+  t.sH = t.axis == (t.h + 1) % 3 ? 1.0 : -1.0;  // (curl E)_h = dE_{h+2}/dx_{h+1} - dE_{h+1}/dx_{h+2}
+  return t;
+}
+
+// Incident field of a TFSF source for steps 0..nsteps-1, in FP64 on the host (it does not depend on
+// the 3-D fields): a one-dimensional Yee line along the travel axis, the 3-D update restricted to the
+// axis with a = 1/eps_background, driven by the source's soft pulse four cells upstream of the
+// sampling point K. einc[n] = E^n at K (the plane), hinc[n] = H^{n+1/2} at K - 1/2 (travel +) or
+// K + 1/2 (travel -). The line is long enough that nothing reflected from its ends returns to K
+// within nsteps (waves move at most S cells per step).
+void tfsf_incident(const Tfsf& t, double S, int nsteps, std::vector<double>& einc, std::vector<double>& hinc) {
+  const int L = 2 * nsteps + 16, K = nsteps + 8, ks = K - 4 * t.dir;
+  const double ab = 1.0 / t.s.eps_background;
+  std::vector<double> E(L, 0.0), H(L, 0.0);  // H[k] at k + 1/2; E[0] stays 0
+  einc.assign(nsteps, 0.0);
+  hinc.assign(nsteps, 0.0);
+  for (int n = 0; n < nsteps; ++n) {
+    einc[n] = E[K];
+    for (int k = 0; k < L - 1; ++k) H[k] -= S * t.sH * (E[k + 1] - E[k]);
+    hinc[n] = H[t.dir > 0 ? K - 1 : K];
+    for (int k = 1; k < L; ++k) E[k] += S * ab * t.sE * (H[k] - H[k - 1]);
+    E[ks] += t.s.amplitude * pulse(t.s, S, n + 0.5);
+  }
+}
+
 bool box_ok(const int32_t lo[3], const int32_t hi[3], const int n[3], bool allow_empty) {
   for (int d = 0; d < 3; ++d) {
     if (lo[d] < 0 || hi[d] > n[d] || lo[d] > hi[d]) return false;
@@ -272,7 +314,10 @@ struct fdtd_handle {
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
 
   std::vector<fdtd_source> src_host;
-  std::vector<SrcDev> srcs;
+  std::vector<SrcDev> srcs;       // E sources: soft sources and the E corrections of TFSF planes
+  std::vector<SrcDev> hsrcs;      // H corrections of TFSF planes (added to H^{n-1/2} before step n)
+  std::vector<int> src_tfsf, hsrc_tfsf;  // per entry of srcs / hsrcs: its index in tfsf, or -1
+  std::vector<Tfsf> tfsf;
   std::vector<DetDev> dets;
   int64_t det_total_per_step = 0, det_total_fixed = 0;
 
@@ -285,7 +330,7 @@ struct fdtd_handle {
   float* tables = nullptr;     // 3 axes x 2 positions x (b, c, 1/kappa) x n
   float* init = nullptr;       // optional initial state, 6 x vol
   std::vector<float*> src_w;   // per source box weights
-  float* gtab = nullptr;       // nsrc x gtab_cap waveform samples
+  float* gtab = nullptr;       // (srcs + hsrcs) x gtab_cap waveform samples
   int gtab_cap = 0;
   double* det_out = nullptr;   // concatenated detector outputs
   int64_t det_out_cap = 0;
@@ -465,23 +510,33 @@ int upload_tables(fdtd_handle* h) {
   return FDTD_OK;
 }
 
+// Waveform tables of every source entry for steps 0..nsteps-1 (rows: srcs, then hsrcs): g(n + 1/2)
+// for a soft source; for a TFSF plane the incident H^{n+1/2} (its E correction) and E^n (its H
+// correction). A table built for more steps serves fewer (the incident line is causal).
 int ensure_gtab(fdtd_handle* h, int nsteps) {
-  const int ns = (int)h->srcs.size();
-  if (ns == 0) return FDTD_OK;
+  const int ns = (int)h->srcs.size(), nh = (int)h->hsrcs.size(), nr = ns + nh;
+  if (nr == 0) return FDTD_OK;
   if (h->gtab_cap < nsteps) {
     CK(cudaStreamSynchronize(h->stream));
-    dev_free(h, h->gtab, (int64_t)ns * h->gtab_cap * 4);
+    dev_free(h, h->gtab, (int64_t)nr * h->gtab_cap * 4);
     h->gtab = nullptr;
     h->gtab_cap = 0;
-    TRY(dev_alloc(h, (void**)&h->gtab, (int64_t)ns * nsteps * 4));
-    std::vector<float> t((size_t)ns * nsteps);
+    TRY(dev_alloc(h, (void**)&h->gtab, (int64_t)nr * nsteps * 4));
+    std::vector<std::vector<double>> einc(h->tfsf.size()), hinc(h->tfsf.size());
+    for (size_t t = 0; t < h->tfsf.size(); ++t) tfsf_incident(h->tfsf[t], h->courant, nsteps, einc[t], hinc[t]);
+    std::vector<float> t((size_t)nr * nsteps);
     for (int q = 0; q < ns; ++q)
-      for (int n = 0; n < nsteps; ++n) t[(size_t)q * nsteps + n] = (float)pulse(h->src_host[q], h->courant, n + 0.5);
+      for (int n = 0; n < nsteps; ++n)
+        t[(size_t)q * nsteps + n] = h->src_tfsf[q] < 0 ? (float)pulse(h->src_host[q], h->courant, n + 0.5)
+                                                       : (float)hinc[h->src_tfsf[q]][n];
+    for (int q = 0; q < nh; ++q)
+      for (int n = 0; n < nsteps; ++n) t[(size_t)(ns + q) * nsteps + n] = (float)einc[h->hsrc_tfsf[q]][n];
     CK(cudaMemcpyAsync(h->gtab, t.data(), t.size() * 4, cudaMemcpyHostToDevice, h->stream));
     CK(cudaStreamSynchronize(h->stream));  // `t` dies on return
     h->gtab_cap = nsteps;
   }
   for (int q = 0; q < ns; ++q) h->srcs[q].g = h->gtab + (size_t)q * h->gtab_cap;
+  for (int q = 0; q < nh; ++q) h->hsrcs[q].g = h->gtab + (size_t)(ns + q) * h->gtab_cap;
   return FDTD_OK;
 }
 
@@ -595,6 +650,10 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     fa.psiH_cur = h->psi_set(h->psiH + c * pf);
     fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
     fa.step = n;
+    // TFSF H corrections of step n, added to H^{n-1/2} ahead of the step: the fused kernel's H update
+    // then yields H^{n-1/2} - S curl E^n + correction in every cell, halos included
+    for (const SrcDev& hs : h->hsrcs) launch_source(g, fa.cur, hs, n, +1.f, 0, st);
+    launches += (int64_t)h->hsrcs.size();
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
       launch_fwd_fused(fa, h->fmaps[c], st);
@@ -675,6 +734,9 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
       launch_rev_H(ra, rm, st);
     }
     launches += 2;
+    // the inverse H step rebuilt H^{n-1/2} + the TFSF H corrections of step n on R: remove them
+    for (const SrcDev& hs : h->hsrcs) launch_source(g, F, hs, n, -1.f, 1, st);
+    launches += (int64_t)h->hsrcs.size();
     pb = 1 - pb;
   }
   return launches;
@@ -784,6 +846,16 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     if (!box_ok(s.lo, s.hi, n, false)) return fail(FDTD_ERR_INVALID_ARG, "source %d: box outside the grid", q);
     if (!(s.tau_steps > 0) || !(s.wavelength_cells > 0))
       return fail(FDTD_ERR_INVALID_ARG, "source %d: tau and wavelength must be positive", q);
+    if (s.tfsf != 0) {
+      const int ax = std::abs(s.tfsf) - 1;
+      if (ax > 2) return fail(FDTD_ERR_INVALID_ARG, "source %d: tfsf must be 0 or +-1..3", q);
+      if (s.component == ax) return fail(FDTD_ERR_INVALID_ARG, "source %d: a TFSF component must be transverse", q);
+      if (s.hi[ax] - s.lo[ax] != 1)
+        return fail(FDTD_ERR_INVALID_ARG, "source %d: a TFSF plane is one cell thick along its axis", q);
+      if (s.tfsf > 0 ? s.lo[ax] < 1 : s.lo[ax] > n[ax] - 2)
+        return fail(FDTD_ERR_INVALID_ARG, "source %d: the TFSF plane needs its scattered-field side in the grid", q);
+      if (!(s.eps_background > 0)) return fail(FDTD_ERR_INVALID_ARG, "source %d: eps_background must be positive", q);
+    }
   }
   for (int q = 0; q < ndet; ++q) {
     const fdtd_detector& d = det[q];
@@ -798,6 +870,21 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   const int32_t* dlo = design_lo ? design_lo : zlo;
   const int32_t* dhi = design_hi ? design_hi : zlo;
   if (!box_ok(dlo, dhi, n, true)) return fail(FDTD_ERR_INVALID_ARG, "design box outside the grid");
+  for (int q = 0; q < nsrc; ++q) {  // a TFSF plane (E) and its H half plane stay off the design box
+    const fdtd_source& s = src[q];
+    if (s.tfsf == 0) continue;
+    const int ax = std::abs(s.tfsf) - 1;
+    for (int side = 0; side < 2; ++side) {
+      int lo[3] = {s.lo[0], s.lo[1], s.lo[2]}, hi[3] = {s.hi[0], s.hi[1], s.hi[2]};
+      if (side == 1) {
+        lo[ax] -= s.tfsf > 0 ? 1 : 0;
+        hi[ax] = lo[ax] + 1;
+      }
+      bool meet = true;
+      for (int d = 0; d < 3; ++d) meet = meet && lo[d] < dhi[d] && hi[d] > dlo[d];
+      if (meet) return fail(FDTD_ERR_INVALID_ARG, "source %d: a TFSF plane must not meet the design box", q);
+    }
+  }
 
   fdtd_handle* h = new fdtd_handle();
   h->pml = *pml;
@@ -881,36 +968,60 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     dev_free(h, tmp, N * 4);
     if (e != cudaSuccess) return cleanup(fail(FDTD_ERR_CUDA, "copy of eps_inv: %s", cudaGetErrorString(e)));
   }
-  // sources: weights = amplitude * profile, zero where the component is held by a PEC wall
+  // sources: weights = amplitude * profile for a soft source; for a TFSF plane the correction
+  // coefficients times the profile (E: -dir S sE a, H: dir S sH); zero where E is held by a PEC wall
+  auto add_entry = [&](const fdtd_source& s, int comp, const int* lo, const int* hi, double coef, bool times_a,
+                       std::vector<SrcDev>& list) -> int {
+    const int64_t m = box_cells(lo, hi);
+    const int bx = hi[0] - lo[0], by = hi[1] - lo[1];
+    const int c1 = (comp + 1) % 3, c2 = (comp + 2) % 3;
+    std::vector<float> w((size_t)m);
+    for (int64_t t = 0; t < m; ++t) {
+      const int p[3] = {lo[0] + int(t % bx), lo[1] + int((t / bx) % by), lo[2] + int(t / ((int64_t)bx * by))};
+      const double prof = s.profile ? (double)s.profile[t] : 1.0;
+      const bool held = comp < 3 && (p[c1] == 0 || p[c2] == 0);
+      w[(size_t)t] = held ? 0.f : (float)(coef * prof);
+    }
+    float* dw = nullptr;
+    int r = dev_alloc(h, (void**)&dw, m * 4);
+    if (r != FDTD_OK) return r;
+    h->src_w.push_back(dw);
+    if (cudaMemcpyAsync(dw, w.data(), m * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)  // `w` dies on return
+      return fail(FDTD_ERR_CUDA, "source upload failed");
+    SrcDev sd;
+    sd.comp = comp;
+    for (int d = 0; d < 3; ++d) {
+      sd.lo[d] = lo[d];
+      sd.hi[d] = hi[d];
+    }
+    sd.w = dw;
+    sd.g = nullptr;
+    if (times_a) launch_source_scale_a(g, h->a, sd, h->stream);
+    list.push_back(sd);
+    return FDTD_OK;
+  };
   for (int q = 0; q < nsrc; ++q) {
     const fdtd_source& s = src[q];
     h->src_host.push_back(s);
     h->src_host.back().profile = nullptr;
-    const int64_t m = box_cells(s.lo, s.hi);
-    const int bx = s.hi[0] - s.lo[0], by = s.hi[1] - s.lo[1];
-    const int c1 = (s.component + 1) % 3, c2 = (s.component + 2) % 3;
-    std::vector<float> w((size_t)m);
-    for (int64_t t = 0; t < m; ++t) {
-      const int p[3] = {s.lo[0] + int(t % bx), s.lo[1] + int((t / bx) % by), s.lo[2] + int(t / ((int64_t)bx * by))};
-      const double prof = s.profile ? (double)s.profile[t] : 1.0;
-      w[(size_t)t] = (p[c1] == 0 || p[c2] == 0) ? 0.f : (float)(s.amplitude * prof);
+    if (s.tfsf == 0) {
+      if ((rc = add_entry(s, s.component, s.lo, s.hi, s.amplitude, false, h->srcs)) != FDTD_OK) return cleanup(rc);
+      h->src_tfsf.push_back(-1);
+      continue;
     }
-    float* dw = nullptr;
-    if ((rc = dev_alloc(h, (void**)&dw, m * 4)) != FDTD_OK) return cleanup(rc);
-    h->src_w.push_back(dw);
-    if (cudaMemcpyAsync(dw, w.data(), m * 4, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
-        cudaStreamSynchronize(h->stream) != cudaSuccess)  // `w` dies at the end of this iteration
-      return cleanup(fail(FDTD_ERR_CUDA, "source upload failed"));
-    SrcDev sd;
-    sd.comp = s.component;
-    for (int d = 0; d < 3; ++d) {
-      sd.lo[d] = s.lo[d];
-      sd.hi[d] = s.hi[d];
-    }
-    sd.w = dw;
-    sd.g = nullptr;
-    h->srcs.push_back(sd);
+    const Tfsf t = make_tfsf(s);
+    const int it = (int)h->tfsf.size();
+    h->tfsf.push_back(t);
+    if ((rc = add_entry(s, t.c, s.lo, s.hi, -t.dir * courant * t.sE, true, h->srcs)) != FDTD_OK) return cleanup(rc);
+    h->src_tfsf.push_back(it);
+    int lo[3] = {s.lo[0], s.lo[1], s.lo[2]}, hi[3] = {s.hi[0], s.hi[1], s.hi[2]};
+    lo[t.axis] = s.lo[t.axis] - (t.dir > 0 ? 1 : 0);  // the scattered-side H half plane
+    hi[t.axis] = lo[t.axis] + 1;
+    if ((rc = add_entry(s, 3 + t.h, lo, hi, t.dir * courant * t.sH, false, h->hsrcs)) != FDTD_OK) return cleanup(rc);
+    h->hsrc_tfsf.push_back(it);
   }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cleanup(fail(FDTD_ERR_CUDA, "source set-up failed"));
   for (int q = 0; q < ndet; ++q) {
     const fdtd_detector& d = det[q];
     DetDev dd;

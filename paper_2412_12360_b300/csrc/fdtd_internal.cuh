@@ -123,6 +123,7 @@ __host__ __device__ inline int64_t psi_elems(const Geo& g, int d) {
 // ---- launchers (fdtd_kernels.cu) --------------------------------------------------------------
 void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, float sign, int only_R,
                    cudaStream_t s);
+void launch_source_scale_a(const Geo& g, const float* a, const SrcDev& src, cudaStream_t s);
 void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,
                             double* partial, cudaStream_t s);
 void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s);

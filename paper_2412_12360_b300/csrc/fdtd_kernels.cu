@@ -58,10 +58,19 @@ __global__ void k_source(Geo g, Fields F, SrcDev src, int step, float sign, int 
   if (m >= box_count(src.lo, src.hi)) return;
   int p[3];
   box_cell(src.lo, src.hi, m, p);
-  if (only_R && !in_R(g, src.comp, false, p)) return;
+  if (only_R && !in_R(g, src.comp % 3, src.comp >= 3, p)) return;  // comp 3..5: an H component
   const float v = src.w[m] * src.g[step];
   float* e = F.f[src.comp] + cell_index(g, p[0], p[1], p[2]);
   *e += sign * v;
+}
+
+// Multiply a source's box weights by a = 1/eps of each cell (the E correction of a TFSF plane).
+__global__ void k_source_scale_a(Geo g, const float* __restrict__ a, SrcDev src) {
+  const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (m >= box_count(src.lo, src.hi)) return;
+  int p[3];
+  box_cell(src.lo, src.hi, m, p);
+  const_cast<float*>(src.w)[m] *= a[cell_index(g, p[0], p[1], p[2])];
 }
 
 __global__ void k_det_point(Geo g, Fields F, DetDev d, int step, double* out) {
@@ -246,6 +255,11 @@ void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, f
   const int64_t n = (int64_t)(src.hi[0] - src.lo[0]) * (src.hi[1] - src.lo[1]) * (src.hi[2] - src.lo[2]);
   if (n <= 0) return;
   k_source<<<blocks_for(n, 256), 256, 0, s>>>(g, F, src, step, sign, only_R);
+}
+
+void launch_source_scale_a(const Geo& g, const float* a, const SrcDev& src, cudaStream_t s) {
+  const int64_t n = (int64_t)(src.hi[0] - src.lo[0]) * (src.hi[1] - src.lo[1]) * (src.hi[2] - src.lo[2]);
+  if (n > 0) k_source_scale_a<<<blocks_for(n, 256), 256, 0, s>>>(g, a, src);
 }
 
 void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,

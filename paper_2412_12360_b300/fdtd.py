@@ -48,7 +48,8 @@ class fdtd_pml(C.Structure):
 class fdtd_source(C.Structure):
     _fields_ = [("component", C.c_int32), ("lo", C.c_int32 * 3), ("hi", C.c_int32 * 3),
                 ("profile", C.POINTER(C.c_float)), ("amplitude", C.c_double),
-                ("wavelength_cells", C.c_double), ("tau_steps", C.c_double), ("t0_steps", C.c_double)]
+                ("wavelength_cells", C.c_double), ("tau_steps", C.c_double), ("t0_steps", C.c_double),
+                ("tfsf", C.c_int32), ("eps_background", C.c_double)]
 
 
 class fdtd_detector(C.Structure):
@@ -182,6 +183,8 @@ class Solver:
             srcs[q].wavelength_cells = float(s.wavelength_cells)
             srcs[q].tau_steps = float(s.tau_steps)
             srcs[q].t0_steps = float(s.t0_steps)
+            srcs[q].tfsf = int(getattr(s, "tfsf", 0))
+            srcs[q].eps_background = float(getattr(s, "eps_background", 1.0))
         dets = (fdtd_detector * max(1, len(scene.detectors)))()
         for q, dt in enumerate(scene.detectors):
             dets[q].kind = int(dt.kind)

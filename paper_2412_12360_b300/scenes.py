@@ -30,7 +30,9 @@ SPEED_OF_LIGHT = 299792458.0
 
 @dataclass
 class Source:
-    """Soft source on E component `component` over the cell box [lo, hi)."""
+    """Source on E component `component` over the cell box [lo, hi): a soft source (tfsf = 0) or the
+    plane of a one-sided total-field / scattered-field source (tfsf = +-(axis + 1), the sign giving
+    the direction of travel; the box is one cell thick along the axis)."""
     component: int
     lo: Tuple[int, int, int]
     hi: Tuple[int, int, int]
@@ -39,6 +41,8 @@ class Source:
     wavelength_cells: float = 20.0
     tau_steps: float = 0.0          # 0: filled in as one period by `default_pulse`
     t0_steps: float = 0.0
+    tfsf: int = 0
+    eps_background: float = 1.0     # TFSF: permittivity of the incident-field line
 
 
 @dataclass
