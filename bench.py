@@ -16,6 +16,7 @@ workload (the full grid for a few time steps).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -43,6 +44,10 @@ def workload(name):
     elif name == "cavity_32":
         sc = scenes.cavity_32(500)
         desc = "cavity_32: 32^3 PEC box, 8^3 eps=2.25 cube, Ez dipole, 500 steps fwd + 500 reversed"
+    elif name == "design_96_tfsf":
+        sc = scenes.design_box_scene((96, 96, 96), 10, 40, 2000, 1234, 1.0, 12.1, 20.0, "design_96_tfsf", tfsf=True)
+        desc = ("design_96_tfsf: design_96 with the Gaussian beam injected by a one-sided TFSF plane (+z) "
+                "instead of a soft sheet, 2000 steps fwd + 2000 reversed")
     elif name == "waveguide_600":
         sc = scenes.waveguide_600()
         desc = ("waveguide_600: 600^3 grid, 12-cell CPML, Si core eps=12.25 in SiO2 eps=2.085, 200^3 design "
@@ -583,6 +588,66 @@ def run_design(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_checkpoint(args, world, rank, local):
+    """Time reversal against the checkpointing gradients of Sec. 2.2 on the same workload and device:
+    per gradient method the device time of the forward + gradient, the forward steps evaluated and the
+    device memory the method holds beyond the solver (face history, or stored full states)."""
+    import torch
+    from paper_2412_12360_b300 import fdtd
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    sc, desc = workload(args.workload)
+    if args.time_steps:
+        sc.nsteps = args.time_steps
+        desc += " [time steps overridden: %d]" % args.time_steps
+    T = sc.nsteps
+    stream = torch.cuda.Stream(device=dev)
+    g_dev = torch.from_numpy(objective_grad(sc, T)).to(dev)
+    grad = torch.zeros(sc.design_shape(), dtype=torch.float32, device=dev)
+    nx, ny, nz = sc.n
+    nxp = (nx + 31) // 32 * 32
+    L = [sc.pml[0] + sc.pml[1], sc.pml[2] + sc.pml[3], sc.pml[4] + sc.pml[5]]
+    pf = 2 * (nz * ny * L[0] + nz * L[1] * nxp + L[2] * ny * nxp)
+    state_bytes = (6 * nxp * ny * nz + 2 * pf) * 4
+    face_bytes = fdtd.footprint_bytes(sc, T, True) - fdtd.footprint_bytes(sc, T, False)
+    runs = [("time_reversal", None, None), ("halving", 0, 0)] + [("treeverse", 1, k) for k in args.ckpt_slots]
+    out = []
+    with torch.cuda.stream(stream):
+        solver = fdtd.Solver(sc, stream=stream)
+        for name, method, slots in runs:
+            def once():
+                if method is None:
+                    solver.fdtd_forward(T, record_faces=True)
+                    solver.fdtd_backward(g_dev, grad)
+                    return T
+                solver.fdtd_forward(T)
+                return solver.fdtd_backward_checkpointed(g_dev, grad, method, slots)
+            once()  # warm-up (graph capture, tables)
+            stream.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            steps = once()
+            b.record(stream)
+            stream.synchronize()
+            ms = a.elapsed_time(b)
+            nstates = None if method is None else (math.ceil(math.log2(T)) + 1 if method == 0 else slots)
+            held = face_bytes if method is None else nstates * state_bytes
+            out.append({"method": name, "slots": nstates, "ms": round(ms, 2),
+                        "gcell_steps_per_s": round(sc.ncells * T / (ms * 1e-3) / 1e9, 4),
+                        "forward_steps_in_gradient": steps, "held_bytes": int(held)})
+        solver.close()
+    if rank != 0:
+        return
+    line = {"metric": "fwd+grad time and memory: time reversal vs checkpointing (Sec. 2.2)", "unit": "ms",
+            "value": out[0]["ms"], "higher_is_better": False, "n_gpus": world, "methods": out,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "grid": list(sc.n), "time_steps": T,
+                       "state_bytes": state_bytes, "face_history_bytes": int(face_bytes)}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -605,6 +670,9 @@ def main():
     ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference check of --batched")
+    ap.add_argument("--checkpoint", action="store_true",
+                    help="compare time reversal with the checkpointing gradients instead")
+    ap.add_argument("--ckpt-slots", type=int, nargs="+", default=[4, 12])
     ap.add_argument("--design-loop", action="store_true", help="measure the inverse-design loop instead")
     ap.add_argument("--design-iters", type=int, default=10)
     args = ap.parse_args()
@@ -617,6 +685,8 @@ def main():
         run_batched(args, world, rank, local)
     elif args.design_loop:
         run_design(args, world, rank, local)
+    elif args.checkpoint:
+        run_checkpoint(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

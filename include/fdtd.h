@@ -154,6 +154,24 @@ int fdtd_design_adam_step(fdtd_handle* h, const float* dL_drho, float* theta, fl
                           int32_t t, double lr, double beta1, double beta2, double eps, double proj_beta,
                           double proj_eta);
 
+/* Sec. 2.2's checkpointing alternative to time reversal (for comparison): the same gradient as
+ * fdtd_backward for the last forward, but the forward state each adjoint step needs is recomputed
+ * from full stored states (fields and CPML memories) instead of rebuilt by the inverse step; no face
+ * record is used. method 0: recursive halving (ceil(log2 n) + 1 stored states, (n/2) log2 n extra
+ * forward steps for n = 2^j); method 1: treeverse / binomial checkpointing with `slots` stored states
+ * (the schedule minimising the forward steps, by dynamic programming). Each adjoint step re-evaluates
+ * its own forward step from its input state, as in revolve. dL_ddet and dL_deps as in fdtd_backward;
+ * forward_steps (may be NULL) receives the forward steps evaluated. The stored states are allocated
+ * for the call and freed before it returns; afterwards the solver's fields hold an intermediate state.
+ * STATE if no forward has run; INVALID_ARG for a bad method, slots < 1 (method 1), a NULL output or a
+ * design box in the PML. */
+int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_deps, int32_t method, int32_t slots,
+                               int64_t* forward_steps);
+
+/* Forward steps fdtd_backward_checkpointed evaluates for nsteps steps (host only, no GPU); -1 for bad
+ * arguments. */
+int64_t fdtd_checkpoint_cost(int32_t nsteps, int32_t method, int32_t slots);
+
 /* rho_out = P(theta) with the projection of fdtd_design_adam_step (used when proj_beta changes between
  * steps, and for the first densities). theta and rho_out: DEVICE pointers of design-box cells, fp32,
  * enqueued on the solver's stream. INVALID_ARG on a NULL or host pointer, proj_beta < 0 or proj_eta

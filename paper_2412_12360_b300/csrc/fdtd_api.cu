@@ -702,6 +702,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     ra.dhi[d] = h->design_hi[d];
   }
   ra.dLda = h->dLda;
+  ra.inverse = 1;
   ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
   ra.status = h->status;
@@ -1175,6 +1176,262 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
 
 int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
   return backward_scaled(h, dL_ddet, dL_deps, 1.0);
+}
+
+// ---- Checkpointing gradient (Sec. 2.2: the recomputation alternative to time reversal) -------------
+// The adjoint of step n needs the forward state after step n. Instead of rebuilding it with the
+// inverse step, a checkpointing schedule keeps full states (fields and CPML memories) in `slots`
+// buffers and recomputes the others forward from the nearest one. Each adjoint step re-evaluates its
+// own forward step from its input state (as in Griewank's revolve), so reversing l steps evaluates
+// at least l forward steps.
+//   recursive halving: split the range in the middle, keep the middle state while the upper half is
+//     reversed, recurse; ceil(log2 l) + 1 states, (l/2) log2 l extra forward steps for l = 2^j;
+//   treeverse (binomial checkpointing) with c states: the split minimising the forward steps, by
+//     dynamic programming over T(l, k) = min_m [m + T(l - m, k - 1) + T(m, k)], T(1, k) = 1,
+//     T(l, 0) = l (l + 1) / 2 (k free states besides the one holding the range's start).
+namespace {
+
+struct CkptTable {
+  int L = 0, K = 0;
+  std::vector<int64_t> T;  // (L + 1) x (K + 1)
+  std::vector<int> M;      // argmin split length
+  int64_t& t(int l, int k) { return T[(size_t)l * (K + 1) + k]; }
+  int& m(int l, int k) { return M[(size_t)l * (K + 1) + k]; }
+  void build(int L_, int K_) {
+    L = L_;
+    K = K_;
+    T.assign((size_t)(L + 1) * (K + 1), 0);
+    M.assign((size_t)(L + 1) * (K + 1), 0);
+    for (int l = 1; l <= L; ++l) t(l, 0) = (int64_t)l * (l + 1) / 2;
+    for (int k = 1; k <= K; ++k) {
+      t(1, k) = 1;
+      for (int l = 2; l <= L; ++l) {
+        int64_t best = INT64_MAX;
+        int bm = 1;
+        for (int s = 1; s < l; ++s) {
+          const int64_t c = s + t(l - s, k - 1) + t(s, k);
+          if (c < best) {
+            best = c;
+            bm = s;
+          }
+        }
+        t(l, k) = best;
+        m(l, k) = bm;
+      }
+    }
+  }
+};
+
+int64_t halving_cost(int l) { return l <= 1 ? l : l / 2 + halving_cost(l - l / 2) + halving_cost(l / 2); }
+
+int halving_depth(int l) { return l <= 1 ? 1 : 1 + std::max(halving_depth(l - l / 2), halving_depth(l / 2)); }
+
+struct Checkpointer {
+  fdtd_handle* h;
+  cudaStream_t st;
+  int method;
+  int nslots;
+  CkptTable tab;
+  std::vector<float*> slot;
+  int64_t slot_floats = 0;
+  int pos = -1;             // step index of the state held in the solver's current buffers
+  int64_t fsteps = 0;       // forward steps evaluated
+  int pb = 0;               // psi-bar ping-pong
+  FwdArgs fa;
+  RevArgs ra;
+  PsiSet PEb[2], PHb[2];
+
+  float* state_field() const { return h->fields + (int64_t)h->cur * 6 * h->g.vol; }
+  void copy_state(float* dst_f, float* dst_e, float* dst_h, const float* src_f, const float* src_e, const float* src_h) {
+    const int64_t pf = h->psi_floats();
+    cudaMemcpyAsync(dst_f, src_f, 6 * h->g.vol * 4, cudaMemcpyDeviceToDevice, st);
+    if (pf > 0) {
+      cudaMemcpyAsync(dst_e, src_e, pf * 4, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(dst_h, src_h, pf * 4, cudaMemcpyDeviceToDevice, st);
+    }
+  }
+  void save(int s) {
+    const int64_t pf = h->psi_floats(), V = 6 * h->g.vol;
+    float* b = slot[s];
+    copy_state(b, b + V, b + V + pf, state_field(), h->psiE + h->cur * pf, h->psiH + h->cur * pf);
+  }
+  void restore(int s, int step) {
+    if (pos == step) return;
+    const int64_t pf = h->psi_floats(), V = 6 * h->g.vol;
+    const float* b = slot[s];
+    copy_state(state_field(), h->psiE + h->cur * pf, h->psiH + h->cur * pf, b, b + V, b + V + pf);
+    pos = step;
+  }
+  void advance_to(int target) {
+    const Geo& g = h->g;
+    const int64_t pf = h->psi_floats();
+    for (; pos < target; ++pos) {
+      const int c = h->cur, x = 1 - c;
+      fa.cur = h->F(c);
+      fa.nxt = h->F(x);
+      fa.psiE_cur = h->psi_set(h->psiE + c * pf);
+      fa.psiE_nxt = h->psi_set(h->psiE + x * pf);
+      fa.psiH_cur = h->psi_set(h->psiH + c * pf);
+      fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
+      fa.step = pos;
+      for (const SrcDev& hs : h->hsrcs) launch_source(g, fa.cur, hs, pos, +1.f, 0, st);
+      launch_fwd_fused(fa, h->fmaps[c], st);
+      const Fields Fn = h->F(x);
+      for (size_t q = kMaxSrc; q < h->srcs.size(); ++q) launch_source(g, Fn, h->srcs[q], pos, +1.f, 0, st);
+      h->launches += 1 + (int64_t)h->hsrcs.size() + (int64_t)(h->srcs.size() > kMaxSrc ? h->srcs.size() - kMaxSrc : 0);
+      h->cur = x;
+      ++fsteps;
+    }
+  }
+  void adjoint(int n) {  // the forward state after step n is current
+    const Geo& g = h->g;
+    const Fields F = h->F(), A = h->A();
+    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
+    ra.F = F;
+    ra.step = n;
+    ra.pin = PEb[pb];
+    ra.pout = PEb[1 - pb];
+    launch_rev_E(ra, h->rmaps[h->cur], st);
+    ra.pin = PHb[pb];
+    ra.pout = PHb[1 - pb];
+    launch_rev_H(ra, h->rmaps[h->cur], st);
+    pb = 1 - pb;
+    h->launches += 2 + (int64_t)h->dets.size();
+  }
+  // reverse steps [a, b); the state at a is in slot sa; slots from `top` up are free
+  void reverse(int a, int b, int sa, int top) {
+    const int l = b - a;
+    if (l == 1) {
+      restore(sa, a);
+      advance_to(a + 1);
+      adjoint(a);
+      return;
+    }
+    const int kfree = nslots - top;
+    if (kfree <= 0) {  // no free state: recompute each output from the range's start
+      for (int i = b - 1; i >= a; --i) {
+        restore(sa, a);
+        advance_to(i + 1);
+        adjoint(i);
+      }
+      return;
+    }
+    const int m = a + (method == 0 ? l / 2 : tab.m(l, kfree));
+    restore(sa, a);
+    advance_to(m);
+    save(top);
+    reverse(m, b, top, top + 1);
+    reverse(a, m, sa, top);
+  }
+};
+
+}  // namespace
+
+int64_t fdtd_checkpoint_cost(int32_t nsteps, int32_t method, int32_t slots) {
+  if (nsteps < 0 || (method != 0 && method != 1) || (method == 1 && slots < 1)) return -1;
+  if (nsteps == 0) return 0;
+  if (method == 0) return halving_cost(nsteps);
+  CkptTable t;
+  t.build(nsteps, slots - 1);
+  return t.t(nsteps, slots - 1);
+}
+
+int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_deps, int32_t method, int32_t slots,
+                               int64_t* forward_steps) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (method != 0 && method != 1) return fail(FDTD_ERR_INVALID_ARG, "method must be 0 (halving) or 1 (treeverse)");
+  if (method == 1 && slots < 1) return fail(FDTD_ERR_INVALID_ARG, "treeverse needs at least one state slot");
+  if (h->last_nsteps < 0) return fail(FDTD_ERR_STATE, "no forward has run");
+  const int nsteps = h->last_nsteps;
+  const int64_t ndet = det_total_for(h, nsteps);
+  if (ndet > 0 && !dL_ddet) return fail(FDTD_ERR_INVALID_ARG, "dL_ddet is NULL");
+  const int64_t M = box_cells(h->design_lo, h->design_hi);
+  if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
+  if (!in_r_cells(h, h->design_lo, h->design_hi))
+    return fail(FDTD_ERR_INVALID_ARG, "the design box must lie in the PML-free region");
+  const Geo& g = h->g;
+  const int64_t pf = h->psi_floats();
+  if (!h->adj) {
+    TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
+    TRY(encode_rev_maps(h));
+  }
+  if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
+  if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
+  TRY(ensure_buf(h, &h->dLddet, &h->dLddet_cap, ndet, 8));
+  if (M > 0) TRY(ensure_staging(h));
+  TRY(ensure_gtab(h, nsteps));
+  Checkpointer C;
+  C.h = h;
+  C.st = h->stream;
+  C.method = method;
+  C.nslots = method == 0 ? halving_depth(nsteps) : slots;
+  if (method == 1) C.tab.build(nsteps, slots - 1);
+  C.slot_floats = 6 * g.vol + 2 * pf;
+  C.slot.assign(C.nslots, nullptr);
+  auto free_slots = [&]() {
+    for (float*& b : C.slot) {
+      dev_free(h, b, C.slot_floats * 4);
+      b = nullptr;
+    }
+  };
+  for (int s = 0; s < C.nslots; ++s) {
+    const int rc = dev_alloc(h, (void**)&C.slot[s], C.slot_floats * 4);
+    if (rc != FDTD_OK) {
+      free_slots();
+      return rc;
+    }
+  }
+  FwdArgs& fa = C.fa;
+  fa.g = g;
+  fa.T = h->tab();
+  fa.a = h->a;
+  fa.tz = h->tz;
+  fa.nstage = h->fwd_nstage;
+  fa.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
+  for (int q = 0; q < fa.nsrc; ++q) fa.src[q] = h->srcs[q];
+  fa.ndet = 0;  // recomputed steps sample no detectors
+  fa.det_out = h->det_out;
+  fa.partial = h->partial;
+  fa.status = h->status;
+  RevArgs& ra = C.ra;
+  ra.g = g;
+  ra.T = h->tab();
+  ra.B = h->A();
+  ra.a = h->a;
+  ra.tz = h->tz_rev;
+  for (int d = 0; d < 3; ++d) {
+    ra.dlo[d] = h->design_lo[d];
+    ra.dhi[d] = h->design_hi[d];
+  }
+  ra.dLda = h->dLda;
+  ra.inverse = 0;
+  ra.nsrc = 0;  // sources only matter to the inverse step
+  ra.status = h->status;
+  for (int k = 0; k < 2; ++k) {
+    C.PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
+    C.PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
+  }
+  if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
+  CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
+  if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
+  if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
+  TRY(reset_state(h));
+  C.pos = 0;
+  if (nsteps > 0) {
+    C.save(0);
+    C.reverse(0, nsteps, 0, 1);
+  }
+  if (M > 0) {
+    launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, 1.0, h->stream);
+    h->launches += 1;
+    CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));  // the slots are freed (stream-ordered) below
+  free_slots();
+  h->recorded = false;
+  if (forward_steps) *forward_steps = C.fsteps;
+  return FDTD_OK;
 }
 
 int fdtd_backward_density(fdtd_handle* h, const double* dL_ddet, float* dL_drho) {

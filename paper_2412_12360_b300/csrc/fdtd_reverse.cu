@@ -11,7 +11,9 @@
 // rev_H reads E and Hbar and writes H and Ebar), so in-place updates are race-free. Blocks own a
 // TX x TY column tile and march their z-chunk downwards, so the coefficient of the plane above is
 // carried in registers. The tangential H recorded on the six boundary planes (Sec. 2.2) is written
-// back into H by a copy kernel before each rev_E.
+// back into H by a copy kernel before each rev_E. With RevArgs::inverse = 0 (the checkpointing
+// gradient, whose forward states are recomputed) the kernels leave the forward fields untouched and
+// update only the adjoint fields and dL/da.
 //
 // The adjoint coefficients of one E point (component c, its transverse axes c1 = c+1, c2 = c+2):
 //   u = S a Ebar_c (zero where E_c is held by a PEC wall),
@@ -321,9 +323,11 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
     if (inx) ex -= Sa * (dxa * ikY0 - dxb * ikZ);
     if (iny) ey -= Sa * (dya * ikZ - dyb * ikX0);
     if (inz) ez -= Sa * (dza * ikX0 - dzb * ikY0);
-    A.F.f[0][q] = ex;
-    A.F.f[1][q] = ey;
-    A.F.f[2][q] = ez;
+    if (A.inverse) {
+      A.F.f[0][q] = ex;
+      A.F.f[1][q] = ey;
+      A.F.f[2][q] = ez;
+    }
     // dL/da on the design box (inside R: kappa = 1, psi = 0)
     if (dxy && k >= A.dlo[2] && k < A.dhi[2]) {
       float gs = 0.f;
@@ -429,9 +433,11 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
     const float ez_y = Es[2][ty + 1][tx], ex_y = Es[0][ty + 1][tx];
     const float ey_x = Es[1][ty][tx + 1], ez_x = Es[2][ty][tx + 1];
     const bool rzh = k >= g.rhalf_lo[2] && k <= g.rhalf_hi[2], rzi = k >= g.rint_lo[2] && k <= g.rint_hi[2];
-    if (rxi && ryh && rzh) A.F.f[3][q] = hx + S * ((ez_y - ez) * ikY0 - (ey_up - ey) * ikZ);
-    if (rxh && ryi && rzh) A.F.f[4][q] = hy + S * ((ex_up - ex) * ikZ - (ez_x - ez) * ikX0);
-    if (rxh && ryh && rzi) A.F.f[5][q] = hz + S * ((ey_x - ey) * ikX0 - (ex_y - ex) * ikY0);
+    if (A.inverse) {
+      if (rxi && ryh && rzh) A.F.f[3][q] = hx + S * ((ez_y - ez) * ikY0 - (ey_up - ey) * ikZ);
+      if (rxh && ryi && rzh) A.F.f[4][q] = hy + S * ((ex_up - ex) * ikZ - (ez_x - ez) * ikX0);
+      if (rxh && ryh && rzi) A.F.f[5][q] = hz + S * ((ey_x - ey) * ikX0 - (ex_y - ex) * ikY0);
+    }
     ex_up = ex;
     ey_up = ey;
 

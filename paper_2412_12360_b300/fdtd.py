@@ -71,6 +71,8 @@ SIGNATURES = [
     ("fdtd_set_design_density", C.c_int, [_VP, _VP, C.c_double, C.c_double]),
     ("fdtd_backward_density", C.c_int, [_VP, _VP, _VP]),
     ("fdtd_design_project", C.c_int, [_VP, _VP, _VP, C.c_double, C.c_double]),
+    ("fdtd_backward_checkpointed", C.c_int, [_VP, _VP, _VP, C.c_int32, C.c_int32, C.POINTER(C.c_int64)]),
+    ("fdtd_checkpoint_cost", C.c_int64, [C.c_int32, C.c_int32, C.c_int32]),
     ("fdtd_design_adam_step", C.c_int, [_VP, _VP, _VP, _VP, _VP, _VP, C.c_int32, C.c_double, C.c_double, C.c_double,
                                         C.c_double, C.c_double, C.c_double]),
     ("fdtd_forward", C.c_int, [_VP, C.c_int32, C.c_uint32]),
@@ -113,6 +115,11 @@ def lib():
 
 def last_error() -> str:
     return lib().fdtd_last_error().decode()
+
+
+def checkpoint_cost(nsteps: int, method: int, slots: int = 0) -> int:
+    """Forward steps the checkpointing gradient evaluates (host only)."""
+    return int(lib().fdtd_checkpoint_cost(int(nsteps), int(method), int(slots)))
 
 
 def check(rc):
@@ -261,6 +268,14 @@ class Solver:
         check(lib().fdtd_design_adam_step(self.h, _ptr(dL_drho), _ptr(theta), _ptr(m), _ptr(v), _ptr(rho_out),
                                           int(t), float(lr), float(beta1), float(beta2), float(eps),
                                           float(proj_beta), float(proj_eta)))
+
+    def fdtd_backward_checkpointed(self, dL_ddet, dL_deps, method: int = 0, slots: int = 0) -> int:
+        """Checkpointing gradient of the last forward (method 0 recursive halving, 1 treeverse with
+        `slots` stored states); returns the forward steps it evaluated."""
+        n = C.c_int64(0)
+        check(lib().fdtd_backward_checkpointed(self.h, _ptr(dL_ddet), _ptr(dL_deps), int(method), int(slots),
+                                               C.byref(n)))
+        return int(n.value)
 
     def fdtd_design_project(self, theta, rho_out, proj_beta: float = 0.0, proj_eta: float = 0.5):
         check(lib().fdtd_design_project(self.h, _ptr(theta), _ptr(rho_out), float(proj_beta), float(proj_eta)))
