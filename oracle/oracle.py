@@ -55,6 +55,7 @@ def lib():
         L.orc_gradient.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, C.c_int32, d, d, d]
         L.orc_complex_step.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, P(C.c_int32), C.c_double, d]
         L.orc_cpml_tables.argtypes = [P(_Scene), C.c_int32, d]
+        L.orc_sample.argtypes = [P(_Scene), d, d, d]
         L.orc_waveform.argtypes = [P(_Scene), C.c_int32, C.c_double]
         L.orc_waveform.restype = C.c_double
         _LIB = L
@@ -213,6 +214,17 @@ def complex_step(scene, nsteps, dL_ddet, voxels, h=1e-20):
     rc = lib().orc_complex_step(a.ptr, int(nsteps), _dptr(g), len(voxels),
                                 vox.ctypes.data_as(C.POINTER(C.c_int32)), float(h), _dptr(out))
     assert rc == 0
+    return out
+
+
+def sample(scene, state6, prev6=None):
+    """Detector outputs of one step sampled from given fields: state6 = (E^{n+1}, H^{n+1/2}) as
+    (6, nz, ny, nx), prev6 (optional) supplies E^n in its first three arrays."""
+    a = _SceneArgs(scene)
+    st = np.ascontiguousarray(np.asarray(state6, dtype=np.float64))
+    pv = None if prev6 is None else np.ascontiguousarray(np.asarray(prev6, dtype=np.float64))
+    out = np.zeros(detector_total(scene, 1))
+    lib().orc_sample(a.ptr, _dptr(pv), _dptr(st), _dptr(out))
     return out
 
 

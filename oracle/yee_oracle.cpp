@@ -56,6 +56,14 @@ typedef struct {
 //   0 point series : value of field `component` (0..5 = Ex..Hz) at cell lo, one value per step.
 //   1 |E|^2 sum    : per cell of the box, sum over steps of Ex^2 + Ey^2 + Ez^2 (same-index samples).
 //   2 flux series  : per step, sum over the box of (E x H)[axis] (same-index samples).
+// With interpolation (Sec. 2.1: composite metrics need the staggered components brought to one point
+// in space and time; the paper's evaluation mode), every component is taken at the cell centre
+// (i+1/2, j+1/2, k+1/2): E_c as the mean of its 4 values around the centre (offsets 0/1 along the two
+// axes other than c), H_c as the mean of its 2 values (offsets 0/1 along c); values beyond the grid
+// are 0 (the box plus one cell must lie in the grid).
+//   3 |E|^2 sum, interpolated : per cell, sum over steps of |E^{n+1}(centre)|^2;
+//   4 flux series, interpolated: per step, sum over the box of (E^{n+1/2} x H^{n+1/2})[axis] at the
+//     centres, E^{n+1/2} = (E^n + E^{n+1}) / 2.
 typedef struct {
   int32_t kind;
   int32_t component;
@@ -205,6 +213,8 @@ struct Sim {
   size_t det_total = 0;
   int nsteps;
   std::vector<Tfsf> tfsf;           // per source (used where the source has tfsf != 0)
+  bool time_interp = false;         // some detector needs E^n beside E^{n+1} (kind 4)
+  mutable std::vector<T> prevE[3];  // E^n of the step being sampled (kind 4 only)
 
   Sim(const orc_scene& s, int nsteps_) : sc(s), g(s), S(s.courant), cf(make_coefs(s)), nsteps(nsteps_) {
     a.resize(g.N);
@@ -212,13 +222,14 @@ struct Sim {
     tfsf.resize(s.nsrc);
     for (int q = 0; q < s.nsrc; ++q)
       if (s.src[q].tfsf != 0) tfsf[q] = make_tfsf(s.src[q], S, nsteps);
+    for (int q = 0; q < s.ndet; ++q) time_interp = time_interp || s.det[q].kind == 4;
     for (int q = 0; q < s.ndet; ++q) {
       det_offset.push_back(det_total);
       det_total += det_size(s.det[q]);
     }
   }
   size_t det_size(const orc_detector& d) const {
-    if (d.kind == 1)
+    if (d.kind == 1 || d.kind == 3)
       return size_t(d.hi[0] - d.lo[0]) * (d.hi[1] - d.lo[1]) * (d.hi[2] - d.lo[2]);
     return size_t(nsteps);
   }
@@ -331,6 +342,34 @@ struct Sim {
     }
   }
 
+  // Cell-centre values of E_c (mean of 4) and H_c (mean of 2) at cell p; 0 beyond the grid.
+  T at_or0(const std::vector<T>& f, const int* p) const {
+    for (int d = 0; d < 3; ++d)
+      if (p[d] >= g.n[d]) return T(0);
+    return f[g.at(p)];
+  }
+  T e_centre(const std::vector<T>& E, int c, const int* p) const {
+    T s = T(0);
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[m3(c + 1)] += a;
+        q[m3(c + 2)] += b;
+        s += at_or0(E, q);
+      }
+    return 0.25 * s;
+  }
+  T h_centre(const std::vector<T>& H, int c, const int* p) const {
+    int q[3] = {p[0], p[1], p[2]};
+    q[c] += 1;
+    return 0.5 * (H[g.at(p)] + at_or0(H, q));
+  }
+  // E^n, kept before the E update of step n when a kind-4 detector needs it
+  void keep_prev(const State<T>& st) const {
+    if (time_interp)
+      for (int c = 0; c < 3; ++c) prevE[c] = st.F[c];
+  }
+
   // Detectors sample E^{n+1} and H^{n+1/2} after step n.
   void sample(const State<T>& st, int n, std::vector<T>& out) const {
     for (int q = 0; q < sc.ndet; ++q) {
@@ -346,7 +385,7 @@ struct Sim {
               const size_t p = g.at(i, j, k);
               o[m] += st.F[0][p] * st.F[0][p] + st.F[1][p] * st.F[1][p] + st.F[2][p] * st.F[2][p];
             }
-      } else {
+      } else if (d.kind == 2) {
         const int a1 = m3(d.axis + 1), a2 = m3(d.axis + 2);
         T f = T(0);
         for (int k = d.lo[2]; k < d.hi[2]; ++k)
@@ -356,6 +395,29 @@ struct Sim {
               f += st.F[a1][p] * st.F[3 + a2][p] - st.F[a2][p] * st.F[3 + a1][p];
             }
         o[n] = f;
+      } else if (d.kind == 3) {
+        size_t m = 0;
+        for (int k = d.lo[2]; k < d.hi[2]; ++k)
+          for (int j = d.lo[1]; j < d.hi[1]; ++j)
+            for (int i = d.lo[0]; i < d.hi[0]; ++i, ++m) {
+              const int p[3] = {i, j, k};
+              for (int c = 0; c < 3; ++c) {
+                const T e = e_centre(st.F[c], c, p);
+                o[m] += e * e;
+              }
+            }
+      } else if (d.kind == 4) {
+        const int a1 = m3(d.axis + 1), a2 = m3(d.axis + 2);
+        T f = T(0);
+        for (int k = d.lo[2]; k < d.hi[2]; ++k)
+          for (int j = d.lo[1]; j < d.hi[1]; ++j)
+            for (int i = d.lo[0]; i < d.hi[0]; ++i) {
+              const int p[3] = {i, j, k};
+              const T e1 = 0.5 * (e_centre(prevE[a1], a1, p) + e_centre(st.F[a1], a1, p));
+              const T e2 = 0.5 * (e_centre(prevE[a2], a2, p) + e_centre(st.F[a2], a2, p));
+              f += e1 * h_centre(st.F[3 + a2], a2, p) - e2 * h_centre(st.F[3 + a1], a1, p);
+            }
+        o[n] = f;
       }
     }
   }
@@ -363,6 +425,7 @@ struct Sim {
   void step(State<T>& st, int n, std::vector<T>* det) const {
     update_H(st);
     add_h_sources(st, n, +1.0);
+    if (det) keep_prev(st);
     update_E(st);
     add_sources(st, n, +1.0);
     if (det) sample(st, n, *det);
@@ -375,6 +438,30 @@ struct Sim {
   // read. `gy` holds dL/d(detector outputs).
   // Each forward statement is transposed in turn (scatter form), in reverse order.
   // ---------------------------------------------------------------------------------------------
+  // Transposes of e_centre and h_centre: add w times each stencil weight to the stencil points.
+  void e_centre_T(std::vector<T>& Eb, int c, const int* p, T w) const {
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b) {
+        int q[3] = {p[0], p[1], p[2]};
+        q[m3(c + 1)] += a;
+        q[m3(c + 2)] += b;
+        if (q[0] < g.n[0] && q[1] < g.n[1] && q[2] < g.n[2]) Eb[g.at(q)] += 0.25 * w;
+      }
+  }
+  void h_centre_T(std::vector<T>& Hb, int c, const int* p, T w) const {
+    Hb[g.at(p)] += 0.5 * w;
+    int q[3] = {p[0], p[1], p[2]};
+    q[c] += 1;
+    if (q[c] < g.n[c]) Hb[g.at(q)] += 0.5 * w;
+  }
+  // E^n for the kind-4 detectors of step n (the state before the step)
+  void set_prev(const State<T>& before) const {
+    if (time_interp)
+      for (int c = 0; c < 3; ++c) prevE[c] = before.F[c];
+  }
+
+  // Detector terms through the state after step n (E^{n+1}, H^{n+1/2}); kind 4 also reads E^n
+  // (set_prev) for its H term.
   void inject_detectors(const State<T>& fw, int n, const double* gy, State<T>& ad) const {
     for (int q = 0; q < sc.ndet; ++q) {
       const orc_detector& d = sc.det[q];
@@ -389,7 +476,7 @@ struct Sim {
               const size_t p = g.at(i, j, k);
               for (int c = 0; c < 3; ++c) ad.F[c][p] += 2.0 * gq[m] * fw.F[c][p];
             }
-      } else {
+      } else if (d.kind == 2) {
         const int a1 = m3(d.axis + 1), a2 = m3(d.axis + 2);
         for (int k = d.lo[2]; k < d.hi[2]; ++k)
           for (int j = d.lo[1]; j < d.hi[1]; ++j)
@@ -400,7 +487,48 @@ struct Sim {
               ad.F[a2][p] -= gq[n] * fw.F[3 + a1][p];
               ad.F[3 + a1][p] -= gq[n] * fw.F[a2][p];
             }
+      } else if (d.kind == 3) {
+        size_t m = 0;
+        for (int k = d.lo[2]; k < d.hi[2]; ++k)
+          for (int j = d.lo[1]; j < d.hi[1]; ++j)
+            for (int i = d.lo[0]; i < d.hi[0]; ++i, ++m) {
+              const int p[3] = {i, j, k};
+              for (int c = 0; c < 3; ++c) e_centre_T(ad.F[c], c, p, 2.0 * gq[m] * e_centre(fw.F[c], c, p));
+            }
+      } else if (d.kind == 4) {
+        const int a1 = m3(d.axis + 1), a2 = m3(d.axis + 2);
+        const T G = T(gq[n]);
+        for (int k = d.lo[2]; k < d.hi[2]; ++k)
+          for (int j = d.lo[1]; j < d.hi[1]; ++j)
+            for (int i = d.lo[0]; i < d.hi[0]; ++i) {
+              const int p[3] = {i, j, k};
+              const T h1 = h_centre(fw.F[3 + a1], a1, p), h2 = h_centre(fw.F[3 + a2], a2, p);
+              const T e1 = 0.5 * (e_centre(prevE[a1], a1, p) + e_centre(fw.F[a1], a1, p));
+              const T e2 = 0.5 * (e_centre(prevE[a2], a2, p) + e_centre(fw.F[a2], a2, p));
+              // F = e1 h2 - e2 h1, e = (E^n + E^{n+1}) / 2
+              e_centre_T(ad.F[a1], a1, p, 0.5 * G * h2);
+              e_centre_T(ad.F[a2], a2, p, -0.5 * G * h1);
+              h_centre_T(ad.F[3 + a2], a2, p, G * e1);
+              h_centre_T(ad.F[3 + a1], a1, p, -G * e2);
+            }
       }
+    }
+  }
+
+  // The kind-4 terms through E^n, added once the adjoint holds dL/d(state before step n).
+  void inject_detectors_prev(const State<T>& fw, int n, const double* gy, State<T>& ad) const {
+    for (int q = 0; q < sc.ndet; ++q) {
+      const orc_detector& d = sc.det[q];
+      if (d.kind != 4) continue;
+      const int a1 = m3(d.axis + 1), a2 = m3(d.axis + 2);
+      const T G = T(gy[det_offset[q] + n]);
+      for (int k = d.lo[2]; k < d.hi[2]; ++k)
+        for (int j = d.lo[1]; j < d.hi[1]; ++j)
+          for (int i = d.lo[0]; i < d.hi[0]; ++i) {
+            const int p[3] = {i, j, k};
+            e_centre_T(ad.F[a1], a1, p, 0.5 * G * h_centre(fw.F[3 + a2], a2, p));
+            e_centre_T(ad.F[a2], a2, p, -0.5 * G * h_centre(fw.F[3 + a1], a1, p));
+          }
     }
   }
 
@@ -486,6 +614,7 @@ struct Sim {
     // sources add a constant: their transpose is the identity on the adjoint
     adjoint_E(fw, ad, dLda);
     adjoint_H(ad);
+    inject_detectors_prev(fw, n, gy, ad);
   }
 
   // ---------------------------------------------------------------------------------------------
@@ -704,7 +833,10 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
       traj[n + 1] = traj[n];
       sim.step(traj[n + 1], n, &d);
     }
-    for (int n = nsteps - 1; n >= 0; --n) sim.adjoint_step(traj[n + 1], n, dL_ddet, ad, dLda);
+    for (int n = nsteps - 1; n >= 0; --n) {
+      sim.set_prev(traj[n]);
+      sim.adjoint_step(traj[n + 1], n, dL_ddet, ad, dLda);
+    }
   } else if (method == 1) {
     if (interval < 1) return -1;
     std::vector<State<double>> ckpt;
@@ -721,7 +853,10 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
         traj.push_back(traj.back());
         sim.step(traj.back(), n, nullptr);
       }
-      for (int n = n1 - 1; n >= n0; --n) sim.adjoint_step(traj[n - n0 + 1], n, dL_ddet, ad, dLda);
+      for (int n = n1 - 1; n >= n0; --n) {
+        sim.set_prev(traj[n - n0]);
+        sim.adjoint_step(traj[n - n0 + 1], n, dL_ddet, ad, dLda);
+      }
     }
   } else if (method == 2) {
     State<double> st(N);
@@ -731,6 +866,7 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
       sim.update_H(st);
       sim.add_h_sources(st, n, +1.0);
       sim.record_faces(st, fs, rec[n]);
+      sim.keep_prev(st);
       sim.update_E(st);
       sim.add_sources(st, n, +1.0);
       sim.sample(st, n, d);
@@ -738,6 +874,11 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
     for (int n = nsteps - 1; n >= 0; --n) {
       // st holds E^{n+1} and H^{n+1/2} on R; psi_E is zero on R
       sim.replay_faces(st, fs, rec[n]);
+      if (sim.time_interp) {  // E^n on R, by one inverse step on a copy
+        State<double> before = st;
+        sim.inverse_step(before, n);
+        sim.set_prev(before);
+      }
       sim.adjoint_step(st, n, dL_ddet, ad, dLda);
       sim.inverse_step(st, n);
     }
@@ -776,6 +917,23 @@ int orc_cpml_tables(const orc_scene* s, int32_t axis, double* out) {
   const int N = s->n[axis];
   const std::vector<double>* v[6] = {&a.b_int, &a.c_int, &a.kappa_int, &a.b_half, &a.c_half, &a.kappa_half};
   for (int t = 0; t < 6; ++t) std::memcpy(out + t * N, v[t]->data(), N * sizeof(double));
+  return 0;
+}
+
+// Detector outputs of one step sampled from given fields (for inspection): prev6 supplies E^n (its
+// first three arrays; may be NULL for E^n = E^{n+1}), state6 the fields after the step (E^{n+1},
+// H^{n+1/2}); out receives orc_detector_total(s, 1) values.
+int orc_sample(const orc_scene* s, const double* prev6, const double* state6, double* out) {
+  Sim<double> sim(*s, 1);
+  State<double> st(sim.g.N);
+  sim.load_initial(st, state6);
+  for (int c = 0; c < 3; ++c) {
+    sim.prevE[c] = st.F[c];
+    if (prev6) std::memcpy(sim.prevE[c].data(), prev6 + c * sim.g.N, sim.g.N * sizeof(double));
+  }
+  std::vector<double> d(sim.det_total, 0.0);
+  sim.sample(st, 0, d);
+  std::memcpy(out, d.data(), d.size() * sizeof(double));
   return 0;
 }
 

@@ -24,6 +24,8 @@ EX, EY, EZ, HX, HY, HZ = range(6)
 DET_POINT_SERIES = 0   # one field component at one cell, every step
 DET_PLANE_E2_SUM = 1   # per cell of a box: sum over steps of Ex^2 + Ey^2 + Ez^2
 DET_PLANE_FLUX = 2     # per step: sum over a box of (E x H) along an axis
+DET_PLANE_E2_SUM_INTERP = 3  # as 1, with E interpolated to the cell centres
+DET_PLANE_FLUX_INTERP = 4    # as 2, with E and H at the cell centres and E at time n + 1/2
 
 SPEED_OF_LIGHT = 299792458.0
 
