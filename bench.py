@@ -48,6 +48,10 @@ def workload(name):
         sc = scenes.design_box_scene((96, 96, 96), 10, 40, 2000, 1234, 1.0, 12.1, 20.0, "design_96_tfsf", tfsf=True)
         desc = ("design_96_tfsf: design_96 with the Gaussian beam injected by a one-sided TFSF plane (+z) "
                 "instead of a soft sheet, 2000 steps fwd + 2000 reversed")
+    elif name == "design_96_interp":
+        sc = scenes.design_box_scene((96, 96, 96), 10, 40, 2000, 1234, 1.0, 12.1, 20.0, "design_96_interp", interp=True)
+        desc = ("design_96_interp: design_96 with the |E|^2 plane taken from E interpolated to the cell centres, "
+                "2000 steps fwd + 2000 reversed")
     elif name == "waveguide_600":
         sc = scenes.waveguide_600()
         desc = ("waveguide_600: 600^3 grid, 12-cell CPML, Si core eps=12.25 in SiO2 eps=2.085, 200^3 design "
@@ -66,7 +70,8 @@ def objective_grad(sc, nsteps):
     """dL/d(detector) for L = sum of every detector output (the |E|^2 plane sum or the flux sum)."""
     n = 0
     for d in sc.detectors:
-        n += nsteps if d.kind != scenes.DET_PLANE_E2_SUM else int(np.prod([d.hi[k] - d.lo[k] for k in range(3)]))
+        per_cell = d.kind in (scenes.DET_PLANE_E2_SUM, scenes.DET_PLANE_E2_SUM_INTERP)
+        n += int(np.prod([d.hi[k] - d.lo[k] for k in range(3)])) if per_cell else nsteps
     return np.ones(n, dtype=np.float64)
 
 

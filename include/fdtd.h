@@ -58,6 +58,14 @@ extern "C" {
 #define FDTD_DET_POINT_SERIES 0    /* field `component` (0..5) at cell lo, one value per step */
 #define FDTD_DET_PLANE_E2_SUM 1    /* per cell of [lo, hi): sum over steps of Ex^2 + Ey^2 + Ez^2 */
 #define FDTD_DET_PLANE_FLUX 2      /* per step: sum over [lo, hi) of (E x H)[axis] */
+/* Interpolated forms (Sec. 2.1: composite metrics need the staggered components brought to one point
+ * in space and time; the paper's evaluation mode). Every component is taken at the cell centre: E_c
+ * as the mean of its 4 values around it (offsets 0/1 along the two axes other than c), H_c as the
+ * mean of its 2 values (offsets 0/1 along c); the box plus one cell along each axis must lie in the
+ * grid (and, for a gradient, in the PML-free region). */
+#define FDTD_DET_PLANE_E2_SUM_INTERP 3  /* per cell of [lo, hi): sum over steps of |E^{n+1}(centre)|^2 */
+#define FDTD_DET_PLANE_FLUX_INTERP 4    /* per step: sum over [lo, hi) of (E^{n+1/2} x H^{n+1/2})[axis] at the
+                                         * centres, E^{n+1/2} = (E^n + E^{n+1}) / 2 */
 
 typedef struct fdtd_handle fdtd_handle;
 
@@ -102,8 +110,9 @@ typedef struct {
 } fdtd_source;
 
 /* Detector (Sec. 2.1: detectors record field values at intermediate time steps; composite values
- * use same-index components without interpolation). Output sizes: POINT_SERIES and PLANE_FLUX give
- * nsteps doubles, PLANE_E2_SUM gives one double per box cell (x fastest). */
+ * use same-index components without interpolation, or the interpolated kinds above). Output sizes:
+ * POINT_SERIES and the PLANE_FLUX kinds give nsteps doubles, the PLANE_E2_SUM kinds one double per box
+ * cell (x fastest). */
 typedef struct {
   int32_t kind;                    /* FDTD_DET_* */
   int32_t component;               /* POINT_SERIES: 0..5 = Ex..Hz */

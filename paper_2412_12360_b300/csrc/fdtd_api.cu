@@ -319,6 +319,8 @@ struct fdtd_handle {
   std::vector<int> src_tfsf, hsrc_tfsf;  // per entry of srcs / hsrcs: its index in tfsf, or -1
   std::vector<Tfsf> tfsf;
   std::vector<DetDev> dets;
+  std::vector<char> det_inline;   // per detector: sampled inside the fused forward kernel
+  std::vector<float*> det_slab;   // per detector: 3 slabs (E^{n+1}, H^{n+1/2}, E^n) for kind 4, else null
   int64_t det_total_per_step = 0, det_total_fixed = 0;
 
   // device memory
@@ -550,8 +552,9 @@ int ensure_det(fdtd_handle* h, int nsteps) {
   int64_t off = 0, pneed = 0;
   for (auto& d : h->dets) {
     d.off = off;
-    off += d.kind == FDTD_DET_PLANE_E2_SUM ? box_cells(d.lo, d.hi) : nsteps;
-    if (d.kind == FDTD_DET_PLANE_FLUX) {
+    const bool per_cell = d.kind == FDTD_DET_PLANE_E2_SUM || d.kind == FDTD_DET_PLANE_E2_SUM_INTERP;
+    off += per_cell ? box_cells(d.lo, d.hi) : nsteps;
+    if (d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) {
       d.poff = pneed;
       pneed += (int64_t)d.nblk * nsteps;
     }
@@ -621,6 +624,46 @@ int encode_rev_maps(fdtd_handle* h) {
 
 // ---- the time loops -------------------------------------------------------------------------------
 
+// Detector adjoints of reverse step n, part 0 (start of the step: every detector's terms through the
+// state after step n; the interpolated flux first copies E^{n+1} and H^{n+1/2} into its slabs),
+// part 1 (after rev_E: the interpolated flux's H terms, with E^n copied from the rebuilt fields, or
+// already in its slab when `e0_ready`) and part 2 (after rev_H: the interpolated flux's E^n terms).
+int64_t enqueue_det_adjoint(fdtd_handle* h, const Fields& F, const Fields& A, int n, int part, cudaStream_t st,
+                            bool e0_ready = false) {
+  const Geo& g = h->g;
+  int64_t launches = 0;
+  for (size_t q = 0; q < h->dets.size(); ++q) {
+    const DetDev& d = h->dets[q];
+    float* sl = h->det_slab[q];
+    const int64_t sf = sl ? interp_slab_floats(d) : 0;
+    float *sE1 = sl, *sH = sl + sf, *sE0 = sl + 2 * sf;
+    if (d.kind <= FDTD_DET_PLANE_FLUX) {
+      if (part == 0) {
+        launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
+        ++launches;
+      }
+    } else if (d.kind == FDTD_DET_PLANE_E2_SUM_INTERP) {
+      if (part == 0) {
+        launch_interp_adjoint(g, F, A, d, n, h->dLddet, 0, nullptr, nullptr, nullptr, st);
+        ++launches;
+      }
+    } else {
+      if (part == 0) {
+        launch_slab_copy(g, F, d, 0, sE1, st);
+        launch_slab_copy(g, F, d, 3, sH, st);
+        launches += 2;
+      } else if (part == 1 && !e0_ready) {
+        launch_slab_copy(g, F, d, 0, sE0, st);
+        ++launches;
+      }
+      launch_interp_adjoint(g, F, A, d, n, h->dLddet, part, sE0, sE1, sH, st);
+      ++launches;
+    }
+  }
+  return launches;
+}
+
+
 // Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
 // fused kernel's slots), then the fixed-order flux sums. Mutates h->cur as it goes.
 int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st, std::vector<Ev>* evs) {
@@ -636,8 +679,9 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.nstage = h->fwd_nstage;
   fa.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < fa.nsrc; ++q) fa.src[q] = h->srcs[q];
-  fa.ndet = (int)std::min<size_t>(h->dets.size(), kMaxDet);
-  for (int q = 0; q < fa.ndet; ++q) fa.det[q] = h->dets[q];
+  fa.ndet = 0;
+  for (size_t q = 0; q < h->dets.size(); ++q)
+    if (h->det_inline[q]) fa.det[fa.ndet++] = h->dets[q];
   fa.det_out = h->det_out;
   fa.partial = h->partial;
   fa.status = h->status;
@@ -666,12 +710,17 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
       launches += 1;
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
-    for (size_t q = kMaxDet; q < h->dets.size(); ++q, ++launches)
-      launch_detector_sample(g, Fn, h->dets[q], n, h->det_out, h->partial, st);
+    for (size_t q = 0; q < h->dets.size(); ++q) {
+      if (h->det_inline[q]) continue;
+      const DetDev& d = h->dets[q];
+      if (d.kind <= FDTD_DET_PLANE_FLUX) launch_detector_sample(g, Fn, d, n, h->det_out, h->partial, st);
+      else launch_detector_interp(g, h->F(c), Fn, d, n, h->det_out, h->partial, st);  // E^n is in cur
+      ++launches;
+    }
     h->cur = x;
   }
   for (const auto& d : h->dets)
-    if (d.kind == FDTD_DET_PLANE_FLUX && nsteps > 0) {
+    if ((d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) && nsteps > 0) {
       launch_flux_finalize(d, nsteps, h->partial, h->det_out, st);
       launches += 1;
     }
@@ -712,8 +761,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   for (int n = nsteps - 1; n >= 0; --n) {
     if (!h->dets.empty()) {
       ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
-      for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
-      launches += (int64_t)h->dets.size();
+      launches += enqueue_det_adjoint(h, F, A, n, 0, st);
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
     ra.step = n;
@@ -728,6 +776,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
       ra.pout = PEb[1 - pb];
       launch_rev_E(ra, rm, st);
     }
+    launches += enqueue_det_adjoint(h, F, A, n, 1, st);  // interpolated flux: H terms, E^n rebuilt
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
       ra.pin = PHb[pb];
@@ -738,6 +787,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     // the inverse H step rebuilt H^{n-1/2} + the TFSF H corrections of step n on R: remove them
     for (const SrcDev& hs : h->hsrcs) launch_source(g, F, hs, n, -1.f, 1, st);
     launches += (int64_t)h->hsrcs.size();
+    launches += enqueue_det_adjoint(h, F, A, n, 2, st);  // interpolated flux: E^n terms
     pb = 1 - pb;
   }
   return launches;
@@ -860,11 +910,13 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   }
   for (int q = 0; q < ndet; ++q) {
     const fdtd_detector& d = det[q];
-    if (d.kind < 0 || d.kind > 2) return fail(FDTD_ERR_INVALID_ARG, "detector %d: unknown kind", q);
+    if (d.kind < 0 || d.kind > 4) return fail(FDTD_ERR_INVALID_ARG, "detector %d: unknown kind", q);
     if (!box_ok(d.lo, d.hi, n, false)) return fail(FDTD_ERR_INVALID_ARG, "detector %d: box outside the grid", q);
+    if (d.kind >= FDTD_DET_PLANE_E2_SUM_INTERP && (d.hi[0] >= n[0] || d.hi[1] >= n[1] || d.hi[2] >= n[2]))
+      return fail(FDTD_ERR_INVALID_ARG, "detector %d: an interpolated box needs one more cell inside the grid", q);
     if (d.kind == FDTD_DET_POINT_SERIES && (d.component < 0 || d.component > 5))
       return fail(FDTD_ERR_INVALID_ARG, "detector %d: component must be 0..5", q);
-    if (d.kind == FDTD_DET_PLANE_FLUX && (d.axis < 0 || d.axis > 2))
+    if ((d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) && (d.axis < 0 || d.axis > 2))
       return fail(FDTD_ERR_INVALID_ARG, "detector %d: axis must be 0..2", q);
   }
   int32_t zlo[3] = {0, 0, 0};
@@ -1037,8 +1089,12 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     dd.nblk = 0;
     dd.poff = 0;
     const int64_t m = box_cells(d.lo, d.hi);
-    if (d.kind == FDTD_DET_PLANE_FLUX) {
-      if (q < kMaxDet) {  // summed inside the fused kernel: one slot per block that meets the box
+    // the first kMaxDet same-index detectors are sampled inside the fused forward kernel
+    int ninline = 0;
+    for (char c : h->det_inline) ninline += c;
+    const bool inl = d.kind <= FDTD_DET_PLANE_FLUX && ninline < kMaxDet;
+    if (d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) {
+      if (inl) {  // summed inside the fused kernel: one slot per block that meets the box
         const int tx = fused_tile_x(), ty = fused_tile_y();
         dd.nblk = ((d.hi[0] - 1) / tx - d.lo[0] / tx + 1) * ((d.hi[1] - 1) / ty - d.lo[1] / ty + 1) *
                   ((d.hi[2] - 1) / h->tz - d.lo[2] / h->tz + 1);
@@ -1046,9 +1102,15 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
         dd.nblk = (int)std::min<int64_t>(148, std::max<int64_t>(1, (m + 4095) / 4096));
       }
     }
-    if (d.kind == FDTD_DET_PLANE_E2_SUM) h->det_total_fixed += m;
+    if (d.kind == FDTD_DET_PLANE_E2_SUM || d.kind == FDTD_DET_PLANE_E2_SUM_INTERP) h->det_total_fixed += m;
     else h->det_total_per_step += 1;
+    float* slab = nullptr;
+    if (d.kind == FDTD_DET_PLANE_FLUX_INTERP &&
+        (rc = dev_alloc(h, (void**)&slab, 3 * interp_slab_floats(dd) * 4)) != FDTD_OK)
+      return cleanup(rc);
     h->dets.push_back(dd);
+    h->det_inline.push_back(inl ? 1 : 0);
+    h->det_slab.push_back(slab);
   }
   *out = h;
   return FDTD_OK;
@@ -1063,6 +1125,8 @@ int fdtd_destroy(fdtd_handle* h) {
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, h->stream);
   for (float* p : h->src_w) cudaFreeAsync(p, h->stream);
+  for (float* p : h->det_slab)
+    if (p) cudaFreeAsync(p, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
   cudaGetLastError();
@@ -1113,9 +1177,13 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   if (nsteps < 0) return fail(FDTD_ERR_INVALID_ARG, "nsteps must be >= 0");
   const bool record = (flags & FDTD_RECORD_FACES) != 0;
   if (record) {
-    for (const auto& d : h->dets)
-      if (!in_r_cells(h, d.lo, d.hi))
+    for (const auto& d : h->dets) {
+      int hi[3] = {d.hi[0], d.hi[1], d.hi[2]};
+      if (d.kind >= FDTD_DET_PLANE_E2_SUM_INTERP)  // the interpolation stencil reaches one cell further
+        for (int k = 0; k < 3; ++k) hi[k] += 1;
+      if (!in_r_cells(h, d.lo, hi))
         return fail(FDTD_ERR_INVALID_ARG, "a detector lies in the PML; backward needs detectors in the PML-free region");
+    }
     if (!in_r_cells(h, h->design_lo, h->design_hi))
       return fail(FDTD_ERR_INVALID_ARG, "the design box must lie in the PML-free region");
   }
@@ -1274,6 +1342,10 @@ struct Checkpointer {
       fa.psiH_cur = h->psi_set(h->psiH + c * pf);
       fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
       fa.step = pos;
+      if (pos == target - 1)  // E^n of the step the next adjoint reverses, for the interpolated flux
+        for (size_t q = 0; q < h->dets.size(); ++q)
+          if (h->dets[q].kind == FDTD_DET_PLANE_FLUX_INTERP)
+            launch_slab_copy(g, fa.cur, h->dets[q], 0, h->det_slab[q] + 2 * interp_slab_floats(h->dets[q]), st);
       for (const SrcDev& hs : h->hsrcs) launch_source(g, fa.cur, hs, pos, +1.f, 0, st);
       launch_fwd_fused(fa, h->fmaps[c], st);
       const Fields Fn = h->F(x);
@@ -1283,20 +1355,21 @@ struct Checkpointer {
       ++fsteps;
     }
   }
-  void adjoint(int n) {  // the forward state after step n is current
-    const Geo& g = h->g;
+  void adjoint(int n) {  // the forward state after step n is current (E^n of it in the slabs)
     const Fields F = h->F(), A = h->A();
-    for (const auto& d : h->dets) launch_detector_adjoint(g, F, A, d, n, h->dLddet, st);
+    h->launches += enqueue_det_adjoint(h, F, A, n, 0, st);
     ra.F = F;
     ra.step = n;
     ra.pin = PEb[pb];
     ra.pout = PEb[1 - pb];
     launch_rev_E(ra, h->rmaps[h->cur], st);
+    h->launches += enqueue_det_adjoint(h, F, A, n, 1, st, true);
     ra.pin = PHb[pb];
     ra.pout = PHb[1 - pb];
     launch_rev_H(ra, h->rmaps[h->cur], st);
+    h->launches += enqueue_det_adjoint(h, F, A, n, 2, st);
     pb = 1 - pb;
-    h->launches += 2 + (int64_t)h->dets.size();
+    h->launches += 2;
   }
   // reverse steps [a, b); the state at a is in slot sa; slots from `top` up are free
   void reverse(int a, int b, int sa, int top) {

@@ -123,6 +123,14 @@ __host__ __device__ inline int64_t psi_elems(const Geo& g, int d) {
 // ---- launchers (fdtd_kernels.cu) --------------------------------------------------------------
 void launch_source(const Geo& g, const Fields& F, const SrcDev& src, int step, float sign, int only_R,
                    cudaStream_t s);
+// interpolated detectors (fdtd_interp.cu)
+int64_t interp_slab_floats(const DetDev& d);
+void launch_detector_interp(const Geo& g, const Fields& P, const Fields& F, const DetDev& d, int step, double* out,
+                            double* partial, cudaStream_t s);
+void launch_slab_copy(const Geo& g, const Fields& F, const DetDev& d, int comp0, float* out, cudaStream_t s);
+void launch_interp_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
+                           const double* dL_ddet, int part, const float* slabE0, const float* slabE1,
+                           const float* slabH, cudaStream_t s);
 void launch_source_scale_a(const Geo& g, const float* a, const SrcDev& src, cudaStream_t s);
 void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int step, double* out,
                             double* partial, cudaStream_t s);

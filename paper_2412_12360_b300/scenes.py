@@ -170,11 +170,13 @@ def cavity_32(nsteps: int = 500) -> Scene:
 
 
 def design_box_scene(n=(96, 96, 96), pml=10, design=40, nsteps=2000, seed=1234,
-                     eps_lo=1.0, eps_hi=12.1, wavelength_cells=20.0, name=None, tfsf=False) -> Scene:
+                     eps_lo=1.0, eps_hi=12.1, wavelength_cells=20.0, name=None, tfsf=False,
+                     interp=False) -> Scene:
     """Cubic grid with a CPML on every face, an Ex Gaussian-beam sheet near z-lo (a soft source, or
     with tfsf=True a one-sided TFSF plane sending the beam towards +z), a centred design box with
     eps = eps_lo + (eps_hi - eps_lo) rho, rho ~ U[0,1), and a time-integrated |E|^2 plane near z-hi
-    (objective: the sum of that plane)."""
+    (objective: the sum of that plane; with interp=True the plane uses E interpolated to the cell
+    centres)."""
     nx, ny, nz = n
     S = courant_from_factor(0.99)
     eps = np.ones((nz, ny, nx), dtype=np.float64)
@@ -191,7 +193,8 @@ def design_box_scene(n=(96, 96, 96), pml=10, design=40, nsteps=2000, seed=1234,
     prof = gaussian_sheet((hi_r[1] - lo_r[1], hi_r[0] - lo_r[0]), w0)[None]
     src = default_pulse(Source(EX, (lo_r[0], lo_r[1], zs), (hi_r[0], hi_r[1], zs + 1), prof, 1.0,
                                wavelength_cells, tfsf=3 if tfsf else 0), S)
-    det = Detector(DET_PLANE_E2_SUM, (lo_r[0], lo_r[1], zd), (hi_r[0], hi_r[1], zd + 1))
+    det = Detector(DET_PLANE_E2_SUM_INTERP if interp else DET_PLANE_E2_SUM, (lo_r[0], lo_r[1], zd),
+                   (hi_r[0], hi_r[1], zd + 1))
     sc = Scene(name or "design_%d" % nx, n, S, (pml,) * 6, default_sigma_max(S), 1.0, 0.0, 3, inv(eps),
                [src], [det], dlo, dhi, nsteps)
     sc.extra.update(rho=rho, eps_lo=eps_lo, eps_hi=eps_hi, seed=seed)

@@ -106,3 +106,18 @@ def test_gpu_interpolated_detectors_and_gradient(F):
     print("interpolated detectors rel %.3e, dL/deps rel %.3e" % (rel(det_g, det_o), rel(grad_g, grad_o)))
     assert rel(det_g, det_o) < 1e-4
     assert rel(grad_g, grad_o) < 1e-3
+
+
+@pytest.mark.gpu
+def test_gpu_interpolated_detectors_checkpointed_gradient(F):
+    """The checkpointing gradient takes E^n of the interpolated flux from the recomputed state."""
+    sc = interp_scene(120)
+    g = np.random.default_rng(7).standard_normal(O.detector_total(sc, 120))
+    grad_o, _, _ = O.gradient(sc, 120, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(120)
+        d = np.zeros(sc.design_shape(), dtype=np.float32)
+        s.fdtd_backward_checkpointed(g, d, 1, 5)
+    e = float(np.linalg.norm(d - grad_o) / np.linalg.norm(grad_o))
+    print("interpolated detectors, treeverse gradient rel %.3e" % e)
+    assert e < 1e-3
