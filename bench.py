@@ -662,7 +662,8 @@ def main():
     ap.add_argument("--workload", default="design_96")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override the workload's time steps (profiling runs only; not a bench line)")
-    ap.add_argument("--profile-every", type=int, default=16)
+    ap.add_argument("--profile-every", type=int, default=64,
+                    help="time every Nth step's kernels with CUDA events (each bracket costs a few us)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the dominant kernel from an ncu capture (null if stale)")
     ap.add_argument("--no-e2e", action="store_true")
