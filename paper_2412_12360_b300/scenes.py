@@ -193,8 +193,10 @@ def design_box_scene(n=(96, 96, 96), pml=10, design=40, nsteps=2000, seed=1234,
     prof = gaussian_sheet((hi_r[1] - lo_r[1], hi_r[0] - lo_r[0]), w0)[None]
     src = default_pulse(Source(EX, (lo_r[0], lo_r[1], zs), (hi_r[0], hi_r[1], zs + 1), prof, 1.0,
                                wavelength_cells, tfsf=3 if tfsf else 0), S)
-    det = Detector(DET_PLANE_E2_SUM_INTERP if interp else DET_PLANE_E2_SUM, (lo_r[0], lo_r[1], zd),
-                   (hi_r[0], hi_r[1], zd + 1))
+    if interp:  # the interpolation stencil reaches one cell beyond the box: keep it in the PML-free region
+        det = Detector(DET_PLANE_E2_SUM_INTERP, (lo_r[0], lo_r[1], zd), (hi_r[0] - 1, hi_r[1] - 1, zd + 1))
+    else:
+        det = Detector(DET_PLANE_E2_SUM, (lo_r[0], lo_r[1], zd), (hi_r[0], hi_r[1], zd + 1))
     sc = Scene(name or "design_%d" % nx, n, S, (pml,) * 6, default_sigma_max(S), 1.0, 0.0, 3, inv(eps),
                [src], [det], dlo, dhi, nsteps)
     sc.extra.update(rho=rho, eps_lo=eps_lo, eps_hi=eps_hi, seed=seed)
