@@ -168,7 +168,8 @@ int fdtd_design_adam_step(fdtd_handle* h, const float* dL_drho, float* theta, fl
  * from full stored states (fields and CPML memories) instead of rebuilt by the inverse step; no face
  * record is used. method 0: recursive halving (ceil(log2 n) + 1 stored states, (n/2) log2 n extra
  * forward steps for n = 2^j); method 1: treeverse / binomial checkpointing with `slots` stored states
- * (the schedule minimising the forward steps, by dynamic programming). Each adjoint step re-evaluates
+ * (the schedule minimising the forward steps: by dynamic programming up to 4096 steps, from the
+ * equal binomial closed form beyond). Each adjoint step re-evaluates
  * its own forward step from its input state, as in revolve. dL_ddet and dL_deps as in fdtd_backward;
  * forward_steps (may be NULL) receives the forward steps evaluated. The stored states are allocated
  * for the call and freed before it returns; afterwards the solver's fields hold an intermediate state.

@@ -1290,13 +1290,52 @@ struct CkptTable {
   }
 };
 
+// The same T in closed form (binomial checkpointing; it equals the dynamic programme, which the tests
+// check): with c = k + 1 states and r the least integer with l <= C(c + r - 1, c),
+// T(l, k) = r l - C(c + r - 1, c + 1). Used where the table would be too large (l above kTableMax).
+constexpr int kTableMax = 4096;
+
+int64_t binom_sat(int64_t n, int64_t k) {  // C(n, k), saturating at 2^62
+  if (k < 0 || k > n) return 0;
+  k = std::min(k, n - k);
+  long double v = 1;
+  for (int64_t i = 1; i <= k; ++i) {
+    v = v * (long double)(n - k + i) / (long double)i;
+    if (v > 4.6e18L) return int64_t(1) << 62;
+  }
+  return (int64_t)(v + 0.5L);
+}
+
+int64_t ckpt_closed(int64_t l, int k) {
+  if (l <= 1) return l;
+  const int64_t c = k + 1;
+  int64_t r = 1;
+  while (binom_sat(c + r - 1, c) < l) ++r;
+  return r * l - binom_sat(c + r - 1, c + 1);
+}
+
+// The optimal first split for (l, k): f(m) = m + T(l - m, k - 1) + T(m, k) is a sum of convex
+// functions of m (T is piecewise linear with growing slopes), so its first minimum is the smallest m
+// with f(m + 1) - f(m) >= 0, found by bisection.
+int ckpt_split(int l, int k) {
+  auto f = [&](int m) { return m + ckpt_closed(l - m, k - 1) + ckpt_closed(m, k); };
+  int lo = 1, hi = l - 1;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int mid = lo + (hi - lo) / 2;
+    if (f(mid + 1) - f(mid) >= 0) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 int64_t halving_cost(int l) { return l <= 1 ? l : l / 2 + halving_cost(l - l / 2) + halving_cost(l / 2); }
 
 int halving_depth(int l) { return l <= 1 ? 1 : 1 + std::max(halving_depth(l - l / 2), halving_depth(l / 2)); }
 
 struct Checkpointer {
-  fdtd_handle* h;
-  cudaStream_t st;
+  fdtd_handle* h = nullptr;
+  cudaStream_t st = nullptr;
+  bool dry = false;         // count the schedule's forward steps without running anything
   int method;
   int nslots;
   CkptTable tab;
@@ -1319,18 +1358,28 @@ struct Checkpointer {
     }
   }
   void save(int s) {
+    if (dry) return;
     const int64_t pf = h->psi_floats(), V = 6 * h->g.vol;
     float* b = slot[s];
     copy_state(b, b + V, b + V + pf, state_field(), h->psiE + h->cur * pf, h->psiH + h->cur * pf);
   }
   void restore(int s, int step) {
     if (pos == step) return;
+    if (dry) {
+      pos = step;
+      return;
+    }
     const int64_t pf = h->psi_floats(), V = 6 * h->g.vol;
     const float* b = slot[s];
     copy_state(state_field(), h->psiE + h->cur * pf, h->psiH + h->cur * pf, b, b + V, b + V + pf);
     pos = step;
   }
   void advance_to(int target) {
+    if (dry) {
+      fsteps += std::max(0, target - pos);
+      pos = std::max(pos, target);
+      return;
+    }
     const Geo& g = h->g;
     const int64_t pf = h->psi_floats();
     for (; pos < target; ++pos) {
@@ -1356,6 +1405,7 @@ struct Checkpointer {
     }
   }
   void adjoint(int n) {  // the forward state after step n is current (E^n of it in the slabs)
+    if (dry) return;
     const Fields F = h->F(), A = h->A();
     h->launches += enqueue_det_adjoint(h, F, A, n, 0, st);
     ra.F = F;
@@ -1389,7 +1439,7 @@ struct Checkpointer {
       }
       return;
     }
-    const int m = a + (method == 0 ? l / 2 : tab.m(l, kfree));
+    const int m = a + (method == 0 ? l / 2 : (tab.L > 0 ? tab.m(l, kfree) : ckpt_split(l, kfree)));
     restore(sa, a);
     advance_to(m);
     save(top);
@@ -1403,10 +1453,15 @@ struct Checkpointer {
 int64_t fdtd_checkpoint_cost(int32_t nsteps, int32_t method, int32_t slots) {
   if (nsteps < 0 || (method != 0 && method != 1) || (method == 1 && slots < 1)) return -1;
   if (nsteps == 0) return 0;
-  if (method == 0) return halving_cost(nsteps);
-  CkptTable t;
-  t.build(nsteps, slots - 1);
-  return t.t(nsteps, slots - 1);
+  // run the schedule fdtd_backward_checkpointed runs, counting its forward steps
+  Checkpointer C;
+  C.dry = true;
+  C.method = method;
+  C.nslots = method == 0 ? halving_depth(nsteps) : slots;
+  if (method == 1 && nsteps <= kTableMax) C.tab.build(nsteps, slots - 1);
+  C.pos = 0;
+  C.reverse(0, nsteps, 0, 1);
+  return C.fsteps;
 }
 
 int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_deps, int32_t method, int32_t slots,
@@ -1438,7 +1493,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
   C.st = h->stream;
   C.method = method;
   C.nslots = method == 0 ? halving_depth(nsteps) : slots;
-  if (method == 1) C.tab.build(nsteps, slots - 1);
+  if (method == 1 && nsteps <= kTableMax) C.tab.build(nsteps, slots - 1);
   C.slot_floats = 6 * g.vol + 2 * pf;
   C.slot.assign(C.nslots, nullptr);
   auto free_slots = [&]() {

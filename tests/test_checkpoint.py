@@ -1,6 +1,7 @@
 """Checkpointing gradient, the recomputation alternative to time reversal (arXiv 2412.12360 Sec. 2.2).
 
-Host pins (CPU): recursive halving evaluates n + (n/2) log2 n forward steps for n = 2^j (the paper's
+Host pins (CPU, from a dry run of the schedule the GPU runs): recursive halving evaluates
+n + (n/2) log2 n forward steps for n = 2^j (the paper's
 "n/2 log2 n additional forward function calls" beyond the n taped ones); the treeverse schedule
 matches the binomial-checkpointing closed form T = r l - C(c + r - 1, c + 1), r the least integer with
 l <= C(c + r - 1, c), for c stored states (c = 1 gives l (l + 1) / 2, c >= l gives 2 l - 1).
@@ -33,6 +34,10 @@ def test_treeverse_binomial_closed_form():
     for c in (1, 2, 3, 5, 8):
         for l in list(range(1, 60)) + [97, 200, 333]:
             assert fdtd.checkpoint_cost(l, 1, c) == binomial_cost(l, c), (l, c)
+    # long runs (the paper's 5 nm and 2.5 nm cases have 20980 and 41960 steps) use the closed form
+    # for the splits; the schedule they give still evaluates the closed-form count
+    for l, c in ((4097, 5), (20980, 10), (41960, 30), (9999, 3)):
+        assert fdtd.checkpoint_cost(l, 1, c) == binomial_cost(l, c), (l, c)
     assert fdtd.checkpoint_cost(50, 1, 1) == 50 * 51 // 2
     assert fdtd.checkpoint_cost(40, 1, 40) == 79
     for n in (64, 100, 256):  # with as many states as halving uses, treeverse never does worse
