@@ -58,6 +58,8 @@ def _create(scene, courant=None, pml=None, src=None, det=None, design=None):
     for s in (src if src is not None else sc.sources):
         srcs[ns].component = s[0] if isinstance(s, tuple) else s.component
         lo, hi = (s[1], s[2]) if isinstance(s, tuple) else (s.lo, s.hi)
+        srcs[ns].tfsf = s[3] if isinstance(s, tuple) and len(s) > 3 else 0
+        srcs[ns].eps_background = s[4] if isinstance(s, tuple) and len(s) > 4 else 1.0
         for d in range(3):
             srcs[ns].lo[d] = lo[d]
             srcs[ns].hi[d] = hi[d]
@@ -102,6 +104,41 @@ def test_create_rejects_bad_input_before_any_device_work(L):
     assert rc == F.FDTD_ERR_INVALID_ARG and "axis" in msg
     rc, msg = _create(sc, design=((4, 4, 4), (40, 8, 8)))
     assert rc == F.FDTD_ERR_INVALID_ARG and "design" in msg
+
+
+def test_create_rejects_bad_tfsf_and_interpolated_detectors(L):
+    sc = S.cavity_32(10)
+    design = ((10, 10, 10), (20, 20, 20))
+    ok = (0, (4, 4, 8), (28, 28, 9), 3)  # Ex plane at z = 8, travelling +z
+    rc, msg = _create(sc, src=[(2, (4, 4, 8), (28, 28, 9), 3)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "transverse" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 8), (28, 28, 10), 3)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "thick" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 0), (28, 28, 1), 3)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "scattered" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 31), (28, 28, 32), -3)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "scattered" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 8), (28, 28, 9), 4)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "tfsf" in msg
+    rc, msg = _create(sc, src=[ok[:4] + (0.0,)], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "eps_background" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 15), (28, 28, 16), 3)], design=design)  # the plane in the box
+    assert rc == F.FDTD_ERR_INVALID_ARG and "design" in msg
+    rc, msg = _create(sc, src=[(0, (4, 4, 20), (28, 28, 21), 3)], design=design)  # H half plane 19 in the box
+    assert rc == F.FDTD_ERR_INVALID_ARG and "design" in msg
+    rc, msg = _create(sc, det=[(3, 0, 0, (4, 4, 20), (32, 28, 21))], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "interpolated" in msg
+    rc, msg = _create(sc, det=[(4, 0, 5, (4, 4, 20), (28, 28, 21))], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "axis" in msg
+    rc, msg = _create(sc, det=[(5, 0, 0, (4, 4, 20), (28, 28, 21))], design=design)
+    assert rc == F.FDTD_ERR_INVALID_ARG and "kind" in msg
+
+
+def test_checkpoint_cost_rejects_bad_arguments(L):
+    assert L.fdtd_checkpoint_cost(-1, 0, 0) == -1
+    assert L.fdtd_checkpoint_cost(10, 2, 3) == -1
+    assert L.fdtd_checkpoint_cost(10, 1, 0) == -1
+    assert L.fdtd_checkpoint_cost(0, 1, 3) == 0
 
 
 def test_null_handle_calls_fail_cleanly(L):
