@@ -214,16 +214,32 @@ def oracle_sample(sc, nsteps):
     return time.perf_counter() - t0
 
 
-def cpu_baseline(sc, target_s=15.0):
+def cpu_baseline(sc, target_s=15.0, workload_name=None):
     probe = 2
     t = oracle_sample(sc, probe)
     steps = max(probe, min(400, int(probe * target_s / max(t, 1e-3))))
     t = oracle_sample(sc, steps)
     cores = os.cpu_count()
-    return {"value": sc.ncells * steps / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "full %dx%dx%d grid, %d time steps fwd + %d reversed (FP64 C++ oracle, OpenMP over "
-                      "z-planes in the forward and inverse loops, serial adjoint loops), %.1f s"
-                      % (sc.n[0], sc.n[1], sc.n[2], steps, steps, t)}
+    out = {"value": sc.ncells * steps / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "full %dx%dx%d grid, %d time steps fwd + %d reversed (FP64 C++ oracle, OpenMP over "
+                     "z-planes in the forward and inverse loops, serial adjoint loops), %.1f s"
+                     % (sc.n[0], sc.n[1], sc.n[2], steps, steps, t)}
+    if workload_name:  # the same oracle on one core (a child process with OMP_NUM_THREADS=1)
+        code = ("import sys; sys.path.insert(0, %r); import bench; sc, _ = bench.workload(%r); "
+                "print(bench.oracle_sample(sc, %d))")
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        try:
+            t1 = float(subprocess.run([sys.executable, "-c", code % (ROOT, workload_name, 1)], env=env,
+                                      capture_output=True, text=True, timeout=300).stdout.split()[-1])
+            s1 = max(1, min(steps, int(target_s / 2 / max(t1, 1e-3))))
+            t1 = float(subprocess.run([sys.executable, "-c", code % (ROOT, workload_name, s1)], env=env,
+                                      capture_output=True, text=True, timeout=600).stdout.split()[-1])
+            out["value_1core"] = sc.ncells * s1 / t1 / 1e9
+            out["sample_1core"] = "%d time steps fwd + %d reversed on 1 core, %.1f s" % (s1, s1, t1)
+        except (subprocess.SubprocessError, ValueError, IndexError) as e:
+            out["value_1core"] = None
+            out["sample_1core"] = "not measured: %s" % type(e).__name__
+    return out
 
 
 # ---- our arm ----------------------------------------------------------------------------------------------
@@ -375,7 +391,7 @@ def run_ours(args, world, rank, local):
             "roofline": roof, "e2e": e2e, "gpu_launches": int(launches * world),
             "wall_s": round(wall, 3), "clocks": clk}
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds, None if args.time_steps else args.workload)
     print(json.dumps(line), flush=True)
 
 
