@@ -131,3 +131,25 @@ def test_gpu_tfsf_gradient_and_roundtrip(F):
     assert rel(det_g, det_o) < 1e-4
     assert rel(grad_g, grad_o) < 1e-3
     assert rel(back[m], init[m]) < 1e-4
+
+
+@pytest.mark.gpu
+def test_gpu_tfsf_with_interpolated_flux_and_checkpointing(F):
+    """TFSF plane, interpolated flux detector and the treeverse gradient together, against the oracle."""
+    sc = tfsf_design_scene(160)
+    sc.detectors = [S.Detector(S.DET_PLANE_FLUX_INTERP, (7, 7, 30), (22, 20, 31), axis=2),
+                    S.Detector(S.DET_PLANE_E2_SUM_INTERP, (7, 7, 32), (22, 20, 33))]
+    g = np.random.default_rng(10).standard_normal(O.detector_total(sc, 160))
+    grad_o, _, det_o = O.gradient(sc, 160, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(160, record_faces=True)
+        det_g = s.detectors()
+        grad_tr = s.gradient(g)
+        s.fdtd_forward(160)
+        grad_ck = np.zeros(sc.design_shape(), dtype=np.float32)
+        s.fdtd_backward_checkpointed(g, grad_ck, 1, 6)
+    print("tfsf + interpolated detectors: detectors %.3e, time reversal %.3e, treeverse %.3e" % (
+        rel(det_g, det_o), rel(grad_tr, grad_o), rel(grad_ck, grad_o)))
+    assert rel(det_g, det_o) < 1e-4
+    assert rel(grad_tr, grad_o) < 1e-3
+    assert rel(grad_ck, grad_o) < 1e-3
