@@ -447,9 +447,10 @@ def run_serve(args, world, rank, local):
 def run_batched(args, world, rank, local):
     """A batch of designs of one scene (default: 16 designs of a 240x240x960 waveguide, 12-cell CPML,
     120^3 design box each, rho seeds 500..515, flux objective, 3000 steps) through the
-    torch.autograd.Function: forward of every design, then the backward. Recompute mode (forward
-    again per design before its reverse sweep, one face history held at a time) when the histories of
-    all designs do not fit in device memory. Beside the throughput, a central finite-difference check
+    torch.autograd.Function: forward of every design, then the backward. The designs whose face
+    histories fit in device memory beside all the states keep them from the forward pass; the others
+    recompute (forward again with the face record right before their reverse sweep, after the kept
+    histories have been freed). Beside the throughput, a central finite-difference check
     of dL/drho of design 0 on 4 voxels (indices from seed 99) with delta rho 1e-2 and 1e-3."""
     import torch
     from paper_2412_12360_b300 import autograd, fdtd, ranks
@@ -460,12 +461,11 @@ def run_batched(args, world, rank, local):
     ids = ranks.shard(args.batch, world, rank)
     scs = [scenes.waveguide_batch_member(b, T) for b in ids]
     free, _ = torch.cuda.mem_get_info(dev)
-    base = sum(fdtd.footprint_bytes(sc, T, record_faces=False) for sc in scs)
-    hist = max(fdtd.footprint_bytes(sc, T, record_faces=True) - fdtd.footprint_bytes(sc, T, record_faces=False)
-               for sc in scs)
-    mode = "keep" if autograd.fits_in_memory(scs, T, int(0.85 * free)) else "recompute"
-    if mode == "recompute" and base + hist > 0.85 * free:
-        raise SystemExit("batch does not fit even one design at a time: %d + %d bytes" % (base, hist))
+    # as many designs as fit keep their face histories; the others recompute theirs in backward
+    nkeep = autograd.histories_that_fit(scs, T, int(0.85 * free))
+    if nkeep < 0:
+        raise SystemExit("batch does not fit even one design at a time")
+    mode = "keep" if nkeep == len(scs) else ("recompute" if nkeep == 0 else nkeep)
     eps_lo, eps_hi = scs[0].extra["eps_lo"], scs[0].extra["eps_hi"]
     solvers = [fdtd.Solver(sc) for sc in scs]
     rho = torch.stack([torch.from_numpy(sc.extra["rho"]) for sc in scs]).to(dev).requires_grad_(True)
@@ -522,8 +522,9 @@ def run_batched(args, world, rank, local):
             "seconds": round(t_max, 3), "designs": args.batch, "mode": mode, "dtype": "f32", "data": "synthetic",
             "scaling": "weak", "fd_check": fd,
             "config": {"workload": "%d designs of a 240x240x960 waveguide (along z), 12-cell CPML, 120^3 design box "
-                                   "each, rho~U[0,1) seeds 500.., flux objective, %d steps; recompute mode re-runs "
-                                   "each forward with the face record before its reverse sweep" % (args.batch, T)}}
+                                   "each, rho~U[0,1) seeds 500.., flux objective, %d steps; mode = designs that keep "
+                                   "their face histories ('keep': all, 'recompute': none), the others re-run their "
+                                   "forward with the face record before their reverse sweep" % (args.batch, T)}}
     print(json.dumps(line), flush=True)
 
 

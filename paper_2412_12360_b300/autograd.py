@@ -12,7 +12,10 @@ mode "keep" records the boundary faces during the forward pass and reverses from
 and one reversed sweep per design). mode "recompute" runs a plain forward first and, in backward,
 runs the recorded forward again immediately before the reverse sweep of each design and frees that
 history afterwards, so only one face history at a time is held in device memory (used for batches
-whose histories do not fit).
+whose histories do not fit). An integer mode k is the mix of the two: designs 0..k-1 keep their
+histories from the forward pass, the others recompute; the backward reverses the kept designs first
+and frees each history, so the recomputed ones find the room (for batches where some, but not all,
+histories fit beside the states).
 """
 from __future__ import annotations
 
@@ -35,13 +38,14 @@ class FDTDSolve(torch.autograd.Function):
             raise TypeError("rho must be a CUDA float32 tensor [B, dz, dy, dx]")
         if rho.shape[0] != len(solvers):
             raise ValueError("one solver per design is needed")
-        if mode not in ("keep", "recompute"):
-            raise ValueError("mode is 'keep' or 'recompute'")
+        if isinstance(mode, bool) or not (mode in ("keep", "recompute") or (isinstance(mode, int) and mode >= 0)):
+            raise ValueError("mode is 'keep', 'recompute' or the number of designs that keep their histories")
+        nkeep = len(solvers) if mode == "keep" else (0 if mode == "recompute" else min(int(mode), len(solvers)))
         outs: List[torch.Tensor] = []
         rho_c = rho.detach().contiguous()
         for b, s in enumerate(solvers):
             s.fdtd_set_design_density(rho_c[b], eps_lo, eps_hi)
-            s.fdtd_forward(nsteps, record_faces=(mode == "keep"))
+            s.fdtd_forward(nsteps, record_faces=b < nkeep)
             d = _det_buffer(s, rho.device)
             s.fdtd_read_detectors(d)
             outs.append(d)
@@ -49,6 +53,7 @@ class FDTDSolve(torch.autograd.Function):
         ctx.eps = (float(eps_lo), float(eps_hi))
         ctx.nsteps = int(nsteps)
         ctx.mode = mode
+        ctx.nkeep = nkeep
         ctx.save_for_backward(rho_c)
         return torch.stack(outs)
 
@@ -57,20 +62,35 @@ class FDTDSolve(torch.autograd.Function):
         (rho_c,) = ctx.saved_tensors
         grad = torch.empty_like(rho_c)
         gd = g.detach().to(torch.float64).contiguous()
-        for b, s in enumerate(ctx.solvers):
-            if ctx.mode == "recompute":
+        for b, s in enumerate(ctx.solvers):  # the designs that kept their histories come first
+            if b >= ctx.nkeep:
                 s.fdtd_set_design_density(rho_c[b], *ctx.eps)
                 s.fdtd_forward(ctx.nsteps, record_faces=True)
             s.fdtd_backward_density(gd[b], grad[b])
-            if ctx.mode == "recompute":
-                s.fdtd_release_history()  # only one design's history is held at a time
+            if ctx.mode != "keep":
+                s.fdtd_release_history()  # room for the designs still to recompute
         return grad, None, None, None, None, None
 
 
 def solve(rho: torch.Tensor, solvers: Sequence["fdtd.Solver"], eps_lo: float, eps_hi: float, nsteps: int,
-          mode: str = "keep") -> torch.Tensor:
+          mode="keep") -> torch.Tensor:
     """Differentiable detector outputs [B, n_det] for densities rho [B, dz, dy, dx]."""
     return FDTDSolve.apply(rho, solvers, eps_lo, eps_hi, nsteps, mode)
+
+
+def histories_that_fit(scenes, nsteps: int, budget_bytes: int) -> int:
+    """How many designs (from the first) can keep their face histories beside every design's state;
+    the rest recompute (the mode to pass to `solve`). -1 when not even the states and one history fit."""
+    base = sum(fdtd.footprint_bytes(sc, nsteps, record_faces=False) for sc in scenes)
+    hist = [fdtd.footprint_bytes(sc, nsteps, record_faces=True) - fdtd.footprint_bytes(sc, nsteps, record_faces=False)
+            for sc in scenes]
+    if base + max(hist, default=0) > budget_bytes:
+        return -1
+    k, used = 0, base
+    while k < len(scenes) and used + hist[k] <= budget_bytes:
+        used += hist[k]
+        k += 1
+    return k
 
 
 def fits_in_memory(scenes, nsteps: int, budget_bytes: int) -> bool:
