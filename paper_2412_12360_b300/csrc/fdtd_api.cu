@@ -311,6 +311,7 @@ struct fdtd_handle {
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
   int tz_rev = 8;                 // z-planes per block of the reverse kernels
+  int rev_nstage = 4;             // stages of the reverse kernels' plane rings
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
 
   std::vector<fdtd_source> src_host;
@@ -746,6 +747,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   ra.B = A;
   ra.a = h->a;
   ra.tz = h->tz_rev;
+  ra.nstage = h->rev_nstage;
   for (int d = 0; d < 3; ++d) {
     ra.dlo[d] = h->design_lo[d];
     ra.dhi[d] = h->design_hi[d];
@@ -966,8 +968,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     int per_sm3 = 0, per_sm4 = 0, nsm = 0;
     if ((rc = prepare_fwd_fused(3, &per_sm3)) != FDTD_OK) return cleanup(rc);
     if ((rc = prepare_fwd_fused(4, &per_sm4)) != FDTD_OK) return cleanup(rc);
-    int per_sm_rev = 0;
-    if ((rc = prepare_rev(&per_sm_rev)) != FDTD_OK) return cleanup(rc);
+    int per_sm_rev3 = 0, per_sm_rev4 = 0;
+    if ((rc = prepare_rev(3, &per_sm_rev3)) != FDTD_OK) return cleanup(rc);
+    if ((rc = prepare_rev(4, &per_sm_rev4)) != FDTD_OK) return cleanup(rc);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
@@ -982,7 +985,13 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     const bool ring4 = per_sm4 >= per_sm3;
     h->fwd_nstage = ring4 ? 4 : 3;
     const int64_t slots_f = ring4 ? slots4 : slots3;
-    const int64_t slots_r = (int64_t)nsm * std::max(1, per_sm_rev);
+    // reverse: a 4-stage ring (three blocks per SM) when the sweep fills at least four waves of
+    // them, else 3 stages (four per SM: on one B300 the 96^3 solve ran 8 % faster, 600^3 3 % slower)
+    const int64_t slots_r4 = (int64_t)nsm * std::max(1, per_sm_rev4), slots_r3 = (int64_t)nsm * std::max(1, per_sm_rev3);
+    const int tz_r4 = choose_tz(nxy_rev, n[2], slots_r4);
+    const bool rev_ring4 = nxy_rev * ((n[2] + tz_r4 - 1) / tz_r4) >= 4 * slots_r4;
+    h->rev_nstage = rev_ring4 ? 4 : 3;
+    const int64_t slots_r = rev_ring4 ? slots_r4 : slots_r3;
     h->tz = choose_tz(nxy, n[2], slots_f);
     h->tz_rev = choose_tz(nxy_rev, n[2], slots_r);
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
@@ -1527,6 +1536,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
   ra.B = h->A();
   ra.a = h->a;
   ra.tz = h->tz_rev;
+  ra.nstage = h->rev_nstage;
   for (int d = 0; d < 3; ++d) {
     ra.dlo[d] = h->design_lo[d];
     ra.dhi[d] = h->design_hi[d];

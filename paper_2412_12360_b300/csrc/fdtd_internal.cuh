@@ -159,6 +159,7 @@ struct RevArgs {
   int nsrc;
   SrcDev src[kMaxSrc];
   int* status;             // device status word: bit 0 set when a bounded wait gave up
+  int nstage;              // stages of the plane ring (3 or 4)
   int inverse;             // 1: rebuild the previous fields in place (time reversal); 0: adjoint only
                            // (the forward state comes from elsewhere, e.g. recomputation)
 };

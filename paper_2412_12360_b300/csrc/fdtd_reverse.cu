@@ -58,7 +58,7 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
 
 // ---------------------------------------------------------------------------------------------
 // Plane staging. Both kernels march their z-chunk downwards and read every plane through a ring of
-// NSTAGE shared-memory stages filled by TMA bulk tensor copies (one elected thread issues them; the
+// NS shared-memory stages filled by TMA bulk tensor copies (one elected thread issues them; the
 // block waits on one mbarrier per stage). Two box shapes are used: "own" boxes are the tile itself
 // (TX x TY at (i0, j0)); "wide" boxes add one cell on one side in x and y (BW x BH), either on the
 // high side (origin (i0, j0): the +x, +y neighbours) or on the low side (origin (i0-4, j0-1), 4 cells
@@ -66,7 +66,8 @@ __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int 
 // grid the copies read 0, which is what the PEC walls and the zero adjoint give.
 // ---------------------------------------------------------------------------------------------
 constexpr int BW = TX + 4, BH = TY + 1;
-constexpr int NSTAGE = 4;
+// NS = stages of the ring: 4 (three blocks per SM) on grids that fill several waves of blocks, 3
+// (four blocks per SM, so that the short z-chunks of small grids run side by side) otherwise
 constexpr int round128(int b) { return (b + 127) / 128 * 128; }
 constexpr uint32_t OWN3 = 3 * TX * TY * 4, WIDE3 = 3 * BW * BH * 4, WIDE1 = BW * BH * 4;
 
@@ -79,29 +80,31 @@ constexpr int RH_E = 0, RH_H = RH_E + round128(WIDE3), RH_HB = RH_H + round128(O
               RH_EB = RH_HB + round128(WIDE3), RH_STAGE = RH_EB + round128(OWN3);
 constexpr uint32_t RH_TX = WIDE3 + OWN3 + WIDE3 + OWN3;
 
-constexpr int RE_SMEM = NSTAGE * RE_STAGE + NSTAGE * 8 + 128;
-constexpr int RH_SMEM = NSTAGE * RH_STAGE + NSTAGE * 8 + 128;
+constexpr int re_smem(int ns) { return ns * RE_STAGE + ns * 8 + 128; }
+constexpr int rh_smem(int ns) { return ns * RH_STAGE + ns * 8 + 128; }
 
 typedef const float (*Own3)[TY][TX];
 typedef const float (*Wide3)[BH][BW];
 typedef const float (*Wide1)[BW];
 
 // Stage ring of a downward march over planes ktop, ktop-1, ..., kbot: plane p is use number
-// (ktop - p) / NSTAGE of stage (ktop - p) % NSTAGE.
+// (ktop - p) / NS of stage (ktop - p) % NS.
+template <int NS>
 struct DownRing {
   unsigned char* base;
   uint64_t* bar;
   int stage_bytes, ktop;
-  __device__ unsigned char* at(int p) const { return base + ((ktop - p) % NSTAGE) * stage_bytes; }
-  __device__ uint64_t* bar_of(int p) const { return &bar[(ktop - p) % NSTAGE]; }
-  __device__ bool wait(int p) const { return mbar_wait(bar_of(p), ((ktop - p) / NSTAGE) & 1); }
+  __device__ unsigned char* at(int p) const { return base + ((ktop - p) % NS) * stage_bytes; }
+  __device__ uint64_t* bar_of(int p) const { return &bar[(ktop - p) % NS]; }
+  __device__ bool wait(int p) const { return mbar_wait(bar_of(p), ((ktop - p) / NS) & 1); }
 };
 
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
   return p + ((128 - (smem_addr(p) & 127)) & 127);
 }
 
-__device__ __forceinline__ void issue_rev_E(const RevMaps& M, const DownRing& R, int i0, int j0, int p) {
+template <class Ring>
+__device__ __forceinline__ void issue_rev_E(const RevMaps& M, const Ring& R, int i0, int j0, int p) {
   unsigned char* st = R.at(p);
   uint64_t* b = R.bar_of(p);
   mbar_arrive_expect(b, RE_TX);
@@ -112,7 +115,8 @@ __device__ __forceinline__ void issue_rev_E(const RevMaps& M, const DownRing& R,
   tma_load_box(st + RE_A, &M.a_high, i0, j0, p, 0, b);
 }
 
-__device__ __forceinline__ void issue_rev_H(const RevMaps& M, const DownRing& R, int i0, int j0, int p) {
+template <class Ring>
+__device__ __forceinline__ void issue_rev_H(const RevMaps& M, const Ring& R, int i0, int j0, int p) {
   unsigned char* st = R.at(p);
   uint64_t* b = R.bar_of(p);
   mbar_arrive_expect(b, RH_TX);
@@ -125,7 +129,8 @@ __device__ __forceinline__ void issue_rev_H(const RevMaps& M, const DownRing& R,
 // ---------------------------------------------------------------------------------------------
 // rev_E
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_constant__ RevMaps M) {
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E(const RevArgs A, const __grid_constant__ RevMaps M) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align128(smem_raw);
 
@@ -143,7 +148,7 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
   const int q0 = j * g.nxp + i;
   const float S = g.S;
   const int ktop = k1 - 1, kbot = max(k0 - 1, 0);  // planes staged: H(k-1) is read below the chunk
-  const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RE_STAGE), RE_STAGE, ktop};
+  const DownRing<NSTAGE> R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RE_STAGE), RE_STAGE, ktop};
   bool waited = true;
 
   pdl_wait();  // the fields come after the previous kernel of the stream
@@ -344,7 +349,8 @@ __global__ void __launch_bounds__(NT, 3) k_rev_E(const RevArgs A, const __grid_c
 // ---------------------------------------------------------------------------------------------
 // rev_H
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_constant__ RevMaps M) {
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs A, const __grid_constant__ RevMaps M) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align128(smem_raw);
 
@@ -362,7 +368,7 @@ __global__ void __launch_bounds__(NT, 3) k_rev_H(const RevArgs A, const __grid_c
   const int q0 = j * g.nxp + i;
   const float S = g.S;
   const int ktop = k1 - 1, kbot = max(k0 - 1, 0);  // planes staged: Hbar(k-1) is read below the chunk
-  const DownRing R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RH_STAGE), RH_STAGE, ktop};
+  const DownRing<NSTAGE> R{sm, reinterpret_cast<uint64_t*>(sm + NSTAGE * RH_STAGE), RH_STAGE, ktop};
   bool waited = true;
 
   pdl_wait();  // the fields come after the previous kernel of the stream
@@ -527,12 +533,14 @@ int rev_tile_y() { return TY; }
 MapBox rev_box_own() { return {TX, TY}; }
 MapBox rev_box_wide() { return {BW, BH}; }
 
-int prepare_rev(int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_rev_E, cudaFuncAttributeMaxDynamicSharedMemorySize, RE_SMEM);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rev_H, cudaFuncAttributeMaxDynamicSharedMemorySize, RH_SMEM);
+int prepare_rev(int nstage, int* blocks_per_sm) {
+  auto ke = nstage == 3 ? k_rev_E<3> : k_rev_E<4>;
+  auto kh = nstage == 3 ? k_rev_H<3> : k_rev_H<4>;
+  cudaError_t e = cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, re_smem(nstage));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, rh_smem(nstage));
   int be = 0, bh = 0;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, k_rev_E, NT, RE_SMEM);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, k_rev_H, NT, RH_SMEM);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, ke, NT, re_smem(nstage));
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, kh, NT, rh_smem(nstage));
   *blocks_per_sm = std::min(be, bh);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -540,13 +548,15 @@ int prepare_rev(int* blocks_per_sm) {
 void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  launch_pdl(k_rev_E, grid, dim3(NT), RE_SMEM, s, a, m);
+  if (a.nstage == 3) launch_pdl(k_rev_E<3>, grid, dim3(NT), re_smem(3), s, a, m);
+  else launch_pdl(k_rev_E<4>, grid, dim3(NT), re_smem(4), s, a, m);
 }
 
 void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
   dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  launch_pdl(k_rev_H, grid, dim3(NT), RH_SMEM, s, a, m);
+  if (a.nstage == 3) launch_pdl(k_rev_H<3>, grid, dim3(NT), rh_smem(3), s, a, m);
+  else launch_pdl(k_rev_H<4>, grid, dim3(NT), rh_smem(4), s, a, m);
 }
 
 }  // namespace fdtd

@@ -44,7 +44,7 @@ struct RevMaps {
 
 MapBox rev_box_own();
 MapBox rev_box_wide();
-int prepare_rev(int* blocks_per_sm);
+int prepare_rev(int nstage, int* blocks_per_sm);
 void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s);
 void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s);
 
