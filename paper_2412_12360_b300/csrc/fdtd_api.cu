@@ -307,6 +307,8 @@ struct fdtd_handle {
   double spacing = 0, courant = 0;
   cudaStream_t stream = nullptr;  // caller's stream
   cudaStream_t cap = nullptr;     // private stream used only to capture the time loops
+  cudaStream_t side = nullptr;    // captured beside `cap`: the face copies, off the critical path
+  cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};  // fork / join points of `side`
   int32_t design_lo[3] = {0, 0, 0}, design_hi[3] = {0, 0, 0};
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
@@ -686,8 +688,13 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.det_out = h->det_out;
   fa.partial = h->partial;
   fa.status = h->status;
+  // The face record of step n runs on the side stream, beside step n+1 (which only reads that
+  // buffer); step n+2 overwrites it, so its fused kernel waits for the copy, and so does a TFSF H
+  // correction of step n+1, which writes that buffer's H.
   for (int n = 0; n < nsteps; ++n) {
     const int c = h->cur, x = 1 - c;
+    if (faces && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
+    if (faces && n >= 1 && !h->hsrcs.empty()) cudaStreamWaitEvent(st, h->ev_join[(n - 1) % 2], 0);
     fa.cur = h->F(c);
     fa.nxt = h->F(x);
     fa.psiE_cur = h->psi_set(h->psiE + c * pf);
@@ -706,8 +713,13 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     launches += 1;
     const Fields Fn = h->F(x);
     if (faces) {  // H^{n+1/2} on the boundary faces
-      ProfScope ps(h, evs, st, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, st);
+      cudaEventRecord(h->ev_fork, st);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      {
+        ProfScope ps(h, evs, h->side, FDTD_KERNEL_FACE_COPY, n);
+        launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, h->side);
+      }
+      cudaEventRecord(h->ev_join[n % 2], h->side);
       launches += 1;
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
@@ -719,6 +731,10 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
       ++launches;
     }
     h->cur = x;
+  }
+  if (faces) {  // join the side stream
+    if (nsteps >= 2) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 2) % 2], 0);
+    if (nsteps >= 1) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 1) % 2], 0);
   }
   for (const auto& d : h->dets)
     if ((d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) && nsteps > 0) {
@@ -760,6 +776,22 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   const RevMaps& rm = h->rmaps[h->cur];
   int64_t launches = 0;
   int pb = 0;
+  // The face replay of step n (the recorded H^{n+1/2} written back outside R) runs on the side
+  // stream beside rev_H(n+1), which neither reads nor writes H outside R; rev_E(n) waits for it.
+  const bool faces = h->faces.per_step > 0;
+  auto replay = [&](int n) {
+    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    {
+      ProfScope ps(h, evs, h->side, FDTD_KERNEL_FACE_COPY, n);
+      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, h->side);
+    }
+    cudaEventRecord(h->ev_join[n % 2], h->side);
+    launches += 1;
+  };
+  if (faces && nsteps > 0) {
+    cudaEventRecord(h->ev_fork, st);
+    replay(nsteps - 1);
+  }
   for (int n = nsteps - 1; n >= 0; --n) {
     if (!h->dets.empty()) {
       ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
@@ -767,16 +799,16 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
     ra.step = n;
-    if (h->faces.per_step > 0) {  // H^{n+1/2} on the boundary faces, from the record
-      ProfScope ps(h, evs, st, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, st);
-      launches += 1;
-    }
+    if (faces) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
       ra.pin = PEb[pb];
       ra.pout = PEb[1 - pb];
       launch_rev_E(ra, rm, st);
+    }
+    if (faces && n > 0) {  // rev_E(n) has read the faces of step n: replay those of step n-1
+      cudaEventRecord(h->ev_fork, st);
+      replay(n - 1);
     }
     launches += enqueue_det_adjoint(h, F, A, n, 1, st);  // interpolated flux: H terms, E^n rebuilt
     {
@@ -958,10 +990,13 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   };
   const Geo& g = h->g;
   int rc;
-  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
     cudaError_t e = cudaGetLastError();
-    h->cap = nullptr;
-    return cleanup(fail(FDTD_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+    return cleanup(fail(FDTD_ERR_CUDA, "stream or event creation: %s", cudaGetErrorString(e)));
   }
   {
     // z-chunks of the marching kernels, each for its own number of resident blocks per SM
@@ -1138,6 +1173,10 @@ int fdtd_destroy(fdtd_handle* h) {
     if (p) cudaFreeAsync(p, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->side) cudaStreamDestroy(h->side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  for (cudaEvent_t e : h->ev_join)
+    if (e) cudaEventDestroy(e);
   cudaGetLastError();
   delete h;
   return FDTD_OK;
