@@ -1544,19 +1544,16 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
   if (method == 1 && nsteps <= kTableMax) C.tab.build(nsteps, slots - 1);
   C.slot_floats = 6 * g.vol + 2 * pf;
   C.slot.assign(C.nslots, nullptr);
-  auto free_slots = [&]() {
-    for (float*& b : C.slot) {
-      dev_free(h, b, C.slot_floats * 4);
-      b = nullptr;
+  struct SlotGuard {  // frees the stored states on every way out (stream-ordered, after the work)
+    Checkpointer& c;
+    ~SlotGuard() {
+      for (float*& b : c.slot) {
+        dev_free(c.h, b, c.slot_floats * 4);
+        b = nullptr;
+      }
     }
-  };
-  for (int s = 0; s < C.nslots; ++s) {
-    const int rc = dev_alloc(h, (void**)&C.slot[s], C.slot_floats * 4);
-    if (rc != FDTD_OK) {
-      free_slots();
-      return rc;
-    }
-  }
+  } guard{C};
+  for (int s = 0; s < C.nslots; ++s) TRY(dev_alloc(h, (void**)&C.slot[s], C.slot_floats * 4));
   FwdArgs& fa = C.fa;
   fa.g = g;
   fa.T = h->tab();
@@ -1604,8 +1601,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
     CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));  // the slots are freed (stream-ordered) below
-  free_slots();
+  CK(cudaStreamSynchronize(h->stream));
   h->recorded = false;
   if (forward_steps) *forward_steps = C.fsteps;
   return FDTD_OK;
