@@ -323,6 +323,7 @@ struct fdtd_handle {
   std::vector<Tfsf> tfsf;
   std::vector<DetDev> dets;
   std::vector<char> det_inline;   // per detector: sampled inside the fused forward kernel
+  std::vector<char> det_fold;     // per detector: its adjoint added by rev_H of the following step
   std::vector<float*> det_slab;   // per detector: 3 slabs (E^{n+1}, H^{n+1/2}, E^n) for kind 4, else null
   int64_t det_total_per_step = 0, det_total_fixed = 0;
 
@@ -631,12 +632,14 @@ int encode_rev_maps(fdtd_handle* h) {
 // state after step n; the interpolated flux first copies E^{n+1} and H^{n+1/2} into its slabs),
 // part 1 (after rev_E: the interpolated flux's H terms, with E^n copied from the rebuilt fields, or
 // already in its slab when `e0_ready`) and part 2 (after rev_H: the interpolated flux's E^n terms).
+// With `folded`, part 0 skips the detectors whose adjoint rev_H of step n+1 has already added.
 int64_t enqueue_det_adjoint(fdtd_handle* h, const Fields& F, const Fields& A, int n, int part, cudaStream_t st,
-                            bool e0_ready = false) {
+                            bool e0_ready = false, bool folded = false) {
   const Geo& g = h->g;
   int64_t launches = 0;
   for (size_t q = 0; q < h->dets.size(); ++q) {
     const DetDev& d = h->dets[q];
+    if (folded && h->det_fold[q]) continue;
     float* sl = h->det_slab[q];
     const int64_t sf = sl ? interp_slab_floats(d) : 0;
     float *sE1 = sl, *sH = sl + sf, *sE0 = sl + 2 * sf;
@@ -773,6 +776,17 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
   for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
   ra.status = h->status;
+  ra.gy = h->dLddet;
+  ra.ndet = 0;
+  for (size_t q = 0; q < h->dets.size(); ++q)
+    if (h->det_fold[q]) {
+      DetDev d = h->dets[q];
+      if (d.kind == FDTD_DET_POINT_SERIES)  // the point is the one-cell box at lo
+        for (int k = 0; k < 3; ++k) d.hi[k] = d.lo[k] + 1;
+      ra.det[ra.ndet++] = d;
+    }
+  bool unfolded = false;  // a detector whose adjoint needs a launch of its own at every step
+  for (size_t q = 0; q < h->dets.size(); ++q) unfolded |= !h->det_fold[q];
   const RevMaps& rm = h->rmaps[h->cur];
   int64_t launches = 0;
   int pb = 0;
@@ -793,9 +807,11 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     replay(nsteps - 1);
   }
   for (int n = nsteps - 1; n >= 0; --n) {
-    if (!h->dets.empty()) {
+    // the folded detectors' adjoints of step n come from rev_H(n+1); the last step has none before it
+    const bool folded = n < nsteps - 1;
+    if (unfolded || (!folded && ra.ndet > 0)) {
       ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
-      launches += enqueue_det_adjoint(h, F, A, n, 0, st);
+      launches += enqueue_det_adjoint(h, F, A, n, 0, st, false, folded);
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
     ra.step = n;
@@ -815,6 +831,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
       ra.pin = PHb[pb];
       ra.pout = PHb[1 - pb];
+      ra.det_step = n - 1;  // -1 at n = 0: nothing left to fold
       launch_rev_H(ra, rm, st);
     }
     launches += 2;
@@ -1152,8 +1169,14 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     if (d.kind == FDTD_DET_PLANE_FLUX_INTERP &&
         (rc = dev_alloc(h, (void**)&slab, 3 * interp_slab_floats(dd) * 4)) != FDTD_OK)
       return cleanup(rc);
+    // the first kMaxDet detectors whose adjoint reads only E are folded into rev_H's E-bar write
+    int nfold = 0;
+    for (char c : h->det_fold) nfold += c;
+    const bool fold = (d.kind == FDTD_DET_PLANE_E2_SUM || (d.kind == FDTD_DET_POINT_SERIES && d.component < 3)) &&
+                      nfold < kMaxDet;
     h->dets.push_back(dd);
     h->det_inline.push_back(inl ? 1 : 0);
+    h->det_fold.push_back(fold ? 1 : 0);
     h->det_slab.push_back(slab);
   }
   *out = h;
@@ -1580,6 +1603,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
   ra.dLda = h->dLda;
   ra.inverse = 0;
   ra.nsrc = 0;  // sources only matter to the inverse step
+  ra.ndet = 0;  // every detector adjoint by its own launch: rev_H of the next step runs on another state
   ra.status = h->status;
   for (int k = 0; k < 2; ++k) {
     C.PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);

@@ -162,6 +162,13 @@ struct RevArgs {
   int nstage;              // stages of the plane ring (3 or 4)
   int inverse;             // 1: rebuild the previous fields in place (time reversal); 0: adjoint only
                            // (the forward state comes from elsewhere, e.g. recomputation)
+  // Detector adjoints folded into rev_H's E-bar write: the terms of detector step det_step (-1: none)
+  // of the ndet detectors in det (points on an E component, boxes of time-integrated |E|^2), which
+  // use only E after that step, the E that rev_H of the following step holds. gy: dL/d(outputs).
+  int ndet = 0;
+  int det_step = -1;
+  const double* gy = nullptr;
+  DetDev det[kMaxDet];
 };
 
 int fused_tile_x();

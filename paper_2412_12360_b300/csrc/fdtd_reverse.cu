@@ -5,7 +5,9 @@
 //             for the adjoint: Hbar += sum of the E-update coefficients P of the neighbouring E points
 //             (with the CPML memories psi-bar of E);
 //   rev_H(n): the inverse H update H^{n-1/2} = H^{n+1/2} + S curl_f(E^n) on R, and the transpose of the
-//             H update: Ebar += sum of the H-update coefficients Q of the neighbouring H points.
+//             H update: Ebar += sum of the H-update coefficients Q of the neighbouring H points,
+//             plus the adjoints of the detectors of step n-1 that read only E (E^n, held here), which
+//             would otherwise take a launch of their own at the start of reverse step n-1.
 //
 // Each kernel reads only fields it does not write (rev_E reads H and Ebar and writes E and Hbar;
 // rev_H reads E and Hbar and writes H and Ebar), so in-place updates are race-free. Blocks own a
@@ -394,6 +396,11 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs
   const PsiSet& Pi = A.pin;
   const PsiSet& Po = A.pout;
   const bool lay_xy = (sX0 & sXm & sY0 & sYm) >= 0;  // this column or its -x/-y neighbour is in a layer
+  unsigned det_xy = 0;  // folded detectors whose box holds this column
+  if (A.det_step >= 0)
+    for (int s = 0; s < A.ndet; ++s)
+      if (own && i >= A.det[s].lo[0] && i < A.det[s].hi[0] && j >= A.det[s].lo[1] && j < A.det[s].hi[1])
+        det_xy |= 1u << s;
 
   // E_x, E_y of the own column at k1 (the plane above the chunk)
   float ex_up = 0.f, ey_up = 0.f;
@@ -451,76 +458,98 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs
     // neighbours, then the CPML corrections axis by axis
     const float wy_m = k > 0 ? -S * bym : 0.f, wx_m = k > 0 ? -S * bxm : 0.f;  // w at (i, j, k-1)
     const int sZm = k > 0 ? T.sidx[2][k - 1] : -1;
+    float nbx, nby, nbz;  // the new E-bar
     if (!lay_xy && sZ < 0 && sZm < 0) {  // no layer along any axis at this point or its neighbours
-      if (j > 0 && k > 0) A.B.f[0][q] = ebx + ((wy_m - wy) + (-wz_y + wz));
-      if (i > 0 && k > 0) A.B.f[1][q] = eby + ((wz_x - wz) + (-wx_m + wx));
-      if (i > 0 && j > 0) A.B.f[2][q] = ebz + ((wx_y - wx) + (-wy_x + wy));
-      continue;
+      nbx = ebx + ((wy_m - wy) + (-wz_y + wz));
+      nby = eby + ((wz_x - wz) + (-wx_m + wx));
+      nbz = ebz + ((wx_y - wx) + (-wy_x + wy));
+    } else {
+      float cex = 0.f, cey = 0.f, cez = 0.f;
+      if (sX0 >= 0 || sXm >= 0) {  // along x: Q1 of H_z (2,0) and Q2 of H_y (1,0), own and -x
+        float e1z = 0.f, e2y = 0.f, n1z = 0.f, n2y = 0.f;
+        if (sX0 >= 0) {
+          const int z = zx_of(g, j, k, sX0);
+          const float cX = T.c[0][1][i], bX = T.b[0][1][i];
+          const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
+          e1z = acorr(wz, ikX0, cX, p20);
+          e2y = acorr(-wy, ikX0, cX, p10);
+          Po.p[2][0][z] = bX * (p20 + wz);
+          Po.p[1][0][z] = bX * (p10 - wy);
+        }
+        if (sXm >= 0) {
+          const int z = zx_of(g, j, k, sXm);
+          const float cX = T.c[0][1][i - 1];
+          n1z = acorr(wz_x, ikXm, cX, Pi.p[2][0][z]);
+          n2y = acorr(-wy_x, ikXm, cX, Pi.p[1][0][z]);
+        }
+        cey += n1z - e1z;
+        cez += n2y - e2y;
+      }
+      if (sY0 >= 0 || sYm >= 0) {  // along y: Q1 of H_x (0,1) and Q2 of H_z (2,1), own and -y
+        float e1x = 0.f, e2z = 0.f, n1x = 0.f, n2z = 0.f;
+        if (sY0 >= 0) {
+          const int z = zy_of(g, i, k, sY0);
+          const float cY = T.c[1][1][j], bY = T.b[1][1][j];
+          const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
+          e1x = acorr(wx, ikY0, cY, p01);
+          e2z = acorr(-wz, ikY0, cY, p21);
+          Po.p[0][1][z] = bY * (p01 + wx);
+          Po.p[2][1][z] = bY * (p21 - wz);
+        }
+        if (sYm >= 0) {
+          const int z = zy_of(g, i, k, sYm);
+          const float cY = T.c[1][1][j - 1];
+          n1x = acorr(wx_y, ikYm, cY, Pi.p[0][1][z]);
+          n2z = acorr(-wz_y, ikYm, cY, Pi.p[2][1][z]);
+        }
+        cex += n2z - e2z;
+        cez += n1x - e1x;
+      }
+      if (sZ >= 0 || sZm >= 0) {  // along z: Q1 of H_y (1,2) and Q2 of H_x (0,2), own and -z
+        float e1y = 0.f, e2x = 0.f, m1y = 0.f, m2x = 0.f;
+        if (sZ >= 0) {
+          const int z = zz_of(g, i, j, sZ);
+          const float cZ = T.c[2][1][k], bZ = T.b[2][1][k];
+          const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
+          e1y = acorr(wy, ikZ, cZ, p12);
+          e2x = acorr(-wx, ikZ, cZ, p02);
+          Po.p[1][2][z] = bZ * (p12 + wy);
+          Po.p[0][2][z] = bZ * (p02 - wx);
+        }
+        if (sZm >= 0) {
+          const int z = zz_of(g, i, j, sZm);
+          const float ikZm = T.ik[2][1][k - 1], cZ = T.c[2][1][k - 1];
+          m1y = acorr(wy_m, ikZm, cZ, Pi.p[1][2][z]);
+          m2x = acorr(-wx_m, ikZm, cZ, Pi.p[0][2][z]);
+        }
+        cex += m1y - e1y;
+        cey += m2x - e2x;
+      }
+      nbx = ebx + (((wy_m - wy) + (-wz_y + wz)) + cex);
+      nby = eby + (((wz_x - wz) + (-wx_m + wx)) + cey);
+      nbz = ebz + (((wx_y - wx) + (-wy_x + wy)) + cez);
     }
-    float cex = 0.f, cey = 0.f, cez = 0.f;
-    if (sX0 >= 0 || sXm >= 0) {  // along x: Q1 of H_z (2,0) and Q2 of H_y (1,0), own and -x
-      float e1z = 0.f, e2y = 0.f, n1z = 0.f, n2y = 0.f;
-      if (sX0 >= 0) {
-        const int z = zx_of(g, j, k, sX0);
-        const float cX = T.c[0][1][i], bX = T.b[0][1][i];
-        const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
-        e1z = acorr(wz, ikX0, cX, p20);
-        e2y = acorr(-wy, ikX0, cX, p10);
-        Po.p[2][0][z] = bX * (p20 + wz);
-        Po.p[1][0][z] = bX * (p10 - wy);
+    if (det_xy) {  // folded detector adjoints, one after the other in detector order
+      for (int s = 0; s < A.ndet; ++s) {
+        const DetDev& d = A.det[s];
+        if (!((det_xy >> s) & 1u) || k < d.lo[2] || k >= d.hi[2]) continue;
+        if (d.kind == FDTD_DET_POINT_SERIES) {
+          const float v = (float)A.gy[d.off + A.det_step];
+          if (d.comp == 0) nbx += v;
+          else if (d.comp == 1) nby += v;
+          else nbz += v;
+        } else {  // |E|^2 summed over the steps: dL/dE = 2 g E
+          const double w = 2.0 * A.gy[d.off + box_offset(d.lo, d.hi, i, j, k)];
+          nbx += (float)(w * (double)ex);
+          nby += (float)(w * (double)ey);
+          nbz += (float)(w * (double)ez);
+        }
       }
-      if (sXm >= 0) {
-        const int z = zx_of(g, j, k, sXm);
-        const float cX = T.c[0][1][i - 1];
-        n1z = acorr(wz_x, ikXm, cX, Pi.p[2][0][z]);
-        n2y = acorr(-wy_x, ikXm, cX, Pi.p[1][0][z]);
-      }
-      cey += n1z - e1z;
-      cez += n2y - e2y;
     }
-    if (sY0 >= 0 || sYm >= 0) {  // along y: Q1 of H_x (0,1) and Q2 of H_z (2,1), own and -y
-      float e1x = 0.f, e2z = 0.f, n1x = 0.f, n2z = 0.f;
-      if (sY0 >= 0) {
-        const int z = zy_of(g, i, k, sY0);
-        const float cY = T.c[1][1][j], bY = T.b[1][1][j];
-        const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
-        e1x = acorr(wx, ikY0, cY, p01);
-        e2z = acorr(-wz, ikY0, cY, p21);
-        Po.p[0][1][z] = bY * (p01 + wx);
-        Po.p[2][1][z] = bY * (p21 - wz);
-      }
-      if (sYm >= 0) {
-        const int z = zy_of(g, i, k, sYm);
-        const float cY = T.c[1][1][j - 1];
-        n1x = acorr(wx_y, ikYm, cY, Pi.p[0][1][z]);
-        n2z = acorr(-wz_y, ikYm, cY, Pi.p[2][1][z]);
-      }
-      cex += n2z - e2z;
-      cez += n1x - e1x;
-    }
-    if (sZ >= 0 || sZm >= 0) {  // along z: Q1 of H_y (1,2) and Q2 of H_x (0,2), own and -z
-      float e1y = 0.f, e2x = 0.f, m1y = 0.f, m2x = 0.f;
-      if (sZ >= 0) {
-        const int z = zz_of(g, i, j, sZ);
-        const float cZ = T.c[2][1][k], bZ = T.b[2][1][k];
-        const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
-        e1y = acorr(wy, ikZ, cZ, p12);
-        e2x = acorr(-wx, ikZ, cZ, p02);
-        Po.p[1][2][z] = bZ * (p12 + wy);
-        Po.p[0][2][z] = bZ * (p02 - wx);
-      }
-      if (sZm >= 0) {
-        const int z = zz_of(g, i, j, sZm);
-        const float ikZm = T.ik[2][1][k - 1], cZ = T.c[2][1][k - 1];
-        m1y = acorr(wy_m, ikZm, cZ, Pi.p[1][2][z]);
-        m2x = acorr(-wx_m, ikZm, cZ, Pi.p[0][2][z]);
-      }
-      cex += m1y - e1y;
-      cey += m2x - e2x;
-    }
-    if (j > 0 && k > 0) A.B.f[0][q] = ebx + (((wy_m - wy) + (-wz_y + wz)) + cex);
-    if (i > 0 && k > 0) A.B.f[1][q] = eby + (((wz_x - wz) + (-wx_m + wx)) + cey);
-    if (i > 0 && j > 0) A.B.f[2][q] = ebz + (((wx_y - wx) + (-wy_x + wy)) + cez);
+    // E components on the PEC walls keep E-bar = 0
+    if (j > 0 && k > 0) A.B.f[0][q] = nbx;
+    if (i > 0 && k > 0) A.B.f[1][q] = nby;
+    if (i > 0 && j > 0) A.B.f[2][q] = nbz;
   }
   if (!waited) atomicOr(A.status, 1);
 }

@@ -178,6 +178,42 @@ def test_gradient_matches_oracle_ragged(F):
     assert e < 1e-3
 
 
+def folded_scene(all_folded, nsteps=300, seed=45):
+    """Detectors whose adjoints the reverse H kernel adds (points on E components, |E|^2 planes, two of
+    them overlapping), alone or with more of them than it takes and with H-point and flux detectors
+    that keep launches of their own."""
+    sc = ragged_scene(nsteps, seed)
+    dets = [H.point_probe(S.EX, (40, 20, 24)),
+            S.Detector(S.DET_PLANE_E2_SUM, (8, 9, 26), (60, 36, 27)),
+            S.Detector(S.DET_PLANE_E2_SUM, (30, 20, 25), (50, 30, 28)),
+            H.point_probe(S.EY, (12, 33, 29))]
+    if not all_folded:
+        dets += [S.Detector(S.DET_PLANE_E2_SUM, (10, 8, 27), (30, 20, 29)),
+                 H.point_probe(S.HZ, (44, 12, 26)),
+                 S.Detector(S.DET_PLANE_FLUX, (58, 7, 8), (59, 39, 30), axis=0)]
+    sc.detectors = dets
+    return sc
+
+
+@pytest.mark.parametrize("all_folded", [True, False])
+def test_gradient_folded_detector_adjoints(F, all_folded):
+    sc = folded_scene(all_folded)
+    rng = np.random.default_rng(10)
+    g = rng.standard_normal(O.detector_total(sc, sc.nsteps))
+    grad_o, _, _ = O.gradient(sc, sc.nsteps, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(sc.nsteps, record_faces=True)
+        grad_g = s.gradient(g)
+        # the checkpointed gradient adds every detector adjoint by its own launch
+        out = np.zeros(sc.design_shape(), dtype=np.float32)
+        s.fdtd_backward_checkpointed(g, out, 0)
+    e, e_c = rel_l2(grad_g, grad_o), rel_l2(grad_g, out)
+    print("folded detector adjoints (all folded: %s): dL/deps rel L2 %.3e vs oracle, %.3e vs checkpointed"
+          % (all_folded, e, e_c))
+    assert e < 1e-3
+    assert e_c < 1e-4
+
+
 def test_gradient_pec_point_detectors(F):
     sc = S.cavity_32(300)
     rng = np.random.default_rng(8)
