@@ -1050,6 +1050,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       const int v = std::atoi(e);
       if (v >= 1) h->tz = h->tz_rev = std::min(v, n[2]);
     }
+    if (const char* e = std::getenv("FDTD_REV_NSTAGE")) {  // override: ring stages of the reverse kernels
+      const int v = std::atoi(e);
+      if (v == 3 || v == 4) h->rev_nstage = v;
+    }
     h->tz = std::min(h->tz, fused_max_tz());
     h->tz_rev = std::min(h->tz_rev, fused_max_tz());
   }

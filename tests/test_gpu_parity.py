@@ -214,6 +214,21 @@ def test_gradient_folded_detector_adjoints(F, all_folded):
     assert e_c < 1e-4
 
 
+@pytest.mark.parametrize("scene", ["ragged", "odd_x"])
+def test_gradient_four_stage_reverse_kernels(F, scene, monkeypatch):
+    """The reverse kernels' 4-stage instantiation (the one large grids run) on small scenes."""
+    monkeypatch.setenv("FDTD_REV_NSTAGE", "4")
+    sc = ragged_scene(300) if scene == "ragged" else odd_scene(300, pml=(5, 0, 4, 6, 6, 3))
+    g = np.random.default_rng(11).standard_normal(O.detector_total(sc, 300))
+    grad_o, _, _ = O.gradient(sc, 300, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(300, record_faces=True)
+        grad_g = s.gradient(g)
+    e = rel_l2(grad_g, grad_o)
+    print("%s 300 steps, 4-stage reverse: dL/deps rel L2 %.3e" % (scene, e))
+    assert e < 1e-3
+
+
 def test_gradient_pec_point_detectors(F):
     sc = S.cavity_32(300)
     rng = np.random.default_rng(8)
