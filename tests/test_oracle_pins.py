@@ -300,6 +300,51 @@ def test_reciprocity_of_point_responses():
         assert np.max(np.abs(d1 - d2)) < 1e-12 * np.max(np.abs(d1))
 
 
+def mirror(f, axis, n_axis, sign, half):
+    """The field array f (nz, ny, nx) reflected through the grid's mid-plane along `axis` (0 = x):
+    half-position components (index i at i + 1/2) map i -> N-1-i, integer-position ones i -> N-i
+    (index 0 and the implicit index N are the PEC walls, both 0), times `sign`."""
+    ax = 2 - axis
+    g = np.zeros_like(f)
+    idx = np.arange(n_axis)
+    src = (n_axis - 1 - idx) if half else (n_axis - idx)
+    ok = (src >= 0) & (src < n_axis) & (half | (idx > 0))
+    take = [slice(None)] * 3
+    put = [slice(None)] * 3
+    take[ax] = src[ok]
+    put[ax] = idx[ok]
+    g[tuple(put)] = sign * f[tuple(take)]
+    return g
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_mirror_symmetry_of_fields(axis):
+    """A scene symmetric under reflection through the mid-plane x = N/2 (or y = N/2): permittivity
+    varying only along the other axes, equal CPML on the two mirrored faces, an E_z point source on the
+    mid-plane. The fields are then mirror images: E_z, E_t (the other tangential E) and H_n (H along the
+    mirror normal) even, E_n and the tangential H odd (E is a polar vector, H an axial one)."""
+    n = (24, 20, 22)
+    nx, ny, nz = n
+    rng = np.random.default_rng(41)
+    prof = rng.uniform(0.25, 1.0, (nz, ny if axis == 0 else 1, nx if axis == 1 else 1)).astype(np.float32)
+    eps_inv = np.ascontiguousarray(np.broadcast_to(prof, (nz, ny, nx)))
+    c = [n[0] // 2, n[1] // 2, 9]
+    c[1 - axis] = 7  # off-centre along the other axis, so that no second symmetry hides an error
+    sc = H.box_scene(n, pml=(4, 4, 3, 3, 5, 2), eps_inv=eps_inv, sources=[H.point_source(2, tuple(c), 8.0)])
+    f, _ = O.forward(sc, 160)
+    N = n[axis]
+    # per component: sign under the reflection, half-position along the mirror axis
+    for comp in range(6):
+        is_h = comp >= 3
+        along = comp % 3 == axis
+        half = along != is_h  # E_a is at a half position along a, H_a at an integer one
+        sign = (-1.0 if along else 1.0) * (-1.0 if is_h else 1.0)
+        g = mirror(f[comp], axis, N, sign, half)
+        scale = np.max(np.abs(f[comp]))
+        assert scale > 1e-8, comp
+        assert np.max(np.abs(f[comp] - g)) <= 1e-12 * scale, (comp, np.max(np.abs(f[comp] - g)) / scale)
+
+
 def test_superposition_of_sources():
     n = (12, 11, 10)
     sa = H.point_source(2, (3, 4, 5), 8.0)
