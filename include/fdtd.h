@@ -277,8 +277,20 @@ int fdtd_release_history(fdtd_handle* h);
 int fdtd_plane_flux_noalloc(const float* fields6, const fdtd_grid* grid, int32_t axis, const int32_t lo[3],
                             const int32_t hi[3], double* out, void* cuda_stream);
 
-/* Wait for all work of the handle's stream. */
+/* Wait for all work of the handle's stream, then report what its kernels flagged since the last
+ * report (and clear it): FDTD_ERR_TIMEOUT when a bounded device-side wait for a TMA copy gave up,
+ * FDTD_ERR_NONFINITE when a field check found a NaN or an infinity (after which the fields, detector
+ * outputs and gradients of that work are invalid; the handle stays usable). Calls that return
+ * results into host buffers (fdtd_read_detectors, fdtd_backward, fdtd_get_fields, ...) wait and
+ * report the same way. */
 int fdtd_synchronize(fdtd_handle* h);
+
+/* Non-finite field checks: every forward checks the fields after its last step, every backward the
+ * rebuilt and the adjoint fields at its end (one read of the arrays, the sum of their squares in FP64
+ * per thread, which is finite exactly when every value is). With every > 0 the forward also checks
+ * after every `every`-th step, so that a solve that has blown up is caught while it runs. The result
+ * is reported by fdtd_synchronize. INVALID_ARG for NULL or every < 0. */
+int fdtd_set_check_interval(fdtd_handle* h, int32_t every);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* fdtd_last_error(void);

@@ -274,7 +274,7 @@ struct Ev {
 struct LoopGraph {
   cudaGraphExec_t exec = nullptr;
   int nsteps = -1;
-  int key = -1;
+  int64_t key = -1;
   uint64_t gen = 0;
   std::vector<Ev> ev;      // timing events recorded by the graph (profiling only)
   int64_t launches = 0;    // kernels per replay
@@ -367,6 +367,8 @@ struct fdtd_handle {
   // launch accounting and sampled event timing
   int64_t launches = 0;
   int prof_every = 0;  // 0 = off
+  int check_every = 0;  // non-finite field check every this many forward steps (0: at the end of a sweep only)
+  int nsm = 148;        // SMs of the device
   double prof_ms[FDTD_KERNEL_KINDS] = {0};
   int64_t prof_n[FDTD_KERNEL_KINDS] = {0};
 
@@ -733,6 +735,11 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
       else launch_detector_interp(g, h->F(c), Fn, d, n, h->det_out, h->partial, st);  // E^n is in cur
       ++launches;
     }
+    // the non-finite check of the state after this step: periodic, and after the last step
+    if (n == nsteps - 1 || (h->check_every > 0 && (n + 1) % h->check_every == 0)) {
+      launch_check_finite(Fn.f[0], 6 * g.vol, h->status, h->nsm, st);
+      ++launches;
+    }
     h->cur = x;
   }
   if (faces) {  // join the side stream
@@ -841,7 +848,24 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     launches += enqueue_det_adjoint(h, F, A, n, 2, st);  // interpolated flux: E^n terms
     pb = 1 - pb;
   }
+  if (nsteps > 0) {  // the non-finite check of the rebuilt and the adjoint fields
+    launch_check_finite(F.f[0], 6 * g.vol, h->status, h->nsm, st);
+    launch_check_finite(A.f[0], 6 * g.vol, h->status, h->nsm, st);
+    launches += 2;
+  }
   return launches;
+}
+
+// Wait for the handle's stream and report what the kernels flagged in the status word, clearing it.
+int sync_status(fdtd_handle* h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st == 0) return FDTD_OK;
+  CK(cudaMemsetAsync(h->status, 0, 4, h->stream));
+  if (st & kStatusTimeout)
+    return fail(FDTD_ERR_TIMEOUT, "a device-side wait for a TMA copy gave up (status %d); results are invalid", st);
+  return fail(FDTD_ERR_NONFINITE, "a field check found a NaN or an infinity; results are invalid");
 }
 
 // Read the timing events of every profiled replay still pending (waits for the stream). Called
@@ -868,7 +892,7 @@ int prof_collect(fdtd_handle* h) {
 
 // Replay the cached graph of a time loop, capturing it first if its shape or buffers changed.
 template <class Enqueue>
-int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int key, Enqueue enqueue) {
+int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int64_t key, Enqueue enqueue) {
   if (nsteps == 0) return FDTD_OK;
   if (lg.pending) TRY(prof_collect(h));  // its events are about to be recorded again
   const int cur0 = h->cur;
@@ -1026,6 +1050,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       return cleanup(fail(FDTD_ERR_CUDA, "device attributes: %s", cudaGetErrorString(cudaGetLastError())));
+    h->nsm = nsm;
     // column tiles of the forward and of the reverse kernels
     const int64_t nxy = (int64_t)((n[0] + fused_tile_x() - 1) / fused_tile_x()) *
                         ((n[1] + fused_tile_y() - 1) / fused_tile_y());
@@ -1270,7 +1295,7 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   if (record && h->faces.per_step > 0)
     TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)nsteps, h->faces.per_step * 4));
   TRY(reset_state(h));
-  const int key = (record ? 1 : 0) | (h->prof_every << 1);
+  const int64_t key = (record ? 1 : 0) | ((int64_t)h->prof_every << 1) | ((int64_t)h->check_every << 32);
   TRY(run_loop(h, h->gfwd, nsteps, key, [&](cudaStream_t st, std::vector<Ev>* evs) {
     return enqueue_forward(h, nsteps, record, st, evs);
   }));
@@ -1302,7 +1327,7 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
-  const int key = h->cur | (h->prof_every << 1);
+  const int64_t key = h->cur | ((int64_t)h->prof_every << 1);
   TRY(run_loop(h, h->gbwd, nsteps, key,
                [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
   if (M > 0) {
@@ -1313,7 +1338,7 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   CK(cudaGetLastError());
   h->consumed = true;
   TRY(prof_collect(h));
-  if (M > 0 && is_host_pointer(dL_deps)) CK(cudaStreamSynchronize(h->stream));
+  if (M > 0 && is_host_pointer(dL_deps)) return sync_status(h);
   return FDTD_OK;
 }
 
@@ -1623,16 +1648,19 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
     C.save(0);
     C.reverse(0, nsteps, 0, 1);
   }
+  if (nsteps > 0) {  // the non-finite check of the adjoint fields
+    launch_check_finite(h->adj, 6 * g.vol, h->status, h->nsm, h->stream);
+    h->launches += 1;
+  }
   if (M > 0) {
     launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, 1.0, h->stream);
     h->launches += 1;
     CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
   h->recorded = false;
   if (forward_steps) *forward_steps = C.fsteps;
-  return FDTD_OK;
+  return sync_status(h);
 }
 
 int fdtd_backward_density(fdtd_handle* h, const double* dL_ddet, float* dL_drho) {
@@ -1695,7 +1723,7 @@ int fdtd_read_detectors(fdtd_handle* h, double* out) {
   const int64_t n = det_total_for(h, h->last_nsteps);
   if (n == 0) return FDTD_OK;
   CK(cudaMemcpyAsync(out, h->det_out, n * 8, cudaMemcpyDefault, h->stream));
-  if (is_host_pointer(out)) CK(cudaStreamSynchronize(h->stream));
+  if (is_host_pointer(out)) return sync_status(h);
   return FDTD_OK;
 }
 
@@ -1711,8 +1739,7 @@ int fdtd_get_fields(fdtd_handle* h, float* out6) {
   h->launches += 1;
   const int64_t N = (int64_t)h->g.n[0] * h->g.n[1] * h->g.n[2];
   CK(cudaMemcpyAsync(out6, h->staging, 6 * N * 4, cudaMemcpyDefault, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  return FDTD_OK;
+  return sync_status(h);
 }
 
 int64_t fdtd_bytes_allocated(fdtd_handle* h) { return h ? h->bytes : -1; }
@@ -1752,13 +1779,13 @@ int fdtd_release_history(fdtd_handle* h) {
 
 int fdtd_synchronize(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
-  CK(cudaStreamSynchronize(h->stream));
-  int st = 0;
-  CK(cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost));
-  if (st != 0) {
-    CK(cudaMemset(h->status, 0, 4));
-    return fail(FDTD_ERR_TIMEOUT, "a device-side wait for a TMA copy gave up (status %d); results are invalid", st);
-  }
+  return sync_status(h);
+}
+
+int fdtd_set_check_interval(fdtd_handle* h, int32_t every) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (every < 0) return fail(FDTD_ERR_INVALID_ARG, "every must be >= 0");
+  h->check_every = every;
   return FDTD_OK;
 }
 

@@ -22,6 +22,9 @@ constexpr int kMaxFaceSeg = 12;
 constexpr int kPitchAlign = 32;
 constexpr int kMaxSrc = 4;    // sources handled inside the fused kernels (the rest by extra launches)
 constexpr int kMaxDet = 4;    // detectors handled inside the fused kernels
+// bits of the device status word
+constexpr int kStatusTimeout = 1;    // a bounded wait for a TMA copy gave up
+constexpr int kStatusNonFinite = 2;  // a field check found a NaN or an infinity
 
 struct Geo {
   int n[3];           // cells nx, ny, nz
@@ -138,6 +141,9 @@ void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, do
 void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record, cudaStream_t s);
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s);
+// Flag kStatusNonFinite in *status if one of the n floats at p (n a multiple of 4, p 16-byte aligned)
+// is NaN or infinite.
+void launch_check_finite(const float* p, int64_t n, int* status, int nsm, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, double scale, cudaStream_t s);
 void launch_design_adam(const float* g_rho, float* theta, float* m, float* v, float* rho, int64_t n, int t, double lr,

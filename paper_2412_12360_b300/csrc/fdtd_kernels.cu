@@ -170,6 +170,22 @@ __global__ void k_det_adjoint(Geo g, Fields F, Fields A, DetDev d, int step, con
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// non-finite check: each thread sums the squares of its share of n floats in FP64 (an energy-like
+// sum that cannot overflow for float inputs) and flags the status word when its sum is not finite,
+// which happens exactly when one of its values is NaN or infinite. n is a multiple of 4 and p is
+// 16-byte aligned (whole field arrays of pitch-padded planes).
+// ---------------------------------------------------------------------------------------------
+__global__ void k_check_finite(const float4* __restrict__ p, int64_t n4, int* status) {
+  pdl_wait();
+  double e = 0.0;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n4; m += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = p[m];
+    e += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+  }
+  if (!isfinite(e)) atomicOr(status, kStatusNonFinite);
+}
+
 __global__ void k_set_density(Geo g, float* a, int lo0, int lo1, int lo2, int hi0, int hi1, int hi2,
                               const float* rho, float eps_lo, float deps) {
   const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -287,6 +303,13 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
                              const double* dL_ddet, cudaStream_t s) {
   const int64_t n = d.kind == 0 ? 1 : (int64_t)(d.hi[0] - d.lo[0]) * (d.hi[1] - d.lo[1]) * (d.hi[2] - d.lo[2]);
   launch_pdl(k_det_adjoint, dim3(blocks_for(n, 256)), dim3(256), 0, s, g, F, A, d, step, dL_ddet);
+}
+
+void launch_check_finite(const float* p, int64_t n, int* status, int nsm, cudaStream_t s) {
+  if (n <= 0) return;
+  const int64_t n4 = n / 4;
+  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(n4, 256), 4 * (int64_t)nsm);
+  launch_pdl(k_check_finite, dim3(blocks), dim3(256), 0, s, reinterpret_cast<const float4*>(p), n4, status);
 }
 
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
+    ("fdtd_set_check_interval", C.c_int, [_VP, C.c_int32]),
     ("fdtd_last_error", C.c_char_p, []),
     ("fdtd_version", C.c_char_p, []),
 ]
@@ -282,6 +283,10 @@ class Solver:
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))
+
+    def fdtd_set_check_interval(self, every: int):
+        """Check the fields for NaN / infinity every `every` forward steps too (0: at sweep ends only)."""
+        check(lib().fdtd_set_check_interval(self.h, int(every)))
 
     def fdtd_bytes_allocated(self) -> int:
         return int(lib().fdtd_bytes_allocated(self.h))

@@ -97,6 +97,7 @@ class Server:
         self._stop = False
         self._streams: List[object] = []
         self.peak_inflight = 0
+        self.cancelled = 0  # requests cancelled by their client before admission
         self._thread = threading.Thread(target=self._loop, name="fdtd-server", daemon=True)
         self._thread.start()
 
@@ -149,6 +150,7 @@ class Server:
             job.done.record(job.stream)
 
     def _retire(self, job: _Job):
+        job.solver.fdtd_synchronize()  # raises on a timeout or non-finite fields (the client gets it)
         det = job.det.cpu().numpy()
         grad = job.grad.cpu().numpy()
         job.solver.close()
@@ -177,10 +179,16 @@ class Server:
                     progressed = True
             while True:
                 with self._lock:
+                    while self._queue and self._queue[0].future.cancelled():  # Future.cancel() by the client
+                        self._queue.popleft()
+                        self.cancelled += 1
                     if not self._queue or admit_count([self._queue[0].footprint], len(self._inflight), self._used,
                                                       self.budget, self.max_inflight) == 0:
                         break
                     job = self._queue.popleft()
+                    if not job.future.set_running_or_notify_cancel():  # cancelled in between
+                        self.cancelled += 1
+                        continue
                 self._used += job.footprint
                 try:
                     self._admit(job)

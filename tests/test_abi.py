@@ -146,6 +146,8 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.fdtd_backward(None, None, None) == F.FDTD_ERR_INVALID_ARG
     assert L.fdtd_destroy(None) == F.FDTD_OK
     assert L.fdtd_bytes_allocated(None) == -1
+    assert L.fdtd_synchronize(None) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_set_check_interval(None, 8) == F.FDTD_ERR_INVALID_ARG
 
 
 def test_footprint_grows_with_steps_and_faces(L):

@@ -265,6 +265,46 @@ def test_device_and_host_buffers_agree_and_runs_are_deterministic(F):
     assert np.array_equal(outs[0][0], det_h) and np.array_equal(outs[0][1], out_h)
 
 
+def test_nonfinite_fields_are_reported_and_the_handle_recovers(F):
+    """A NaN in the initial state (an input, not a device fault) spreads through the solve; the field
+    checks flag it, fdtd_synchronize and the host-buffer reads report NONFINITE, and the same handle
+    then solves a clean problem to the oracle's result. The periodic check changes no result."""
+    sc = ragged_scene(120)
+    nx, ny, nz = sc.n
+    init = np.zeros((6, nz, ny, nx), dtype=np.float32)
+    init[2, 20, 22, 35] = np.nan
+    f_o, d_o = O.forward(sc, 120)
+    with F.Solver(sc) as s:
+        s.fdtd_set_initial_fields(init)
+        s.fdtd_forward(120, record_faces=True)
+        with pytest.raises(F.FDTDError) as e:
+            s.fdtd_synchronize()
+        assert "NONFINITE" in str(e.value)
+        s.fdtd_synchronize()  # reported once, then cleared
+        s.fdtd_forward(120, record_faces=True)
+        with pytest.raises(F.FDTDError) as e:
+            s.detectors()  # a host-buffer read reports it too
+        assert "NONFINITE" in str(e.value)
+        # a NaN in dL/d(outputs) poisons the adjoint fields: the backward reports it
+        s.fdtd_set_initial_fields(None)
+        s.fdtd_forward(120, record_faces=True)
+        s.fdtd_synchronize()
+        g = np.ones(O.detector_total(sc, 120))
+        g[5] = np.nan
+        with pytest.raises(F.FDTDError) as e:
+            s.gradient(g)
+        assert "NONFINITE" in str(e.value)
+        # clean again, with a check every 7 steps: results equal the oracle's and the unchecked run's
+        s.fdtd_forward(120)
+        plain = s.fields()
+        s.fdtd_set_check_interval(7)
+        s.fdtd_forward(120)
+        checked = s.fields()
+        s.fdtd_synchronize()
+    assert np.array_equal(plain, checked)
+    assert rel_l2(checked, f_o) < 1e-4
+
+
 def test_state_errors_and_byte_budget(F):
     sc = S.cavity_32(20)
     with F.Solver(sc) as s:

@@ -37,6 +37,37 @@ def test_served_results_equal_alone_and_in_the_mix(cuda_ok):
         assert np.array_equal(g0, r.dL_deps)
 
 
+def test_served_cancellation_and_failure_reporting(cuda_ok):
+    """A queued request the client cancels is never admitted; one whose fields blow up (a NaN in its
+    design permittivity, an input) fails with NONFINITE; the others complete with their standalone
+    results."""
+    from concurrent.futures import CancelledError
+
+    from paper_2412_12360_b300 import fdtd, serve
+    scenes = _mix(3)
+    bad = _mix(1)[0]
+    bad.eps_inv = bad.eps_inv.copy()
+    lo, hi = bad.design_lo, bad.design_hi
+    bad.eps_inv[(lo[2] + hi[2]) // 2, (lo[1] + hi[1]) // 2, (lo[0] + hi[0]) // 2] = np.nan
+    alone = serve.run_sequential([scenes[0], scenes[2]])
+    with serve.Server(max_inflight=1) as srv:
+        f0 = srv.submit(scenes[0])
+        f1 = srv.submit(scenes[1])
+        fb = srv.submit(bad)
+        f2 = srv.submit(scenes[2])
+        assert f1.cancel()  # one slot: the first request runs, the rest wait
+        r0, r2 = f0.result(timeout=600), f2.result(timeout=600)
+        with pytest.raises(fdtd.FDTDError) as e:
+            fb.result(timeout=600)
+        assert "NONFINITE" in str(e.value)
+        with pytest.raises(CancelledError):
+            f1.result(timeout=1)
+        assert srv.cancelled == 1
+    for (d0, g0), r in zip(alone, (r0, r2)):
+        assert np.array_equal(d0, r.detectors)
+        assert np.array_equal(g0, r.dL_deps)
+
+
 def test_served_admission_bounded_by_budget(cuda_ok):
     from paper_2412_12360_b300 import fdtd, serve
     scenes = _mix(5)
