@@ -292,6 +292,18 @@ int fdtd_synchronize(fdtd_handle* h);
  * is reported by fdtd_synchronize. INVALID_ARG for NULL or every < 0. */
 int fdtd_set_check_interval(fdtd_handle* h, int32_t every);
 
+/* Debugging aid against out-of-row accesses. Every row of the field arrays (both buffers), the adjoint
+ * fields and a is padded from nx to the pitch (a multiple of 32 cells); no kernel reads the padding
+ * or writes it (but see odd nx below). With enable != 0 the padding holds NaN from now on (refilled whenever the arrays are
+ * reset), so a kernel that read it would spread NaN into results (caught by the non-finite checks)
+ * and one that wrote it leaves a non-NaN value, which fdtd_check_canaries counts (waits for the
+ * stream; *overwritten = 0 when every canary is intact). Grids whose nx is a multiple of 32 have no
+ * padding. For odd nx the forward kernel, which stores x-adjacent cell pairs, writes zeros into
+ * column nx of the field arrays (never read), so their canaries start at column nx + 1.
+ * enable = 0 puts zeros back. INVALID_ARG for NULL; fdtd_check_canaries: STATE when off. */
+int fdtd_set_canaries(fdtd_handle* h, int32_t enable);
+int fdtd_check_canaries(fdtd_handle* h, int64_t* overwritten);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* fdtd_last_error(void);
 

@@ -5,6 +5,7 @@
 // and replayed for every later solve of the same shape, so a solve costs one graph launch per phase
 // instead of thousands of kernel launches.
 #include <algorithm>
+#include <limits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -368,6 +369,7 @@ struct fdtd_handle {
   int64_t launches = 0;
   int prof_every = 0;  // 0 = off
   int check_every = 0;  // non-finite field check every this many forward steps (0: at the end of a sweep only)
+  bool canary = false;  // NaN canaries in the pitch padding of the field, adjoint and a arrays
   int nsm = 148;        // SMs of the device
   double prof_ms[FDTD_KERNEL_KINDS] = {0};
   int64_t prof_n[FDTD_KERNEL_KINDS] = {0};
@@ -570,10 +572,25 @@ int ensure_det(fdtd_handle* h, int nsteps) {
   return FDTD_OK;
 }
 
+// NaN canaries in the pitch padding of both field buffers, the adjoint fields and a (canary mode).
+// For odd nx the forward kernel, which stores x-adjacent cell pairs, writes zeros into column nx of
+// the field arrays (never read: the tensor maps end at nx), so their canaries start one column later.
+int field_canary_x0(const fdtd_handle* h) { return h->g.n[0] + (h->g.n[0] & 1); }
+
+void fill_canaries(fdtd_handle* h, bool fields, bool adj, bool a) {
+  if (!h->canary) return;
+  const int64_t rows = (int64_t)h->g.n[1] * h->g.n[2];
+  const float nan = std::numeric_limits<float>::quiet_NaN();
+  if (fields) launch_fill_padding(h->g, h->fields, 12 * rows, field_canary_x0(h), nan, h->nsm, h->stream);
+  if (adj && h->adj) launch_fill_padding(h->g, h->adj, 6 * rows, h->g.n[0], nan, h->nsm, h->stream);
+  if (a) launch_fill_padding(h->g, h->a, rows, h->g.n[0], nan, h->nsm, h->stream);
+}
+
 int reset_state(fdtd_handle* h) {
   h->cur = 0;
   if (h->init) CK(cudaMemcpyAsync(h->fields, h->init, 6 * h->g.vol * 4, cudaMemcpyDeviceToDevice, h->stream));
   else CK(cudaMemsetAsync(h->fields, 0, 6 * h->g.vol * 4, h->stream));
+  fill_canaries(h, true, false, false);
   const int64_t pf = h->psi_floats();
   if (pf > 0) {
     CK(cudaMemsetAsync(h->psiE, 0, 2 * pf * 4, h->stream));
@@ -737,7 +754,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     }
     // the non-finite check of the state after this step: periodic, and after the last step
     if (n == nsteps - 1 || (h->check_every > 0 && (n + 1) % h->check_every == 0)) {
-      launch_check_finite(Fn.f[0], 6 * g.vol, h->status, h->nsm, st);
+      launch_check_finite(g, Fn.f[0], 6 * g.vol, h->status, h->nsm, st);
       ++launches;
     }
     h->cur = x;
@@ -849,8 +866,8 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     pb = 1 - pb;
   }
   if (nsteps > 0) {  // the non-finite check of the rebuilt and the adjoint fields
-    launch_check_finite(F.f[0], 6 * g.vol, h->status, h->nsm, st);
-    launch_check_finite(A.f[0], 6 * g.vol, h->status, h->nsm, st);
+    launch_check_finite(g, F.f[0], 6 * g.vol, h->status, h->nsm, st);
+    launch_check_finite(g, A.f[0], 6 * g.vol, h->status, h->nsm, st);
     launches += 2;
   }
   return launches;
@@ -1325,6 +1342,7 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   if (M > 0) TRY(ensure_staging(h));
   if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
   CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
+  fill_canaries(h, false, true, false);
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
   const int64_t key = h->cur | ((int64_t)h->prof_every << 1);
@@ -1640,6 +1658,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
   }
   if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
   CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
+  fill_canaries(h, false, true, false);
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
   TRY(reset_state(h));
@@ -1649,7 +1668,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
     C.reverse(0, nsteps, 0, 1);
   }
   if (nsteps > 0) {  // the non-finite check of the adjoint fields
-    launch_check_finite(h->adj, 6 * g.vol, h->status, h->nsm, h->stream);
+    launch_check_finite(g, h->adj, 6 * g.vol, h->status, h->nsm, h->stream);
     h->launches += 1;
   }
   if (M > 0) {
@@ -1780,6 +1799,37 @@ int fdtd_release_history(fdtd_handle* h) {
 int fdtd_synchronize(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   return sync_status(h);
+}
+
+int fdtd_set_canaries(fdtd_handle* h, int32_t enable) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  h->canary = enable != 0;
+  const int64_t rows = (int64_t)h->g.n[1] * h->g.n[2];
+  if (h->canary) fill_canaries(h, true, true, true);
+  else {  // back to zero padding
+    launch_fill_padding(h->g, h->fields, 12 * rows, h->g.n[0], 0.f, h->nsm, h->stream);
+    if (h->adj) launch_fill_padding(h->g, h->adj, 6 * rows, h->g.n[0], 0.f, h->nsm, h->stream);
+    launch_fill_padding(h->g, h->a, rows, h->g.n[0], 0.f, h->nsm, h->stream);
+  }
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int fdtd_check_canaries(fdtd_handle* h, int64_t* overwritten) {
+  if (!h || !overwritten) return fail(FDTD_ERR_INVALID_ARG, "NULL handle or output");
+  if (!h->canary) return fail(FDTD_ERR_STATE, "canaries are off");
+  TRY(ensure_staging(h));
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(h->staging);
+  CK(cudaMemsetAsync(cnt, 0, 8, h->stream));
+  const int64_t rows = (int64_t)h->g.n[1] * h->g.n[2];
+  launch_count_padding(h->g, h->fields, 12 * rows, field_canary_x0(h), cnt, h->nsm, h->stream);
+  if (h->adj) launch_count_padding(h->g, h->adj, 6 * rows, h->g.n[0], cnt, h->nsm, h->stream);
+  launch_count_padding(h->g, h->a, rows, h->g.n[0], cnt, h->nsm, h->stream);
+  unsigned long long c = 0;
+  CK(cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *overwritten = (int64_t)c;
+  return FDTD_OK;
 }
 
 int fdtd_set_check_interval(fdtd_handle* h, int32_t every) {

@@ -141,9 +141,14 @@ void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, do
 void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record, cudaStream_t s);
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s);
-// Flag kStatusNonFinite in *status if one of the n floats at p (n a multiple of 4, p 16-byte aligned)
-// is NaN or infinite.
-void launch_check_finite(const float* p, int64_t n, int* status, int nsm, cudaStream_t s);
+// Flag kStatusNonFinite in *status if one of the grid cells of the n floats at p (whole pitch-padded
+// arrays: n a multiple of 4, p 16-byte aligned) is NaN or infinite; the pitch padding is not read.
+void launch_check_finite(const Geo& g, const float* p, int64_t n, int* status, int nsm, cudaStream_t s);
+// Pitch-padding canaries of nrows rows at base, in columns x0 .. nxp-1: fill them with v, or add the
+// number of them that are not NaN to *count (a debugging aid against writes out of a row).
+void launch_fill_padding(const Geo& g, float* base, int64_t nrows, int x0, float v, int nsm, cudaStream_t s);
+void launch_count_padding(const Geo& g, const float* base, int64_t nrows, int x0, unsigned long long* count,
+                          int nsm, cudaStream_t s);
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,
                           float* dL_deps, double scale, cudaStream_t s);
 void launch_design_adam(const float* g_rho, float* theta, float* m, float* v, float* rho, int64_t n, int t, double lr,

@@ -171,19 +171,43 @@ __global__ void k_det_adjoint(Geo g, Fields F, Fields A, DetDev d, int step, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// non-finite check: each thread sums the squares of its share of n floats in FP64 (an energy-like
-// sum that cannot overflow for float inputs) and flags the status word when its sum is not finite,
-// which happens exactly when one of its values is NaN or infinite. n is a multiple of 4 and p is
-// 16-byte aligned (whole field arrays of pitch-padded planes).
+// non-finite check: each thread sums the squares of its share of the grid cells of n floats (rows of
+// nxp floats, the first nx of them cells, the rest pitch padding) in FP64, an energy-like sum that
+// cannot overflow for float inputs, and flags the status word when its sum is not finite, which
+// happens exactly when one of its values is NaN or infinite. n and nxp are multiples of 4 and p is
+// 16-byte aligned (whole field arrays of pitch-padded planes), so a float4 never straddles two rows.
 // ---------------------------------------------------------------------------------------------
-__global__ void k_check_finite(const float4* __restrict__ p, int64_t n4, int* status) {
+__global__ void k_check_finite(const float4* __restrict__ p, int64_t n4, int nx, int nxp, int* status) {
   pdl_wait();
   double e = 0.0;
   for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n4; m += (int64_t)gridDim.x * blockDim.x) {
     const float4 v = p[m];
-    e += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+    const int x = (int)((4 * m) % nxp);  // column of v.x
+    if (x < nx) e += (double)v.x * v.x;
+    if (x + 1 < nx) e += (double)v.y * v.y;
+    if (x + 2 < nx) e += (double)v.z * v.z;
+    if (x + 3 < nx) e += (double)v.w * v.w;
   }
   if (!isfinite(e)) atomicOr(status, kStatusNonFinite);
+}
+
+// ---------------------------------------------------------------------------------------------
+// pitch-padding canaries (a debugging aid): fill the padding columns x0 .. nxp-1 of nrows rows with a
+// value, or count the entries there that are no longer NaN (a kernel wrote out of its row)
+// ---------------------------------------------------------------------------------------------
+__global__ void k_fill_padding(float* base, int64_t nrows, int x0, int nxp, float v) {
+  const int w = nxp - x0;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < nrows * w; m += (int64_t)gridDim.x * blockDim.x)
+    base[(m / w) * nxp + x0 + m % w] = v;
+}
+
+__global__ void k_count_padding(const float* __restrict__ base, int64_t nrows, int x0, int nxp,
+                                unsigned long long* count) {
+  const int w = nxp - x0;
+  unsigned long long c = 0;
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < nrows * w; m += (int64_t)gridDim.x * blockDim.x)
+    c += isnan(base[(m / w) * nxp + x0 + m % w]) ? 0ull : 1ull;
+  if (c) atomicAdd(count, c);
 }
 
 __global__ void k_set_density(Geo g, float* a, int lo0, int lo1, int lo2, int hi0, int hi1, int hi2,
@@ -305,11 +329,25 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
   launch_pdl(k_det_adjoint, dim3(blocks_for(n, 256)), dim3(256), 0, s, g, F, A, d, step, dL_ddet);
 }
 
-void launch_check_finite(const float* p, int64_t n, int* status, int nsm, cudaStream_t s) {
+void launch_check_finite(const Geo& g, const float* p, int64_t n, int* status, int nsm, cudaStream_t s) {
   if (n <= 0) return;
   const int64_t n4 = n / 4;
   const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(n4, 256), 4 * (int64_t)nsm);
-  launch_pdl(k_check_finite, dim3(blocks), dim3(256), 0, s, reinterpret_cast<const float4*>(p), n4, status);
+  launch_pdl(k_check_finite, dim3(blocks), dim3(256), 0, s, reinterpret_cast<const float4*>(p), n4, g.n[0], g.nxp,
+             status);
+}
+
+void launch_fill_padding(const Geo& g, float* base, int64_t nrows, int x0, float v, int nsm, cudaStream_t s) {
+  if (x0 >= g.nxp || nrows <= 0) return;
+  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(nrows * (g.nxp - x0), 256), 4 * (int64_t)nsm);
+  k_fill_padding<<<blocks, 256, 0, s>>>(base, nrows, x0, g.nxp, v);
+}
+
+void launch_count_padding(const Geo& g, const float* base, int64_t nrows, int x0, unsigned long long* count,
+                          int nsm, cudaStream_t s) {
+  if (x0 >= g.nxp || nrows <= 0) return;
+  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(nrows * (g.nxp - x0), 256), 4 * (int64_t)nsm);
+  k_count_padding<<<blocks, 256, 0, s>>>(base, nrows, x0, g.nxp, count);
 }
 
 void launch_grad_finalize(const Geo& g, const float* a, const int* dlo, const int* dhi, const double* dLda,

@@ -91,6 +91,8 @@ SIGNATURES = [
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
     ("fdtd_set_check_interval", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_set_canaries", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_check_canaries", C.c_int, [_VP, C.POINTER(C.c_int64)]),
     ("fdtd_last_error", C.c_char_p, []),
     ("fdtd_version", C.c_char_p, []),
 ]
@@ -287,6 +289,16 @@ class Solver:
     def fdtd_set_check_interval(self, every: int):
         """Check the fields for NaN / infinity every `every` forward steps too (0: at sweep ends only)."""
         check(lib().fdtd_set_check_interval(self.h, int(every)))
+
+    def fdtd_set_canaries(self, enable: bool):
+        """NaN canaries in the arrays' pitch padding (a debugging aid)."""
+        check(lib().fdtd_set_canaries(self.h, 1 if enable else 0))
+
+    def fdtd_check_canaries(self) -> int:
+        """Padding entries some kernel overwrote since the canaries were set (0: all intact)."""
+        n = C.c_int64(0)
+        check(lib().fdtd_check_canaries(self.h, C.byref(n)))
+        return int(n.value)
 
     def fdtd_bytes_allocated(self) -> int:
         return int(lib().fdtd_bytes_allocated(self.h))

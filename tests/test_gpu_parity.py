@@ -305,6 +305,39 @@ def test_nonfinite_fields_are_reported_and_the_handle_recovers(F):
     assert rel_l2(checked, f_o) < 1e-4
 
 
+@pytest.mark.parametrize("scene", ["ragged", "odd_x", "tfsf_interp"])
+def test_pitch_padding_canaries_stay_intact(F, scene):
+    """NaN canaries in the pitch padding of every field, adjoint and permittivity row: a forward with the
+    face record, the time-reversal and the checkpointing gradients leave every canary in place, read
+    none (no NaN reaches a result) and give bitwise the results of the same runs without canaries."""
+    if scene == "ragged":
+        sc = ragged_scene(150)
+    elif scene == "odd_x":
+        sc = odd_scene(150, pml=(5, 0, 4, 6, 6, 3))
+    else:
+        sc = S.design_box_scene((45, 38, 41), 6, 12, 150, 21, name="canary", tfsf=True, interp=True)
+    assert sc.n[0] % 32 != 0  # a grid with pitch padding
+    g = np.random.default_rng(12).standard_normal(O.detector_total(sc, sc.nsteps))
+    out = []
+    for canary in (False, True):
+        with F.Solver(sc) as s:
+            if canary:
+                s.fdtd_set_canaries(True)
+            s.fdtd_forward(sc.nsteps, record_faces=True)
+            det = s.detectors()
+            grad = s.gradient(g)
+            ck = np.zeros(sc.design_shape(), dtype=np.float32)
+            s.fdtd_backward_checkpointed(g, ck, 1, 3)
+            fields = s.fields()
+            if canary:
+                assert s.fdtd_check_canaries() == 0
+            s.fdtd_synchronize()
+        out.append((det, grad, ck, fields))
+    for a, b in zip(*out):
+        assert np.all(np.isfinite(b))
+        assert np.array_equal(a, b)
+
+
 def test_state_errors_and_byte_budget(F):
     sc = S.cavity_32(20)
     with F.Solver(sc) as s:
