@@ -211,8 +211,17 @@ int fdtd_read_detectors(fdtd_handle* h, double* out);
 /* Number of doubles fdtd_read_detectors writes for the last forward (or -1 on error). */
 int64_t fdtd_detector_total(fdtd_handle* h);
 
-/* Current fields (host or device, 6*nx*ny*nz floats, field-major, x fastest, pitch removed). */
+/* The outputs of detector idx (0-based, in the order given to fdtd_create) of the last forward, into
+ * a host or device buffer of fdtd_detector_size(h, idx) doubles: one value per step for the point and
+ * flux kinds, one per box cell (x fastest) for the |E|^2 kinds. A host buffer waits for the stream
+ * and reports as fdtd_synchronize does. INVALID_ARG for NULL or a bad idx, STATE before a forward. */
+int fdtd_read_detector(fdtd_handle* h, int32_t idx, double* out);
+int64_t fdtd_detector_size(fdtd_handle* h, int32_t idx);  /* -1 on error */
+
+/* Current fields (host or device, 6*nx*ny*nz floats, field-major, x fastest, pitch removed).
+ * fdtd_fields is the same call. */
 int fdtd_get_fields(fdtd_handle* h, float* out6);
+int fdtd_fields(fdtd_handle* h, float* out6);
 
 /* Bytes of device memory a solve of this size needs (fields, coefficients, adjoint state and a
  * face history for nsteps when record_faces != 0); for admission by HBM footprint. -1 on bad input. */

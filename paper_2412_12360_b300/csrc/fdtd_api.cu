@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 #include "fdtd_tma.cuh"
@@ -885,6 +887,13 @@ int sync_status(fdtd_handle* h) {
   return fail(FDTD_ERR_NONFINITE, "a field check found a NaN or an infinity; results are invalid");
 }
 
+// NVTX range over a host call (the enqueue; the GPU work of a captured loop is one graph launch), so
+// that profilers can attribute and filter by phase
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Read the timing events of every profiled replay still pending (waits for the stream). Called
 // before a pending graph is replayed again, after a backward, and by fdtd_profile_read, so a
 // forward followed by a backward costs one wait at the end instead of one between the two.
@@ -1290,6 +1299,7 @@ int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6) {
 }
 
 int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
+  NvtxRange range("fdtd_forward");
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (nsteps < 0) return fail(FDTD_ERR_INVALID_ARG, "nsteps must be >= 0");
   const bool record = (flags & FDTD_RECORD_FACES) != 0;
@@ -1361,6 +1371,7 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
 }
 
 int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
+  NvtxRange range("fdtd_backward");
   return backward_scaled(h, dL_ddet, dL_deps, 1.0);
 }
 
@@ -1584,6 +1595,7 @@ int64_t fdtd_checkpoint_cost(int32_t nsteps, int32_t method, int32_t slots) {
 
 int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_deps, int32_t method, int32_t slots,
                                int64_t* forward_steps) {
+  NvtxRange range("fdtd_backward_checkpointed");
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (method != 0 && method != 1) return fail(FDTD_ERR_INVALID_ARG, "method must be 0 (halving) or 1 (treeverse)");
   if (method == 1 && slots < 1) return fail(FDTD_ERR_INVALID_ARG, "treeverse needs at least one state slot");
@@ -1746,6 +1758,25 @@ int fdtd_read_detectors(fdtd_handle* h, double* out) {
   return FDTD_OK;
 }
 
+int64_t fdtd_detector_size(fdtd_handle* h, int32_t idx) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (idx < 0 || idx >= (int32_t)h->dets.size()) return fail(FDTD_ERR_INVALID_ARG, "detector %d does not exist", idx);
+  const DetDev& d = h->dets[idx];
+  const bool per_cell = d.kind == FDTD_DET_PLANE_E2_SUM || d.kind == FDTD_DET_PLANE_E2_SUM_INTERP;
+  return per_cell ? box_cells(d.lo, d.hi) : (h->last_nsteps < 0 ? 0 : h->last_nsteps);
+}
+
+int fdtd_read_detector(fdtd_handle* h, int32_t idx, double* out) {
+  if (!h || !out) return fail(FDTD_ERR_INVALID_ARG, "NULL argument");
+  if (idx < 0 || idx >= (int32_t)h->dets.size()) return fail(FDTD_ERR_INVALID_ARG, "detector %d does not exist", idx);
+  if (h->last_nsteps < 0) return fail(FDTD_ERR_STATE, "no forward has run");
+  const int64_t n = fdtd_detector_size(h, idx);
+  if (n == 0) return FDTD_OK;
+  CK(cudaMemcpyAsync(out, h->det_out + h->dets[idx].off, n * 8, cudaMemcpyDefault, h->stream));
+  if (is_host_pointer(out)) return sync_status(h);
+  return FDTD_OK;
+}
+
 int64_t fdtd_detector_total(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   return det_total_for(h, h->last_nsteps < 0 ? 0 : h->last_nsteps);
@@ -1760,6 +1791,8 @@ int fdtd_get_fields(fdtd_handle* h, float* out6) {
   CK(cudaMemcpyAsync(out6, h->staging, 6 * N * 4, cudaMemcpyDefault, h->stream));
   return sync_status(h);
 }
+
+int fdtd_fields(fdtd_handle* h, float* out6) { return fdtd_get_fields(h, out6); }
 
 int64_t fdtd_bytes_allocated(fdtd_handle* h) { return h ? h->bytes : -1; }
 

@@ -80,6 +80,9 @@ SIGNATURES = [
     ("fdtd_read_detectors", C.c_int, [_VP, _VP]),
     ("fdtd_detector_total", C.c_int64, [_VP]),
     ("fdtd_get_fields", C.c_int, [_VP, _VP]),
+    ("fdtd_fields", C.c_int, [_VP, _VP]),
+    ("fdtd_read_detector", C.c_int, [_VP, C.c_int32, _VP]),
+    ("fdtd_detector_size", C.c_int64, [_VP, C.c_int32]),
     ("fdtd_footprint_bytes", C.c_int64, [C.POINTER(fdtd_grid), C.POINTER(fdtd_pml), C.c_int32, C.c_int32,
                                          _I3, _I3]),
     ("fdtd_set_byte_budget", C.c_int, [C.c_int64]),
@@ -252,6 +255,20 @@ class Solver:
 
     def fdtd_get_fields(self, out6):
         check(lib().fdtd_get_fields(self.h, _ptr(out6)))
+
+    def fdtd_read_detector(self, idx: int, out):
+        check(lib().fdtd_read_detector(self.h, int(idx), _ptr(out)))
+
+    def fdtd_detector_size(self, idx: int) -> int:
+        n = int(lib().fdtd_detector_size(self.h, int(idx)))
+        if n < 0:
+            raise FDTDError(n, last_error())
+        return n
+
+    def detector(self, idx: int) -> np.ndarray:
+        out = np.zeros(max(1, self.fdtd_detector_size(idx)), dtype=np.float64)
+        self.fdtd_read_detector(idx, out)
+        return out[: self.fdtd_detector_size(idx)]
 
     def fdtd_set_initial_fields(self, fields6):
         check(lib().fdtd_set_initial_fields(self.h, _ptr(fields6)))

@@ -150,6 +150,9 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.fdtd_set_check_interval(None, 8) == F.FDTD_ERR_INVALID_ARG
     assert L.fdtd_set_canaries(None, 1) == F.FDTD_ERR_INVALID_ARG
     assert L.fdtd_check_canaries(None, None) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_read_detector(None, 0, None) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_detector_size(None, 0) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_fields(None, None) == F.FDTD_ERR_INVALID_ARG
 
 
 def test_footprint_grows_with_steps_and_faces(L):

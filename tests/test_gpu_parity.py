@@ -109,6 +109,10 @@ def test_forward_and_gradient_odd_x_extent(F):
         s.fdtd_forward(400)
         f_g = s.fields()
         d_g = s.detectors()
+        per = [s.detector(q) for q in range(len(sc.detectors))]  # one detector at a time
+        with pytest.raises(F.FDTDError):
+            s.fdtd_detector_size(len(sc.detectors))
+    assert np.array_equal(np.concatenate(per), d_g)
     e = rel_l2(f_g, f_o)
     print("odd_x 400 steps: fields rel L2 %.3e" % e)
     assert e < 1e-4
