@@ -294,6 +294,13 @@ int fdtd_plane_flux_noalloc(const float* fields6, const fdtd_grid* grid, int32_t
  * report the same way. */
 int fdtd_synchronize(fdtd_handle* h);
 
+/* Where the face copies run (default 1): with enable != 0 the per-step face record (forward) and
+ * replay (backward) are captured on a second stream beside the stencil kernels, which shortens a
+ * step on small grids when the captured loop is replayed many times; with 0 they run in line on the
+ * handle's stream, which keeps the captured graph smaller and cheaper to build, the better choice for
+ * a handle that solves once (served requests). Results are the same either way. INVALID_ARG for NULL. */
+int fdtd_set_face_overlap(fdtd_handle* h, int32_t enable);
+
 /* Non-finite field checks: every forward checks the fields after its last step, every backward the
  * rebuilt and the adjoint fields at its end (one read of the arrays, the sum of their squares in FP64
  * per thread, which is finite exactly when every value is). With every > 0 the forward also checks

@@ -312,6 +312,7 @@ struct fdtd_handle {
   cudaStream_t cap = nullptr;     // private stream used only to capture the time loops
   cudaStream_t side = nullptr;    // captured beside `cap`: the face copies, off the critical path
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};  // fork / join points of `side`
+  bool face_overlap = true;  // face copies on `side`, beside the stencil kernels (else in line on the stream)
   int32_t design_lo[3] = {0, 0, 0}, design_hi[3] = {0, 0, 0};
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
@@ -714,11 +715,12 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.status = h->status;
   // The face record of step n runs on the side stream, beside step n+1 (which only reads that
   // buffer); step n+2 overwrites it, so its fused kernel waits for the copy, and so does a TFSF H
-  // correction of step n+1, which writes that buffer's H.
+  // correction of step n+1, which writes that buffer's H. Without face_overlap it runs in line.
+  const bool ovl = faces && h->face_overlap;
   for (int n = 0; n < nsteps; ++n) {
     const int c = h->cur, x = 1 - c;
-    if (faces && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
-    if (faces && n >= 1 && !h->hsrcs.empty()) cudaStreamWaitEvent(st, h->ev_join[(n - 1) % 2], 0);
+    if (ovl && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
+    if (ovl && n >= 1 && !h->hsrcs.empty()) cudaStreamWaitEvent(st, h->ev_join[(n - 1) % 2], 0);
     fa.cur = h->F(c);
     fa.nxt = h->F(x);
     fa.psiE_cur = h->psi_set(h->psiE + c * pf);
@@ -737,13 +739,16 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     launches += 1;
     const Fields Fn = h->F(x);
     if (faces) {  // H^{n+1/2} on the boundary faces
-      cudaEventRecord(h->ev_fork, st);
-      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-      {
-        ProfScope ps(h, evs, h->side, FDTD_KERNEL_FACE_COPY, n);
-        launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, h->side);
+      cudaStream_t fs = ovl ? h->side : st;
+      if (ovl) {
+        cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(h->side, h->ev_fork, 0);
       }
-      cudaEventRecord(h->ev_join[n % 2], h->side);
+      {
+        ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
+        launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, fs);
+      }
+      if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
       launches += 1;
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
@@ -761,7 +766,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
     }
     h->cur = x;
   }
-  if (faces) {  // join the side stream
+  if (ovl) {  // join the side stream
     if (nsteps >= 2) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 2) % 2], 0);
     if (nsteps >= 1) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 1) % 2], 0);
   }
@@ -818,17 +823,20 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   int pb = 0;
   // The face replay of step n (the recorded H^{n+1/2} written back outside R) runs on the side
   // stream beside rev_H(n+1), which neither reads nor writes H outside R; rev_E(n) waits for it.
+  // Without face_overlap it runs in line, right before rev_E(n).
   const bool faces = h->faces.per_step > 0;
+  const bool ovl = faces && h->face_overlap;
   auto replay = [&](int n) {
-    cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    cudaStream_t fs = ovl ? h->side : st;
+    if (ovl) cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     {
-      ProfScope ps(h, evs, h->side, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, h->side);
+      ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
+      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
     }
-    cudaEventRecord(h->ev_join[n % 2], h->side);
+    if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
     launches += 1;
   };
-  if (faces && nsteps > 0) {
+  if (ovl && nsteps > 0) {
     cudaEventRecord(h->ev_fork, st);
     replay(nsteps - 1);
   }
@@ -841,14 +849,15 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     }
     for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
     ra.step = n;
-    if (faces) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
+    if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
+    else if (faces) replay(n);
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
       ra.pin = PEb[pb];
       ra.pout = PEb[1 - pb];
       launch_rev_E(ra, rm, st);
     }
-    if (faces && n > 0) {  // rev_E(n) has read the faces of step n: replay those of step n-1
+    if (ovl && n > 0) {  // rev_E(n) has read the faces of step n: replay those of step n-1
       cudaEventRecord(h->ev_fork, st);
       replay(n - 1);
     }
@@ -1322,7 +1331,8 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   if (record && h->faces.per_step > 0)
     TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)nsteps, h->faces.per_step * 4));
   TRY(reset_state(h));
-  const int64_t key = (record ? 1 : 0) | ((int64_t)h->prof_every << 1) | ((int64_t)h->check_every << 32);
+  const int64_t key = (record ? 1 : 0) | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2) |
+                      ((int64_t)h->check_every << 32);
   TRY(run_loop(h, h->gfwd, nsteps, key, [&](cudaStream_t st, std::vector<Ev>* evs) {
     return enqueue_forward(h, nsteps, record, st, evs);
   }));
@@ -1355,7 +1365,7 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   fill_canaries(h, false, true, false);
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
-  const int64_t key = h->cur | ((int64_t)h->prof_every << 1);
+  const int64_t key = h->cur | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2);
   TRY(run_loop(h, h->gbwd, nsteps, key,
                [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
   if (M > 0) {
@@ -1862,6 +1872,12 @@ int fdtd_check_canaries(fdtd_handle* h, int64_t* overwritten) {
   CK(cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   *overwritten = (int64_t)c;
+  return FDTD_OK;
+}
+
+int fdtd_set_face_overlap(fdtd_handle* h, int32_t enable) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  h->face_overlap = enable != 0;
   return FDTD_OK;
 }
 

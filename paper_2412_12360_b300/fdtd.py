@@ -94,6 +94,7 @@ SIGNATURES = [
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
     ("fdtd_set_check_interval", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_set_face_overlap", C.c_int, [_VP, C.c_int32]),
     ("fdtd_set_canaries", C.c_int, [_VP, C.c_int32]),
     ("fdtd_check_canaries", C.c_int, [_VP, C.POINTER(C.c_int64)]),
     ("fdtd_last_error", C.c_char_p, []),
@@ -306,6 +307,10 @@ class Solver:
     def fdtd_set_check_interval(self, every: int):
         """Check the fields for NaN / infinity every `every` forward steps too (0: at sweep ends only)."""
         check(lib().fdtd_set_check_interval(self.h, int(every)))
+
+    def fdtd_set_face_overlap(self, enable: bool):
+        """Face copies beside the stencil kernels (True, for handles that solve repeatedly) or in line."""
+        check(lib().fdtd_set_face_overlap(self.h, 1 if enable else 0))
 
     def fdtd_set_canaries(self, enable: bool):
         """NaN canaries in the arrays' pitch padding (a debugging aid)."""

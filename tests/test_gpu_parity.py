@@ -342,6 +342,21 @@ def test_pitch_padding_canaries_stay_intact(F, scene):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("scene", ["ragged", "tfsf_interp"])
+def test_face_copies_in_line_or_overlapped_give_the_same_results(F, scene):
+    sc = ragged_scene(150) if scene == "ragged" else S.design_box_scene(
+        (45, 38, 41), 6, 12, 150, 21, name="ovl", tfsf=True, interp=True)
+    g = np.random.default_rng(13).standard_normal(O.detector_total(sc, sc.nsteps))
+    out = []
+    for ovl in (True, False):
+        with F.Solver(sc) as s:
+            s.fdtd_set_face_overlap(ovl)
+            s.fdtd_forward(sc.nsteps, record_faces=True)
+            out.append((s.detectors(), s.gradient(g), s.fields()))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
+
+
 def test_state_errors_and_byte_budget(F):
     sc = S.cavity_32(20)
     with F.Solver(sc) as s:
