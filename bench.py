@@ -689,8 +689,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="measure the continuous-batching server instead")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-load", type=float, default=1.5, help="offered load / sequential capacity")
-    ap.add_argument("--serve-slots", type=int, default=3,
-                    help="requests in flight at once (on one B300, 3 gave the best throughput and latency)")
+    ap.add_argument("--serve-slots", type=int, default=2,
+                    help="requests in flight at once (on one B300, 2-4 gave the same throughput, 2 the lowest latency)")
     ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference check of --batched")

@@ -301,6 +301,12 @@ int fdtd_synchronize(fdtd_handle* h);
  * a handle that solves once (served requests). Results are the same either way. INVALID_ARG for NULL. */
 int fdtd_set_face_overlap(fdtd_handle* h, int32_t enable);
 
+/* How the time loops run (default 1): with enable != 0 each forward and backward loop is captured
+ * once into a CUDA graph and replayed (the graph is rebuilt when the step count or the buffers
+ * change); with 0 its kernels are launched directly on the stream, which spares building a graph
+ * for a handle that solves once. Results are the same either way. INVALID_ARG for NULL. */
+int fdtd_set_graphs(fdtd_handle* h, int32_t enable);
+
 /* Non-finite field checks: every forward checks the fields after its last step, every backward the
  * rebuilt and the adjoint fields at its end (one read of the arrays, the sum of their squares in FP64
  * per thread, which is finite exactly when every value is). With every > 0 the forward also checks

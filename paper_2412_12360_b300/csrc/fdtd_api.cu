@@ -313,6 +313,8 @@ struct fdtd_handle {
   cudaStream_t side = nullptr;    // captured beside `cap`: the face copies, off the critical path
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};  // fork / join points of `side`
   bool face_overlap = true;  // face copies on `side`, beside the stencil kernels (else in line on the stream)
+  bool use_graphs = true;    // time loops captured into CUDA graphs (else launched directly)
+  bool capturing = false;    // a time loop is being captured
   int32_t design_lo[3] = {0, 0, 0}, design_hi[3] = {0, 0, 0};
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
@@ -445,10 +447,16 @@ struct ProfScope {
     e.kind = kind;
     evs->push_back(e);
     idx = (int)evs->size() - 1;
-    cudaEventRecordWithFlags((*evs)[idx].a, st, cudaEventRecordExternal);
+    ext = h->capturing;
+    record((*evs)[idx].a);
   }
   ~ProfScope() {
-    if (idx >= 0) cudaEventRecordWithFlags((*evs)[idx].b, st, cudaEventRecordExternal);
+    if (idx >= 0) record((*evs)[idx].b);
+  }
+  bool ext = false;  // inside a capture: the event becomes an event-record node of the graph
+  void record(cudaEvent_t e) const {
+    if (ext) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
 };
 
@@ -925,17 +933,29 @@ int prof_collect(fdtd_handle* h) {
   return FDTD_OK;
 }
 
-// Replay the cached graph of a time loop, capturing it first if its shape or buffers changed.
+// Replay the cached graph of a time loop, capturing it first if its shape or buffers changed; with
+// use_graphs off, launch the loop's kernels directly on the stream instead (no graph to build: the
+// cheaper choice for a handle that solves once).
 template <class Enqueue>
 int run_loop(fdtd_handle* h, LoopGraph& lg, int nsteps, int64_t key, Enqueue enqueue) {
   if (nsteps == 0) return FDTD_OK;
   if (lg.pending) TRY(prof_collect(h));  // its events are about to be recorded again
+  if (!h->use_graphs) {
+    lg.reset();
+    const int64_t n = enqueue(h->stream, h->prof_every > 0 ? &lg.ev : nullptr);
+    CK(cudaGetLastError());
+    h->launches += n;
+    lg.pending = h->prof_every > 0 && !lg.ev.empty();
+    return FDTD_OK;
+  }
   const int cur0 = h->cur;
   if (!(lg.exec && lg.nsteps == nsteps && lg.key == key && lg.gen == h->gen)) {
     lg.reset();
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
     lg.launches = enqueue(h->cap, h->prof_every > 0 ? &lg.ev : nullptr);
+    h->capturing = false;
     cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
     if (e != cudaSuccess) {
       h->cur = cur0;
@@ -1872,6 +1892,12 @@ int fdtd_check_canaries(fdtd_handle* h, int64_t* overwritten) {
   CK(cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   *overwritten = (int64_t)c;
+  return FDTD_OK;
+}
+
+int fdtd_set_graphs(fdtd_handle* h, int32_t enable) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  h->use_graphs = enable != 0;
   return FDTD_OK;
 }
 

@@ -95,6 +95,7 @@ SIGNATURES = [
     ("fdtd_synchronize", C.c_int, [_VP]),
     ("fdtd_set_check_interval", C.c_int, [_VP, C.c_int32]),
     ("fdtd_set_face_overlap", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_set_graphs", C.c_int, [_VP, C.c_int32]),
     ("fdtd_set_canaries", C.c_int, [_VP, C.c_int32]),
     ("fdtd_check_canaries", C.c_int, [_VP, C.POINTER(C.c_int64)]),
     ("fdtd_last_error", C.c_char_p, []),
@@ -311,6 +312,10 @@ class Solver:
     def fdtd_set_face_overlap(self, enable: bool):
         """Face copies beside the stencil kernels (True, for handles that solve repeatedly) or in line."""
         check(lib().fdtd_set_face_overlap(self.h, 1 if enable else 0))
+
+    def fdtd_set_graphs(self, enable: bool):
+        """Time loops captured into CUDA graphs (True, for repeated solves) or launched directly."""
+        check(lib().fdtd_set_graphs(self.h, 1 if enable else 0))
 
     def fdtd_set_canaries(self, enable: bool):
         """NaN canaries in the arrays' pitch padding (a debugging aid)."""

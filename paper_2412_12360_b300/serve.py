@@ -9,11 +9,10 @@ already running. Completion is detected with CUDA events; finished requests retu
 outputs and dL/deps and free their memory (stream-ordered, so other requests keep running), which
 admits the next ones.
 
-The numerical work of every request is the library's (one captured graph per sweep); a request's
-result does not depend on what else is in flight, so it is the same alone and in the mix. A request's
-handle solves once, so its face copies run in line (fdtd_set_face_overlap(0)): capturing them on a
-second stream shortens repeated solves but makes the graph of a single solve slower to build, which
-on one B300 cost the served stream 14 % (16.0 vs 13.8 Gcell-steps/s) and the sequential one 6 %.
+The numerical work of every request is the library's; a request's result does not depend on what
+else is in flight, so it is the same alone and in the mix. A request's handle solves once, so it runs
+its time loops as direct launches with the face copies in line (see one_shot), both here and in the
+sequential baseline.
 """
 from __future__ import annotations
 
@@ -25,6 +24,16 @@ from dataclasses import dataclass, field
 from typing import Deque, List, Optional
 
 import numpy as np
+
+
+def one_shot(solver):
+    """Configure a handle that solves once: time loops launched directly rather than captured into
+    CUDA graphs, face copies in line rather than on a second stream. Building the graphs of a single
+    solve costs more host time than replaying them saves; on one B300 the sequential stream of served
+    requests ran at 13.8 Gcell-steps/s with the library defaults, 14.7 with in-line face copies and
+    15.9 with direct launches as well (results bitwise the same)."""
+    solver.fdtd_set_graphs(False)
+    solver.fdtd_set_face_overlap(False)
 
 
 def admit_count(queue_footprints, inflight: int, used: int, budget: int, max_inflight: int) -> int:
@@ -73,13 +82,14 @@ class Server:
     """Continuous-batching solver service on one GPU.
 
     budget_bytes: device memory the server may give to requests (default: 85 % of the free memory).
-    max_inflight: requests running at once. More overlap is not always faster: on one B300 the served
-    stream of 64^3 .. 200^3 requests peaked at 3 (2: 15.3, 3: 15.9, 6: 15.6, 16: 13.6 Gcell-steps/s),
-    where the latency was also lowest after 2.
+    max_inflight: requests running at once. On one B300 the served stream of 64^3 .. 200^3 requests at
+    1.5x the sequential capacity ran at 16.1 Gcell-steps/s with 2, 3 or 4 in flight (the large grids,
+    most of the work, fill the GPU alone), with the lowest latency at 2 (p50 2.2 s, p99 3.5 s; 3: 2.5,
+    4.0 s).
     objective: dL/d(detector) used when a request gives none (default: ones, i.e. L = sum of outputs).
     """
 
-    def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 3, device: int = 0,
+    def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 2, device: int = 0,
                  footprint=None):
         import torch
         from . import fdtd
@@ -140,7 +150,7 @@ class Server:
         job.admitted = time.perf_counter()
         with torch.cuda.stream(job.stream):
             job.solver = fdtd.Solver(sc, stream=job.stream)
-            job.solver.fdtd_set_face_overlap(False)  # solves once: the smaller graph is built faster
+            one_shot(job.solver)
             job.solver.fdtd_forward(sc.nsteps, record_faces=True)
             ndet = job.solver.fdtd_detector_total()
             g = job.dL_ddet if job.dL_ddet is not None else np.ones(ndet)
@@ -214,7 +224,7 @@ def run_sequential(scenes, device: int = 0):
     out = []
     for sc in scenes:
         with fdtd.Solver(sc) as s:
-            s.fdtd_set_face_overlap(False)  # one solve per handle, as in the server
+            one_shot(s)  # one solve per handle, as in the server
             s.fdtd_forward(sc.nsteps, record_faces=True)
             det = s.detectors()
             grad = s.gradient(np.ones(s.fdtd_detector_total()))

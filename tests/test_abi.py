@@ -154,6 +154,7 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.fdtd_detector_size(None, 0) == F.FDTD_ERR_INVALID_ARG
     assert L.fdtd_fields(None, None) == F.FDTD_ERR_INVALID_ARG
     assert L.fdtd_set_face_overlap(None, 0) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_set_graphs(None, 0) == F.FDTD_ERR_INVALID_ARG
 
 
 def test_footprint_grows_with_steps_and_faces(L):

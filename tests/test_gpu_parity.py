@@ -343,18 +343,27 @@ def test_pitch_padding_canaries_stay_intact(F, scene):
 
 
 @pytest.mark.parametrize("scene", ["ragged", "tfsf_interp"])
-def test_face_copies_in_line_or_overlapped_give_the_same_results(F, scene):
+def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene):
+    """Face copies overlapped or in line, time loops captured into graphs or launched directly (with
+    the per-launch profiling events on): bitwise the same detectors, gradients and fields."""
     sc = ragged_scene(150) if scene == "ragged" else S.design_box_scene(
         (45, 38, 41), 6, 12, 150, 21, name="ovl", tfsf=True, interp=True)
     g = np.random.default_rng(13).standard_normal(O.detector_total(sc, sc.nsteps))
     out = []
-    for ovl in (True, False):
+    for ovl, graphs in ((True, True), (False, True), (True, False), (False, False)):
         with F.Solver(sc) as s:
             s.fdtd_set_face_overlap(ovl)
-            s.fdtd_forward(sc.nsteps, record_faces=True)
-            out.append((s.detectors(), s.gradient(g), s.fields()))
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+            s.fdtd_set_graphs(graphs)
+            s.fdtd_profile(True, 16)
+            for _ in range(2):  # the second solve replays (or relaunches) the loops
+                s.fdtd_forward(sc.nsteps, record_faces=True)
+                r = (s.detectors(), s.gradient(g), s.fields())
+            prof = s.fdtd_profile_read()
+        assert prof["fused_fwd"][1] > 0 and prof["rev_E"][1] > 0
+        out.append(r)
+    for o in out[1:]:
+        for a, b in zip(out[0], o):
+            assert np.array_equal(a, b)
 
 
 def test_state_errors_and_byte_budget(F):
