@@ -308,8 +308,8 @@ int fdtd_set_face_overlap(fdtd_handle* h, int32_t enable);
 int fdtd_set_graphs(fdtd_handle* h, int32_t enable);
 
 /* Non-finite field checks: every forward checks the fields after its last step, every backward the
- * rebuilt and the adjoint fields at its end (one read of the arrays, the sum of their squares in FP64
- * per thread, which is finite exactly when every value is). With every > 0 the forward also checks
+ * rebuilt and the adjoint fields at its end (one read of the arrays, testing the exponent bits of
+ * every value). With every > 0 the forward also checks
  * after every `every`-th step, so that a solve that has blown up is caught while it runs. The result
  * is reported by fdtd_synchronize. INVALID_ARG for NULL or every < 0. */
 int fdtd_set_check_interval(fdtd_handle* h, int32_t every);

@@ -171,24 +171,34 @@ __global__ void k_det_adjoint(Geo g, Fields F, Fields A, DetDev d, int step, con
 }
 
 // ---------------------------------------------------------------------------------------------
-// non-finite check: each thread sums the squares of its share of the grid cells of n floats (rows of
-// nxp floats, the first nx of them cells, the rest pitch padding) in FP64, an energy-like sum that
-// cannot overflow for float inputs, and flags the status word when its sum is not finite, which
-// happens exactly when one of its values is NaN or infinite. n and nxp are multiples of 4 and p is
-// 16-byte aligned (whole field arrays of pitch-padded planes), so a float4 never straddles two rows.
+// non-finite check of the grid cells of nrows rows of nxp floats (the first nx of them cells, the
+// rest pitch padding): a value is NaN or infinite exactly when its exponent bits are all ones, a test
+// on the bits (integer work, so the kernel runs at memory speed; the FP64 units of this part are far
+// too few for a per-value FP64 sum). A warp walks a row in float4 steps (nxp is a multiple of 32 and
+// p 16-byte aligned: whole field arrays of pitch-padded planes).
 // ---------------------------------------------------------------------------------------------
-__global__ void k_check_finite(const float4* __restrict__ p, int64_t n4, int nx, int nxp, int* status) {
+__device__ __forceinline__ unsigned nonfinite_bit(float v) {
+  return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u ? 1u : 0u;
+}
+
+__global__ void k_check_finite(const float4* __restrict__ p, int64_t nrows, int nx, int nxp, int* status) {
   pdl_wait();
-  double e = 0.0;
-  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n4; m += (int64_t)gridDim.x * blockDim.x) {
-    const float4 v = p[m];
-    const int x = (int)((4 * m) % nxp);  // column of v.x
-    if (x < nx) e += (double)v.x * v.x;
-    if (x + 1 < nx) e += (double)v.y * v.y;
-    if (x + 2 < nx) e += (double)v.z * v.z;
-    if (x + 3 < nx) e += (double)v.w * v.w;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5, nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int row4 = nxp / 4, nx4 = (nx + 3) / 4;
+  unsigned bad = 0;
+  for (int64_t r = w0; r < nrows; r += nw) {
+    const float4* row = p + r * row4;
+    for (int c = lane; c < nx4; c += 32) {
+      const float4 v = row[c];
+      const int x = 4 * c;
+      bad |= nonfinite_bit(v.x);  // x < nx: c < nx4
+      if (x + 1 < nx) bad |= nonfinite_bit(v.y);
+      if (x + 2 < nx) bad |= nonfinite_bit(v.z);
+      if (x + 3 < nx) bad |= nonfinite_bit(v.w);
+    }
   }
-  if (!isfinite(e)) atomicOr(status, kStatusNonFinite);
+  if (bad) atomicOr(status, kStatusNonFinite);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -331,10 +341,10 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
 
 void launch_check_finite(const Geo& g, const float* p, int64_t n, int* status, int nsm, cudaStream_t s) {
   if (n <= 0) return;
-  const int64_t n4 = n / 4;
-  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(n4, 256), 4 * (int64_t)nsm);
-  launch_pdl(k_check_finite, dim3(blocks), dim3(256), 0, s, reinterpret_cast<const float4*>(p), n4, g.n[0], g.nxp,
-             status);
+  const int64_t nrows = n / g.nxp;  // whole rows of the pitch-padded arrays
+  const unsigned blocks = (unsigned)std::min<int64_t>(blocks_for(nrows, 8), 8 * (int64_t)nsm);  // 8 warps a block
+  launch_pdl(k_check_finite, dim3(blocks), dim3(256), 0, s, reinterpret_cast<const float4*>(p), nrows, g.n[0],
+             g.nxp, status);
 }
 
 void launch_fill_padding(const Geo& g, float* base, int64_t nrows, int x0, float v, int nsm, cudaStream_t s) {
