@@ -406,7 +406,8 @@ def run_serve(args, world, rank, local):
     torch.cuda.set_device(local)
     rng = np.random.default_rng(7)
     ids = ranks.shard(args.serve_requests, world, rank)
-    all_scenes = [scenes.served_request(r, rng) for r in range(args.serve_requests)]
+    grids = scenes.SERVED_GRIDS if args.serve_grids == "mix" else scenes.SERVED_GRIDS[:2]
+    all_scenes = [scenes.served_request(r, rng, grids) for r in range(args.serve_requests)]
     mine = [all_scenes[r] for r in ids]
     cells = sum(sc.ncells * sc.nsteps for sc in mine)
     serve.run_sequential(mine[:1])                     # warm-up: library load, first captures
@@ -438,9 +439,10 @@ def run_serve(args, world, rank, local):
             "offered_load": args.serve_load, "slots": args.serve_slots, "peak_inflight": peak,
             "results_equal_alone_and_in_mix": bool(same), "higher_is_better": True, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "served stream: Poisson arrivals, grids {64^3, 96^3, 128x128x256, 200^3}, "
+            "config": {"workload": "served stream: Poisson arrivals, grids {%s}, "
                                    "1000-3000 steps, 10-cell CPML, random rho per request (seed 10000+id), "
-                                   "arrival seed 8, %d requests" % args.serve_requests}}
+                                   "arrival seed 8, %d requests"
+                                   % (", ".join("x".join(map(str, g)) for g in grids), args.serve_requests)}}
     print(json.dumps(line), flush=True)
 
 
@@ -689,6 +691,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="measure the continuous-batching server instead")
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serve-load", type=float, default=1.5, help="offered load / sequential capacity")
+    ap.add_argument("--serve-grids", choices=["mix", "small"], default="mix",
+                    help="served grids: the four-size mix, or only the 64^3 and 96^3 requests")
     ap.add_argument("--serve-slots", type=int, default=2,
                     help="requests in flight at once (on one B300, 2-4 gave the same throughput, 2 the lowest latency)")
     ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")

@@ -268,10 +268,13 @@ def waveguide_batch_member(b: int, nsteps: int = 3000, n=(240, 240, 960), design
     return waveguide_scene(n, 12, design, nsteps, 500 + b, 2, name="waveguide_batch_%d" % b)
 
 
-def served_request(req_id: int, rng: np.random.Generator) -> Scene:
-    """A served fwd+grad request: grid from {64^3, 96^3, 128x128x256, 200^3}, 1000-3000 steps,
-    10-cell CPML, design box of half the extent, rho seed 10000 + id."""
-    grids = [(64, 64, 64), (96, 96, 96), (128, 128, 256), (200, 200, 200)]
+SERVED_GRIDS = [(64, 64, 64), (96, 96, 96), (128, 128, 256), (200, 200, 200)]
+
+
+def served_request(req_id: int, rng: np.random.Generator, grids=None) -> Scene:
+    """A served fwd+grad request: grid drawn from `grids` (default {64^3, 96^3, 128x128x256, 200^3}),
+    1000-3000 steps, 10-cell CPML, design box of half the extent, rho seed 10000 + id."""
+    grids = SERVED_GRIDS if grids is None else grids
     n = grids[int(rng.integers(len(grids)))]
     nsteps = int(rng.integers(1000, 3001))
     design = min(n) // 2
