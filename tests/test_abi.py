@@ -106,6 +106,20 @@ def test_create_rejects_bad_input_before_any_device_work(L):
     assert rc == F.FDTD_ERR_INVALID_ARG and "design" in msg
 
 
+def test_create_rejects_grids_beyond_the_index_range(L):
+    """Per-array offsets are 32-bit: a grid whose pitch-padded field array reaches 2^31 cells, or an
+    axis outside [2, 65536], is refused before any device work."""
+    sc = S.cavity_32(10)
+    for n, what in (((2048, 1024, 1024), "2^31"), ((1, 32, 32), "range"), ((70000, 4, 4), "range")):
+        g = F.make_grid(n)
+        p = F.make_pml(sc)
+        eps = np.ones(1, dtype=np.float32)
+        h = C.c_void_p()
+        rc = F.lib().fdtd_create(C.byref(h), C.byref(g), 0.0, float(sc.courant), eps.ctypes.data, None, 0, None, 0,
+                                 C.byref(p), F._I3(0, 0, 0), F._I3(0, 0, 0), None)
+        assert rc == F.FDTD_ERR_INVALID_ARG and what in F.last_error(), (n, F.last_error())
+
+
 def test_create_rejects_bad_tfsf_and_interpolated_detectors(L):
     sc = S.cavity_32(10)
     design = ((10, 10, 10), (20, 20, 20))

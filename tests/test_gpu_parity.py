@@ -366,6 +366,52 @@ def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene):
             assert np.array_equal(a, b)
 
 
+def test_degenerate_solves(F):
+    """No sources (everything stays zero), no detectors (nothing to differentiate), an empty design box
+    (backward writes nothing), and the shortest solves (1 and 2 steps: the first reverse step's
+    detector adjoint by its own launch, the later ones folded into the reverse H kernel) against the
+    oracle."""
+    quiet = ragged_scene(50)
+    quiet.sources = []
+    with F.Solver(quiet) as s:
+        s.fdtd_forward(50, record_faces=True)
+        assert not np.any(s.fields()) and not np.any(s.detectors())
+        g = np.ones(O.detector_total(quiet, 50))
+        assert not np.any(s.gradient(g))
+    blind = ragged_scene(50)
+    blind.detectors = []
+    with F.Solver(blind) as s:
+        s.fdtd_forward(50, record_faces=True)
+        assert s.fdtd_detector_total() == 0
+        assert not np.any(s.gradient(np.zeros(0)))
+    nodesign = ragged_scene(50)
+    nodesign.design_lo = nodesign.design_hi = (30, 20, 20)
+    with F.Solver(nodesign) as s:
+        s.fdtd_forward(50, record_faces=True)
+        out = s.gradient(np.ones(O.detector_total(nodesign, 50)))
+        assert out.size == 0
+    for nsteps in (1, 2, 3):
+        sc = ragged_scene(nsteps)
+        # a source in the design box that is already on at the first steps, probes beside it
+        sc.sources = [H.point_source(S.EZ, (30, 20, 20), wavelength=4.0)]
+        sc.sources[0].t0_steps = 1.5
+        sc.detectors = [H.point_probe(S.EZ, (30, 20, 20)), H.point_probe(S.EX, (30, 20, 21)),
+                        S.Detector(S.DET_PLANE_E2_SUM, (26, 16, 20), (35, 25, 21)),
+                        S.Detector(S.DET_PLANE_FLUX, (26, 16, 21), (35, 25, 22), axis=2)]
+        g = np.random.default_rng(14).standard_normal(O.detector_total(sc, nsteps))
+        grad_o, _, det_o = O.gradient(sc, nsteps, g, O.METHOD_TIME_REVERSAL)
+        with F.Solver(sc) as s:
+            s.fdtd_forward(nsteps, record_faces=True)
+            det_g = s.detectors()
+            grad_g = s.gradient(g)
+        assert np.max(np.abs(det_o)) > 0, nsteps
+        assert rel_l2(det_g, det_o) < 1e-5, nsteps
+        if nsteps == 1:  # E^1 is the source alone (H^{1/2} = 0): nothing depends on eps yet
+            assert not np.any(grad_o) and not np.any(grad_g)
+        else:
+            assert np.max(np.abs(grad_o)) > 0 and rel_l2(grad_g, grad_o) < 1e-5, nsteps
+
+
 def test_state_errors_and_byte_budget(F):
     sc = S.cavity_32(20)
     with F.Solver(sc) as s:
