@@ -164,11 +164,13 @@ class Server:
             job.done.record(job.stream)
 
     def _retire(self, job: _Job):
-        job.solver.fdtd_synchronize()  # raises on a timeout or non-finite fields (the client gets it)
-        det = job.det.cpu().numpy()
-        grad = job.grad.cpu().numpy()
-        job.solver.close()
-        self._streams.append(job.stream)
+        try:
+            job.solver.fdtd_synchronize()  # raises on a timeout or non-finite fields (the client gets it)
+            det = job.det.cpu().numpy()
+            grad = job.grad.cpu().numpy()
+        finally:  # the request's memory and stream go back whatever happened
+            job.solver.close()
+            self._streams.append(job.stream)
         job.future.set_result(Result(det, grad, job.arrival, job.admitted, time.perf_counter()))
 
     def _loop(self):
