@@ -53,6 +53,7 @@ def lib():
         L.orc_forward.argtypes = [P(_Scene), C.c_int32, d, d, d]
         L.orc_roundtrip.argtypes = [P(_Scene), C.c_int32, d, d, d]
         L.orc_gradient.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, C.c_int32, d, d, d]
+        L.orc_gradient_from.argtypes = [P(_Scene), C.c_int32, d, d, C.c_int32, C.c_int32, d, d, d]
         L.orc_complex_step.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, P(C.c_int32), C.c_double, d]
         L.orc_cpml_tables.argtypes = [P(_Scene), C.c_int32, d]
         L.orc_sample.argtypes = [P(_Scene), d, d, d]
@@ -184,8 +185,9 @@ def roundtrip(scene, nsteps, init=None):
 METHOD_STORE_ALL, METHOD_CHECKPOINT, METHOD_TIME_REVERSAL = 0, 1, 2
 
 
-def gradient(scene, nsteps, dL_ddet, method=METHOD_TIME_REVERSAL, interval=16, full=False):
-    """dL/deps on the design box (shape (dz, dy, dx)) for L = sum(dL_ddet * detectors).
+def gradient(scene, nsteps, dL_ddet, method=METHOD_TIME_REVERSAL, interval=16, full=False, init=None):
+    """dL/deps on the design box (shape (dz, dy, dx)) for L = sum(dL_ddet * detectors), for the forward
+    from `init` (fields (6, nz, ny, nx): E^0, H^{-1/2}; None: zero fields).
 
     Returns (dL_deps, dL_da over the whole grid or None, detector vector).
     """
@@ -197,8 +199,9 @@ def gradient(scene, nsteps, dL_ddet, method=METHOD_TIME_REVERSAL, interval=16, f
     out = np.zeros(max(1, int(np.prod(a.design_shape()))))
     full_arr = np.zeros(a.N) if (full and method != METHOD_TIME_REVERSAL) else None
     det = np.zeros(max(1, ntot))
-    rc = lib().orc_gradient(a.ptr, int(nsteps), _dptr(g), int(method), int(interval), _dptr(out),
-                            _dptr(full_arr), _dptr(det))
+    init_arr = _fields_in(a, init)
+    rc = lib().orc_gradient_from(a.ptr, int(nsteps), _dptr(init_arr), _dptr(g), int(method), int(interval),
+                                 _dptr(out), _dptr(full_arr), _dptr(det))
     assert rc == 0
     dshape = a.design_shape()
     grad = out[: int(np.prod(dshape))].reshape(dshape)

@@ -813,14 +813,15 @@ int orc_roundtrip(const orc_scene* s, int32_t nsteps, const double* init6, doubl
   return 0;
 }
 
-// Reverse-mode gradient of L = sum(dL_ddet * detectors) with respect to eps on the design box.
+// Reverse-mode gradient of L = sum(dL_ddet * detectors) with respect to eps on the design box, for
+// the forward from init6 (E^0 then H^{-1/2}, 6*N values, or NULL for zero fields).
 //   method 0: store every state (tiny grids only)
 //   method 1: full-state checkpoint every `interval` steps, recompute each segment
 //   method 2: time reversal with face record and replay
 // dL_deps: design-box-shaped output (x fastest). dLda_full: optional N-sized dL/da (methods 0, 1).
 // det: optional detector outputs of the forward pass.
-int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int32_t method, int32_t interval,
-                 double* dL_deps, double* dLda_full, double* det) {
+int orc_gradient_from(const orc_scene* s, int32_t nsteps, const double* init6, const double* dL_ddet,
+                      int32_t method, int32_t interval, double* dL_deps, double* dLda_full, double* det) {
   Sim<double> sim(*s, nsteps);
   const size_t N = sim.g.N;
   std::vector<double> dLda(N, 0.0);
@@ -829,6 +830,7 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
   if (method == 0) {
     std::vector<State<double>> traj(nsteps + 1, State<double>(0));
     traj[0].resize(N);
+    sim.load_initial(traj[0], init6);
     for (int n = 0; n < nsteps; ++n) {
       traj[n + 1] = traj[n];
       sim.step(traj[n + 1], n, &d);
@@ -841,6 +843,7 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
     if (interval < 1) return -1;
     std::vector<State<double>> ckpt;
     State<double> st(N);
+    sim.load_initial(st, init6);
     for (int n = 0; n < nsteps; ++n) {
       if (n % interval == 0) ckpt.push_back(st);
       sim.step(st, n, &d);
@@ -860,6 +863,7 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
     }
   } else if (method == 2) {
     State<double> st(N);
+    sim.load_initial(st, init6);
     const auto fs = sim.face_set();
     std::vector<std::vector<double>> rec(nsteps);
     for (int n = 0; n < nsteps; ++n) {
@@ -888,6 +892,11 @@ int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int3
   finish_gradient(sim, dLda, dL_deps, (method == 2) ? nullptr : dLda_full);
   if (det) std::memcpy(det, d.data(), d.size() * sizeof(double));
   return 0;
+}
+
+int orc_gradient(const orc_scene* s, int32_t nsteps, const double* dL_ddet, int32_t method, int32_t interval,
+                 double* dL_deps, double* dLda_full, double* det) {
+  return orc_gradient_from(s, nsteps, nullptr, dL_ddet, method, interval, dL_deps, dLda_full, det);
 }
 
 // Complex-step derivative dL/deps at each listed voxel: eps_v -> eps_v + i h, one forward per voxel,
