@@ -4,8 +4,9 @@ design_96 (the bench workload: 96^3, 10-cell CPML, 40^3 design box, 2000 steps):
 plane and the whole dL/deps against the FP64 oracle. waveguide_600 (600^3, 216 M cells): properties
 that hold at any size, on the full grid for a shortened run: the fp32 time-reversal round trip
 returns to the (zero) initial state, and dL/drho agrees with a central difference along a uniform
-density shift. waveguide_600 and the 240x240x960 batch member: element-wise parity of fields, probe
-series and dL/deps at sampled points, from the oracle's solve of each point's light cone.
+density shift. waveguide_600, the 240x240x960 batch member and the two largest served grids:
+element-wise parity of fields, probe series and dL/deps at sampled points, from the oracle's solve
+of each point's light cone.
 """
 import numpy as np
 import pytest
@@ -75,7 +76,7 @@ def test_waveguide600_roundtrip_and_directional_derivative(cuda_ok):
     assert abs(fd - dd) <= 2e-2 * abs(dd)
 
 
-@pytest.mark.parametrize("config", ["waveguide_600", "waveguide_batch_member"])
+@pytest.mark.parametrize("config", ["waveguide_600", "waveguide_batch_member", "served_200", "served_128x128x256"])
 def test_full_size_light_cone_parity(cuda_ok, config):
     """Element-wise parity on the full grids of the large configurations, in the launch configuration
     the bench times (same grid, so the same tiles, z-chunks and stage rings): from a seeded random
@@ -93,9 +94,15 @@ def test_full_size_light_cone_parity(cuda_ok, config):
     if config == "waveguide_600":
         sc = S.waveguide_600(n_steps)
         probes = [(300, 300, 300), (64, 48, 60), (543, 561, 541)]
-    else:
+    elif config == "waveguide_batch_member":
         sc = S.waveguide_batch_member(0, n_steps)
         probes = [(120, 120, 480), (32, 64, 240), (207, 200, 928)]
+    elif config == "served_200":  # the largest grid of the served stream
+        sc = S.design_box_scene((200, 200, 200), 10, 100, n_steps, 10007)
+        probes = [(100, 100, 100), (32, 48, 30), (171, 160, 170)]
+    else:
+        sc = S.design_box_scene((128, 128, 256), 10, 64, n_steps, 10003)
+        probes = [(64, 64, 128), (96, 32, 40), (33, 96, 227)]
     nx, ny, nz = sc.n
     p = sc.pml
     for q in probes:  # the sub-boxes stay inside the PML-free region
