@@ -76,21 +76,85 @@ def test_waveguide600_roundtrip_and_directional_derivative(cuda_ok):
     assert abs(fd - dd) <= 2e-2 * abs(dd)
 
 
-@pytest.mark.parametrize("config", ["waveguide_600", "waveguide_batch_member", "served_200", "served_128x128x256"])
-def test_full_size_light_cone_parity(cuda_ok, config):
-    """Element-wise parity on the full grids of the large configurations, in the launch configuration
-    the bench times (same grid, so the same tiles, z-chunks and stage rings): from a seeded random
-    state on the PML-free region, n steps forward and the time-reversal gradient. In n steps a Yee
-    update moves information at most one cell per step, so the fields within r cells of a probe point
-    q, the probe's series and dL/deps on the box of radius r around q depend only on the state and the
-    permittivity within n + r cells of q (the adjoint of the probe reaches the box within n steps
-    too). The FP64 oracle solves that sub-box (PEC walls n + r + 3 cells away, too far to matter) from
-    the same state and gives those values exactly. Probe points sit on tile and z-chunk boundaries and
-    in the random-density design region."""
+def _window(sc, q, M):
+    """The sub-box of the cells within M of q, clipped to the grid, and its CPML: the grid's layer on
+    each face the sub-box shares with the grid (the graded coefficients depend only on the distance
+    to that face), none on the faces inside the grid (walls M cells from q, too far to matter)."""
+    lo = [max(0, q[d] - M) for d in range(3)]
+    hi = [min(sc.n[d], q[d] + M + 1) for d in range(3)]
+    pml = []
+    for d in range(3):
+        pml += [sc.pml[2 * d] if lo[d] == 0 else 0, sc.pml[2 * d + 1] if hi[d] == sc.n[d] else 0]
+    return lo, hi, tuple(pml)
+
+
+def _light_cone_check(sc, probes, n_steps, r, label):
+    """From a seeded random state on the PML-free region, n steps forward and the time-reversal
+    gradient on the full grid (the launch configuration of that grid). probes[0] carries a point
+    detector and the design box of radius r; every probe compares the fields of its block of radius
+    r. In n steps a Yee update moves information at most one cell per step, so those values depend
+    only on the state, the permittivity and the CPML within n + r cells of the probe: the FP64
+    oracle's solve of that window from the same state gives them exactly."""
     import torch
     from paper_2412_12360_b300 import fdtd
-    n_steps, r = 12, 3
     M = n_steps + r + 3
+    nx, ny, nz = sc.n
+    p = sc.pml
+    q0 = probes[0]
+    for d in range(3):  # the detector and the design box lie in the PML-free region
+        assert p[2 * d] <= q0[d] - r and q0[d] + r < sc.n[d] - p[2 * d + 1]
+    sc.sources = []
+    sc.detectors = [S.Detector(S.DET_POINT_SERIES, q0, tuple(v + 1 for v in q0), component=S.EZ)]
+    sc.design_lo = tuple(v - r for v in q0)
+    sc.design_hi = tuple(v + r + 1 for v in q0)
+    dev = torch.device("cuda")
+    gen = torch.Generator(device=dev).manual_seed(77)
+    init = torch.zeros((6, nz, ny, nx), dtype=torch.float32, device=dev)
+    init[:, p[4]:nz - p[5], p[2]:ny - p[3], p[0]:nx - p[1]] = (
+        2 * torch.rand((6, nz - p[4] - p[5], ny - p[2] - p[3], nx - p[0] - p[1]), generator=gen, device=dev) - 1)
+    g = np.random.default_rng(78).standard_normal(n_steps)
+    fields = torch.empty_like(init)
+    with fdtd.Solver(sc) as s:
+        s.fdtd_set_initial_fields(init)
+        s.fdtd_forward(n_steps, record_faces=True)
+        s.fdtd_get_fields(fields)
+        det_g = s.detectors()
+        grad_g = s.gradient(g)
+    for qi, q in enumerate(probes):
+        lo, hi, pm = _window(sc, q, M)
+        sl = (slice(None),) + tuple(slice(lo[d], hi[d]) for d in (2, 1, 0))
+        c = tuple(q[d] - lo[d] for d in range(3))
+        nsub = tuple(hi[d] - lo[d] for d in range(3))
+        extra = {}
+        if qi == 0:
+            extra = dict(detectors=[S.Detector(S.DET_POINT_SERIES, c, tuple(v + 1 for v in c), component=S.EZ)],
+                         design=(tuple(v - r for v in c), tuple(v + r + 1 for v in c)))
+        sub = H.box_scene(nsub, pml=pm, eps_inv=np.ascontiguousarray(sc.eps_inv[sl[1:]]), courant=sc.courant,
+                          sigma_max=sc.sigma_max, nsteps=n_steps, **extra)
+        sub_init = init[sl].double().cpu().numpy()
+        f_o, _ = O.forward(sub, n_steps, init=sub_init)
+        bl = [(max(0, c[d] - r), min(nsub[d], c[d] + r + 1)) for d in range(3)]
+        blk = (slice(None),) + tuple(slice(*bl[d]) for d in (2, 1, 0))
+        gblk = (slice(None),) + tuple(slice(bl[d][0] + lo[d], bl[d][1] + lo[d]) for d in (2, 1, 0))
+        f_g = fields[gblk].double().cpu().numpy()
+        e_f = float(np.max(np.abs(f_g - f_o[blk])) / np.max(np.abs(f_o[blk])))
+        msg = "%s probe %s (window CPML %s): fields %.2e" % (label, q, pm, e_f)
+        if qi == 0:
+            grad_o, _, det_o = O.gradient(sub, n_steps, g, O.METHOD_STORE_ALL, init=sub_init)
+            e_d = float(np.max(np.abs(det_g - det_o)) / np.max(np.abs(det_o)))
+            e_g = rel(grad_g, grad_o)
+            msg += ", probe series %.2e, dL/deps %.2e" % (e_d, e_g)
+            assert e_d < 1e-5 and e_g < 1e-4, msg
+        print(msg)
+        assert e_f < 1e-5, msg
+
+
+@pytest.mark.parametrize("config", ["waveguide_600", "waveguide_batch_member", "served_200", "served_128x128x256"])
+def test_full_size_light_cone_parity(cuda_ok, config):
+    """Element-wise parity on the full grids of the large configurations, in their launch
+    configurations (same grid, so the same tiles, z-chunks and stage rings): probe points inside the
+    PML-free region on tile and z-chunk boundaries and in the random-density design region."""
+    n_steps, r = 12, 3
     if config == "waveguide_600":
         sc = S.waveguide_600(n_steps)
         probes = [(300, 300, 300), (64, 48, 60), (543, 561, 541)]
@@ -103,51 +167,19 @@ def test_full_size_light_cone_parity(cuda_ok, config):
     else:
         sc = S.design_box_scene((128, 128, 256), 10, 64, n_steps, 10003)
         probes = [(64, 64, 128), (96, 32, 40), (33, 96, 227)]
-    nx, ny, nz = sc.n
-    p = sc.pml
-    for q in probes:  # the sub-boxes stay inside the PML-free region
-        for d in range(3):
-            assert p[2 * d] <= q[d] - M and q[d] + M < sc.n[d] - p[2 * d + 1], (q, d)
-    q0 = probes[0]
-    sc.sources = []
-    sc.detectors = [S.Detector(S.DET_POINT_SERIES, q, tuple(v + 1 for v in q), component=S.EZ) for q in probes]
-    sc.design_lo = tuple(v - r for v in q0)
-    sc.design_hi = tuple(v + r + 1 for v in q0)
-    dev = torch.device("cuda")
-    gen = torch.Generator(device=dev).manual_seed(77)
-    init = torch.zeros((6, nz, ny, nx), dtype=torch.float32, device=dev)
-    init[:, p[4]:nz - p[5], p[2]:ny - p[3], p[0]:nx - p[1]] = (
-        2 * torch.rand((6, nz - p[4] - p[5], ny - p[2] - p[3], nx - p[0] - p[1]), generator=gen, device=dev) - 1)
-    g = np.random.default_rng(78).standard_normal(len(probes) * n_steps)
-    fields = torch.empty_like(init)
-    with fdtd.Solver(sc) as s:
-        s.fdtd_set_initial_fields(init)
-        s.fdtd_forward(n_steps, record_faces=True)
-        s.fdtd_get_fields(fields)
-        det_g = s.detectors()
-        grad_g = s.gradient(g)
-    for qi, q in enumerate(probes):
-        lo = [v - M for v in q]
-        sl = (slice(None), slice(lo[2], lo[2] + 2 * M + 1), slice(lo[1], lo[1] + 2 * M + 1),
-              slice(lo[0], lo[0] + 2 * M + 1))
-        sub_init = init[sl].double().cpu().numpy()
-        eps_sub = np.ascontiguousarray(sc.eps_inv[sl[1:]])
-        c = (M, M, M)
-        sub = H.box_scene((2 * M + 1,) * 3, eps_inv=eps_sub, courant=sc.courant,
-                          detectors=[S.Detector(S.DET_POINT_SERIES, c, (M + 1,) * 3, component=S.EZ)],
-                          design=((M - r,) * 3, (M + r + 1,) * 3), nsteps=n_steps)
-        g_sub = g[qi * n_steps:(qi + 1) * n_steps]
-        grad_o, _, det_o = O.gradient(sub, n_steps, g_sub, O.METHOD_STORE_ALL, init=sub_init)
-        f_o, _ = O.forward(sub, n_steps, init=sub_init)
-        blk = (slice(None), slice(M - r, M + r + 1), slice(M - r, M + r + 1), slice(M - r, M + r + 1))
-        f_g = fields[(slice(None), slice(q[2] - r, q[2] + r + 1), slice(q[1] - r, q[1] + r + 1),
-                      slice(q[0] - r, q[0] + r + 1))].double().cpu().numpy()
-        e_f = float(np.max(np.abs(f_g - f_o[blk])) / np.max(np.abs(f_o[blk])))
-        e_d = float(np.max(np.abs(det_g[qi * n_steps:(qi + 1) * n_steps] - det_o)) / np.max(np.abs(det_o)))
-        msg = "%s probe %s: fields %.2e, probe series %.2e" % (config, q, e_f, e_d)
-        if qi == 0:
-            e_g = rel(grad_g, grad_o)
-            msg += ", dL/deps %.2e" % e_g
-            assert e_g < 1e-4, msg
-        print(msg)
-        assert e_f < 1e-5 and e_d < 1e-5, msg
+    _light_cone_check(sc, probes, n_steps, r, config)
+
+
+@pytest.mark.parametrize("config", ["waveguide_600", "served_200"])
+def test_full_size_light_cone_parity_in_the_cpml(cuda_ok, config):
+    """The same at probes in the CPML layers (faces, an edge, a corner) and at a detector and design box
+    next to a layer, so that the adjoint sweep runs through it: the windows reach the grid's faces and
+    carry the layers of those faces."""
+    n_steps, r = 12, 3
+    if config == "waveguide_600":
+        sc = S.waveguide_600(n_steps)
+        probes = [(16, 300, 300), (6, 6, 6), (593, 300, 580), (300, 590, 300), (300, 300, 595)]
+    else:
+        sc = S.design_box_scene((200, 200, 200), 10, 100, n_steps, 10007)
+        probes = [(186, 100, 13), (3, 100, 100), (197, 197, 5), (100, 192, 100), (50, 4, 196)]
+    _light_cone_check(sc, probes, n_steps, r, config + "_cpml")
