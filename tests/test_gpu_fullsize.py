@@ -4,7 +4,8 @@ design_96 (the bench workload: 96^3, 10-cell CPML, 40^3 design box, 2000 steps):
 plane and the whole dL/deps against the FP64 oracle. waveguide_600 (600^3, 216 M cells): properties
 that hold at any size, on the full grid for a shortened run: the fp32 time-reversal round trip
 returns to the (zero) initial state, and dL/drho agrees with a central difference along a uniform
-density shift. waveguide_600, the 240x240x960 batch member and the two largest served grids:
+density shift. design_96_tfsf and design_96_interp (400 steps): detectors and dL/deps against the
+oracle. waveguide_600, the 240x240x960 batch member and the two largest served grids:
 element-wise parity of fields, probe series and dL/deps at sampled points, from the oracle's solve
 of each point's light cone.
 """
@@ -74,6 +75,28 @@ def test_waveguide600_roundtrip_and_directional_derivative(cuda_ok):
     fd = (L[0] - L[1]) / (2 * delta)
     print("600^3 directional derivative: adjoint %.6e, central difference %.6e" % (dd, fd))
     assert abs(fd - dd) <= 2e-2 * abs(dd)
+
+
+@pytest.mark.parametrize("variant", ["tfsf", "interp"])
+def test_design96_variants_match_oracle(cuda_ok, variant):
+    """The bench's design_96_tfsf and design_96_interp workloads (the same 96^3 grid and launch
+    configuration), shortened to 400 steps so that the beam has crossed the detector plane: the
+    whole detector output and dL/deps against the FP64 oracle."""
+    from paper_2412_12360_b300 import fdtd
+    nsteps = 400
+    sc = S.design_box_scene((96, 96, 96), 10, 40, nsteps, 1234, 1.0, 12.1, 20.0, "design_96_" + variant,
+                            tfsf=variant == "tfsf", interp=variant == "interp")
+    g = np.random.default_rng(79).standard_normal(O.detector_total(sc, nsteps))
+    grad_o, _, det_o = O.gradient(sc, nsteps, g, O.METHOD_TIME_REVERSAL)
+    with fdtd.Solver(sc) as s:
+        s.fdtd_forward(nsteps, record_faces=True)
+        det_g = s.detectors()
+        grad_g = s.gradient(g)
+    e_det, e_grad = rel(det_g, det_o), rel(grad_g, grad_o)
+    print("design_96_%s %d steps: detector rel L2 %.2e, dL/deps rel L2 %.2e" % (variant, nsteps, e_det, e_grad))
+    assert np.max(np.abs(det_o)) > 0 and np.max(np.abs(grad_o)) > 0
+    assert e_det < 1e-4
+    assert e_grad < 1e-3
 
 
 def _window(sc, q, M):
