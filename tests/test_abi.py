@@ -182,3 +182,20 @@ def test_footprint_grows_with_steps_and_faces(L):
     assert f2 - f1 == 2000 * per_step
     # fields (6) + a + adjoint fields (6), each 96^3 fp32 (pitch 96)
     assert f0 >= 13 * 96 ** 3 * 4
+
+
+def test_missing_library_fails_loudly():
+    """Without the built library the binding raises at first use: there is no CPU fallback."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2412_12360_b300 import fdtd, scenes\n"
+            "fdtd.LIB_PATH = '/nonexistent/libfdtd.so'\n"
+            "try:\n"
+            "    fdtd.Solver(scenes.cavity_32(10))\n"
+            "except ImportError as e:\n"
+            "    print('raised:', e)\n"
+            "    sys.exit(0)\n"
+            "sys.exit(3)\n") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "not built" in r.stdout, (r.returncode, r.stdout, r.stderr)
