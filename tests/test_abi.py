@@ -199,3 +199,21 @@ def test_missing_library_fails_loudly():
             "sys.exit(3)\n") % ROOT
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "not built" in r.stdout, (r.returncode, r.stdout, r.stderr)
+
+
+def test_product_and_oracle_are_separate():
+    """The product package and the CUDA library neither import nor include the oracle, and the oracle
+    neither imports nor includes the product (the seeded input builders in scenes.py hold no method
+    arithmetic and are the one module both use)."""
+    pkg = os.path.join(ROOT, "paper_2412_12360_b300")
+    product = glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*.*")) + \
+        glob.glob(os.path.join(ROOT, "include", "*.h"))
+    for f in product:
+        text = open(f).read()
+        assert not re.search(r"^\s*(from|import)\s+oracle\b|#include\s*[<\"].*oracle", text, re.M), f
+    for f in glob.glob(os.path.join(ROOT, "oracle", "*.*")):
+        if not f.endswith((".py", ".cpp", ".h", ".c")):
+            continue
+        text = open(f).read()
+        assert not re.search(r"paper_2412_12360_b300\.(fdtd|serve|autograd|design|ranks)|csrc|fdtd_internal|libfdtd",
+                             text), f
