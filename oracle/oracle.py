@@ -40,26 +40,31 @@ class _Scene(C.Structure):
 _LIB = None
 
 
+def load(path):
+    """The oracle library at `path` with its entry points typed (lib() loads the built one)."""
+    L = C.CDLL(path)
+    P = C.POINTER
+    d = P(C.c_double)
+    L.orc_detector_total.argtypes = [P(_Scene), C.c_int32]
+    L.orc_detector_total.restype = C.c_int64
+    L.orc_face_count.argtypes = [P(_Scene)]
+    L.orc_face_count.restype = C.c_int64
+    L.orc_forward.argtypes = [P(_Scene), C.c_int32, d, d, d]
+    L.orc_roundtrip.argtypes = [P(_Scene), C.c_int32, d, d, d]
+    L.orc_gradient.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, C.c_int32, d, d, d]
+    L.orc_gradient_from.argtypes = [P(_Scene), C.c_int32, d, d, C.c_int32, C.c_int32, d, d, d]
+    L.orc_complex_step.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, P(C.c_int32), C.c_double, d]
+    L.orc_cpml_tables.argtypes = [P(_Scene), C.c_int32, d]
+    L.orc_sample.argtypes = [P(_Scene), d, d, d]
+    L.orc_waveform.argtypes = [P(_Scene), C.c_int32, C.c_double]
+    L.orc_waveform.restype = C.c_double
+    return L
+
+
 def lib():
     global _LIB
     if _LIB is None:
-        L = C.CDLL(_build.build())
-        P = C.POINTER
-        d = P(C.c_double)
-        L.orc_detector_total.argtypes = [P(_Scene), C.c_int32]
-        L.orc_detector_total.restype = C.c_int64
-        L.orc_face_count.argtypes = [P(_Scene)]
-        L.orc_face_count.restype = C.c_int64
-        L.orc_forward.argtypes = [P(_Scene), C.c_int32, d, d, d]
-        L.orc_roundtrip.argtypes = [P(_Scene), C.c_int32, d, d, d]
-        L.orc_gradient.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, C.c_int32, d, d, d]
-        L.orc_gradient_from.argtypes = [P(_Scene), C.c_int32, d, d, C.c_int32, C.c_int32, d, d, d]
-        L.orc_complex_step.argtypes = [P(_Scene), C.c_int32, d, C.c_int32, P(C.c_int32), C.c_double, d]
-        L.orc_cpml_tables.argtypes = [P(_Scene), C.c_int32, d]
-        L.orc_sample.argtypes = [P(_Scene), d, d, d]
-        L.orc_waveform.argtypes = [P(_Scene), C.c_int32, C.c_double]
-        L.orc_waveform.restype = C.c_double
-        _LIB = L
+        _LIB = load(_build.build())
     return _LIB
 
 

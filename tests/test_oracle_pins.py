@@ -480,13 +480,45 @@ def _cpml_probe(nz, pml_hi_z, nsteps):
     return O.forward(sc, nsteps)[1]
 
 
-def test_cpml_reflection_below_minus_40_db():
-    nsteps = 200
+# The reflection bar: the oracle's polynomial-graded CPML (m = 3, kappa_max = 1, alpha_max = 0,
+# sigma_max = 0.8 (m + 1) S) measures -76 dB on this probe; a grading error that every face shares
+# (so that mirror symmetry and GPU parity cannot see it) raises it above -65 dB.
+CPML_BAR_DB = -65.0
+
+
+def _cpml_reflection_db(nsteps=200):
     ref = _cpml_probe(32 + 96, 8, nsteps)          # far boundary: its echo arrives after the window
     short = _cpml_probe(32, 8, nsteps)             # CPML 3 cells beyond the probe
+    return 20 * math.log10(np.max(np.abs(short - ref)) / np.max(np.abs(ref)))
+
+
+def test_cpml_reflection_below_minus_65_db():
+    nsteps = 200
+    ref = _cpml_probe(32 + 96, 8, nsteps)
     pec = _cpml_probe(32, 0, nsteps)               # same domain closed by PEC: strong reflection
-    peak = np.max(np.abs(ref))
-    r_cpml = np.max(np.abs(short - ref)) / peak
-    r_pec = np.max(np.abs(pec - ref)) / peak
+    r_pec = np.max(np.abs(pec - ref)) / np.max(np.abs(ref))
     assert r_pec > 0.1
-    assert r_cpml < 1e-2, 20 * math.log10(r_cpml)
+    db = _cpml_reflection_db(nsteps)
+    assert db < CPML_BAR_DB, db
+
+
+@pytest.mark.parametrize("plant", ["swap_integer_and_half_tables", "depth_from_the_wrong_plane"])
+def test_cpml_bar_fails_planted_grading_errors(plant, tmp_path, monkeypatch):
+    """The reflection bar bites: a copy of the oracle with a grading error planted on every face
+    (the integer- and half-position tables exchanged, or the depth counted from one cell outside the
+    interface) fails it, while both sides of the comparison use the same planted copy."""
+    from oracle import build as OB
+    src = open(OB.SRC).read()
+    if plant == "swap_integer_and_half_tables":
+        bad = src.replace("grade(s, d, double(i), a.b_int[i]", "grade(s, d, i + 0.5, a.b_int[i]")
+        bad = bad.replace("grade(s, d, i + 0.5, a.b_half[i]", "grade(s, d, double(i), a.b_half[i]")
+    else:
+        bad = src.replace("d = (p0 - x) / p0;", "d = (p0 - 1 - x) / p0;")
+        bad = bad.replace("d = (x - (N - p1)) / p1;", "d = (x + 1 - (N - p1)) / p1;")
+    assert bad != src
+    cpp = tmp_path / "planted.cpp"
+    cpp.write_text(bad)
+    lib = OB.compile_source(str(cpp), str(tmp_path / "planted.so"))
+    monkeypatch.setattr(O, "_LIB", O.load(lib))
+    db = _cpml_reflection_db()
+    assert db > CPML_BAR_DB, (plant, db)
