@@ -269,20 +269,22 @@ int fdtd_release_history(fdtd_handle* h);
 
 /* Allocation-free Poynting flux: out = sum over the cell box [lo, hi) of (E x H)[axis] for the fields
  * the caller passes. The paper has no counterpart; this is a library utility for callers that cannot
- * call cudaMalloc (code running while a CUDA graph is captured, hosts that give the library a fixed
- * memory budget, real-time loops that must not stall on an allocation). It allocates nothing: its
- * partial sums live in a fixed device array of 1024 doubles that the library reserves when it is
- * loaded and that every GPU that loads the library keeps until the process exits, so a box may hold
- * at most 4194304 cells (larger boxes give INVALID_ARG). The sum is the same fixed-order two-pass
- * reduction as the solver's flux detector (per-block double partial sums, then one ordered sum).
- *   fields6: device, 6*nx*ny*nz floats (Ex..Hz, field-major, x fastest, no row pitch: the layout
- *            fdtd_get_fields writes); not modified.
- *   out:     device, one double, written.
+ * call cudaMalloc (hosts that give the library a fixed memory budget, real-time loops that must not
+ * stall on an allocation). It allocates nothing: its partial sums live in a fixed device array of
+ * 1024 doubles that the library reserves when it is loaded and that every GPU that loads the library
+ * keeps until the process exits, so a box may hold at most 4194304 cells (larger boxes give
+ * INVALID_ARG). The sum is a fixed-order two-pass FP64 reduction (per-block partial sums, then one
+ * ordered sum): deterministic from call to call, equal to the solver's flux detector to rounding.
+ *   fields6: device memory of the current device, 6*nx*ny*nz floats (Ex..Hz, field-major, x fastest,
+ *            no row pitch: the layout fdtd_get_fields writes); not modified.
+ *   out:     device memory of the current device, one double, written.
+ * A host pointer or another GPU's buffer gives INVALID_ARG before anything is launched.
  * Work is enqueued on cuda_stream (NULL = legacy default stream); the call does not synchronise.
- * The first call on a device looks up the array's device address with that device current: make
- * that first call before any stream capture. Every call shares the array, so calls whose GPU work
- * overlaps (other streams, other host threads) race and can return wrong sums: serialise them.
- * Each call writes every partial sum it reads, so the array needs no clearing. */
+ * The first call on a device looks up the array's device address with that device current and keeps
+ * it for the life of the process (a cudaDeviceReset after that is not supported). Every call shares
+ * the array, so calls whose GPU work overlaps (other streams, other host threads) race and can
+ * return wrong sums: serialise them. Each call writes every partial sum it reads, so the array
+ * needs no clearing. */
 int fdtd_plane_flux_noalloc(const float* fields6, const fdtd_grid* grid, int32_t axis, const int32_t lo[3],
                             const int32_t hi[3], double* out, void* cuda_stream);
 

@@ -304,6 +304,16 @@ int fdtd::set_error(int code, const char* msg) {
   return code;
 }
 
+bool fdtd::on_current_device(const void* p) {
+  int dev = -1;
+  cudaPointerAttributes at;
+  if (!p || cudaGetDevice(&dev) != cudaSuccess || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 struct fdtd_handle {
   Geo g{};
   fdtd_pml pml{};

@@ -216,4 +216,8 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // Record `msg` as the calling thread's last error (fdtd_last_error) and return `code`.
 int set_error(int code, const char* msg);
 
+// Whether p points to device or managed memory of the current CUDA device (false for host memory,
+// another GPU's memory, or when no device can be queried).
+bool on_current_device(const void* p);
+
 }  // namespace fdtd

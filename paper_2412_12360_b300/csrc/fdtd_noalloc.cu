@@ -1,10 +1,11 @@
 // Poynting flux of caller-provided fields through a cell box, computed without allocating memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being captured, hosts that
-// hand the library a fixed memory budget up front, or real-time loops where an allocation may stall.
-// This entry point runs the same two-pass, fixed-order reduction as the flux detector of the solver
-// (per-block double partial sums, then one ordered sum), but keeps the partial sums in a fixed array
-// in device memory that the library reserves when it is loaded, instead of scratch it allocates.
+// Some callers cannot call cudaMalloc: hosts that hand the library a fixed memory budget up front,
+// or real-time loops where an allocation may stall. This entry point computes the flux with a
+// two-pass, fixed-order FP64 reduction (per-block partial sums, then one ordered sum: deterministic
+// from call to call, equal to the solver's flux detector to rounding), but keeps the partial sums in
+// a fixed array in device memory that the library reserves when it is loaded, instead of scratch it
+// allocates.
 //
 // The array holds kMaxSlots partial sums (8 KiB); every GPU that loads the library keeps it until the
 // process exits. Each block reduces kCellsPerBlock cells, so a box may hold at most
@@ -64,7 +65,9 @@ __global__ void k_flux_sum(const double* __restrict__ slots, int nslots, double*
   *out = s;
 }
 
-// Device address of the slot array on the current device, looked up once per device.
+// Device address of the slot array on the current device, looked up once per device and kept for the
+// life of the process (a cudaDeviceReset after the first call is not supported: the address would
+// be stale).
 int slot_address(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
@@ -102,6 +105,11 @@ extern "C" int fdtd_plane_flux_noalloc(const float* fields6, const fdtd_grid* gr
   if (nslots > kMaxSlots)
     return fdtd::set_error(FDTD_ERR_INVALID_ARG,
                            "fdtd_plane_flux_noalloc: box exceeds the 4194304-cell maximum of the fixed scratch");
+  // both buffers must be device (or managed) memory of the current device: a host pointer or another
+  // GPU's buffer is refused before anything is launched
+  if (!fdtd::on_current_device(fields6) || !fdtd::on_current_device(out))
+    return fdtd::set_error(FDTD_ERR_INVALID_ARG,
+                           "fdtd_plane_flux_noalloc: fields6 and out must be device memory of the current device");
   double* slots = nullptr;
   const int rc = slot_address(&slots);
   if (rc != FDTD_OK) return rc;

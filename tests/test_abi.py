@@ -171,6 +171,19 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.fdtd_set_graphs(None, 0) == F.FDTD_ERR_INVALID_ARG
 
 
+def test_noalloc_flux_refuses_host_buffers_before_any_launch(L):
+    """The allocation-free flux call takes device memory of the current device only: host buffers (or,
+    with no GPU, anything) are refused with INVALID_ARG before a kernel is launched."""
+    grid = F.make_grid((4, 4, 4))
+    fields = np.zeros(6 * 64, dtype=np.float32)
+    out = np.zeros(1, dtype=np.float64)
+    rc = L.fdtd_plane_flux_noalloc(fields.ctypes.data, C.byref(grid), 2, F._I3(0, 0, 1), F._I3(4, 4, 2),
+                                   out.ctypes.data, None)
+    assert rc == F.FDTD_ERR_INVALID_ARG
+    assert "device memory" in F.last_error()
+    assert out[0] == 0.0
+
+
 def test_footprint_grows_with_steps_and_faces(L):
     sc = S.design_96(2000)
     f0 = F.footprint_bytes(sc, 2000, record_faces=False)

@@ -103,3 +103,34 @@ def test_autograd_density_gradient_matches_oracle(cuda_ok, mode):
         assert np.linalg.norm(det[b].detach().cpu().numpy() - det_o) / np.linalg.norm(det_o) < 1e-4
     for s in solvers:
         s.close()
+
+
+def test_autograd_orders_solver_streams_against_torch_streams(cuda_ok):
+    """Solvers on streams of their own, the call made under another torch stream: the inputs are
+    produced on torch's current stream right before the call and the loss reads the outputs right
+    after it, so a missing ordering between the streams would show as wrong values."""
+    import torch
+    from paper_2412_12360_b300 import autograd, fdtd
+    scenes = [S.design_box_scene((40, 36, 44), 6, 12, 160, 31 + b, name="as%d" % b) for b in range(2)]
+    eps_lo, eps_hi = scenes[0].extra["eps_lo"], scenes[0].extra["eps_hi"]
+    solver_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    solvers = [fdtd.Solver(sc, stream=st) for sc, st in zip(scenes, solver_streams)]
+    caller = torch.cuda.Stream()
+    rho0 = torch.stack([torch.from_numpy(sc.extra["rho"]) for sc in scenes]).cuda()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(caller):
+        big = torch.empty(64 * 1024 * 1024, device="cuda").uniform_()   # keeps the caller's stream busy
+        rho = (rho0 + 0.0 * big[: rho0.numel()].view_as(rho0)).requires_grad_(True)
+        det = autograd.solve(rho, solvers, eps_lo, eps_hi, 160, "keep")
+        w = torch.linspace(0.5, 1.5, det.shape[1], dtype=torch.float64, device="cuda")
+        loss = (det * w).sum()
+        loss.backward()
+    torch.cuda.synchronize()
+    grad = rho.grad.cpu().numpy()
+    for b, sc in enumerate(scenes):
+        grad_o, _, det_o = O.gradient(sc, 160, w.cpu().numpy(), O.METHOD_TIME_REVERSAL)
+        ref = (eps_hi - eps_lo) * grad_o
+        assert np.linalg.norm(grad[b] - ref) / np.linalg.norm(ref) < 1e-3
+        assert np.linalg.norm(det[b].detach().cpu().numpy() - det_o) / np.linalg.norm(det_o) < 1e-4
+    for s in solvers:
+        s.close()

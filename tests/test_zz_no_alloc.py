@@ -1,6 +1,6 @@
 """The allocation-free flux entry point (fdtd_plane_flux_noalloc) against the solver's flux detector.
 
-Callers that cannot allocate device memory (graph capture, fixed budgets, real-time loops) use
+Callers that cannot allocate device memory (a fixed memory budget, real-time loops) use
 fdtd_plane_flux_noalloc, whose scratch is a fixed array reserved at load time. Its result must
 match the existing path: the flux detector of fdtd_forward, whose last sample is the flux of the
 final fields. This file is named to be collected last.
