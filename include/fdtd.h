@@ -242,7 +242,9 @@ int fdtd_set_byte_budget(int64_t bytes);
 #define FDTD_KERNEL_FUSED_REV 5    /* reverse step in one sweep */
 #define FDTD_KERNEL_FACE_COPY 6    /* boundary-face record (forward) or replay (reverse) of one step */
 #define FDTD_KERNEL_DET_ADJ 7      /* detector adjoints of one reverse step */
-#define FDTD_KERNEL_KINDS 8
+#define FDTD_KERNEL_INV_FUSED 8    /* reverse: inverse E and H of one step in one sweep, and dL/da */
+#define FDTD_KERNEL_ADJ_FUSED 9    /* reverse: adjoint of one step (Hbar then Ebar) in one sweep */
+#define FDTD_KERNEL_KINDS 10
 
 /* Number of kernels this handle has launched since creation (or -1). */
 int64_t fdtd_launch_count(fdtd_handle* h);

@@ -329,8 +329,10 @@ struct fdtd_handle {
   FaceSet faces{};
   int tz = 8;                     // z-planes per block of the forward kernel
   int tz_rev = 8;                 // z-planes per block of the reverse kernels
-  int rev_nstage = 4;             // stages of the reverse kernels' plane rings
+  int rev_nstage = 4;             // stages of the reverse kernels' plane rings (checkpointing gradient)
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
+  int tz_inv = 8, inv_nstage = 4; // fused inverse step: z-planes per block, ring stages
+  int tz_adj = 8, adj_nstage = 4; // fused adjoint step
 
   std::vector<fdtd_source> src_host;
   std::vector<SrcDev> srcs;       // E sources: soft sources and the E corrections of TFSF planes
@@ -360,7 +362,8 @@ struct fdtd_handle {
   int64_t partial_cap = 0;
   float* face_hist = nullptr;  // steps x faces.per_step
   int64_t face_cap_steps = 0;
-  float* adj = nullptr;        // 6 x vol adjoint fields
+  float* adj = nullptr;        // 2 x 6 x vol adjoint fields, double-buffered (the fused adjoint step reads
+                               // one and writes the other; the checkpointing gradient uses buffer 0)
   float* psibar = nullptr;     // 2 buffers x (psi-bar E + psi-bar H)
   double* dLda = nullptr;      // design box
   double* dLddet = nullptr;    // device copy of dL/d(detectors)
@@ -368,7 +371,9 @@ struct fdtd_handle {
   float* staging = nullptr;    // 6 x N, unpitched
   int* status = nullptr;       // device status word written by the kernels (bounded waits)
   FwdMaps fmaps[2];            // TMA maps of the forward kernel reading field buffer 0 or 1
-  RevMaps rmaps[2];            // TMA maps of the reverse kernels on field buffer 0 or 1 (and adj)
+  RevMaps rmaps[2];            // TMA maps of the reverse kernels on field buffer 0 or 1 (and adj 0)
+  InvMaps imaps[2];            // TMA maps of the fused inverse step reading field buffer 0 or 1
+  AdjMaps amaps[2];            // TMA maps of the fused adjoint step reading adjoint buffer 0 or 1
   int64_t bytes = 0;
   uint64_t gen = 1;            // bumped whenever a buffer used by a captured loop is reallocated
 
@@ -415,9 +420,9 @@ struct fdtd_handle {
     return f;
   }
   Fields F() const { return F(cur); }
-  Fields A() const {
+  Fields A(int b = 0) const {
     Fields f;
-    for (int c = 0; c < 6; ++c) f.f[c] = adj + c * g.vol;
+    for (int c = 0; c < 6; ++c) f.f[c] = adj + (int64_t)b * 6 * g.vol + c * g.vol;
     return f;
   }
   // psi pointers over a buffer laid out axis by axis, two components per axis
@@ -603,7 +608,7 @@ void fill_canaries(fdtd_handle* h, bool fields, bool adj, bool a) {
   const int64_t rows = (int64_t)h->g.n[1] * h->g.n[2];
   const float nan = std::numeric_limits<float>::quiet_NaN();
   if (fields) launch_fill_padding(h->g, h->fields, 12 * rows, field_canary_x0(h), nan, h->nsm, h->stream);
-  if (adj && h->adj) launch_fill_padding(h->g, h->adj, 6 * rows, h->g.n[0], nan, h->nsm, h->stream);
+  if (adj && h->adj) launch_fill_padding(h->g, h->adj, 12 * rows, h->g.n[0], nan, h->nsm, h->stream);
   if (a) launch_fill_padding(h->g, h->a, rows, h->g.n[0], nan, h->nsm, h->stream);
 }
 
@@ -643,6 +648,23 @@ bool is_host_pointer(const void* p) {
     return true;
   }
   return at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged;
+}
+
+// Both adjoint buffers, with the TMA maps of the kernels that read them: the fused adjoint step (either
+// buffer) and the reverse kernels of the checkpointing gradient (buffer 0).
+int encode_rev_maps(fdtd_handle* h);
+int ensure_adjoint(fdtd_handle* h) {
+  if (h->adj) return FDTD_OK;
+  const Geo& g = h->g;
+  TRY(dev_alloc(h, (void**)&h->adj, 12 * g.vol * 4));
+  TRY(encode_rev_maps(h));
+  for (int b = 0; b < 2; ++b) {
+    const Fields Ab = h->A(b);
+    TRY(encode_field_map(&h->amaps[b].eb, Ab.f[0], g, 3, adj_box_e()));
+    TRY(encode_field_map(&h->amaps[b].hb, Ab.f[3], g, 3, adj_box_h()));
+    TRY(encode_field_map(&h->amaps[b].a, h->a, g, 1, adj_box_e()));
+  }
+  return FDTD_OK;
 }
 
 // TMA maps of the reverse kernels (fdtd_reverse.cu): over each field buffer and the adjoint fields.
@@ -796,107 +818,123 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   return launches;
 }
 
-// Reverse (Sec. 2.2): per step, the detector adjoints, the face record of the step written back into H,
-// the inverse-E / adjoint-H kernel (which also removes the sources) and the inverse-H / adjoint-E
-// kernel, in place on the current field buffer.
+// Reverse (Sec. 2.2): per step n, from the state after step n (E^{n+1}, H^{n+1/2} in field buffer `pc`,
+// the adjoint of that state in adjoint buffer `ac`):
+//   the detector adjoints of step n that need a launch of their own (all of them at the last step);
+//   the recorded H^{n+1/2} written back on the boundary faces (just outside R) of buffer pc;
+//   the fused inverse step: E^n, H^{n-1/2} on R into buffer 1 - pc, and dL/da on the design box;
+//   the fused adjoint step: the adjoint of (E^n, H^{n-1/2}) into adjoint buffer 1 - ac, plus the
+//   adjoints of the E-only detectors of step n - 1 (from E^n in buffer 1 - pc);
+//   the TFSF H corrections of step n removed from H^{n-1/2} on R.
 int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
-  const Fields F = h->F(), A = h->A();
   PsiSet PEb[2], PHb[2];  // psi-bar layout: [E 0][H 0][E 1][H 1]
   for (int k = 0; k < 2; ++k) {
     PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
     PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
   }
-  RevArgs ra;
-  ra.g = g;
-  ra.T = h->tab();
-  ra.F = F;
-  ra.B = A;
-  ra.a = h->a;
-  ra.tz = h->tz_rev;
-  ra.nstage = h->rev_nstage;
+  InvArgs ia;
+  ia.g = g;
+  ia.a = h->a;
+  ia.tz = h->tz_inv;
+  ia.nstage = h->inv_nstage;
+  ia.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
+  for (int q = 0; q < ia.nsrc; ++q) ia.src[q] = h->srcs[q];
   for (int d = 0; d < 3; ++d) {
-    ra.dlo[d] = h->design_lo[d];
-    ra.dhi[d] = h->design_hi[d];
+    ia.dlo[d] = h->design_lo[d];
+    ia.dhi[d] = h->design_hi[d];
   }
-  ra.dLda = h->dLda;
-  ra.inverse = 1;
-  ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
-  for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
-  ra.status = h->status;
-  ra.gy = h->dLddet;
-  ra.ndet = 0;
+  ia.dLda = box_cells(h->design_lo, h->design_hi) > 0 ? h->dLda : nullptr;
+  ia.status = h->status;
+  AdjArgs aa;
+  aa.g = g;
+  aa.T = h->tab();
+  aa.a = h->a;
+  aa.tz = h->tz_adj;
+  aa.nstage = h->adj_nstage;
+  aa.status = h->status;
+  aa.gy = h->dLddet;
+  aa.ndet = 0;
   for (size_t q = 0; q < h->dets.size(); ++q)
     if (h->det_fold[q]) {
       DetDev d = h->dets[q];
       if (d.kind == FDTD_DET_POINT_SERIES)  // the point is the one-cell box at lo
         for (int k = 0; k < 3; ++k) d.hi[k] = d.lo[k] + 1;
-      ra.det[ra.ndet++] = d;
+      aa.det[aa.ndet++] = d;
     }
   bool unfolded = false;  // a detector whose adjoint needs a launch of its own at every step
   for (size_t q = 0; q < h->dets.size(); ++q) unfolded |= !h->det_fold[q];
-  const RevMaps& rm = h->rmaps[h->cur];
   int64_t launches = 0;
-  int pb = 0;
-  // The face replay of step n (the recorded H^{n+1/2} written back outside R) runs on the side
-  // stream beside rev_H(n+1), which neither reads nor writes H outside R; rev_E(n) waits for it.
-  // Without face_overlap it runs in line, right before rev_E(n).
+  int pc = h->cur, ac = 0, pb = 0;
+  // The face replay of step n (the recorded H^{n+1/2} written back outside R into buffer pc) runs on
+  // the side stream beside the adjoint step of n + 1, which does not touch the primal fields; the
+  // inverse step of n waits for it. Without face_overlap it runs in line, right before that step.
   const bool faces = h->faces.per_step > 0;
   const bool ovl = faces && h->face_overlap;
-  auto replay = [&](int n) {
+  auto replay = [&](int n, int buf) {
     cudaStream_t fs = ovl ? h->side : st;
     if (ovl) cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     {
       ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, F, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
+      launch_face_copy(g, h->F(buf), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
     }
     if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
     launches += 1;
   };
   if (ovl && nsteps > 0) {
     cudaEventRecord(h->ev_fork, st);
-    replay(nsteps - 1);
+    replay(nsteps - 1, pc);
   }
   for (int n = nsteps - 1; n >= 0; --n) {
-    // the folded detectors' adjoints of step n come from rev_H(n+1); the last step has none before it
+    const Fields Fc = h->F(pc), Fn = h->F(1 - pc), Ac = h->A(ac), An = h->A(1 - ac);
+    // the folded detectors' adjoints of step n come from the adjoint step of n + 1; the last step has none
     const bool folded = n < nsteps - 1;
-    if (unfolded || (!folded && ra.ndet > 0)) {
+    if (unfolded || (!folded && aa.ndet > 0)) {
       ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
-      launches += enqueue_det_adjoint(h, F, A, n, 0, st, false, folded);
+      launches += enqueue_det_adjoint(h, Fc, Ac, n, 0, st, false, folded);
     }
-    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, F, h->srcs[q], n, -1.f, 1, st);
-    ra.step = n;
+    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fc, h->srcs[q], n, -1.f, 1, st);
     if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
-    else if (faces) replay(n);
+    else if (faces) replay(n, pc);
     {
-      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
-      ra.pin = PEb[pb];
-      ra.pout = PEb[1 - pb];
-      launch_rev_E(ra, rm, st);
+      ProfScope ps(h, evs, st, FDTD_KERNEL_INV_FUSED, n);
+      ia.cur = Fc;
+      ia.nxt = Fn;
+      ia.step = n;
+      for (int c = 0; c < 3; ++c) ia.eb[c] = Ac.f[c];
+      launch_inv(ia, h->imaps[pc], st);
     }
-    if (ovl && n > 0) {  // rev_E(n) has read the faces of step n: replay those of step n-1
+    if (ovl && n > 0) {  // the faces of step n - 1 go into buffer 1 - pc, which the inverse step has written
       cudaEventRecord(h->ev_fork, st);
-      replay(n - 1);
+      replay(n - 1, 1 - pc);
     }
-    launches += enqueue_det_adjoint(h, F, A, n, 1, st);  // interpolated flux: H terms, E^n rebuilt
+    launches += enqueue_det_adjoint(h, Fn, Ac, n, 1, st);  // interpolated flux: H terms, E^n in Fn
     {
-      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
-      ra.pin = PHb[pb];
-      ra.pout = PHb[1 - pb];
-      ra.det_step = n - 1;  // -1 at n = 0: nothing left to fold
-      launch_rev_H(ra, rm, st);
+      ProfScope ps(h, evs, st, FDTD_KERNEL_ADJ_FUSED, n);
+      aa.cur = Ac;
+      aa.nxt = An;
+      aa.prim = Fn;
+      aa.pinE = PEb[pb];
+      aa.poutE = PEb[1 - pb];
+      aa.pinH = PHb[pb];
+      aa.poutH = PHb[1 - pb];
+      aa.det_step = n - 1;  // -1 at n = 0: nothing left to fold
+      launch_adj(aa, h->amaps[ac], st);
     }
     launches += 2;
     // the inverse H step rebuilt H^{n-1/2} + the TFSF H corrections of step n on R: remove them
-    for (const SrcDev& hs : h->hsrcs) launch_source(g, F, hs, n, -1.f, 1, st);
+    for (const SrcDev& hs : h->hsrcs) launch_source(g, Fn, hs, n, -1.f, 1, st);
     launches += (int64_t)h->hsrcs.size();
-    launches += enqueue_det_adjoint(h, F, A, n, 2, st);  // interpolated flux: E^n terms
+    launches += enqueue_det_adjoint(h, Fn, An, n, 2, st);  // interpolated flux: E^n terms
+    pc = 1 - pc;
+    ac = 1 - ac;
     pb = 1 - pb;
   }
+  h->cur = pc;
   if (nsteps > 0) {  // the non-finite check of the rebuilt and the adjoint fields
-    launch_check_finite(g, F.f[0], 6 * g.vol, h->status, h->nsm, st);
-    launch_check_finite(g, A.f[0], 6 * g.vol, h->status, h->nsm, st);
+    launch_check_finite(g, h->F(pc).f[0], 6 * g.vol, h->status, h->nsm, st);
+    launch_check_finite(g, h->A(ac).f[0], 6 * g.vol, h->status, h->nsm, st);
     launches += 2;
   }
   return launches;
@@ -1012,7 +1050,7 @@ int64_t fdtd_footprint_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t
   b += 13 * g.vol * 4;                                // fields (double-buffered) + a
   b += 4 * psi_bytes(g);                              // forward psi of E and H, double-buffered
   b += (int64_t)7 * (g.n[0] + g.n[1] + g.n[2]) * 4;   // CPML and slab-index tables
-  b += 6 * g.vol * 4;                                 // adjoint fields
+  b += 12 * g.vol * 4;                                // adjoint fields (double-buffered)
   b += 4 * psi_bytes(g);                              // adjoint psi, double-buffered
   int64_t design = 0;
   if (design_lo && design_hi) design = box_cells(design_lo, design_hi);
@@ -1136,13 +1174,27 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     const int64_t slots_r = rev_ring4 ? slots_r4 : slots_r3;
     h->tz = choose_tz(nxy, n[2], slots_f);
     h->tz_rev = choose_tz(nxy_rev, n[2], slots_r);
+    // fused inverse and adjoint steps: like the forward, a 4-stage ring when it keeps as many blocks
+    // resident per SM as 3 stages do, else 3 stages; z-chunks for their own resident blocks
+    for (int which = 0; which < 2; ++which) {
+      int b3 = 0, b4 = 0;
+      if ((rc = (which == 0 ? prepare_inv(3, &b3) : prepare_adj(3, &b3))) != FDTD_OK) return cleanup(rc);
+      if ((rc = (which == 0 ? prepare_inv(4, &b4) : prepare_adj(4, &b4))) != FDTD_OK) return cleanup(rc);
+      const bool r4 = b4 >= b3;
+      const int64_t slots = (int64_t)nsm * std::max(1, r4 ? b4 : b3);
+      const int tzv = std::min(choose_tz(nxy, n[2], slots), which == 0 ? inv_max_tz() : adj_max_tz());
+      (which == 0 ? h->inv_nstage : h->adj_nstage) = r4 ? 4 : 3;
+      (which == 0 ? h->tz_inv : h->tz_adj) = tzv;
+    }
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
       const int v = std::atoi(e);
-      if (v >= 1) h->tz = h->tz_rev = std::min(v, n[2]);
+      if (v >= 1) h->tz = h->tz_rev = h->tz_inv = h->tz_adj = std::min(v, n[2]);
     }
+    h->tz_inv = std::min(h->tz_inv, inv_max_tz());
+    h->tz_adj = std::min(h->tz_adj, adj_max_tz());
     if (const char* e = std::getenv("FDTD_REV_NSTAGE")) {  // override: ring stages of the reverse kernels
       const int v = std::atoi(e);
-      if (v == 3 || v == 4) h->rev_nstage = v;
+      if (v == 3 || v == 4) h->rev_nstage = h->inv_nstage = h->adj_nstage = v;
     }
     h->tz = std::min(h->tz, fused_max_tz());
     h->tz_rev = std::min(h->tz_rev, fused_max_tz());
@@ -1157,6 +1209,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     if ((rc = encode_field_map(&h->fmaps[b].e, Fb.f[0], g, 3, fwd_box_e())) != FDTD_OK) return cleanup(rc);
     if ((rc = encode_field_map(&h->fmaps[b].h, Fb.f[3], g, 3, fwd_box_h())) != FDTD_OK) return cleanup(rc);
     if ((rc = encode_field_map(&h->fmaps[b].a, h->a, g, 1, fwd_box_a())) != FDTD_OK) return cleanup(rc);
+    if ((rc = encode_field_map(&h->imaps[b].e, Fb.f[0], g, 3, inv_box_e())) != FDTD_OK) return cleanup(rc);
+    if ((rc = encode_field_map(&h->imaps[b].h, Fb.f[3], g, 3, inv_box_h())) != FDTD_OK) return cleanup(rc);
+    if ((rc = encode_field_map(&h->imaps[b].a, h->a, g, 1, inv_box_e())) != FDTD_OK) return cleanup(rc);
   }
   const int64_t pf = h->psi_floats();
   if ((rc = dev_alloc(h, (void**)&h->psiE, 2 * pf * 4)) != FDTD_OK) return cleanup(rc);
@@ -1382,16 +1437,13 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
-  if (!h->adj) {
-    TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
-    TRY(encode_rev_maps(h));
-  }
+  TRY(ensure_adjoint(h));
   if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
   if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
   TRY(ensure_buf(h, &h->dLddet, &h->dLddet_cap, ndet, 8));
   if (M > 0) TRY(ensure_staging(h));
   if (ndet > 0) CK(cudaMemcpyAsync(h->dLddet, dL_ddet, ndet * 8, cudaMemcpyDefault, h->stream));
-  CK(cudaMemsetAsync(h->adj, 0, 6 * g.vol * 4, h->stream));
+  CK(cudaMemsetAsync(h->adj, 0, 12 * g.vol * 4, h->stream));
   fill_canaries(h, false, true, false);
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
@@ -1649,10 +1701,7 @@ int fdtd_backward_checkpointed(fdtd_handle* h, const double* dL_ddet, float* dL_
     return fail(FDTD_ERR_INVALID_ARG, "the design box must lie in the PML-free region");
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
-  if (!h->adj) {
-    TRY(dev_alloc(h, (void**)&h->adj, 6 * g.vol * 4));
-    TRY(encode_rev_maps(h));
-  }
+  TRY(ensure_adjoint(h));
   if (!h->psibar && pf > 0) TRY(dev_alloc(h, (void**)&h->psibar, 4 * pf * 4));
   if (!h->dLda && M > 0) TRY(dev_alloc(h, (void**)&h->dLda, M * 8));
   TRY(ensure_buf(h, &h->dLddet, &h->dLddet_cap, ndet, 8));
@@ -1881,7 +1930,7 @@ int fdtd_set_canaries(fdtd_handle* h, int32_t enable) {
   if (h->canary) fill_canaries(h, true, true, true);
   else {  // back to zero padding
     launch_fill_padding(h->g, h->fields, 12 * rows, h->g.n[0], 0.f, h->nsm, h->stream);
-    if (h->adj) launch_fill_padding(h->g, h->adj, 6 * rows, h->g.n[0], 0.f, h->nsm, h->stream);
+    if (h->adj) launch_fill_padding(h->g, h->adj, 12 * rows, h->g.n[0], 0.f, h->nsm, h->stream);
     launch_fill_padding(h->g, h->a, rows, h->g.n[0], 0.f, h->nsm, h->stream);
   }
   CK(cudaGetLastError());
@@ -1896,7 +1945,7 @@ int fdtd_check_canaries(fdtd_handle* h, int64_t* overwritten) {
   CK(cudaMemsetAsync(cnt, 0, 8, h->stream));
   const int64_t rows = (int64_t)h->g.n[1] * h->g.n[2];
   launch_count_padding(h->g, h->fields, 12 * rows, field_canary_x0(h), cnt, h->nsm, h->stream);
-  if (h->adj) launch_count_padding(h->g, h->adj, 6 * rows, h->g.n[0], cnt, h->nsm, h->stream);
+  if (h->adj) launch_count_padding(h->g, h->adj, 12 * rows, h->g.n[0], cnt, h->nsm, h->stream);
   launch_count_padding(h->g, h->a, rows, h->g.n[0], cnt, h->nsm, h->stream);
   unsigned long long c = 0;
   CK(cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, h->stream));

@@ -365,8 +365,15 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __gr
         const int x = i + c, e = ex + c;
         const float dzy = a0[2][ey + 1][e] - a0[2][ey][e], dyz = a1[1][ey][e] - a0[1][ey][e];
         const float dxz = a1[0][ey][e] - a0[0][ey][e], dzx = a0[2][ey][e + 1] - a0[2][ey][e];
+        // the CPML terms in the order the owner of plane k0 - 1 adds them (x, y, then z), so that both
+        // give the same bits and the result does not depend on the z-chunk
         float cx = dzy - dyz, cy = dxz - dzx;
         if constexpr (XY) {
+          const int sX = c == 0 ? sX0 : sX1;
+          if (sX >= 0) {
+            const Coef cxh = coef_at(tabX, 3, cx0 + c);
+            cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
+          }
           if (sY >= 0) {
             const Coef cyh = coef_at(tabY, 3, ry);
             cx += corr<false>(dzy, cyh.ik, cyh.b, cyh.c, PHi.p[0][1][zy_of(g, x, km, sY)], nullptr, 0);
@@ -377,13 +384,6 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __gr
           const int zz = zz_of(g, x, j, sZ);
           cx -= corr<false>(dyz, cz.ik, cz.b, cz.c, PHi.p[0][2][zz], nullptr, 0);
           cy += corr<false>(dxz, cz.ik, cz.b, cz.c, PHi.p[1][2][zz], nullptr, 0);
-        }
-        if constexpr (XY) {
-          const int sX = c == 0 ? sX0 : sX1;
-          if (sX >= 0) {
-            const Coef cxh = coef_at(tabX, 3, cx0 + c);
-            cy -= corr<false>(dzx, cxh.ik, cxh.b, cxh.c, PHi.p[1][0][zx_of(g, j, km, sX)], nullptr, 0);
-          }
         }
         hxm[c] = R.H(0)[0][ey][e] - S * cx;
         hym[c] = R.H(0)[1][ey][e] - S * cy;

@@ -111,6 +111,12 @@ __host__ __device__ inline int slab_index(const Geo& g, int d, int x) {
   return -1;
 }
 
+// slab index of position x along an axis with n cells and layers p0, p1 (-1 off the layers): the
+// same index for the integer and the half position x (+ 1/2)
+__host__ __device__ inline int slab_of_pos(int x, int n, int p0, int p1) {
+  return x < p0 ? x : (x >= n - p1 ? p0 + x - (n - p1) : -1);
+}
+
 __host__ __device__ inline int64_t psi_index(const Geo& g, int d, int i, int j, int k, int s) {
   if (d == 0) return ((int64_t)k * g.n[1] + j) * g.slab[0] + s;
   if (d == 1) return ((int64_t)k * g.slab[1] + s) * g.nxp + i;
@@ -176,6 +182,43 @@ struct RevArgs {
   // Detector adjoints folded into rev_H's E-bar write: the terms of detector step det_step (-1: none)
   // of the ndet detectors in det (points on an E component, boxes of time-integrated |E|^2), which
   // use only E after that step, the E that rev_H of the following step holds. gy: dL/d(outputs).
+  int ndet = 0;
+  int det_step = -1;
+  const double* gy = nullptr;
+  DetDev det[kMaxDet];
+};
+
+// Arguments of the fused inverse step (fdtd_inverse.cu): read `cur` (E^{n+1}, H^{n+1/2} with the
+// boundary faces replayed), write `nxt` (E^n, H^{n-1/2} on the PML-free region R), and accumulate
+// dL/da += S Ebar . curl_b(H^{n+1/2}) on the design box from the adjoint of E^{n+1} in `eb`.
+struct InvArgs {
+  Geo g;
+  Fields cur, nxt;
+  const float* a;
+  int step;
+  int tz;
+  int nstage;
+  int nsrc;
+  SrcDev src[kMaxSrc];
+  int dlo[3], dhi[3];      // design box
+  double* dLda;            // null: no gradient
+  const float* eb[3];      // adjoint of E^{n+1}
+  int* status;
+};
+
+// Arguments of the fused adjoint step (fdtd_adjoint.cu): read the adjoint fields `cur`, write `nxt`;
+// psi-bar memories of E and H read from pinE/pinH and written to poutE/poutH; the folded detector
+// adjoints of step det_step (-1: none) read E of that step from `prim`.
+struct AdjArgs {
+  Geo g;
+  Tables T;
+  Fields cur, nxt;
+  Fields prim;
+  PsiSet pinE, poutE, pinH, poutH;
+  const float* a;
+  int tz;
+  int nstage;
+  int* status;
   int ndet = 0;
   int det_step = -1;
   const double* gy = nullptr;

@@ -48,6 +48,28 @@ int prepare_rev(int nstage, int* blocks_per_sm);
 void launch_rev_E(const RevArgs& a, const RevMaps& m, cudaStream_t s);
 void launch_rev_H(const RevArgs& a, const RevMaps& m, cudaStream_t s);
 
+// The maps the fused inverse step reads (fdtd_inverse.cu): E^{n+1} and a over the tile plus the high
+// halo, H^{n+1/2} over the tile plus both halos.
+struct InvMaps {
+  CUtensorMap e, h, a;
+};
+MapBox inv_box_e();   // E^{n+1} and a
+MapBox inv_box_h();   // H^{n+1/2}
+int prepare_inv(int nstage, int* blocks_per_sm);
+int inv_max_tz();
+void launch_inv(const InvArgs& a, const InvMaps& m, cudaStream_t s);
+
+// The maps the fused adjoint step reads (fdtd_adjoint.cu): Ebar and a over the tile with both halos,
+// Hbar over the tile with the low halo, all from the adjoint buffer being read.
+struct AdjMaps {
+  CUtensorMap eb, hb, a;
+};
+MapBox adj_box_e();   // Ebar and a
+MapBox adj_box_h();   // Hbar
+int prepare_adj(int nstage, int* blocks_per_sm);
+int adj_max_tz();
+void launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s);
+
 #if defined(__CUDACC__)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }

@@ -24,7 +24,8 @@ FDTD_ERR_STATE = -5
 FDTD_ERR_NONFINITE = -6
 FDTD_ERR_TIMEOUT = -7
 FDTD_RECORD_FACES = 1
-KERNEL_NAMES = ["update_H", "update_E", "rev_E", "rev_H", "fused_fwd", "fused_rev", "face_copy", "det_adj"]
+KERNEL_NAMES = ["update_H", "update_E", "rev_E", "rev_H", "fused_fwd", "fused_rev", "face_copy", "det_adj",
+                "inv_fused", "adj_fused"]
 
 ERROR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSTABLE", -3: "OOM", -4: "CUDA", -5: "STATE",
                -6: "NONFINITE", -7: "TIMEOUT"}
@@ -341,10 +342,11 @@ class Solver:
 
     def fdtd_profile_read(self):
         """{kernel name: (total ms of the timed launches, number timed)}."""
-        ms = np.zeros(8, dtype=np.float64)
-        cnt = np.zeros(8, dtype=np.int64)
-        check(lib().fdtd_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data, 8))
-        return {KERNEL_NAMES[k]: (float(ms[k]), int(cnt[k])) for k in range(8) if cnt[k] > 0}
+        nk = len(KERNEL_NAMES)
+        ms = np.zeros(nk, dtype=np.float64)
+        cnt = np.zeros(nk, dtype=np.int64)
+        check(lib().fdtd_profile_read(self.h, ms.ctypes.data, cnt.ctypes.data, nk))
+        return {KERNEL_NAMES[k]: (float(ms[k]), int(cnt[k])) for k in range(nk) if cnt[k] > 0}
 
     # --- numpy conveniences (host buffers) ------------------------------------------------------
     def detectors(self) -> np.ndarray:

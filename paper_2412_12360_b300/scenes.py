@@ -213,8 +213,9 @@ def waveguide_scene(n=(600, 600, 600), pml=12, design=200, nsteps=4000, seed=600
                     core=(25, 11), eps_clad=2.085, eps_core=12.25, wavelength_cells=77.5,
                     name=None) -> Scene:
     """Si waveguide (eps 12.25, core `core` cells) along `axis` in SiO2 (eps 2.085), a centred design
-    box eps = 2.085 + 10.165 rho, an E sheet over the core cross-section near the low end and a
-    Poynting-flux plane near the high end (objective: the time sum of the flux)."""
+    box eps = 2.085 + 10.165 rho (`design` cells per axis, or (dx, dy, dz)), an E sheet over the core
+    cross-section near the low end and a Poynting-flux plane near the high end (objective: the time
+    sum of the flux)."""
     nx, ny, nz = n
     S = courant_from_factor(0.99)
     eps = np.full((nz, ny, nx), eps_clad, dtype=np.float32)
@@ -227,9 +228,10 @@ def waveguide_scene(n=(600, 600, 600), pml=12, design=200, nsteps=4000, seed=600
     c_hi[t2] = c_lo[t2] + core[1]
     sl = tuple(slice(c_lo[d], c_hi[d]) for d in (2, 1, 0))
     eps[sl] = eps_core
-    dlo = tuple((n[d] - design) // 2 for d in range(3))
-    dhi = tuple(dlo[d] + design for d in range(3))
-    rho = uniform_rho((design, design, design), seed)
+    dsz = (design,) * 3 if np.isscalar(design) else tuple(int(v) for v in design)
+    dlo = tuple((n[d] - dsz[d]) // 2 for d in range(3))
+    dhi = tuple(dlo[d] + dsz[d] for d in range(3))
+    rho = uniform_rho(dsz[::-1], seed)
     eps[dlo[2]:dhi[2], dlo[1]:dhi[1], dlo[0]:dhi[0]] = (
         np.float32(eps_clad) + np.float32(eps_core - eps_clad) * rho)
     # source sheet over the core cross-section, transverse component t1
@@ -261,6 +263,15 @@ def waveguide_scene(n=(600, 600, 600), pml=12, design=200, nsteps=4000, seed=600
 def waveguide_600(nsteps: int = 4000) -> Scene:
     """600^3 (216 M cells), dx = 20 nm, 12-cell CPML, Si waveguide along x, 200^3 design box."""
     return waveguide_scene((600, 600, 600), 12, 200, nsteps, 600, 0, name="waveguide_600")
+
+
+def waveguide_600_slab(nz: int = 64, nsteps: int = 4000) -> Scene:
+    """A z-slab of waveguide_600: its full 600 x 600 cross-section (12-cell CPML, Si core along x, the
+    sheet source at x = 22 and the flux plane at x = 577) over nz planes with a 12-cell CPML at both
+    z ends, and the design box cut to 200 x 200 x (nz - 24). A bounded sample of the large solve for
+    timing the CPU oracle, whose FP64 state for the full grid is about 70 GB."""
+    return waveguide_scene((600, 600, nz), 12, (200, 200, nz - 24), nsteps, 600, 0,
+                           name="waveguide_600_slab%d" % nz)
 
 
 def waveguide_batch_member(b: int, nsteps: int = 3000, n=(240, 240, 960), design=120) -> Scene:

@@ -218,19 +218,59 @@ def test_gradient_folded_detector_adjoints(F, all_folded):
     assert e_c < 1e-4
 
 
+@pytest.mark.parametrize("nstage", ["3", "4"])
 @pytest.mark.parametrize("scene", ["ragged", "odd_x"])
-def test_gradient_four_stage_reverse_kernels(F, scene, monkeypatch):
-    """The reverse kernels' 4-stage instantiation (the one large grids run) on small scenes."""
-    monkeypatch.setenv("FDTD_REV_NSTAGE", "4")
+def test_gradient_three_and_four_stage_reverse_kernels(F, scene, nstage, monkeypatch):
+    """Both ring sizes of the reverse kernels (the fused inverse and adjoint steps of time reversal,
+    and the reverse kernels of the checkpointing gradient) on small scenes: each size is what some grid
+    runs by default."""
+    monkeypatch.setenv("FDTD_REV_NSTAGE", nstage)
     sc = ragged_scene(300) if scene == "ragged" else odd_scene(300, pml=(5, 0, 4, 6, 6, 3))
     g = np.random.default_rng(11).standard_normal(O.detector_total(sc, 300))
     grad_o, _, _ = O.gradient(sc, 300, g, O.METHOD_TIME_REVERSAL)
     with F.Solver(sc) as s:
         s.fdtd_forward(300, record_faces=True)
         grad_g = s.gradient(g)
-    e = rel_l2(grad_g, grad_o)
-    print("%s 300 steps, 4-stage reverse: dL/deps rel L2 %.3e" % (scene, e))
-    assert e < 1e-3
+        grad_c = np.zeros(sc.design_shape(), dtype=np.float32)
+        s.fdtd_forward(300)
+        s.fdtd_backward_checkpointed(g, grad_c, 1, 6)
+    e, e_c = rel_l2(grad_g, grad_o), rel_l2(grad_c, grad_o)
+    print("%s 300 steps, %s-stage reverse: dL/deps rel L2 %.3e (time reversal), %.3e (checkpointing)"
+          % (scene, nstage, e, e_c))
+    assert e < 1e-3 and e_c < 1e-3
+
+
+@pytest.mark.parametrize("scene", ["ragged", "tfsf_interp"])
+def test_results_do_not_depend_on_the_z_chunk(F, scene, monkeypatch):
+    """The z-marching kernels recompute the plane next to their chunk with the same arithmetic as the
+    block that owns it, so the z-planes per block leave fields, detectors and gradients bitwise the same
+    (flux detectors, whose per-block partial sums follow the chunks, to FP64 rounding)."""
+    sc = ragged_scene(120) if scene == "ragged" else S.design_box_scene(
+        (45, 38, 41), 6, 12, 120, 21, name="tz", tfsf=True, interp=True)
+    g = np.random.default_rng(14).standard_normal(O.detector_total(sc, sc.nsteps))
+    out = []
+    for tz in (None, "3", "7"):
+        if tz is None:
+            monkeypatch.delenv("FDTD_TZ", raising=False)
+        else:
+            monkeypatch.setenv("FDTD_TZ", tz)
+        with F.Solver(sc) as s:
+            s.fdtd_forward(sc.nsteps, record_faces=True)
+            det = s.detectors()
+            f_fwd = s.fields()
+            out.append((det, f_fwd, s.gradient(g), s.fields()))
+    flux = np.zeros(out[0][0].shape, dtype=bool)
+    off = 0
+    for d in sc.detectors:
+        n = int(np.prod([d.hi[k] - d.lo[k] for k in range(3)])) if d.kind in (1, 3) else sc.nsteps
+        if d.kind in (2, 4):
+            flux[off:off + n] = True
+        off += n
+    for o in out[1:]:
+        assert np.array_equal(o[0][~flux], out[0][0][~flux])
+        assert np.allclose(o[0][flux], out[0][0][flux], rtol=1e-12, atol=1e-12 * np.abs(out[0][0]).max())
+        for a, b in zip(o[1:], out[0][1:]):
+            assert np.array_equal(a, b)
 
 
 def test_gradient_pec_point_detectors(F):
@@ -359,7 +399,7 @@ def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene):
                 s.fdtd_forward(sc.nsteps, record_faces=True)
                 r = (s.detectors(), s.gradient(g), s.fields())
             prof = s.fdtd_profile_read()
-        assert prof["fused_fwd"][1] > 0 and prof["rev_E"][1] > 0
+        assert prof["fused_fwd"][1] > 0 and prof["inv_fused"][1] > 0 and prof["adj_fused"][1] > 0
         out.append(r)
     for o in out[1:]:
         for a, b in zip(out[0], o):
