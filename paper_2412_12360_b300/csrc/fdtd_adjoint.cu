@@ -78,10 +78,11 @@ __device__ __forceinline__ int zx_of(const Geo& g, int y, int k, int s) { return
 __device__ __forceinline__ int zy_of(const Geo& g, int x, int k, int s) { return (k * g.slab[1] + s) * g.nxp + x; }
 __device__ __forceinline__ int zz_of(const Geo& g, int x, int y, int s) { return (s * g.n[1] + y) * g.nxp + x; }
 
-// CPML part of one adjoint coefficient inside a layer: sv (1/kappa - 1) + c (psibar + sv), rounded in
-// that order (no contraction, so that every evaluation of a coefficient gives the same bits)
-__device__ __forceinline__ float acorr(float sv, float ik, float c, float psi) {
-  return __fadd_rn(__fmul_rn(sv, __fsub_rn(ik, 1.f)), __fmul_rn(c, __fadd_rn(psi, sv)));
+// CPML part of one adjoint coefficient inside a layer: sv (1/kappa - 1) + c (psibar + sv), with
+// km1 = 1/kappa - 1 from the tables, as one fused multiply-add (explicit, so that every evaluation of a
+// coefficient rounds the same way and gives the same bits)
+__device__ __forceinline__ float acorr(float sv, float km1, float c, float psi) {
+  return __fmaf_rn(sv, km1, __fmul_rn(c, __fadd_rn(psi, sv)));
 }
 // the memory update psibar <- b (psibar + sv)
 __device__ __forceinline__ float amem(float sv, float b, float psi) { return __fmul_rn(b, __fadd_rn(psi, sv)); }
@@ -172,7 +173,8 @@ __device__ __forceinline__ void cell_u(float S, int x, int y, int k, int bx, int
   }
 }
 
-// CPML coefficients of one position along an axis (integer positions for E, half positions for H)
+// CPML coefficients of one position along an axis (integer positions for E, half positions for H):
+// b, c and ik = 1/kappa - 1
 struct Coef {
   float b, c, ik;
 };
@@ -212,11 +214,11 @@ struct ZPlane {
 __device__ __forceinline__ ZPlane zplane(const Geo& g, const Tables& T, int k) {
   ZPlane z;
   z.s = (k >= 0 && k < g.n[2]) ? slab_of_pos(k, g.n[2], g.pml[4], g.pml[5]) : -1;
-  z.e = Coef{0.f, 0.f, 1.f};
-  z.h = Coef{0.f, 0.f, 1.f};
+  z.e = Coef{0.f, 0.f, 0.f};
+  z.h = Coef{0.f, 0.f, 0.f};
   if (z.s >= 0) {
-    z.e = Coef{T.b[2][0][k], T.c[2][0][k], T.ik[2][0][k]};
-    z.h = Coef{T.b[2][1][k], T.c[2][1][k], T.ik[2][1][k]};
+    z.e = Coef{T.b[2][0][k], T.c[2][0][k], __fsub_rn(T.ik[2][0][k], 1.f)};
+    z.h = Coef{T.b[2][1][k], T.c[2][1][k], __fsub_rn(T.ik[2][1][k], 1.f)};
   }
   return z;
 }
@@ -354,7 +356,8 @@ __global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __gr
     const int pos = min(max((isx ? i0 : j0) - 1 + col, 0), g.n[ax] - 1);
     const int hf = row / 3, w = row % 3;
     const float* src = w == 0 ? T.b[ax][hf] : (w == 1 ? T.c[ax][hf] : T.ik[ax][hf]);
-    (isx ? tabX[row] : tabY[row])[col] = src[pos];
+    const float v = src[pos];
+    (isx ? tabX[row] : tabY[row])[col] = w == 2 ? __fsub_rn(v, 1.f) : v;  // 1/kappa - 1
   }
   {
     // per-plane flags: bit 1 a folded detector meets the tile at that plane
@@ -508,10 +511,16 @@ __global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __gr
           const int x = i + c;
           const Slabs& sl = c ? sl1 : sl0;
           const int cx = cx0 + c;
-          const float wx = __fmul_rn(-S, hn[c][0]), wy = __fmul_rn(-S, hn[c][1]), wz = __fmul_rn(-S, hn[c][2]);
-          const float wz_x = __fmul_rn(-S, c ? hn[0][2] : hzl), wy_x = __fmul_rn(-S, c ? hn[0][1] : hyl);
-          const float wz_y = __fmul_rn(-S, c ? hzs.y : hzs.x), wx_y = __fmul_rn(-S, c ? hxs.y : hxs.x);
-          const float wy_m = k > 0 ? __fmul_rn(-S, hym[c]) : 0.f, wx_m = k > 0 ? __fmul_rn(-S, hxm[c]) : 0.f;
+          // Hbar_new at the cell and at its -x, -y, -z neighbours (the plane below the grid holds 0)
+          const float hx = hn[c][0], hy = hn[c][1], hz = hn[c][2];
+          const float hz_x = c ? hn[0][2] : hzl, hy_x = c ? hn[0][1] : hyl;
+          const float hz_y = c ? hzs.y : hzs.x, hx_y = c ? hxs.y : hxs.x;
+          const float hy_m = k > 0 ? hym[c] : 0.f, hx_m = k > 0 ? hxm[c] : 0.f;
+          // w = -S Hbar_new, for the CPML terms
+          const float wx = __fmul_rn(-S, hx), wy = __fmul_rn(-S, hy), wz = __fmul_rn(-S, hz);
+          const float wz_x = __fmul_rn(-S, hz_x), wy_x = __fmul_rn(-S, hy_x);
+          const float wz_y = __fmul_rn(-S, hz_y), wx_y = __fmul_rn(-S, hx_y);
+          const float wy_m = __fmul_rn(-S, hy_m), wx_m = __fmul_rn(-S, hx_m);
           float cex = 0.f, cey = 0.f, cez = 0.f;
           const PsiSet& Pi = A.pinH;
           const PsiSet& Po = A.poutH;
@@ -576,9 +585,10 @@ __global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __gr
             cex = __fadd_rn(cex, __fsub_rn(m1y, e1y));
             cey = __fadd_rn(cey, __fsub_rn(m2x, e2x));
           }
-          const float px = __fadd_rn(__fsub_rn(wy_m, wy), __fsub_rn(wz, wz_y));
-          const float py = __fadd_rn(__fsub_rn(wz_x, wz), __fsub_rn(wx, wx_m));
-          const float pz = __fadd_rn(__fsub_rn(wx_y, wx), __fsub_rn(wy, wy_x));
+          // the plain gather of the w values, -S (the H-update coefficient) applied once per component
+          const float px = __fmul_rn(-S, __fadd_rn(__fsub_rn(hy_m, hy), __fsub_rn(hz, hz_y)));
+          const float py = __fmul_rn(-S, __fadd_rn(__fsub_rn(hz_x, hz), __fsub_rn(hx, hx_m)));
+          const float pz = __fmul_rn(-S, __fadd_rn(__fsub_rn(hx_y, hx), __fsub_rn(hy, hy_x)));
           nb[c][0] = __fadd_rn(c ? eo[0].y : eo[0].x, __fadd_rn(px, cex));
           nb[c][1] = __fadd_rn(c ? eo[1].y : eo[1].x, __fadd_rn(py, cey));
           nb[c][2] = __fadd_rn(c ? eo[2].y : eo[2].x, __fadd_rn(pz, cez));
