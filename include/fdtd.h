@@ -205,6 +205,57 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags);
  * faces or a backward already consumed it. */
 int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps);
 
+/* ---- Grouped forms: several solves advanced by one launch per kernel and time step --------------
+ * For serving and batching (the optimisation loops of Sec. 3.2-3.3 solve many designs). The math is
+ * that of fdtd_forward / fdtd_backward, so each handle's detectors and dL/deps are bitwise the same
+ * as when it is solved alone; what changes is that one launch of the fused forward (or inverse, or
+ * adjoint) kernel covers the blocks of every handle of the group, so small grids share the GPU
+ * instead of queueing for it. A solve is started with fdtd_begin, its forward advanced by
+ * fdtd_group_step until its phase is FDTD_PHASE_FORWARD_DONE (detectors readable), its reverse
+ * sweep started with fdtd_begin_backward and advanced the same way until FDTD_PHASE_DONE, and its
+ * gradient read with fdtd_finish_backward. Handles may join a group at any step and in either phase
+ * (continuous batching). Every handle of a group must have been created on the same stream; at most
+ * FDTD_MAX_GROUP handles per call. Grouped steps launch directly (no CUDA graph) and copy the
+ * boundary faces in line. */
+#define FDTD_MAX_GROUP 8
+#define FDTD_PHASE_IDLE 0          /* no incremental solve in progress */
+#define FDTD_PHASE_FORWARD 1       /* forward steps remain */
+#define FDTD_PHASE_FORWARD_DONE 2  /* the forward has finished: detectors readable, fdtd_begin_backward next */
+#define FDTD_PHASE_BACKWARD 3      /* reverse steps remain */
+#define FDTD_PHASE_DONE 4          /* the reverse sweep has finished: fdtd_finish_backward next */
+
+/* Start a forward solve of nsteps steps (flags as fdtd_forward) that fdtd_group_step advances; no step
+ * runs here. INVALID_ARG as fdtd_forward. */
+int fdtd_begin(fdtd_handle* h, int32_t nsteps, uint32_t flags);
+
+/* Start the reverse sweep (Sec. 2.2) of a finished recorded forward begun with fdtd_begin; dL_ddet as in
+ * fdtd_backward. STATE unless the phase is FDTD_PHASE_FORWARD_DONE and the forward recorded faces. */
+int fdtd_begin_backward(fdtd_handle* h, const double* dL_ddet);
+
+/* Advance each of the n handles by up to nsteps steps of its current phase (forward steps, or reverse
+ * steps), with one launch per kernel and step for all of them; handles that finish their phase
+ * meanwhile drop out of the later steps, handles in another phase are left alone. Enqueued on the
+ * handles' common stream; no synchronisation. INVALID_ARG for n outside 1..FDTD_MAX_GROUP, NULL or
+ * repeated handles, handles on different streams or nsteps < 0. */
+int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps);
+
+/* The handle's phase (FDTD_PHASE_*) and the steps its phase has left (either may be NULL). */
+int fdtd_phase(fdtd_handle* h, int32_t* phase, int32_t* steps_left);
+
+/* Write dL/deps (fdtd_finish_backward) or dL/drho for the density of the last fdtd_set_design_density
+ * (fdtd_finish_backward_density) of a finished reverse sweep; host or device buffer as fdtd_backward.
+ * Returns the handle to FDTD_PHASE_IDLE. STATE unless the phase is FDTD_PHASE_DONE. */
+int fdtd_finish_backward(fdtd_handle* h, float* dL_deps);
+int fdtd_finish_backward_density(fdtd_handle* h, float* dL_drho);
+
+/* Whole solves of a group: fdtd_begin of each handle (nsteps[i] steps, flags as fdtd_forward), then
+ * grouped steps until every forward has finished (fdtd_group_forward); fdtd_begin_backward of each
+ * handle, grouped steps until every reverse sweep has finished, and fdtd_finish_backward of each
+ * (fdtd_group_backward, dL_ddet[i] and dL_deps[i] as in fdtd_backward). The handles' last forwards
+ * may have different step counts. */
+int fdtd_group_forward(fdtd_handle* const* hs, int32_t n, const int32_t* nsteps, uint32_t flags);
+int fdtd_group_backward(fdtd_handle* const* hs, int32_t n, const double* const* dL_ddet, float* const* dL_deps);
+
 /* Concatenated detector outputs of the last forward (host or device doubles). */
 int fdtd_read_detectors(fdtd_handle* h, double* out);
 

@@ -312,8 +312,9 @@ constexpr int BAR2_OFF = round128(TYT_OFF + 6 * TABY * 4);
 constexpr int RING2_OFF = round128(BAR2_OFF + 4 * 8);
 constexpr int smem_total(int ns) { return RING2_OFF + ns * STAGE_BYTES + 128; }
 
+// The adjoint step of one request for the block at tile (bx, by), z-chunk bz.
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __grid_constant__ AdjMaps M) {
+__device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
   float(*sHn)[3][NY][NX] = reinterpret_cast<float(*)[3][NY][NX]>(sm + SH_OFF);
@@ -326,8 +327,8 @@ __global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __gr
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int lx = lane & (LX - 1), ty = 2 * warp + (lane >> 4);
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * A.tz;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int k0 = bz * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
@@ -643,15 +644,42 @@ __global__ void __launch_bounds__(NT, 2) k_adj_fused(const AdjArgs A, const __gr
   if (!waited) atomicOr(A.status, kStatusTimeout);
 }
 
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_adj_fused(const __grid_constant__ AdjArgs A, const __grid_constant__ AdjMaps M) {
+  adj_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several requests in one launch (see k_fwd_fused_group).
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_adj_fused_group(const __grid_constant__ AdjGroup G) {
+  int bx, by, bz;
+  const int r = group_locate(G.grid, bx, by, bz);
+  adj_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
+}
+
 }  // namespace
+
+void launch_adj_group(AdjGroup& G, cudaStream_t s) {
+  const int total = group_fill(G.grid, G.n, [&](int r, int* nb) {
+    const Geo& g = G.a[r].g;
+    nb[0] = (g.n[0] + TX - 1) / TX;
+    nb[1] = (g.n[1] + TY - 1) / TY;
+    nb[2] = (g.n[2] + G.a[r].tz - 1) / G.a[r].tz;
+  });
+  if (total == 0) return;
+  if (G.a[0].nstage == 4) launch_pdl(k_adj_fused_group<4>, dim3(total), dim3(NT), smem_total(4), s, G);
+  else launch_pdl(k_adj_fused_group<3>, dim3(total), dim3(NT), smem_total(3), s, G);
+}
 
 MapBox adj_box_e() { return {BW, BH}; }
 MapBox adj_box_h() { return {GW, GH}; }
 
 int prepare_adj(int nstage, int* blocks_per_sm) {
   auto k = nstage == 4 ? k_adj_fused<4> : k_adj_fused<3>;
+  auto kg = nstage == 4 ? k_adj_fused_group<4> : k_adj_fused_group<3>;
   const int smem = smem_total(nstage);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }

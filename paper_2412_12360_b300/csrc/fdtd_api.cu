@@ -5,6 +5,7 @@
 // and replayed for every later solve of the same shape, so a solve costs one graph launch per phase
 // instead of thousands of kernel launches.
 #include <algorithm>
+#include <memory>
 #include <limits>
 #include <cmath>
 #include <cstdarg>
@@ -378,6 +379,11 @@ struct fdtd_handle {
   uint64_t gen = 1;            // bumped whenever a buffer used by a captured loop is reallocated
 
   int last_nsteps = -1;
+  // incremental solve advanced by fdtd_group_step (fdtd_begin ... fdtd_finish_backward)
+  int phase = FDTD_PHASE_IDLE;
+  int step_next = 0;           // forward: the next step to run; reverse: the next step to reverse
+  bool solve_record = false;
+  int rev_pc = 0, rev_ac = 0, rev_pb = 0;  // reverse: primal buffer, adjoint buffer, psi-bar set
   bool recorded = false;
   bool consumed = false;
   bool density = false;        // the design box was last set from a density rho
@@ -732,15 +738,12 @@ int64_t enqueue_det_adjoint(fdtd_handle* h, const Fields& F, const Fields& A, in
 }
 
 
-// Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
-// fused kernel's slots), then the fixed-order flux sums. Mutates h->cur as it goes.
-int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st, std::vector<Ev>* evs) {
-  const Geo& g = h->g;
-  const int64_t pf = h->psi_floats();
-  const bool faces = record && h->faces.per_step > 0;
-  int64_t launches = 0;
+// ---- one forward step, in pieces shared by the solo time loop and the grouped launches --------------
+
+// The arguments of the fused forward kernel that do not change from step to step.
+FwdArgs fwd_base(fdtd_handle* h) {
   FwdArgs fa;
-  fa.g = g;
+  fa.g = h->g;
   fa.T = h->tab();
   fa.a = h->a;
   fa.tz = h->tz;
@@ -753,63 +756,53 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   fa.det_out = h->det_out;
   fa.partial = h->partial;
   fa.status = h->status;
-  // The face record of step n runs on the side stream, beside step n+1 (which only reads that
-  // buffer); step n+2 overwrites it, so its fused kernel waits for the copy, and so does a TFSF H
-  // correction of step n+1, which writes that buffer's H. Without face_overlap it runs in line.
-  const bool ovl = faces && h->face_overlap;
-  for (int n = 0; n < nsteps; ++n) {
-    const int c = h->cur, x = 1 - c;
-    if (ovl && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
-    if (ovl && n >= 1 && !h->hsrcs.empty()) cudaStreamWaitEvent(st, h->ev_join[(n - 1) % 2], 0);
-    fa.cur = h->F(c);
-    fa.nxt = h->F(x);
-    fa.psiE_cur = h->psi_set(h->psiE + c * pf);
-    fa.psiE_nxt = h->psi_set(h->psiE + x * pf);
-    fa.psiH_cur = h->psi_set(h->psiH + c * pf);
-    fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
-    fa.step = n;
-    // TFSF H corrections of step n, added to H^{n-1/2} ahead of the step: the fused kernel's H update
-    // then yields H^{n-1/2} - S curl E^n + correction in every cell, halos included
-    for (const SrcDev& hs : h->hsrcs) launch_source(g, fa.cur, hs, n, +1.f, 0, st);
-    launches += (int64_t)h->hsrcs.size();
-    {
-      ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
-      launch_fwd_fused(fa, h->fmaps[c], st);
-    }
-    launches += 1;
-    const Fields Fn = h->F(x);
-    if (faces) {  // H^{n+1/2} on the boundary faces
-      cudaStream_t fs = ovl ? h->side : st;
-      if (ovl) {
-        cudaEventRecord(h->ev_fork, st);
-        cudaStreamWaitEvent(h->side, h->ev_fork, 0);
-      }
-      {
-        ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
-        launch_face_copy(g, Fn, h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, fs);
-      }
-      if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
-      launches += 1;
-    }
-    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
-    for (size_t q = 0; q < h->dets.size(); ++q) {
-      if (h->det_inline[q]) continue;
-      const DetDev& d = h->dets[q];
-      if (d.kind <= FDTD_DET_PLANE_FLUX) launch_detector_sample(g, Fn, d, n, h->det_out, h->partial, st);
-      else launch_detector_interp(g, h->F(c), Fn, d, n, h->det_out, h->partial, st);  // E^n is in cur
-      ++launches;
-    }
-    // the non-finite check of the state after this step: periodic, and after the last step
-    if (n == nsteps - 1 || (h->check_every > 0 && (n + 1) % h->check_every == 0)) {
-      launch_check_finite(g, Fn.f[0], 6 * g.vol, h->status, h->nsm, st);
-      ++launches;
-    }
-    h->cur = x;
+  return fa;
+}
+
+// The buffers and step index of step n (reading field buffer h->cur).
+void fwd_step_args(fdtd_handle* h, FwdArgs& fa, int n) {
+  const int64_t pf = h->psi_floats();
+  const int c = h->cur, x = 1 - c;
+  fa.cur = h->F(c);
+  fa.nxt = h->F(x);
+  fa.psiE_cur = h->psi_set(h->psiE + c * pf);
+  fa.psiE_nxt = h->psi_set(h->psiE + x * pf);
+  fa.psiH_cur = h->psi_set(h->psiH + c * pf);
+  fa.psiH_nxt = h->psi_set(h->psiH + x * pf);
+  fa.step = n;
+}
+
+// Before the fused kernel of step n: the TFSF H corrections of the step, added to H^{n-1/2} so that
+// the fused kernel's H update yields H^{n-1/2} - S curl E^n + correction in every cell, halos included.
+int64_t fwd_step_pre(fdtd_handle* h, int n, cudaStream_t st) {
+  for (const SrcDev& hs : h->hsrcs) launch_source(h->g, h->F(h->cur), hs, n, +1.f, 0, st);
+  return (int64_t)h->hsrcs.size();
+}
+
+// After the fused kernel of step n (its output in buffer 1 - h->cur) and the face record: the sources
+// and detectors beyond the fused kernel's slots, and the non-finite check (periodic and at the end).
+int64_t fwd_step_post(fdtd_handle* h, int n, int nsteps, cudaStream_t st) {
+  const Geo& g = h->g;
+  const Fields Fn = h->F(1 - h->cur);
+  int64_t launches = 0;
+  for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fn, h->srcs[q], n, +1.f, 0, st);
+  for (size_t q = 0; q < h->dets.size(); ++q) {
+    if (h->det_inline[q]) continue;
+    const DetDev& d = h->dets[q];
+    if (d.kind <= FDTD_DET_PLANE_FLUX) launch_detector_sample(g, Fn, d, n, h->det_out, h->partial, st);
+    else launch_detector_interp(g, h->F(h->cur), Fn, d, n, h->det_out, h->partial, st);  // E^n is in cur
+    ++launches;
   }
-  if (ovl) {  // join the side stream
-    if (nsteps >= 2) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 2) % 2], 0);
-    if (nsteps >= 1) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 1) % 2], 0);
+  if (n == nsteps - 1 || (h->check_every > 0 && (n + 1) % h->check_every == 0)) {
+    launch_check_finite(g, Fn.f[0], 6 * g.vol, h->status, h->nsm, st);
+    ++launches;
   }
+  return launches;
+}
+
+// After the last forward step: the fixed-order sums of the flux detectors.
+int64_t fwd_finish(fdtd_handle* h, int nsteps, cudaStream_t st) {
+  int64_t launches = 0;
   for (const auto& d : h->dets)
     if ((d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) && nsteps > 0) {
       launch_flux_finalize(d, nsteps, h->partial, h->det_out, st);
@@ -818,24 +811,63 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   return launches;
 }
 
-// Reverse (Sec. 2.2): per step n, from the state after step n (E^{n+1}, H^{n+1/2} in field buffer `pc`,
-// the adjoint of that state in adjoint buffer `ac`):
-//   the detector adjoints of step n that need a launch of their own (all of them at the last step);
-//   the recorded H^{n+1/2} written back on the boundary faces (just outside R) of buffer pc;
-//   the fused inverse step: E^n, H^{n-1/2} on R into buffer 1 - pc, and dL/da on the design box;
-//   the fused adjoint step: the adjoint of (E^n, H^{n-1/2}) into adjoint buffer 1 - ac, plus the
-//   adjoints of the E-only detectors of step n - 1 (from E^n in buffer 1 - pc);
-//   the TFSF H corrections of step n removed from H^{n-1/2} on R.
-int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
+// Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
+// fused kernel's slots), then the fixed-order flux sums. Mutates h->cur as it goes.
+int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st, std::vector<Ev>* evs) {
   const Geo& g = h->g;
-  const int64_t pf = h->psi_floats();
-  PsiSet PEb[2], PHb[2];  // psi-bar layout: [E 0][H 0][E 1][H 1]
-  for (int k = 0; k < 2; ++k) {
-    PEb[k] = h->psi_set(h->psibar + (2 * k) * pf);
-    PHb[k] = h->psi_set(h->psibar + (2 * k + 1) * pf);
+  const bool faces = record && h->faces.per_step > 0;
+  int64_t launches = 0;
+  FwdArgs fa = fwd_base(h);
+  // The face record of step n runs on the side stream, beside step n+1 (which only reads that
+  // buffer); step n+2 overwrites it, so its fused kernel waits for the copy, and so does a TFSF H
+  // correction of step n+1, which writes that buffer's H. Without face_overlap it runs in line.
+  const bool ovl = faces && h->face_overlap;
+  for (int n = 0; n < nsteps; ++n) {
+    const int c = h->cur, x = 1 - c;
+    if (ovl && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
+    if (ovl && n >= 1 && !h->hsrcs.empty()) cudaStreamWaitEvent(st, h->ev_join[(n - 1) % 2], 0);
+    fwd_step_args(h, fa, n);
+    launches += fwd_step_pre(h, n, st);
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_FUSED_FWD, n);
+      launch_fwd_fused(fa, h->fmaps[c], st);
+    }
+    launches += 1;
+    if (faces) {  // H^{n+1/2} on the boundary faces
+      cudaStream_t fs = ovl ? h->side : st;
+      if (ovl) {
+        cudaEventRecord(h->ev_fork, st);
+        cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      }
+      {
+        ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
+        launch_face_copy(g, h->F(x), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, fs);
+      }
+      if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
+      launches += 1;
+    }
+    launches += fwd_step_post(h, n, nsteps, st);
+    h->cur = x;
   }
+  if (ovl) {  // join the side stream
+    if (nsteps >= 2) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 2) % 2], 0);
+    if (nsteps >= 1) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 1) % 2], 0);
+  }
+  launches += fwd_finish(h, nsteps, st);
+  return launches;
+}
+
+// ---- one reverse step, in pieces shared by the solo time loop and the grouped launches --------------
+// Reverse step n starts from the state after step n: E^{n+1}, H^{n+1/2} in field buffer pc and the
+// adjoint of that state in adjoint buffer ac; psi-bar memories read from set pb.
+
+PsiSet psibar_set(const fdtd_handle* h, int which, int pb) {  // which 0: of E, 1: of H
+  return h->psi_set(h->psibar + (2 * pb + which) * h->psi_floats());
+}
+
+InvArgs inv_base(fdtd_handle* h) {
   InvArgs ia;
-  ia.g = g;
+  ia.g = h->g;
   ia.a = h->a;
   ia.tz = h->tz_inv;
   ia.nstage = h->inv_nstage;
@@ -847,8 +879,20 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   }
   ia.dLda = box_cells(h->design_lo, h->design_hi) > 0 ? h->dLda : nullptr;
   ia.status = h->status;
+  return ia;
+}
+
+void inv_step_args(fdtd_handle* h, InvArgs& ia, int n, int pc, int ac) {
+  ia.cur = h->F(pc);
+  ia.nxt = h->F(1 - pc);
+  ia.step = n;
+  const Fields Ac = h->A(ac);
+  for (int c = 0; c < 3; ++c) ia.eb[c] = Ac.f[c];
+}
+
+AdjArgs adj_base(fdtd_handle* h) {
   AdjArgs aa;
-  aa.g = g;
+  aa.g = h->g;
   aa.T = h->tab();
   aa.a = h->a;
   aa.tz = h->tz_adj;
@@ -863,8 +907,72 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
         for (int k = 0; k < 3; ++k) d.hi[k] = d.lo[k] + 1;
       aa.det[aa.ndet++] = d;
     }
-  bool unfolded = false;  // a detector whose adjoint needs a launch of its own at every step
-  for (size_t q = 0; q < h->dets.size(); ++q) unfolded |= !h->det_fold[q];
+  return aa;
+}
+
+void adj_step_args(fdtd_handle* h, AdjArgs& aa, int n, int pc, int ac, int pb) {
+  aa.cur = h->A(ac);
+  aa.nxt = h->A(1 - ac);
+  aa.prim = h->F(1 - pc);
+  aa.pinE = psibar_set(h, 0, pb);
+  aa.poutE = psibar_set(h, 0, 1 - pb);
+  aa.pinH = psibar_set(h, 1, pb);
+  aa.poutH = psibar_set(h, 1, 1 - pb);
+  aa.det_step = n - 1;  // -1 at n = 0: nothing left to fold
+}
+
+// Before the inverse step of n: the detector adjoints of step n that need a launch of their own (all of
+// them at the last step, whose folded adjoints no later adjoint step has added), and the sources beyond
+// the inverse kernel's slots taken off E^{n+1} on R.
+int64_t rev_step_pre(fdtd_handle* h, int n, int nsteps, int pc, int ac, cudaStream_t st, std::vector<Ev>* evs) {
+  const Fields Fc = h->F(pc), Ac = h->A(ac);
+  bool unfolded = false;
+  int nfold = 0;
+  for (size_t q = 0; q < h->dets.size(); ++q) {
+    unfolded |= !h->det_fold[q];
+    nfold += h->det_fold[q];
+  }
+  const bool folded = n < nsteps - 1;
+  int64_t launches = 0;
+  if (unfolded || (!folded && nfold > 0)) {
+    ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
+    launches += enqueue_det_adjoint(h, Fc, Ac, n, 0, st, false, folded);
+  }
+  for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(h->g, Fc, h->srcs[q], n, -1.f, 1, st);
+  return launches;
+}
+
+// Between the inverse and the adjoint step: the interpolated fluxes' H terms (E^n now in 1 - pc).
+int64_t rev_step_mid(fdtd_handle* h, int n, int pc, int ac, cudaStream_t st) {
+  return enqueue_det_adjoint(h, h->F(1 - pc), h->A(ac), n, 1, st);
+}
+
+// After the adjoint step: the TFSF H corrections of step n removed from the rebuilt H^{n-1/2} on R,
+// and the interpolated fluxes' E^n terms.
+int64_t rev_step_post(fdtd_handle* h, int n, int pc, int ac, cudaStream_t st) {
+  const Fields Fn = h->F(1 - pc);
+  for (const SrcDev& hs : h->hsrcs) launch_source(h->g, Fn, hs, n, -1.f, 1, st);
+  return (int64_t)h->hsrcs.size() + enqueue_det_adjoint(h, Fn, h->A(1 - ac), n, 2, st);
+}
+
+// After the last reverse step: the non-finite check of the rebuilt and the adjoint fields.
+int64_t rev_finish(fdtd_handle* h, int pc, int ac, cudaStream_t st) {
+  launch_check_finite(h->g, h->F(pc).f[0], 6 * h->g.vol, h->status, h->nsm, st);
+  launch_check_finite(h->g, h->A(ac).f[0], 6 * h->g.vol, h->status, h->nsm, st);
+  return 2;
+}
+
+// Reverse (Sec. 2.2), per step n:
+//   the detector adjoints of step n that need a launch of their own;
+//   the recorded H^{n+1/2} written back on the boundary faces (just outside R) of buffer pc;
+//   the fused inverse step: E^n, H^{n-1/2} on R into buffer 1 - pc, and dL/da on the design box;
+//   the fused adjoint step: the adjoint of (E^n, H^{n-1/2}) into adjoint buffer 1 - ac, plus the
+//   adjoints of the E-only detectors of step n - 1 (from E^n in buffer 1 - pc);
+//   the TFSF H corrections of step n removed from H^{n-1/2} on R.
+int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
+  const Geo& g = h->g;
+  InvArgs ia = inv_base(h);
+  AdjArgs aa = adj_base(h);
   int64_t launches = 0;
   int pc = h->cur, ac = 0, pb = 0;
   // The face replay of step n (the recorded H^{n+1/2} written back outside R into buffer pc) runs on
@@ -887,56 +995,32 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     replay(nsteps - 1, pc);
   }
   for (int n = nsteps - 1; n >= 0; --n) {
-    const Fields Fc = h->F(pc), Fn = h->F(1 - pc), Ac = h->A(ac), An = h->A(1 - ac);
-    // the folded detectors' adjoints of step n come from the adjoint step of n + 1; the last step has none
-    const bool folded = n < nsteps - 1;
-    if (unfolded || (!folded && aa.ndet > 0)) {
-      ProfScope ps(h, evs, st, FDTD_KERNEL_DET_ADJ, n);
-      launches += enqueue_det_adjoint(h, Fc, Ac, n, 0, st, false, folded);
-    }
-    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches) launch_source(g, Fc, h->srcs[q], n, -1.f, 1, st);
+    launches += rev_step_pre(h, n, nsteps, pc, ac, st, evs);
     if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
     else if (faces) replay(n, pc);
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_INV_FUSED, n);
-      ia.cur = Fc;
-      ia.nxt = Fn;
-      ia.step = n;
-      for (int c = 0; c < 3; ++c) ia.eb[c] = Ac.f[c];
+      inv_step_args(h, ia, n, pc, ac);
       launch_inv(ia, h->imaps[pc], st);
     }
     if (ovl && n > 0) {  // the faces of step n - 1 go into buffer 1 - pc, which the inverse step has written
       cudaEventRecord(h->ev_fork, st);
       replay(n - 1, 1 - pc);
     }
-    launches += enqueue_det_adjoint(h, Fn, Ac, n, 1, st);  // interpolated flux: H terms, E^n in Fn
+    launches += rev_step_mid(h, n, pc, ac, st);
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_ADJ_FUSED, n);
-      aa.cur = Ac;
-      aa.nxt = An;
-      aa.prim = Fn;
-      aa.pinE = PEb[pb];
-      aa.poutE = PEb[1 - pb];
-      aa.pinH = PHb[pb];
-      aa.poutH = PHb[1 - pb];
-      aa.det_step = n - 1;  // -1 at n = 0: nothing left to fold
+      adj_step_args(h, aa, n, pc, ac, pb);
       launch_adj(aa, h->amaps[ac], st);
     }
     launches += 2;
-    // the inverse H step rebuilt H^{n-1/2} + the TFSF H corrections of step n on R: remove them
-    for (const SrcDev& hs : h->hsrcs) launch_source(g, Fn, hs, n, -1.f, 1, st);
-    launches += (int64_t)h->hsrcs.size();
-    launches += enqueue_det_adjoint(h, Fn, An, n, 2, st);  // interpolated flux: E^n terms
+    launches += rev_step_post(h, n, pc, ac, st);
     pc = 1 - pc;
     ac = 1 - ac;
     pb = 1 - pb;
   }
   h->cur = pc;
-  if (nsteps > 0) {  // the non-finite check of the rebuilt and the adjoint fields
-    launch_check_finite(g, h->F(pc).f[0], 6 * g.vol, h->status, h->nsm, st);
-    launch_check_finite(g, h->A(ac).f[0], 6 * g.vol, h->status, h->nsm, st);
-    launches += 2;
-  }
+  if (nsteps > 0) launches += rev_finish(h, pc, ac, st);
   return launches;
 }
 
@@ -1392,8 +1476,8 @@ int fdtd_set_initial_fields(fdtd_handle* h, const float* fields6) {
   return FDTD_OK;
 }
 
-int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
-  NvtxRange range("fdtd_forward");
+// Checks and buffers of a forward solve of nsteps steps, and the initial state (no step runs).
+static int forward_prepare(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (nsteps < 0) return fail(FDTD_ERR_INVALID_ARG, "nsteps must be >= 0");
   const bool record = (flags & FDTD_RECORD_FACES) != 0;
@@ -1416,6 +1500,14 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   if (record && h->faces.per_step > 0)
     TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)nsteps, h->faces.per_step * 4));
   TRY(reset_state(h));
+  h->phase = FDTD_PHASE_IDLE;
+  return FDTD_OK;
+}
+
+int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
+  NvtxRange range("fdtd_forward");
+  TRY(forward_prepare(h, nsteps, flags));
+  const bool record = (flags & FDTD_RECORD_FACES) != 0;
   const int64_t key = (record ? 1 : 0) | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2) |
                       ((int64_t)h->check_every << 32);
   TRY(run_loop(h, h->gfwd, nsteps, key, [&](cudaStream_t st, std::vector<Ev>* evs) {
@@ -1426,7 +1518,9 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   return FDTD_OK;
 }
 
-static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps, double scale) {
+// Checks and buffers of the reverse sweep of the last recorded forward: dL/d(det) uploaded, the
+// adjoint fields, their CPML memories and dL/da zeroed.
+static int backward_prepare(fdtd_handle* h, const double* dL_ddet) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   if (!h->recorded || h->consumed)
     return fail(FDTD_ERR_STATE, "backward needs a forward with FDTD_RECORD_FACES that no backward has consumed");
@@ -1434,7 +1528,6 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   const int64_t ndet = det_total_for(h, nsteps);
   if (ndet > 0 && !dL_ddet) return fail(FDTD_ERR_INVALID_ARG, "dL_ddet is NULL");
   const int64_t M = box_cells(h->design_lo, h->design_hi);
-  if (M > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
   const Geo& g = h->g;
   const int64_t pf = h->psi_floats();
   TRY(ensure_adjoint(h));
@@ -1447,11 +1540,14 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   fill_canaries(h, false, true, false);
   if (pf > 0) CK(cudaMemsetAsync(h->psibar, 0, 4 * pf * 4, h->stream));
   if (M > 0) CK(cudaMemsetAsync(h->dLda, 0, M * 8, h->stream));
-  const int64_t key = h->cur | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2);
-  TRY(run_loop(h, h->gbwd, nsteps, key,
-               [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
+  return FDTD_OK;
+}
+
+// dL/deps (times scale) from dL/da into the caller's buffer, after the reverse sweep.
+static int backward_finish(fdtd_handle* h, float* dL_deps, double scale) {
+  const int64_t M = box_cells(h->design_lo, h->design_hi);
   if (M > 0) {
-    launch_grad_finalize(g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, scale, h->stream);
+    launch_grad_finalize(h->g, h->a, h->design_lo, h->design_hi, h->dLda, h->staging, scale, h->stream);
     h->launches += 1;
     CK(cudaMemcpyAsync(dL_deps, h->staging, M * 4, cudaMemcpyDefault, h->stream));
   }
@@ -1462,9 +1558,215 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   return FDTD_OK;
 }
 
+static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps, double scale) {
+  if (h && box_cells(h->design_lo, h->design_hi) > 0 && !dL_deps) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
+  TRY(backward_prepare(h, dL_ddet));
+  const int nsteps = h->last_nsteps;
+  h->phase = FDTD_PHASE_IDLE;
+  const int64_t key = h->cur | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2);
+  TRY(run_loop(h, h->gbwd, nsteps, key,
+               [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
+  return backward_finish(h, dL_deps, scale);
+}
+
 int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
   NvtxRange range("fdtd_backward");
   return backward_scaled(h, dL_ddet, dL_deps, 1.0);
+}
+
+// ---- grouped and incremental solves -------------------------------------------------------------
+
+int fdtd_begin(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
+  TRY(forward_prepare(h, nsteps, flags));
+  h->solve_record = (flags & FDTD_RECORD_FACES) != 0;
+  h->step_next = 0;
+  h->phase = FDTD_PHASE_FORWARD;
+  if (nsteps == 0) {
+    h->phase = FDTD_PHASE_FORWARD_DONE;
+    h->recorded = h->solve_record;
+  }
+  return FDTD_OK;
+}
+
+int fdtd_begin_backward(fdtd_handle* h, const double* dL_ddet) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (h->phase != FDTD_PHASE_FORWARD_DONE) return fail(FDTD_ERR_STATE, "fdtd_begin_backward needs a finished forward");
+  TRY(backward_prepare(h, dL_ddet));
+  h->rev_pc = h->cur;
+  h->rev_ac = 0;
+  h->rev_pb = 0;
+  h->step_next = h->last_nsteps - 1;
+  h->phase = FDTD_PHASE_BACKWARD;
+  if (h->last_nsteps == 0) h->phase = FDTD_PHASE_DONE;
+  return FDTD_OK;
+}
+
+int fdtd_phase(fdtd_handle* h, int32_t* phase, int32_t* steps_left) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (phase) *phase = h->phase;
+  if (steps_left)
+    *steps_left = h->phase == FDTD_PHASE_FORWARD ? h->last_nsteps - h->step_next
+                                                 : (h->phase == FDTD_PHASE_BACKWARD ? h->step_next + 1 : 0);
+  return FDTD_OK;
+}
+
+static int finish_backward_scaled(fdtd_handle* h, float* out, double scale) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (h->phase != FDTD_PHASE_DONE) return fail(FDTD_ERR_STATE, "the reverse sweep has not finished");
+  if (box_cells(h->design_lo, h->design_hi) > 0 && !out) return fail(FDTD_ERR_INVALID_ARG, "dL_deps is NULL");
+  h->phase = FDTD_PHASE_IDLE;
+  return backward_finish(h, out, scale);
+}
+
+int fdtd_finish_backward(fdtd_handle* h, float* dL_deps) { return finish_backward_scaled(h, dL_deps, 1.0); }
+
+int fdtd_finish_backward_density(fdtd_handle* h, float* dL_drho) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  if (!h->density) return fail(FDTD_ERR_STATE, "no design density was set");
+  return finish_backward_scaled(h, dL_drho, h->eps_hi - h->eps_lo);
+}
+
+int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
+  NvtxRange range("fdtd_group_step");
+  if (!hs || n < 1 || n > FDTD_MAX_GROUP || nsteps < 0)
+    return fail(FDTD_ERR_INVALID_ARG, "a group holds 1..%d handles and nsteps >= 0", FDTD_MAX_GROUP);
+  for (int r = 0; r < n; ++r) {
+    if (!hs[r]) return fail(FDTD_ERR_INVALID_ARG, "NULL handle in the group");
+    if (hs[r]->stream != hs[0]->stream) return fail(FDTD_ERR_INVALID_ARG, "the handles of a group share one stream");
+    for (int q = 0; q < r; ++q)
+      if (hs[q] == hs[r]) return fail(FDTD_ERR_INVALID_ARG, "a handle appears twice in the group");
+  }
+  cudaStream_t st = hs[0]->stream;
+  static_assert(FDTD_MAX_GROUP <= kMaxGroup, "group structures hold FDTD_MAX_GROUP requests");
+  for (int t = 0; t < nsteps; ++t) {
+    fdtd_handle* F[FDTD_MAX_GROUP];
+    fdtd_handle* Rv[FDTD_MAX_GROUP];
+    int nf = 0, nr = 0;
+    for (int r = 0; r < n; ++r) {
+      fdtd_handle* h = hs[r];
+      if (h->phase == FDTD_PHASE_FORWARD && h->step_next < h->last_nsteps) F[nf++] = h;
+      else if (h->phase == FDTD_PHASE_BACKWARD && h->step_next >= 0) Rv[nr++] = h;
+    }
+    if (nf + nr == 0) break;
+    if (nf > 0) {  // one forward step of every handle in its forward phase
+      // the group's kernel parameters (large, so kept per host thread rather than on the stack)
+      static thread_local std::unique_ptr<FwdGroup> Gp;
+      if (!Gp) Gp.reset(new FwdGroup());
+      FwdGroup& FG = *Gp;
+      FaceGroup faces{};
+      faces.to_record = 1;
+      for (int r = 0; r < nf; ++r) {
+        fdtd_handle* h = F[r];
+        h->launches += fwd_step_pre(h, h->step_next, st);
+        FG.a[r] = fwd_base(h);
+        fwd_step_args(h, FG.a[r], h->step_next);
+        FG.m[r] = h->fmaps[h->cur];
+      }
+      FG.n = nf;
+      launch_fwd_group(FG, st);
+      for (int r = 0; r < nf; ++r) {
+        fdtd_handle* h = F[r];
+        h->launches += 1;
+        if (h->solve_record && h->faces.per_step > 0) {
+          FaceJob& J = faces.e[faces.n++];
+          J.g = h->g;
+          J.F = h->F(1 - h->cur);
+          J.fs = h->faces;
+          J.rec = h->face_hist + (int64_t)h->step_next * h->faces.per_step;
+          h->launches += 1;
+        }
+      }
+      if (faces.n > 0) launch_face_copy_group(faces, st);
+      for (int r = 0; r < nf; ++r) {
+        fdtd_handle* h = F[r];
+        h->launches += fwd_step_post(h, h->step_next, h->last_nsteps, st);
+        h->cur = 1 - h->cur;
+        if (++h->step_next == h->last_nsteps) {
+          h->launches += fwd_finish(h, h->last_nsteps, st);
+          h->recorded = h->solve_record;
+          h->phase = FDTD_PHASE_FORWARD_DONE;
+        }
+      }
+    }
+    if (nr > 0) {  // one reverse step of every handle in its reverse phase
+      static thread_local std::unique_ptr<InvGroup> IGp;
+      static thread_local std::unique_ptr<AdjGroup> AGp;
+      if (!IGp) IGp.reset(new InvGroup());
+      if (!AGp) AGp.reset(new AdjGroup());
+      InvGroup& IG = *IGp;
+      AdjGroup& AG = *AGp;
+      FaceGroup faces{};
+      faces.to_record = 0;
+      for (int r = 0; r < nr; ++r) {
+        fdtd_handle* h = Rv[r];
+        h->launches += rev_step_pre(h, h->step_next, h->last_nsteps, h->rev_pc, h->rev_ac, st, nullptr);
+        if (h->faces.per_step > 0) {  // H^{n+1/2} on the boundary faces
+          FaceJob& J = faces.e[faces.n++];
+          J.g = h->g;
+          J.F = h->F(h->rev_pc);
+          J.fs = h->faces;
+          J.rec = h->face_hist + (int64_t)h->step_next * h->faces.per_step;
+          h->launches += 1;
+        }
+      }
+      if (faces.n > 0) launch_face_copy_group(faces, st);
+      for (int r = 0; r < nr; ++r) {
+        fdtd_handle* h = Rv[r];
+        IG.a[r] = inv_base(h);
+        inv_step_args(h, IG.a[r], h->step_next, h->rev_pc, h->rev_ac);
+        IG.m[r] = h->imaps[h->rev_pc];
+        h->launches += 1;
+      }
+      IG.n = nr;
+      launch_inv_group(IG, st);
+      for (int r = 0; r < nr; ++r) {
+        fdtd_handle* h = Rv[r];
+        h->launches += rev_step_mid(h, h->step_next, h->rev_pc, h->rev_ac, st);
+        AG.a[r] = adj_base(h);
+        adj_step_args(h, AG.a[r], h->step_next, h->rev_pc, h->rev_ac, h->rev_pb);
+        AG.m[r] = h->amaps[h->rev_ac];
+        h->launches += 1;
+      }
+      AG.n = nr;
+      launch_adj_group(AG, st);
+      for (int r = 0; r < nr; ++r) {
+        fdtd_handle* h = Rv[r];
+        h->launches += rev_step_post(h, h->step_next, h->rev_pc, h->rev_ac, st);
+        h->rev_pc = 1 - h->rev_pc;
+        h->rev_ac = 1 - h->rev_ac;
+        h->rev_pb = 1 - h->rev_pb;
+        if (--h->step_next < 0) {
+          h->cur = h->rev_pc;
+          h->launches += rev_finish(h, h->rev_pc, h->rev_ac, st);
+          h->phase = FDTD_PHASE_DONE;
+        }
+      }
+    }
+  }
+  CK(cudaGetLastError());
+  return FDTD_OK;
+}
+
+int fdtd_group_forward(fdtd_handle* const* hs, int32_t n, const int32_t* nsteps, uint32_t flags) {
+  if (!hs || !nsteps || n < 1 || n > FDTD_MAX_GROUP) return fail(FDTD_ERR_INVALID_ARG, "bad group");
+  int32_t most = 0;
+  for (int r = 0; r < n; ++r) {
+    TRY(fdtd_begin(hs[r], nsteps[r], flags));
+    most = std::max(most, nsteps[r]);
+  }
+  return fdtd_group_step(hs, n, most);
+}
+
+int fdtd_group_backward(fdtd_handle* const* hs, int32_t n, const double* const* dL_ddet, float* const* dL_deps) {
+  if (!hs || !dL_ddet || !dL_deps || n < 1 || n > FDTD_MAX_GROUP) return fail(FDTD_ERR_INVALID_ARG, "bad group");
+  int32_t most = 0;
+  for (int r = 0; r < n; ++r) {
+    TRY(fdtd_begin_backward(hs[r], dL_ddet[r]));
+    most = std::max(most, hs[r]->last_nsteps);
+  }
+  TRY(fdtd_group_step(hs, n, most));
+  for (int r = 0; r < n; ++r) TRY(fdtd_finish_backward(hs[r], dL_deps[r]));
+  return FDTD_OK;
 }
 
 // ---- Checkpointing gradient (Sec. 2.2: the recomputation alternative to time reversal) -------------

@@ -155,8 +155,9 @@ __device__ __forceinline__ Coef coef_at(const float (*tab)[W], int row0, int idx
   return Coef{tab[row0][idx], tab[row0 + 1][idx], tab[row0 + 2][idx]};
 }
 
+// The forward step of one request for the block at tile (bx, by), z-chunk bz.
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __grid_constant__ FwdMaps M) {
+__device__ __forceinline__ void fwd_body(const FwdArgs& A, const FwdMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
   Ring R{sm + RING_OFF, reinterpret_cast<uint64_t*>(sm + BAR_OFF)};
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __gr
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int lx = lane & (LX - 1), ty = 2 * warp + (lane >> 4);
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * A.tz;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int k0 = bz * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int kb = k0 > 0 ? k0 - 1 : k0;  // first plane staged (k0-1 supplies H^{n+1/2} below the chunk)
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
@@ -661,7 +662,6 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __gr
       const int bx0 = d.lo[0] / TX, bx1 = (d.hi[0] - 1) / TX;
       const int by0 = d.lo[1] / TY, by1 = (d.hi[1] - 1) / TY;
       const int bz0 = d.lo[2] / A.tz, bz1 = (d.hi[2] - 1) / A.tz;
-      const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
       if (bx < bx0 || bx > bx1 || by < by0 || by > by1 || bz < bz0 || bz > bz1) continue;
       double sum = 0.0;
       for (int r = 0; r < TY; ++r) sum += wflux[s][r];
@@ -669,6 +669,20 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_fused(const FwdArgs A, const __gr
       A.partial[d.poff + (int64_t)A.step * d.nblk + slotid] = sum;
     }
   }
+}
+
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_fwd_fused(const __grid_constant__ FwdArgs A, const __grid_constant__ FwdMaps M) {
+  fwd_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several requests in one launch: the grid is the concatenation of their grids (x fastest, then y,
+// then the z-chunk), and each block finds its request by the prefix of block counts.
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_fwd_fused_group(const __grid_constant__ FwdGroup G) {
+  int bx, by, bz;
+  const int r = group_locate(G.grid, bx, by, bz);
+  fwd_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
 }
 
 }  // namespace
@@ -683,10 +697,24 @@ MapBox fwd_box_a() { return {TX, TY}; }
 
 int prepare_fwd_fused(int nstage, int* blocks_per_sm) {
   auto k = nstage == 4 ? k_fwd_fused<4> : k_fwd_fused<3>;
+  auto kg = nstage == 4 ? k_fwd_fused_group<4> : k_fwd_fused_group<3>;
   const int smem = smem_bytes(nstage);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
+}
+
+void launch_fwd_group(FwdGroup& G, cudaStream_t s) {
+  const int total = group_fill(G.grid, G.n, [&](int r, int* nb) {
+    const Geo& g = G.a[r].g;
+    nb[0] = (g.n[0] + TX - 1) / TX;
+    nb[1] = (g.n[1] + TY - 1) / TY;
+    nb[2] = (g.n[2] + G.a[r].tz - 1) / G.a[r].tz;
+  });
+  if (total == 0) return;
+  if (G.a[0].nstage == 4) launch_pdl(k_fwd_fused_group<4>, dim3(total), dim3(NT), smem_bytes(4), s, G);
+  else launch_pdl(k_fwd_fused_group<3>, dim3(total), dim3(NT), smem_bytes(3), s, G);
 }
 
 void launch_fwd_fused(const FwdArgs& a, const FwdMaps& m, cudaStream_t s) {

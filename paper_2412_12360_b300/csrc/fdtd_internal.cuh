@@ -145,6 +145,19 @@ void launch_detector_sample(const Geo& g, const Fields& F, const DetDev& d, int 
                             double* partial, cudaStream_t s);
 void launch_flux_finalize(const DetDev& d, int nsteps, const double* partial, double* out, cudaStream_t s);
 void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* rec, int to_record, cudaStream_t s);
+// The face record (to_record = 1) or replay of several requests in one launch (at most 8).
+struct FaceJob {
+  Geo g;
+  Fields F;
+  FaceSet fs;
+  float* rec;
+};
+struct FaceGroup {
+  int n;
+  int to_record;
+  FaceJob e[8];
+};
+void launch_face_copy_group(const FaceGroup& G, cudaStream_t s);
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,
                              const double* dL_ddet, cudaStream_t s);
 // Flag kStatusNonFinite in *status if one of the grid cells of the n floats at p (whole pitch-padded

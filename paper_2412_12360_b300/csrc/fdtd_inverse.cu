@@ -114,8 +114,9 @@ __device__ __forceinline__ float inv_h(float h1, float S, float da, float db) {
   return __fadd_rn(h1, __fmul_rn(S, __fsub_rn(da, db)));
 }
 
+// The inverse step of one request for the block at tile (bx, by), z-chunk bz.
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, 2) k_inv_fused(const InvArgs A, const __grid_constant__ InvMaps M) {
+__device__ __forceinline__ void inv_body(const InvArgs& A, const InvMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
   float(*sEn)[3][NY][NX] = reinterpret_cast<float(*)[3][NY][NX]>(sm + SE_OFF);
@@ -125,8 +126,8 @@ __global__ void __launch_bounds__(NT, 2) k_inv_fused(const InvArgs A, const __gr
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int lx = lane & (LX - 1), ty = 2 * warp + (lane >> 4);
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * A.tz;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int k0 = bz * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
@@ -339,15 +340,42 @@ __global__ void __launch_bounds__(NT, 2) k_inv_fused(const InvArgs A, const __gr
   if (!waited) atomicOr(A.status, kStatusTimeout);
 }
 
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_inv_fused(const __grid_constant__ InvArgs A, const __grid_constant__ InvMaps M) {
+  inv_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Several requests in one launch (see k_fwd_fused_group).
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_inv_fused_group(const __grid_constant__ InvGroup G) {
+  int bx, by, bz;
+  const int r = group_locate(G.grid, bx, by, bz);
+  inv_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
+}
+
 }  // namespace
+
+void launch_inv_group(InvGroup& G, cudaStream_t s) {
+  const int total = group_fill(G.grid, G.n, [&](int r, int* nb) {
+    const Geo& g = G.a[r].g;
+    nb[0] = (g.n[0] + TX - 1) / TX;
+    nb[1] = (g.n[1] + TY - 1) / TY;
+    nb[2] = (g.n[2] + G.a[r].tz - 1) / G.a[r].tz;
+  });
+  if (total == 0) return;
+  if (G.a[0].nstage == 4) launch_pdl(k_inv_fused_group<4>, dim3(total), dim3(NT), smem_bytes(4), s, G);
+  else launch_pdl(k_inv_fused_group<3>, dim3(total), dim3(NT), smem_bytes(3), s, G);
+}
 
 MapBox inv_box_e() { return {EW, EH}; }
 MapBox inv_box_h() { return {HW, HH}; }
 
 int prepare_inv(int nstage, int* blocks_per_sm) {
   auto k = nstage == 4 ? k_inv_fused<4> : k_inv_fused<3>;
+  auto kg = nstage == 4 ? k_inv_fused_group<4> : k_inv_fused_group<3>;
   const int smem = smem_bytes(nstage);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }

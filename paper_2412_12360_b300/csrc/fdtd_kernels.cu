@@ -139,6 +139,25 @@ __global__ void k_face_copy(Geo g, Fields F, FaceSet fs, float* __restrict__ rec
   else *h = rec[sg.off + t];
 }
 
+// the face copies of several requests: blockIdx.z the request, blockIdx.y the segment
+__global__ void k_face_copy_group(const __grid_constant__ FaceGroup G) {
+  pdl_wait();
+  const FaceJob& J = G.e[blockIdx.z];
+  if ((int)blockIdx.y >= J.fs.nseg) return;
+  const FaceSeg& sg = J.fs.seg[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= sg.n1 * sg.n2) return;
+  const int nf = sg.axis == 1 ? sg.n2 : sg.n1;
+  const int f = t % nf, sl = t / nf;
+  int x, y, z;
+  if (sg.axis == 0) { x = sg.idx; y = sg.lo1 + f; z = sg.lo2 + sl; }
+  else if (sg.axis == 1) { y = sg.idx; x = sg.lo2 + f; z = sg.lo1 + sl; }
+  else { z = sg.idx; x = sg.lo1 + f; y = sg.lo2 + sl; }
+  float* h = J.F.f[3 + sg.comp] + cell_index(J.g, x, y, z);
+  if (G.to_record) J.rec[sg.off + t] = *h;
+  else *h = J.rec[sg.off + t];
+}
+
 // ---------------------------------------------------------------------------------------------
 // reverse: detector adjoint (the transpose of the sampling at step n)
 // ---------------------------------------------------------------------------------------------
@@ -331,6 +350,18 @@ void launch_face_copy(const Geo& g, const Fields& F, const FaceSet& fs, float* r
   if (fs.nseg == 0 || mx == 0) return;
   dim3 grid((unsigned)((mx + 255) / 256), fs.nseg);
   launch_pdl(k_face_copy, grid, dim3(256), 0, s, g, F, fs, rec, to_record);
+}
+
+void launch_face_copy_group(const FaceGroup& G, cudaStream_t s) {
+  int64_t mx = 0;
+  int nseg = 0;
+  for (int r = 0; r < G.n; ++r) {
+    nseg = std::max(nseg, G.e[r].fs.nseg);
+    for (int q = 0; q < G.e[r].fs.nseg; ++q) mx = std::max<int64_t>(mx, (int64_t)G.e[r].fs.seg[q].n1 * G.e[r].fs.seg[q].n2);
+  }
+  if (G.n == 0 || nseg == 0 || mx == 0) return;
+  dim3 grid((unsigned)((mx + 255) / 256), nseg, G.n);
+  launch_pdl(k_face_copy_group, grid, dim3(256), 0, s, G);
 }
 
 void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, const DetDev& d, int step,

@@ -70,7 +70,69 @@ int prepare_adj(int nstage, int* blocks_per_sm);
 int adj_max_tz();
 void launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s);
 
+// ---- grouped launches: several requests (solver handles) advanced by one launch -------------------
+constexpr int kMaxGroup = 8;
+
+// The flat grid of a grouped launch: request r owns blocks blk0[r] .. blk0[r + 1] - 1, laid out as its
+// own grid would be (tile x fastest, then tile y, then the z-chunk).
+struct GroupGrid {
+  int n;
+  int blk0[kMaxGroup + 1];
+  int nbx[kMaxGroup], nby[kMaxGroup];
+};
+
+// Fill G's prefix from each request's grid (nb: tiles along x and y, z-chunks); returns the total.
+template <class F>
+inline int group_fill(GroupGrid& G, int n, F grid_of) {
+  G.n = n;
+  G.blk0[0] = 0;
+  for (int r = 0; r < n; ++r) {
+    int nb[3];
+    grid_of(r, nb);
+    G.nbx[r] = nb[0];
+    G.nby[r] = nb[1];
+    G.blk0[r + 1] = G.blk0[r] + nb[0] * nb[1] * nb[2];
+  }
+  return G.blk0[n];
+}
+
+struct FwdGroup {
+  GroupGrid grid;
+  int n;
+  FwdArgs a[kMaxGroup];
+  FwdMaps m[kMaxGroup];
+};
+struct InvGroup {
+  GroupGrid grid;
+  int n;
+  InvArgs a[kMaxGroup];
+  InvMaps m[kMaxGroup];
+};
+struct AdjGroup {
+  GroupGrid grid;
+  int n;
+  AdjArgs a[kMaxGroup];
+  AdjMaps m[kMaxGroup];
+};
+// One launch per kernel for the G.n requests (their nstage must agree; a[r].tz sets each grid).
+void launch_fwd_group(FwdGroup& G, cudaStream_t s);
+void launch_inv_group(InvGroup& G, cudaStream_t s);
+void launch_adj_group(AdjGroup& G, cudaStream_t s);
+
 #if defined(__CUDACC__)
+
+// The request of this block in a grouped launch, and the block's tile and z-chunk within it.
+__device__ __forceinline__ int group_locate(const GroupGrid& G, int& bx, int& by, int& bz) {
+  const int b = blockIdx.x;
+  int r = 0;
+  while (r + 1 < G.n && b >= G.blk0[r + 1]) ++r;
+  const int local = b - G.blk0[r];
+  const int nbx = G.nbx[r], nby = G.nby[r];
+  bx = local % nbx;
+  by = (local / nbx) % nby;
+  bz = local / (nbx * nby);
+  return r;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 

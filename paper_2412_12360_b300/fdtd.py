@@ -27,6 +27,9 @@ FDTD_RECORD_FACES = 1
 KERNEL_NAMES = ["update_H", "update_E", "rev_E", "rev_H", "fused_fwd", "fused_rev", "face_copy", "det_adj",
                 "inv_fused", "adj_fused"]
 
+MAX_GROUP = 8
+PHASE_IDLE, PHASE_FORWARD, PHASE_FORWARD_DONE, PHASE_BACKWARD, PHASE_DONE = range(5)
+
 ERROR_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "UNSTABLE", -3: "OOM", -4: "CUDA", -5: "STATE",
                -6: "NONFINITE", -7: "TIMEOUT"}
 
@@ -94,6 +97,14 @@ SIGNATURES = [
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
+    ("fdtd_begin", C.c_int, [_VP, C.c_int32, C.c_uint32]),
+    ("fdtd_begin_backward", C.c_int, [_VP, _VP]),
+    ("fdtd_group_step", C.c_int, [C.POINTER(_VP), C.c_int32, C.c_int32]),
+    ("fdtd_phase", C.c_int, [_VP, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("fdtd_finish_backward", C.c_int, [_VP, _VP]),
+    ("fdtd_finish_backward_density", C.c_int, [_VP, _VP]),
+    ("fdtd_group_forward", C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(C.c_int32), C.c_uint32]),
+    ("fdtd_group_backward", C.c_int, [C.POINTER(_VP), C.c_int32, C.POINTER(_VP), C.POINTER(_VP)]),
     ("fdtd_set_check_interval", C.c_int, [_VP, C.c_int32]),
     ("fdtd_set_face_overlap", C.c_int, [_VP, C.c_int32]),
     ("fdtd_set_graphs", C.c_int, [_VP, C.c_int32]),
@@ -173,6 +184,35 @@ def footprint_bytes(scene, nsteps: Optional[int] = None, record_faces: bool = Tr
 
 def set_byte_budget(nbytes: int):
     check(lib().fdtd_set_byte_budget(int(nbytes)))
+
+
+def _handles(solvers):
+    arr = (_VP * len(solvers))()
+    for r, s in enumerate(solvers):
+        arr[r] = s.h
+    return arr
+
+
+def group_step(solvers, nsteps: int):
+    """fdtd_group_step: advance every solver's current phase by up to nsteps steps, one launch per
+    kernel and step for the whole group (the solvers must share one stream)."""
+    check(lib().fdtd_group_step(_handles(solvers), len(solvers), int(nsteps)))
+
+
+def group_forward(solvers, nsteps, record_faces: bool = False):
+    """fdtd_group_forward: whole forwards of a group (nsteps: one count per solver, or one for all)."""
+    ns = [int(nsteps)] * len(solvers) if np.isscalar(nsteps) else [int(v) for v in nsteps]
+    check(lib().fdtd_group_forward(_handles(solvers), len(solvers), (C.c_int32 * len(ns))(*ns),
+                                   FDTD_RECORD_FACES if record_faces else 0))
+    for s, n in zip(solvers, ns):
+        s.nsteps = n
+
+
+def group_backward(solvers, dL_ddet, dL_deps):
+    """fdtd_group_backward: the reverse sweeps of a group (lists of per-solver buffers)."""
+    g = (_VP * len(solvers))(*[_ptr(x) for x in dL_ddet])
+    o = (_VP * len(solvers))(*[_ptr(x) for x in dL_deps])
+    check(lib().fdtd_group_backward(_handles(solvers), len(solvers), g, o))
 
 
 class Solver:
@@ -305,6 +345,25 @@ class Solver:
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))
+
+    def fdtd_begin(self, nsteps: int, record_faces: bool = False):
+        check(lib().fdtd_begin(self.h, int(nsteps), FDTD_RECORD_FACES if record_faces else 0))
+        self.nsteps = int(nsteps)
+
+    def fdtd_begin_backward(self, dL_ddet):
+        check(lib().fdtd_begin_backward(self.h, _ptr(dL_ddet)))
+
+    def fdtd_phase(self):
+        """(phase, steps left in it)."""
+        ph, left = C.c_int32(0), C.c_int32(0)
+        check(lib().fdtd_phase(self.h, C.byref(ph), C.byref(left)))
+        return int(ph.value), int(left.value)
+
+    def fdtd_finish_backward(self, dL_deps):
+        check(lib().fdtd_finish_backward(self.h, _ptr(dL_deps)))
+
+    def fdtd_finish_backward_density(self, dL_drho):
+        check(lib().fdtd_finish_backward_density(self.h, _ptr(dL_drho)))
 
     def fdtd_set_check_interval(self, every: int):
         """Check the fields for NaN / infinity every `every` forward steps too (0: at sweep ends only)."""
