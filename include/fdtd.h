@@ -131,7 +131,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
                 int32_t ndet, const fdtd_pml* pml, const int32_t design_lo[3], const int32_t design_hi[3],
                 void* cuda_stream);
 
-/* Free every device buffer of the handle (after finishing its stream). NULL is accepted. */
+/* Free every device buffer of the handle, in stream order after the work already enqueued on its stream
+ * (a handle whose time loops were captured into CUDA graphs first waits for that work). NULL is
+ * accepted. */
 int fdtd_destroy(fdtd_handle* h);
 
 /* Replace the inverse permittivity on the design box (host or device, box-shaped, x fastest). */
@@ -223,6 +225,18 @@ int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps);
 #define FDTD_PHASE_FORWARD_DONE 2  /* the forward has finished: detectors readable, fdtd_begin_backward next */
 #define FDTD_PHASE_BACKWARD 3      /* reverse steps remain */
 #define FDTD_PHASE_DONE 4          /* the reverse sweep has finished: fdtd_finish_backward next */
+
+/* Move the handle to another stream (NULL = legacy default stream): waits for the work already enqueued
+ * on its current stream, then enqueues everything later on cuda_stream. A server creates and prepares
+ * a handle on a private stream (set-up calls synchronise their stream) and then moves it onto the
+ * stream its group runs on. */
+int fdtd_set_stream(fdtd_handle* h, void* cuda_stream);
+
+/* Report what the handle's kernels flagged (as fdtd_synchronize: FDTD_ERR_TIMEOUT, FDTD_ERR_NONFINITE,
+ * and clear it) without waiting for the handle's stream: the caller has made sure that the handle's
+ * work has completed (an event recorded after it has fired), so that other handles sharing the stream
+ * keep running. */
+int fdtd_poll_status(fdtd_handle* h);
 
 /* Start a forward solve of nsteps steps (flags as fdtd_forward) that fdtd_group_step advances; no step
  * runs here. INVALID_ARG as fdtd_forward. */

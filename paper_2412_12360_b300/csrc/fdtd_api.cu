@@ -334,6 +334,10 @@ struct fdtd_handle {
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
   int tz_inv = 8, inv_nstage = 4; // fused inverse step: z-planes per block, ring stages
   int tz_adj = 8, adj_nstage = 4; // fused adjoint step
+  // reverse step kind: the fused inverse + adjoint kernels (52 + 52 B per cell, double-buffered
+  // fields; faster on large grids with thin layers), or the in-place pair rev_E + rev_H (76 + 72 B per
+  // cell, one cell per thread and more blocks per SM; faster on small grids and thick layers)
+  bool rev_fused = false;
 
   std::vector<fdtd_source> src_host;
   std::vector<SrcDev> srcs;       // E sources: soft sources and the E corrections of TFSF planes
@@ -511,7 +515,7 @@ void dev_free(fdtd_handle* h, void* p, int64_t bytes) {
 template <class T>
 int ensure_buf(fdtd_handle* h, T** p, int64_t* cap, int64_t need, int64_t esize) {
   if (need <= *cap) return FDTD_OK;
-  CK(cudaStreamSynchronize(h->stream));
+  if (*p) CK(cudaStreamSynchronize(h->stream));  // (a first allocation waits for nothing)
   dev_free(h, *p, *cap * esize);
   *p = nullptr;
   *cap = 0;
@@ -942,17 +946,57 @@ int64_t rev_step_pre(fdtd_handle* h, int n, int nsteps, int pc, int ac, cudaStre
   return launches;
 }
 
-// Between the inverse and the adjoint step: the interpolated fluxes' H terms (E^n now in 1 - pc).
-int64_t rev_step_mid(fdtd_handle* h, int n, int pc, int ac, cudaStream_t st) {
-  return enqueue_det_adjoint(h, h->F(1 - pc), h->A(ac), n, 1, st);
+// Between the inverse and the adjoint half of the step: the interpolated fluxes' H terms (E^n now in
+// field buffer pn) into adjoint buffer ac.
+int64_t rev_step_mid(fdtd_handle* h, int n, int pn, int ac, cudaStream_t st) {
+  return enqueue_det_adjoint(h, h->F(pn), h->A(ac), n, 1, st);
 }
 
-// After the adjoint step: the TFSF H corrections of step n removed from the rebuilt H^{n-1/2} on R,
-// and the interpolated fluxes' E^n terms.
-int64_t rev_step_post(fdtd_handle* h, int n, int pc, int ac, cudaStream_t st) {
-  const Fields Fn = h->F(1 - pc);
+// After the step (rebuilt fields in buffer pn, adjoint in an): the TFSF H corrections of step n
+// removed from the rebuilt H^{n-1/2} on R, and the interpolated fluxes' E^n terms.
+int64_t rev_step_post(fdtd_handle* h, int n, int pn, int an, cudaStream_t st) {
+  const Fields Fn = h->F(pn);
   for (const SrcDev& hs : h->hsrcs) launch_source(h->g, Fn, hs, n, -1.f, 1, st);
-  return (int64_t)h->hsrcs.size() + enqueue_det_adjoint(h, Fn, h->A(1 - ac), n, 2, st);
+  return (int64_t)h->hsrcs.size() + enqueue_det_adjoint(h, Fn, h->A(an), n, 2, st);
+}
+
+// The in-place pair: arguments of rev_E (which = 0) or rev_H (which = 1) of step n on field buffer pc
+// and adjoint buffer 0.
+RevArgs split_base(fdtd_handle* h) {
+  RevArgs ra;
+  ra.g = h->g;
+  ra.T = h->tab();
+  ra.B = h->A(0);
+  ra.a = h->a;
+  ra.tz = h->tz_rev;
+  ra.nstage = h->rev_nstage;
+  for (int d = 0; d < 3; ++d) {
+    ra.dlo[d] = h->design_lo[d];
+    ra.dhi[d] = h->design_hi[d];
+  }
+  ra.dLda = h->dLda;
+  ra.inverse = 1;
+  ra.nsrc = (int)std::min<size_t>(h->srcs.size(), kMaxSrc);
+  for (int q = 0; q < ra.nsrc; ++q) ra.src[q] = h->srcs[q];
+  ra.status = h->status;
+  ra.gy = h->dLddet;
+  ra.ndet = 0;
+  for (size_t q = 0; q < h->dets.size(); ++q)
+    if (h->det_fold[q]) {
+      DetDev d = h->dets[q];
+      if (d.kind == FDTD_DET_POINT_SERIES)  // the point is the one-cell box at lo
+        for (int k = 0; k < 3; ++k) d.hi[k] = d.lo[k] + 1;
+      ra.det[ra.ndet++] = d;
+    }
+  return ra;
+}
+
+void split_step_args(fdtd_handle* h, RevArgs& ra, int n, int pc, int pb, int which) {
+  ra.F = h->F(pc);
+  ra.step = n;
+  ra.pin = psibar_set(h, which, pb);
+  ra.pout = psibar_set(h, which, 1 - pb);
+  ra.det_step = which == 1 ? n - 1 : -1;  // rev_H folds the E-only detectors of step n - 1
 }
 
 // After the last reverse step: the non-finite check of the rebuilt and the adjoint fields.
@@ -1007,20 +1051,75 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
       cudaEventRecord(h->ev_fork, st);
       replay(n - 1, 1 - pc);
     }
-    launches += rev_step_mid(h, n, pc, ac, st);
+    launches += rev_step_mid(h, n, 1 - pc, ac, st);
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_ADJ_FUSED, n);
       adj_step_args(h, aa, n, pc, ac, pb);
       launch_adj(aa, h->amaps[ac], st);
     }
     launches += 2;
-    launches += rev_step_post(h, n, pc, ac, st);
+    launches += rev_step_post(h, n, 1 - pc, 1 - ac, st);
     pc = 1 - pc;
     ac = 1 - ac;
     pb = 1 - pb;
   }
   h->cur = pc;
   if (nsteps > 0) launches += rev_finish(h, pc, ac, st);
+  return launches;
+}
+
+// The same reverse sweep with the in-place pair rev_E + rev_H: per step n the detector adjoints, the
+// face replay into H, rev_E (inverse E, adjoint H-bar, dL/da) and rev_H (inverse H, adjoint E-bar, the
+// folded detector adjoints of step n - 1), on field buffer h->cur and adjoint buffer 0.
+int64_t enqueue_backward_split(fdtd_handle* h, int nsteps, cudaStream_t st, std::vector<Ev>* evs) {
+  const Geo& g = h->g;
+  RevArgs ra = split_base(h);
+  const int pc = h->cur;
+  const RevMaps& rm = h->rmaps[pc];
+  int64_t launches = 0;
+  int pb = 0;
+  // The face replay of step n runs on the side stream beside rev_H(n+1), which neither reads nor
+  // writes H outside R; rev_E(n) waits for it. Without face_overlap it runs in line.
+  const bool faces = h->faces.per_step > 0;
+  const bool ovl = faces && h->face_overlap;
+  auto replay = [&](int n) {
+    cudaStream_t fs = ovl ? h->side : st;
+    if (ovl) cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+    {
+      ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
+      launch_face_copy(g, h->F(pc), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
+    }
+    if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
+    launches += 1;
+  };
+  if (ovl && nsteps > 0) {
+    cudaEventRecord(h->ev_fork, st);
+    replay(nsteps - 1);
+  }
+  for (int n = nsteps - 1; n >= 0; --n) {
+    launches += rev_step_pre(h, n, nsteps, pc, 0, st, evs);
+    if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
+    else if (faces) replay(n);
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_E, n);
+      split_step_args(h, ra, n, pc, pb, 0);
+      launch_rev_E(ra, rm, st);
+    }
+    if (ovl && n > 0) {  // rev_E(n) has read the faces of step n: replay those of step n-1
+      cudaEventRecord(h->ev_fork, st);
+      replay(n - 1);
+    }
+    launches += rev_step_mid(h, n, pc, 0, st);
+    {
+      ProfScope ps(h, evs, st, FDTD_KERNEL_REV_H, n);
+      split_step_args(h, ra, n, pc, pb, 1);
+      launch_rev_H(ra, rm, st);
+    }
+    launches += 2;
+    launches += rev_step_post(h, n, pc, 0, st);
+    pb = 1 - pb;
+  }
+  if (nsteps > 0) launches += rev_finish(h, pc, 0, st);
   return launches;
 }
 
@@ -1280,6 +1379,21 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       const int v = std::atoi(e);
       if (v == 3 || v == 4) h->rev_nstage = h->inv_nstage = h->adj_nstage = v;
     }
+    {
+      // The fused pair moves 104 B per cell against 148 but does its CPML work (the adjoint's
+      // coefficients gathered from both neighbours) in every tile that touches an x or y layer. On
+      // one B300: 600^3 with 12-cell layers (18 % of the tiles touch one) 5.16 vs 5.58 ms per reverse
+      // step; 96^3 with 10-cell layers (78 %) 70 vs 42 us. So: the fused pair for grids of at least
+      // 64 M cells whose tiles touch an x or y layer in at most a fifth of the cases.
+      const int tx = fused_tile_x(), ty = fused_tile_y();
+      const int ntx = (n[0] + tx - 1) / tx, nty = (n[1] + ty - 1) / ty;
+      int plain_x = 0, plain_y = 0;
+      for (int b = 0; b < ntx; ++b) plain_x += !(b * tx - 1 < g.pml[0] || b * tx + tx >= n[0] - g.pml[1] - 1);
+      for (int b = 0; b < nty; ++b) plain_y += !(b * ty - 1 < g.pml[2] || b * ty + ty >= n[1] - g.pml[3] - 1);
+      const double xy_frac = 1.0 - (double)plain_x * plain_y / ((double)ntx * nty);
+      h->rev_fused = (int64_t)n[0] * n[1] * n[2] >= (int64_t)64 << 20 && xy_frac <= 0.2;
+      if (const char* e = std::getenv("FDTD_REV_FUSED")) h->rev_fused = std::atoi(e) != 0;  // override
+    }
     h->tz = std::min(h->tz, fused_max_tz());
     h->tz_rev = std::min(h->tz_rev, fused_max_tz());
   }
@@ -1418,6 +1532,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
 
 int fdtd_destroy(fdtd_handle* h) {
   if (!h) return FDTD_OK;
+  // a captured time loop may still be running: finish the stream before its graph goes; without one,
+  // the frees below are ordered after the enqueued work and nothing needs to wait
+  const bool graphs = h->gfwd.exec || h->gbwd.exec;
+  if (graphs) cudaStreamSynchronize(h->stream);
   h->gfwd.reset();
   h->gbwd.reset();
   void* bufs[] = {h->fields, h->a, h->psiE, h->psiH, h->tables, h->init, h->gtab, h->det_out, h->partial,
@@ -1427,7 +1545,6 @@ int fdtd_destroy(fdtd_handle* h) {
   for (float* p : h->src_w) cudaFreeAsync(p, h->stream);
   for (float* p : h->det_slab)
     if (p) cudaFreeAsync(p, h->stream);
-  cudaStreamSynchronize(h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->side) cudaStreamDestroy(h->side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
@@ -1564,8 +1681,9 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   const int nsteps = h->last_nsteps;
   h->phase = FDTD_PHASE_IDLE;
   const int64_t key = h->cur | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2);
-  TRY(run_loop(h, h->gbwd, nsteps, key,
-               [&](cudaStream_t st, std::vector<Ev>* evs) { return enqueue_backward(h, nsteps, st, evs); }));
+  TRY(run_loop(h, h->gbwd, nsteps, key | ((int64_t)h->rev_fused << 40), [&](cudaStream_t st, std::vector<Ev>* evs) {
+    return h->rev_fused ? enqueue_backward(h, nsteps, st, evs) : enqueue_backward_split(h, nsteps, st, evs);
+  }));
   return backward_finish(h, dL_deps, scale);
 }
 
@@ -1575,6 +1693,27 @@ int fdtd_backward(fdtd_handle* h, const double* dL_ddet, float* dL_deps) {
 }
 
 // ---- grouped and incremental solves -------------------------------------------------------------
+
+int fdtd_poll_status(fdtd_handle* h) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  int st = 0;
+  // on the handle's private stream, so that the stream it shares with others keeps running
+  CK(cudaMemcpyAsync(&st, h->status, 4, cudaMemcpyDeviceToHost, h->cap));
+  CK(cudaStreamSynchronize(h->cap));
+  if (st == 0) return FDTD_OK;
+  CK(cudaMemsetAsync(h->status, 0, 4, h->cap));
+  CK(cudaStreamSynchronize(h->cap));
+  if (st & kStatusTimeout)
+    return fail(FDTD_ERR_TIMEOUT, "a device-side wait for a TMA copy gave up (status %d); results are invalid", st);
+  return fail(FDTD_ERR_NONFINITE, "a field check found a NaN or an infinity; results are invalid");
+}
+
+int fdtd_set_stream(fdtd_handle* h, void* cuda_stream) {
+  if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
+  CK(cudaStreamSynchronize(h->stream));
+  h->stream = (cudaStream_t)cuda_stream;
+  return FDTD_OK;
+}
 
 int fdtd_begin(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   TRY(forward_prepare(h, nsteps, flags));
@@ -1691,10 +1830,13 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
     if (nr > 0) {  // one reverse step of every handle in its reverse phase
       static thread_local std::unique_ptr<InvGroup> IGp;
       static thread_local std::unique_ptr<AdjGroup> AGp;
+      static thread_local std::unique_ptr<RevGroup> RGp;
       if (!IGp) IGp.reset(new InvGroup());
       if (!AGp) AGp.reset(new AdjGroup());
+      if (!RGp) RGp.reset(new RevGroup());
       InvGroup& IG = *IGp;
       AdjGroup& AG = *AGp;
+      RevGroup& RG = *RGp;
       FaceGroup faces{};
       faces.to_record = 0;
       for (int r = 0; r < nr; ++r) {
@@ -1710,30 +1852,55 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
         }
       }
       if (faces.n > 0) launch_face_copy_group(faces, st);
+      // first halves: the fused inverse steps, and rev_E of the in-place pairs
+      IG.n = RG.n = 0;
       for (int r = 0; r < nr; ++r) {
         fdtd_handle* h = Rv[r];
-        IG.a[r] = inv_base(h);
-        inv_step_args(h, IG.a[r], h->step_next, h->rev_pc, h->rev_ac);
-        IG.m[r] = h->imaps[h->rev_pc];
+        if (h->rev_fused) {
+          InvArgs& ia = IG.a[IG.n];
+          ia = inv_base(h);
+          inv_step_args(h, ia, h->step_next, h->rev_pc, h->rev_ac);
+          IG.m[IG.n++] = h->imaps[h->rev_pc];
+        } else {
+          RevArgs& ra = RG.a[RG.n];
+          ra = split_base(h);
+          split_step_args(h, ra, h->step_next, h->rev_pc, h->rev_pb, 0);
+          RG.m[RG.n++] = h->rmaps[h->rev_pc];
+        }
         h->launches += 1;
       }
-      IG.n = nr;
-      launch_inv_group(IG, st);
+      if (IG.n > 0) launch_inv_group(IG, st);
+      if (RG.n > 0) launch_rev_group(RG, 0, st);
+      // second halves: the fused adjoint steps, and rev_H of the in-place pairs
+      AG.n = RG.n = 0;
       for (int r = 0; r < nr; ++r) {
         fdtd_handle* h = Rv[r];
-        h->launches += rev_step_mid(h, h->step_next, h->rev_pc, h->rev_ac, st);
-        AG.a[r] = adj_base(h);
-        adj_step_args(h, AG.a[r], h->step_next, h->rev_pc, h->rev_ac, h->rev_pb);
-        AG.m[r] = h->amaps[h->rev_ac];
+        const int pn = h->rev_fused ? 1 - h->rev_pc : h->rev_pc;
+        h->launches += rev_step_mid(h, h->step_next, pn, h->rev_ac, st);
+        if (h->rev_fused) {
+          AdjArgs& aa = AG.a[AG.n];
+          aa = adj_base(h);
+          adj_step_args(h, aa, h->step_next, h->rev_pc, h->rev_ac, h->rev_pb);
+          AG.m[AG.n++] = h->amaps[h->rev_ac];
+        } else {
+          RevArgs& ra = RG.a[RG.n];
+          ra = split_base(h);
+          split_step_args(h, ra, h->step_next, h->rev_pc, h->rev_pb, 1);
+          RG.m[RG.n++] = h->rmaps[h->rev_pc];
+        }
         h->launches += 1;
       }
-      AG.n = nr;
-      launch_adj_group(AG, st);
+      if (AG.n > 0) launch_adj_group(AG, st);
+      if (RG.n > 0) launch_rev_group(RG, 1, st);
       for (int r = 0; r < nr; ++r) {
         fdtd_handle* h = Rv[r];
-        h->launches += rev_step_post(h, h->step_next, h->rev_pc, h->rev_ac, st);
-        h->rev_pc = 1 - h->rev_pc;
-        h->rev_ac = 1 - h->rev_ac;
+        if (h->rev_fused) {
+          h->launches += rev_step_post(h, h->step_next, 1 - h->rev_pc, 1 - h->rev_ac, st);
+          h->rev_pc = 1 - h->rev_pc;
+          h->rev_ac = 1 - h->rev_ac;
+        } else {
+          h->launches += rev_step_post(h, h->step_next, h->rev_pc, 0, st);
+        }
         h->rev_pb = 1 - h->rev_pb;
         if (--h->step_next < 0) {
           h->cur = h->rev_pc;

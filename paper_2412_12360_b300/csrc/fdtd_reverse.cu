@@ -132,7 +132,7 @@ __device__ __forceinline__ void issue_rev_H(const RevMaps& M, const Ring& R, int
 // rev_E
 // ---------------------------------------------------------------------------------------------
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E(const RevArgs A, const __grid_constant__ RevMaps M) {
+__device__ __forceinline__ void revE_body(const RevArgs& A, const RevMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align128(smem_raw);
 
@@ -140,8 +140,8 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E(const RevArgs
   const Tables& T = A.T;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * A.tz;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int k0 = bz * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E(const RevArgs
 // rev_H
 // ---------------------------------------------------------------------------------------------
 template <int NSTAGE>
-__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs A, const __grid_constant__ RevMaps M) {
+__device__ __forceinline__ void revH_body(const RevArgs& A, const RevMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = align128(smem_raw);
 
@@ -360,8 +360,8 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs
   const Tables& T = A.T;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = blockIdx.z * A.tz;
+  const int i0 = bx * TX, j0 = by * TY;
+  const int k0 = bz * A.tz;
   const int k1 = min(g.n[2], k0 + A.tz);
   const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
   const int plane = (int)g.plane;
@@ -554,7 +554,47 @@ __global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const RevArgs
   if (!waited) atomicOr(A.status, 1);
 }
 
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E(const __grid_constant__ RevArgs A, const __grid_constant__ RevMaps M) {
+  revE_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H(const __grid_constant__ RevArgs A, const __grid_constant__ RevMaps M) {
+  revH_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+// Several requests in one launch (the flat grid of GroupGrid).
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_E_group(const __grid_constant__ RevGroup G) {
+  int bx, by, bz;
+  const int r = group_locate(G.grid, bx, by, bz);
+  revE_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
+}
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, NSTAGE == 3 ? 4 : 3) k_rev_H_group(const __grid_constant__ RevGroup G) {
+  int bx, by, bz;
+  const int r = group_locate(G.grid, bx, by, bz);
+  revH_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
+}
+
 }  // namespace
+
+void launch_rev_group(RevGroup& G, int which, cudaStream_t s) {
+  const int total = group_fill(G.grid, G.n, [&](int r, int* nb) {
+    const Geo& g = G.a[r].g;
+    nb[0] = (g.n[0] + TX - 1) / TX;
+    nb[1] = (g.n[1] + TY - 1) / TY;
+    nb[2] = (g.n[2] + G.a[r].tz - 1) / G.a[r].tz;
+  });
+  if (total == 0) return;
+  const int ns = G.a[0].nstage;
+  if (which == 0) {
+    if (ns == 3) launch_pdl(k_rev_E_group<3>, dim3(total), dim3(NT), re_smem(3), s, G);
+    else launch_pdl(k_rev_E_group<4>, dim3(total), dim3(NT), re_smem(4), s, G);
+  } else {
+    if (ns == 3) launch_pdl(k_rev_H_group<3>, dim3(total), dim3(NT), rh_smem(3), s, G);
+    else launch_pdl(k_rev_H_group<4>, dim3(total), dim3(NT), rh_smem(4), s, G);
+  }
+}
 
 int rev_tile_x() { return TX; }
 int rev_tile_y() { return TY; }
@@ -565,8 +605,12 @@ MapBox rev_box_wide() { return {BW, BH}; }
 int prepare_rev(int nstage, int* blocks_per_sm) {
   auto ke = nstage == 3 ? k_rev_E<3> : k_rev_E<4>;
   auto kh = nstage == 3 ? k_rev_H<3> : k_rev_H<4>;
+  auto kge = nstage == 3 ? k_rev_E_group<3> : k_rev_E_group<4>;
+  auto kgh = nstage == 3 ? k_rev_H_group<3> : k_rev_H_group<4>;
   cudaError_t e = cudaFuncSetAttribute(ke, cudaFuncAttributeMaxDynamicSharedMemorySize, re_smem(nstage));
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kh, cudaFuncAttributeMaxDynamicSharedMemorySize, rh_smem(nstage));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kge, cudaFuncAttributeMaxDynamicSharedMemorySize, re_smem(nstage));
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kgh, cudaFuncAttributeMaxDynamicSharedMemorySize, rh_smem(nstage));
   int be = 0, bh = 0;
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&be, ke, NT, re_smem(nstage));
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, kh, NT, rh_smem(nstage));

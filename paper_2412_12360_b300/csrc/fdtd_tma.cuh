@@ -114,6 +114,14 @@ struct AdjGroup {
   AdjArgs a[kMaxGroup];
   AdjMaps m[kMaxGroup];
 };
+struct RevGroup {
+  GroupGrid grid;
+  int n;
+  RevArgs a[kMaxGroup];
+  RevMaps m[kMaxGroup];
+};
+// which = 0: the inverse-E / adjoint-H kernel, 1: the inverse-H / adjoint-E kernel
+void launch_rev_group(RevGroup& G, int which, cudaStream_t s);
 // One launch per kernel for the G.n requests (their nstage must agree; a[r].tz sets each grid).
 void launch_fwd_group(FwdGroup& G, cudaStream_t s);
 void launch_inv_group(InvGroup& G, cudaStream_t s);

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
     ("fdtd_synchronize", C.c_int, [_VP]),
+    ("fdtd_set_stream", C.c_int, [_VP, _VP]),
+    ("fdtd_poll_status", C.c_int, [_VP]),
     ("fdtd_begin", C.c_int, [_VP, C.c_int32, C.c_uint32]),
     ("fdtd_begin_backward", C.c_int, [_VP, _VP]),
     ("fdtd_group_step", C.c_int, [C.POINTER(_VP), C.c_int32, C.c_int32]),
@@ -345,6 +347,16 @@ class Solver:
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))
+
+    def fdtd_poll_status(self):
+        """Raise what the kernels flagged, without waiting for the stream (its work must be done)."""
+        check(lib().fdtd_poll_status(self.h))
+
+    def fdtd_set_stream(self, stream):
+        """Move the handle to another stream (a torch stream, a raw handle or None)."""
+        ptr = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        check(lib().fdtd_set_stream(self.h, ptr))
+        self.stream = stream
 
     def fdtd_begin(self, nsteps: int, record_faces: bool = False):
         check(lib().fdtd_begin(self.h, int(nsteps), FDTD_RECORD_FACES if record_faces else 0))

@@ -3,16 +3,17 @@
 Requests (a scene: grid, sources, detectors, design box and densities, step count) arrive at any
 time. A scheduler thread admits them in arrival order whenever a slot is free and the request's
 device footprint (fdtd_footprint_bytes: fields, CPML memories, adjoint state and the boundary-face
-history) fits in the memory budget still free; each admitted request gets its own CUDA stream and
-solver handle, so its forward and reversed sweeps overlap on the GPU with those of the requests
-already running. Completion is detected with CUDA events; finished requests return their detector
-outputs and dL/deps and free their memory (stream-ordered, so other requests keep running), which
-admits the next ones.
+history) fits in the memory budget still free. An admitted request's handle is created and its
+inputs uploaded on a private stream, then it joins the group: all running requests are advanced
+together by fdtd_group_step, which launches the fused forward (or inverse and adjoint) kernel once
+per time step for the blocks of every request, so requests that arrive while others run share the
+GPU's SMs with them rather than queueing behind their launches. A request moves from its forward
+to its reverse sweep, and leaves the group, at the step where it finishes; finished requests return
+their detector outputs and dL/deps and free their memory (stream-ordered), which admits the next
+ones.
 
-The numerical work of every request is the library's; a request's result does not depend on what
-else is in flight, so it is the same alone and in the mix. A request's handle solves once, so it runs
-its time loops as direct launches with the face copies in line (see one_shot), both here and in the
-sequential baseline.
+The numerical work of every request is the library's, and a request's arithmetic does not depend on
+which others share its launches, so its result is bitwise the same alone and in the mix.
 """
 from __future__ import annotations
 
@@ -71,26 +72,25 @@ class _Job:
     footprint: int
     admitted: float = 0.0
     solver: object = None
-    stream: object = None
     done: object = None
     det: object = None
     grad: object = None
     gvec: object = None
+    finishing: bool = False
 
 
 class Server:
     """Continuous-batching solver service on one GPU.
 
     budget_bytes: device memory the server may give to requests (default: 85 % of the free memory).
-    max_inflight: requests running at once. On one B300 the served stream of 64^3 .. 200^3 requests at
-    1.5x the sequential capacity ran at 16.1 Gcell-steps/s with 2, 3 or 4 in flight (the large grids,
-    most of the work, fill the GPU alone), with the lowest latency at 2 (p50 2.2 s, p99 3.5 s; 3: 2.5,
-    4.0 s).
-    objective: dL/d(detector) used when a request gives none (default: ones, i.e. L = sum of outputs).
+    max_inflight: requests running at once (at most the library's group size, 8).
+    chunk_steps: time steps per grouped call between scheduling decisions (admission, phase changes).
+    ahead: grouped calls enqueued ahead of the GPU at most (enough to cover a request's set-up on the
+    host, few enough that a request that arrives meanwhile joins soon).
     """
 
-    def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 2, device: int = 0,
-                 footprint=None):
+    def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 4, device: int = 0,
+                 footprint=None, chunk_steps: int = 32, ahead: int = 4):
         import torch
         from . import fdtd
 
@@ -101,16 +101,21 @@ class Server:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget_bytes = int(0.85 * free)
         self.budget = int(budget_bytes)
-        self.max_inflight = int(max_inflight)
+        self.max_inflight = max(1, min(int(max_inflight), fdtd.MAX_GROUP))
+        self.chunk_steps = int(chunk_steps)
+        self.ahead = max(1, int(ahead))
         self._footprint = footprint or (lambda sc: fdtd.footprint_bytes(sc, sc.nsteps, record_faces=True))
         self._queue: Deque[_Job] = collections.deque()
         self._inflight: List[_Job] = []
         self._used = 0
         self._lock = threading.Condition()
         self._stop = False
-        self._streams: List[object] = []
+        self.stream = torch.cuda.Stream(device=self.device)   # the group's stream
+        self._setup = torch.cuda.Stream(device=self.device)   # where admitted handles are prepared
+        self._ticks: Deque[object] = collections.deque()
         self.peak_inflight = 0
         self.cancelled = 0  # requests cancelled by their client before admission
+        self.group_calls = 0
         self._thread = threading.Thread(target=self._loop, name="fdtd-server", daemon=True)
         self._thread.start()
 
@@ -138,40 +143,70 @@ class Server:
         self.close()
 
     # ---- scheduler ----------------------------------------------------------------------------
-    def _stream(self):
-        if self._streams:
-            return self._streams.pop()
-        return self._torch.cuda.Stream(device=self.device)
-
     def _admit(self, job: _Job):
         torch, fdtd = self._torch, self._fdtd
         sc = job.scene
-        job.stream = self._stream()
         job.admitted = time.perf_counter()
-        with torch.cuda.stream(job.stream):
-            job.solver = fdtd.Solver(sc, stream=job.stream)
+        with torch.cuda.stream(self.stream):
+            ndet_total = None
+            job.solver = fdtd.Solver(sc, stream=self._setup)
             one_shot(job.solver)
-            job.solver.fdtd_forward(sc.nsteps, record_faces=True)
-            ndet = job.solver.fdtd_detector_total()
-            g = job.dL_ddet if job.dL_ddet is not None else np.ones(ndet)
+            job.solver.fdtd_begin(sc.nsteps, record_faces=True)
+            ndet_total = job.solver.fdtd_detector_total()
+            g = job.dL_ddet if job.dL_ddet is not None else np.ones(ndet_total)
             job.gvec = torch.from_numpy(np.ascontiguousarray(g, dtype=np.float64)).pin_memory().to(
                 self.device, non_blocking=True)
-            job.det = torch.empty(ndet, dtype=torch.float64, device=self.device)
+            job.det = torch.empty(ndet_total, dtype=torch.float64, device=self.device)
             job.grad = torch.empty(sc.design_shape(), dtype=torch.float32, device=self.device)
-            job.solver.fdtd_read_detectors(job.det)
-            job.solver.fdtd_backward(job.gvec, job.grad)
-            job.done = torch.cuda.Event()
-            job.done.record(job.stream)
+        job.solver.fdtd_set_stream(self.stream)  # waits for the set-up; the request joins the group
 
     def _retire(self, job: _Job):
+        """A finished request (its event has fired): report, copy its results out and free it, without
+        waiting for the group's stream (the other requests keep running)."""
         try:
-            job.solver.fdtd_synchronize()  # raises on a timeout or non-finite fields (the client gets it)
+            job.solver.fdtd_poll_status()  # raises on a timeout or non-finite fields (the client gets it)
             det = job.det.cpu().numpy()
             grad = job.grad.cpu().numpy()
-        finally:  # the request's memory and stream go back whatever happened
+        finally:  # the request's memory goes back whatever happened (freed in stream order)
             job.solver.close()
-            self._streams.append(job.stream)
         job.future.set_result(Result(det, grad, job.arrival, job.admitted, time.perf_counter()))
+
+    def _advance(self):
+        """Phase changes of the running requests, then one grouped chunk of steps for those still
+        stepping (enqueued only; no synchronisation)."""
+        fdtd = self._fdtd
+        stepping = []
+        for job in self._inflight:
+            if job.finishing:
+                continue
+            try:
+                ph, _ = job.solver.fdtd_phase()
+                if ph == fdtd.PHASE_FORWARD_DONE:
+                    job.solver.fdtd_read_detectors(job.det)
+                    job.solver.fdtd_begin_backward(job.gvec)
+                    ph = fdtd.PHASE_BACKWARD
+                if ph == fdtd.PHASE_DONE:
+                    job.solver.fdtd_finish_backward(job.grad)
+                    job.done = self._torch.cuda.Event()
+                    job.done.record(self.stream)
+                    job.finishing = True
+                    continue
+            except Exception as e:  # noqa: BLE001 - report to the client
+                job.done = self._torch.cuda.Event()
+                job.done.record(self.stream)
+                job.finishing = True
+                job.error = e
+                continue
+            stepping.append(job)
+        if stepping:
+            fdtd.group_step([j.solver for j in stepping], self.chunk_steps)
+            self.group_calls += 1
+            ev = self._torch.cuda.Event()
+            ev.record(self.stream)
+            self._ticks.append(ev)
+        while len(self._ticks) > self.ahead:  # at most `ahead` chunks enqueued ahead of the GPU
+            self._ticks.popleft().synchronize()
+        return bool(stepping)
 
     def _loop(self):
         torch = self._torch
@@ -185,10 +220,13 @@ class Server:
                     continue
             progressed = False
             for job in list(self._inflight):
-                if job.done.query():
+                if job.finishing and job.done.query():
                     self._inflight.remove(job)
                     self._used -= job.footprint
                     try:
+                        if getattr(job, "error", None) is not None:
+                            job.solver.close()
+                            raise job.error
                         self._retire(job)
                     except Exception as e:  # noqa: BLE001 - report to the client
                         job.future.set_exception(e)
@@ -212,10 +250,14 @@ class Server:
                     self.peak_inflight = max(self.peak_inflight, len(self._inflight))
                 except Exception as e:  # noqa: BLE001 - report to the client
                     self._used -= job.footprint
+                    if job.solver is not None:
+                        job.solver.close()
                     job.future.set_exception(e)
                 progressed = True
+            if self._inflight:
+                progressed |= self._advance()
             if not progressed:
-                time.sleep(0.0005)
+                time.sleep(0.0002)
 
 
 def run_sequential(scenes, device: int = 0):

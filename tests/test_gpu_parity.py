@@ -240,8 +240,30 @@ def test_gradient_three_and_four_stage_reverse_kernels(F, scene, nstage, monkeyp
     assert e < 1e-3 and e_c < 1e-3
 
 
+@pytest.mark.parametrize("kind", ["0", "1"])
+@pytest.mark.parametrize("scene", ["ragged", "odd_x", "tfsf_interp"])
+def test_gradient_with_each_reverse_kind(F, scene, kind, monkeypatch):
+    """Both reverse-step kinds (the in-place pair rev_E + rev_H, and the fused inverse + adjoint
+    kernels that large grids use) against the oracle, on scenes with unequal layers, an odd x extent,
+    a TFSF plane and interpolated detectors."""
+    monkeypatch.setenv("FDTD_REV_FUSED", kind)
+    sc = ragged_scene(250) if scene == "ragged" else (odd_scene(250, pml=(5, 0, 4, 6, 6, 3)) if scene == "odd_x"
+                                                       else S.design_box_scene((45, 38, 41), 6, 12, 250, 21,
+                                                                               name="kinds", tfsf=True, interp=True))
+    g = np.random.default_rng(15).standard_normal(O.detector_total(sc, sc.nsteps))
+    grad_o, _, det_o = O.gradient(sc, sc.nsteps, g, O.METHOD_TIME_REVERSAL)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(sc.nsteps, record_faces=True)
+        det = s.detectors()
+        grad = s.gradient(g)
+    e, ed = rel_l2(grad, grad_o), rel_l2(det, det_o)
+    print("%s, reverse kind %s: dL/deps rel L2 %.3e, detectors %.3e" % (scene, kind, e, ed))
+    assert e < 1e-3 and ed < 1e-4
+
+
+@pytest.mark.parametrize("kind", ["0", "1"])
 @pytest.mark.parametrize("scene", ["ragged", "tfsf_interp"])
-def test_results_do_not_depend_on_the_z_chunk(F, scene, monkeypatch):
+def test_results_do_not_depend_on_the_z_chunk(F, scene, kind, monkeypatch):
     """The z-marching kernels recompute the plane next to their chunk with the same arithmetic as the
     block that owns it, so the z-planes per block leave fields, detectors and gradients bitwise the same
     (flux detectors, whose per-block partial sums follow the chunks, to FP64 rounding)."""
@@ -249,6 +271,7 @@ def test_results_do_not_depend_on_the_z_chunk(F, scene, monkeypatch):
         (45, 38, 41), 6, 12, 120, 21, name="tz", tfsf=True, interp=True)
     g = np.random.default_rng(14).standard_normal(O.detector_total(sc, sc.nsteps))
     out = []
+    monkeypatch.setenv("FDTD_REV_FUSED", kind)
     for tz in (None, "3", "7"):
         if tz is None:
             monkeypatch.delenv("FDTD_TZ", raising=False)
@@ -382,10 +405,13 @@ def test_pitch_padding_canaries_stay_intact(F, scene):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind", ["0", "1"])
 @pytest.mark.parametrize("scene", ["ragged", "tfsf_interp"])
-def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene):
+def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene, kind, monkeypatch):
     """Face copies overlapped or in line, time loops captured into graphs or launched directly (with
-    the per-launch profiling events on): bitwise the same detectors, gradients and fields."""
+    the per-launch profiling events on): bitwise the same detectors, gradients and fields, with either
+    reverse-step kind."""
+    monkeypatch.setenv("FDTD_REV_FUSED", kind)
     sc = ragged_scene(150) if scene == "ragged" else S.design_box_scene(
         (45, 38, 41), 6, 12, 150, 21, name="ovl", tfsf=True, interp=True)
     g = np.random.default_rng(13).standard_normal(O.detector_total(sc, sc.nsteps))
@@ -399,7 +425,8 @@ def test_face_copies_and_graphs_on_or_off_give_the_same_results(F, scene):
                 s.fdtd_forward(sc.nsteps, record_faces=True)
                 r = (s.detectors(), s.gradient(g), s.fields())
             prof = s.fdtd_profile_read()
-        assert prof["fused_fwd"][1] > 0 and prof["inv_fused"][1] > 0 and prof["adj_fused"][1] > 0
+        rev = ("inv_fused", "adj_fused") if kind == "1" else ("rev_E", "rev_H")
+        assert prof["fused_fwd"][1] > 0 and prof[rev[0]][1] > 0 and prof[rev[1]][1] > 0
         out.append(r)
     for o in out[1:]:
         for a, b in zip(out[0], o):

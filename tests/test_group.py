@@ -59,15 +59,30 @@ def test_group_abi_rejects_bad_groups_on_the_host():
     assert L.fdtd_finish_backward(None, None) == F.FDTD_ERR_INVALID_ARG
 
 
+def _solvers(F, scs, stream, monkeypatch, kinds):
+    """Solvers on one stream; kinds[r] the reverse kind of solver r (the in-place pair, or the fused
+    kernels), so a group holds both."""
+    out = []
+    for sc, kind in zip(scs, kinds):
+        monkeypatch.setenv("FDTD_REV_FUSED", kind)
+        out.append(F.Solver(sc, stream=stream))
+    monkeypatch.delenv("FDTD_REV_FUSED")
+    return out
+
+
 @pytest.mark.gpu
-def test_group_solves_equal_standalone_solves_bitwise(cuda_ok):
+def test_group_solves_equal_standalone_solves_bitwise(cuda_ok, monkeypatch):
     import torch
     from paper_2412_12360_b300 import fdtd as F
     scs = group_scenes()
     gs = [_gvec(sc, 80 + r) for r, sc in enumerate(scs)]
-    alone = [_alone(F, sc, g) for sc, g in zip(scs, gs)]
+    kinds = ["1", "0", "1", "0"]
+    alone = []
+    for sc, g, kind in zip(scs, gs, kinds):
+        monkeypatch.setenv("FDTD_REV_FUSED", kind)
+        alone.append(_alone(F, sc, g))
     stream = torch.cuda.Stream()
-    solvers = [F.Solver(sc, stream=stream) for sc in scs]
+    solvers = _solvers(F, scs, stream, monkeypatch, kinds)
     F.group_forward(solvers, [sc.nsteps for sc in scs], record_faces=True)
     dets = [s.detectors() for s in solvers]
     grads = [np.zeros(sc.design_shape(), dtype=np.float32) for sc in scs]
@@ -84,7 +99,7 @@ def test_group_solves_equal_standalone_solves_bitwise(cuda_ok):
 
 
 @pytest.mark.gpu
-def test_group_with_handles_joining_in_different_phases(cuda_ok):
+def test_group_with_handles_joining_in_different_phases(cuda_ok, monkeypatch):
     """Continuous batching: a handle starts alone, others join while it runs (one in its forward phase,
     one after another has reached its reverse sweep), and a finished one leaves; every result is the
     standalone result bitwise, and the first one matches the oracle."""
@@ -92,9 +107,13 @@ def test_group_with_handles_joining_in_different_phases(cuda_ok):
     from paper_2412_12360_b300 import fdtd as F
     scs = group_scenes()
     gs = [_gvec(sc, 90 + r) for r, sc in enumerate(scs)]
-    alone = [_alone(F, sc, g) for sc, g in zip(scs, gs)]
+    kinds = ["0", "1", "0", "1"]
+    alone = []
+    for sc, g, kind in zip(scs, gs, kinds):
+        monkeypatch.setenv("FDTD_REV_FUSED", kind)
+        alone.append(_alone(F, sc, g))
     stream = torch.cuda.Stream()
-    solvers = [F.Solver(sc, stream=stream) for sc in scs]
+    solvers = _solvers(F, scs, stream, monkeypatch, kinds)
     grads = [np.zeros(sc.design_shape(), dtype=np.float32) for sc in scs]
     dets = [None] * len(scs)
     active = []
