@@ -293,6 +293,23 @@ int fdtd_fields(fdtd_handle* h, float* out6);
 int64_t fdtd_footprint_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps,
                              int32_t record_faces, const int32_t design_lo[3], const int32_t design_hi[3]);
 
+/* Face-history segments (bounded memory for the reverse sweep of long or large solves): with steps = L > 0
+ * a forward with FDTD_RECORD_FACES of T > L steps keeps the boundary faces (Sec. 2.2) of its last
+ * segment only, the steps from (S - 1) L with S = ceil(T / L), and full states (fields and CPML
+ * memories) at the starts L, 2L, .., (S - 2) L of the other segments; fdtd_backward then regenerates
+ * each earlier segment's faces, when its reverse sweep reaches it, by running that segment's forward
+ * again from its start state (the initial state for the first), which costs T - L extra forward steps
+ * and leaves the gradient equal to the unsegmented one up to the rounding drift of the inverse step
+ * (each segment's reverse sweep starts from the exact forward state). steps = 0 (the default) records
+ * every step. Solves with segments run through fdtd_forward / fdtd_backward only (fdtd_begin refuses
+ * them). INVALID_ARG for NULL or steps < 0. */
+int fdtd_set_segment_steps(fdtd_handle* h, int32_t steps);
+
+/* Bytes of the reverse sweep's history of a solve of nsteps steps with segment length segment_steps
+ * (0: the whole face history): the face record it keeps plus the stored segment start states. -1 on
+ * bad input. */
+int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps, int32_t segment_steps);
+
 /* Cap the device bytes any one handle may allocate (-1 = no cap, the default). Allocations past the
  * cap fail with FDTD_ERR_OOM before reaching the CUDA allocator; used to exercise admission and
  * out-of-memory paths without exhausting the GPU. Process-wide. */

@@ -365,7 +365,15 @@ struct fdtd_handle {
   int64_t det_out_cap = 0;
   double* partial = nullptr;   // flux partial sums (scratch)
   int64_t partial_cap = 0;
-  float* face_hist = nullptr;  // steps x faces.per_step
+  float* face_hist = nullptr;  // steps x faces.per_step (the steps from seg_first on)
+  // face-history segments: with seg_steps = L > 0 a recorded forward of T steps keeps the faces of its
+  // last segment only (steps from seg_first = (S - 1) L, S = ceil(T / L)) and full states (fields and
+  // CPML memories) at the starts L, 2L, .., (S - 2) L of the others; the reverse sweep regenerates a
+  // segment's faces by running its forward again from its start state
+  int seg_steps = 0;
+  int seg_first = 0;
+  float* seg_states = nullptr;
+  int64_t seg_cap = 0;
   int64_t face_cap_steps = 0;
   float* adj = nullptr;        // 2 x 6 x vol adjoint fields, double-buffered (the fused adjoint step reads
                                // one and writes the other; the checkpointing gradient uses buffer 0)
@@ -452,6 +460,9 @@ struct fdtd_handle {
     return P;
   }
   int64_t psi_floats() const { return psi_bytes(g) / (int64_t)sizeof(float); }
+  int64_t state_floats() const { return 6 * g.vol + 2 * psi_floats(); }
+  float* face_at(int n) const { return face_hist + (int64_t)(n - seg_first) * faces.per_step; }
+  int segments(int nsteps) const { return seg_steps > 0 ? (nsteps + seg_steps - 1) / seg_steps : 1; }
 };
 
 namespace {
@@ -815,6 +826,64 @@ int64_t fwd_finish(fdtd_handle* h, int nsteps, cudaStream_t st) {
   return launches;
 }
 
+// The state at the start of segment s (time s L: fields of the current buffer and its CPML memories)
+// into its slot.
+void save_segment_state(fdtd_handle* h, int s, cudaStream_t st) {
+  const int64_t pf = h->psi_floats(), V = 6 * h->g.vol;
+  float* slot = h->seg_states + (int64_t)(s - 1) * h->state_floats();
+  const int c = h->cur;
+  cudaMemcpyAsync(slot, h->fields + (int64_t)c * V, V * 4, cudaMemcpyDeviceToDevice, st);
+  if (pf > 0) {
+    cudaMemcpyAsync(slot + V, h->psiE + c * pf, pf * 4, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(slot + V + pf, h->psiH + c * pf, pf * 4, cudaMemcpyDeviceToDevice, st);
+  }
+}
+
+// Regenerate the faces of segment s for the reverse sweep: its start state (the initial state for
+// s = 0, else the saved one) into field buffer b = pn ^ (L & 1), then its L forward steps with the face
+// record and without detectors, which ends with the exact forward state at time (s + 1) L in buffer
+// pn. Returns the launches.
+int64_t regen_segment(fdtd_handle* h, int s, int pn, cudaStream_t st) {
+  const Geo& g = h->g;
+  const int L = h->seg_steps;
+  const int64_t pf = h->psi_floats(), V = 6 * g.vol;
+  const int b = pn ^ (L & 1);
+  if (s == 0) {
+    if (h->init) cudaMemcpyAsync(h->fields + (int64_t)b * V, h->init, V * 4, cudaMemcpyDeviceToDevice, st);
+    else cudaMemsetAsync(h->fields + (int64_t)b * V, 0, V * 4, st);
+    if (pf > 0) {
+      cudaMemsetAsync(h->psiE + b * pf, 0, pf * 4, st);
+      cudaMemsetAsync(h->psiH + b * pf, 0, pf * 4, st);
+    }
+  } else {
+    const float* slot = h->seg_states + (int64_t)(s - 1) * h->state_floats();
+    cudaMemcpyAsync(h->fields + (int64_t)b * V, slot, V * 4, cudaMemcpyDeviceToDevice, st);
+    if (pf > 0) {
+      cudaMemcpyAsync(h->psiE + b * pf, slot + V, pf * 4, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(h->psiH + b * pf, slot + V + pf, pf * 4, cudaMemcpyDeviceToDevice, st);
+    }
+  }
+  h->seg_first = s * L;
+  const int keep = h->cur;
+  h->cur = b;
+  FwdArgs fa = fwd_base(h);
+  fa.ndet = 0;  // the detectors were sampled by the original forward
+  int64_t launches = 0;
+  for (int n = s * L; n < (s + 1) * L; ++n) {
+    const int c = h->cur;
+    fwd_step_args(h, fa, n);
+    launches += fwd_step_pre(h, n, st);
+    launch_fwd_fused(fa, h->fmaps[c], st);
+    launch_face_copy(g, h->F(1 - c), h->faces, h->face_at(n), 1, st);
+    for (size_t q = kMaxSrc; q < h->srcs.size(); ++q, ++launches)
+      launch_source(g, h->F(1 - c), h->srcs[q], n, +1.f, 0, st);
+    launches += 2;
+    h->cur = 1 - c;
+  }
+  h->cur = keep;
+  return launches;
+}
+
 // Forward: one fused launch per step (plus extra launches for sources and detectors beyond the
 // fused kernel's slots), then the fixed-order flux sums. Mutates h->cur as it goes.
 int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st, std::vector<Ev>* evs) {
@@ -824,8 +893,9 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
   FwdArgs fa = fwd_base(h);
   // The face record of step n runs on the side stream, beside step n+1 (which only reads that
   // buffer); step n+2 overwrites it, so its fused kernel waits for the copy, and so does a TFSF H
-  // correction of step n+1, which writes that buffer's H. Without face_overlap it runs in line.
-  const bool ovl = faces && h->face_overlap;
+  // correction of step n+1, which writes that buffer's H. Without face_overlap (or with segments, whose
+  // first steps record no faces) it runs in line.
+  const bool ovl = faces && h->face_overlap && h->seg_steps == 0;
   for (int n = 0; n < nsteps; ++n) {
     const int c = h->cur, x = 1 - c;
     if (ovl && n >= 2) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);
@@ -837,7 +907,7 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
       launch_fwd_fused(fa, h->fmaps[c], st);
     }
     launches += 1;
-    if (faces) {  // H^{n+1/2} on the boundary faces
+    if (faces && n >= h->seg_first) {  // H^{n+1/2} on the boundary faces
       cudaStream_t fs = ovl ? h->side : st;
       if (ovl) {
         cudaEventRecord(h->ev_fork, st);
@@ -845,13 +915,15 @@ int64_t enqueue_forward(fdtd_handle* h, int nsteps, bool record, cudaStream_t st
       }
       {
         ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
-        launch_face_copy(g, h->F(x), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 1, fs);
+        launch_face_copy(g, h->F(x), h->faces, h->face_at(n), 1, fs);
       }
       if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
       launches += 1;
     }
     launches += fwd_step_post(h, n, nsteps, st);
     h->cur = x;
+    if (faces && h->seg_steps > 0 && (n + 1) % h->seg_steps == 0 && (n + 1) / h->seg_steps <= h->segments(nsteps) - 2)
+      save_segment_state(h, (n + 1) / h->seg_steps, st);
   }
   if (ovl) {  // join the side stream
     if (nsteps >= 2) cudaStreamWaitEvent(st, h->ev_join[(nsteps - 2) % 2], 0);
@@ -1021,15 +1093,15 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
   int pc = h->cur, ac = 0, pb = 0;
   // The face replay of step n (the recorded H^{n+1/2} written back outside R into buffer pc) runs on
   // the side stream beside the adjoint step of n + 1, which does not touch the primal fields; the
-  // inverse step of n waits for it. Without face_overlap it runs in line, right before that step.
+  // inverse step of n waits for it. Without face_overlap (or with segments) it runs in line.
   const bool faces = h->faces.per_step > 0;
-  const bool ovl = faces && h->face_overlap;
+  const bool ovl = faces && h->face_overlap && h->seg_steps == 0;
   auto replay = [&](int n, int buf) {
     cudaStream_t fs = ovl ? h->side : st;
     if (ovl) cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     {
       ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, h->F(buf), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
+      launch_face_copy(g, h->F(buf), h->faces, h->face_at(n), 0, fs);
     }
     if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
     launches += 1;
@@ -1039,6 +1111,7 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     replay(nsteps - 1, pc);
   }
   for (int n = nsteps - 1; n >= 0; --n) {
+    if (faces && n < h->seg_first) launches += regen_segment(h, n / h->seg_steps, pc, st);
     launches += rev_step_pre(h, n, nsteps, pc, ac, st, evs);
     if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
     else if (faces) replay(n, pc);
@@ -1081,13 +1154,13 @@ int64_t enqueue_backward_split(fdtd_handle* h, int nsteps, cudaStream_t st, std:
   // The face replay of step n runs on the side stream beside rev_H(n+1), which neither reads nor
   // writes H outside R; rev_E(n) waits for it. Without face_overlap it runs in line.
   const bool faces = h->faces.per_step > 0;
-  const bool ovl = faces && h->face_overlap;
+  const bool ovl = faces && h->face_overlap && h->seg_steps == 0;
   auto replay = [&](int n) {
     cudaStream_t fs = ovl ? h->side : st;
     if (ovl) cudaStreamWaitEvent(h->side, h->ev_fork, 0);
     {
       ProfScope ps(h, evs, fs, FDTD_KERNEL_FACE_COPY, n);
-      launch_face_copy(g, h->F(pc), h->faces, h->face_hist + (int64_t)n * h->faces.per_step, 0, fs);
+      launch_face_copy(g, h->F(pc), h->faces, h->face_at(n), 0, fs);
     }
     if (ovl) cudaEventRecord(h->ev_join[n % 2], h->side);
     launches += 1;
@@ -1097,6 +1170,7 @@ int64_t enqueue_backward_split(fdtd_handle* h, int nsteps, cudaStream_t st, std:
     replay(nsteps - 1);
   }
   for (int n = nsteps - 1; n >= 0; --n) {
+    if (faces && n < h->seg_first) launches += regen_segment(h, n / h->seg_steps, pc, st);
     launches += rev_step_pre(h, n, nsteps, pc, 0, st, evs);
     if (ovl) cudaStreamWaitEvent(st, h->ev_join[n % 2], 0);  // H^{n+1/2} on the faces is in place
     else if (faces) replay(n);
@@ -1539,7 +1613,7 @@ int fdtd_destroy(fdtd_handle* h) {
   h->gfwd.reset();
   h->gbwd.reset();
   void* bufs[] = {h->fields, h->a, h->psiE, h->psiH, h->tables, h->init, h->gtab, h->det_out, h->partial,
-                  h->face_hist, h->adj, h->psibar, h->dLda, h->dLddet, h->staging, h->status};
+                  h->face_hist, h->adj, h->psibar, h->dLda, h->dLddet, h->staging, h->status, h->seg_states};
   for (void* p : bufs)
     if (p) cudaFreeAsync(p, h->stream);
   for (float* p : h->src_w) cudaFreeAsync(p, h->stream);
@@ -1614,8 +1688,14 @@ static int forward_prepare(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   h->last_nsteps = nsteps;
   TRY(ensure_gtab(h, nsteps));
   TRY(ensure_det(h, nsteps));
-  if (record && h->faces.per_step > 0)
-    TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)nsteps, h->faces.per_step * 4));
+  h->seg_first = 0;
+  if (record && h->faces.per_step > 0) {
+    const int S = h->segments(nsteps);
+    const int held = S > 1 ? h->seg_steps : nsteps;  // steps whose faces the history holds
+    h->seg_first = (S - 1) * h->seg_steps;
+    TRY(ensure_buf(h, &h->face_hist, &h->face_cap_steps, (int64_t)held, h->faces.per_step * 4));
+    if (S > 2) TRY(ensure_buf(h, &h->seg_states, &h->seg_cap, (int64_t)(S - 2), h->state_floats() * 4));
+  }
   TRY(reset_state(h));
   h->phase = FDTD_PHASE_IDLE;
   return FDTD_OK;
@@ -1626,7 +1706,7 @@ int fdtd_forward(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
   TRY(forward_prepare(h, nsteps, flags));
   const bool record = (flags & FDTD_RECORD_FACES) != 0;
   const int64_t key = (record ? 1 : 0) | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2) |
-                      ((int64_t)h->check_every << 32);
+                      ((int64_t)h->check_every << 32) | ((int64_t)h->seg_steps << 44);
   TRY(run_loop(h, h->gfwd, nsteps, key, [&](cudaStream_t st, std::vector<Ev>* evs) {
     return enqueue_forward(h, nsteps, record, st, evs);
   }));
@@ -1681,7 +1761,8 @@ static int backward_scaled(fdtd_handle* h, const double* dL_ddet, float* dL_deps
   const int nsteps = h->last_nsteps;
   h->phase = FDTD_PHASE_IDLE;
   const int64_t key = h->cur | ((int64_t)h->face_overlap << 1) | ((int64_t)h->prof_every << 2);
-  TRY(run_loop(h, h->gbwd, nsteps, key | ((int64_t)h->rev_fused << 40), [&](cudaStream_t st, std::vector<Ev>* evs) {
+  TRY(run_loop(h, h->gbwd, nsteps, key | ((int64_t)h->rev_fused << 40) | ((int64_t)h->seg_steps << 44),
+               [&](cudaStream_t st, std::vector<Ev>* evs) {
     return h->rev_fused ? enqueue_backward(h, nsteps, st, evs) : enqueue_backward_split(h, nsteps, st, evs);
   }));
   return backward_finish(h, dL_deps, scale);
@@ -1716,6 +1797,8 @@ int fdtd_set_stream(fdtd_handle* h, void* cuda_stream) {
 }
 
 int fdtd_begin(fdtd_handle* h, int32_t nsteps, uint32_t flags) {
+  if (h && h->seg_steps > 0 && (flags & FDTD_RECORD_FACES) && h->segments(nsteps) > 1)
+    return fail(FDTD_ERR_INVALID_ARG, "segmented face histories are solved with fdtd_forward / fdtd_backward");
   TRY(forward_prepare(h, nsteps, flags));
   h->solve_record = (flags & FDTD_RECORD_FACES) != 0;
   h->step_next = 0;
@@ -2383,8 +2466,28 @@ int fdtd_release_history(fdtd_handle* h) {
   dev_free(h, h->face_hist, h->face_cap_steps * h->faces.per_step * 4);
   h->face_hist = nullptr;
   h->face_cap_steps = 0;
+  dev_free(h, h->seg_states, h->seg_cap * h->state_floats() * 4);
+  h->seg_states = nullptr;
+  h->seg_cap = 0;
   h->recorded = false;
   return FDTD_OK;
+}
+
+int fdtd_set_segment_steps(fdtd_handle* h, int32_t steps) {
+  if (!h || steps < 0) return fail(FDTD_ERR_INVALID_ARG, "NULL handle or negative segment length");
+  h->seg_steps = steps;
+  h->recorded = false;  // a history recorded with the old setting is not used
+  return FDTD_OK;
+}
+
+int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps, int32_t segment_steps) {
+  if (validate(grid, 0.5, pml) != FDTD_OK || nsteps < 0 || segment_steps < 0) return -1;
+  const Geo g = make_geo(*grid, *pml, 0.5);
+  const int64_t per_step = make_faces(g).per_step * 4;
+  if (segment_steps == 0 || nsteps <= segment_steps) return per_step * nsteps;
+  const int64_t S = (nsteps + segment_steps - 1) / segment_steps;
+  const int64_t state = (6 * g.vol + 2 * (psi_bytes(g) / 4)) * 4;
+  return per_step * segment_steps + std::max<int64_t>(0, S - 2) * state;
 }
 
 int fdtd_synchronize(fdtd_handle* h) {

@@ -99,6 +99,8 @@ SIGNATURES = [
     ("fdtd_synchronize", C.c_int, [_VP]),
     ("fdtd_set_stream", C.c_int, [_VP, _VP]),
     ("fdtd_poll_status", C.c_int, [_VP]),
+    ("fdtd_set_segment_steps", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_history_bytes", C.c_int64, [C.POINTER(fdtd_grid), C.POINTER(fdtd_pml), C.c_int32, C.c_int32]),
     ("fdtd_begin", C.c_int, [_VP, C.c_int32, C.c_uint32]),
     ("fdtd_begin_backward", C.c_int, [_VP, _VP]),
     ("fdtd_group_step", C.c_int, [C.POINTER(_VP), C.c_int32, C.c_int32]),
@@ -182,6 +184,14 @@ def footprint_bytes(scene, nsteps: Optional[int] = None, record_faces: bool = Tr
     ns = scene.nsteps if nsteps is None else nsteps
     return int(lib().fdtd_footprint_bytes(C.byref(g), C.byref(p), int(ns), int(record_faces),
                                           _I3(*scene.design_lo), _I3(*scene.design_hi)))
+
+
+def history_bytes(scene, nsteps: Optional[int] = None, segment_steps: int = 0) -> int:
+    """Device bytes of a solve's reverse-sweep history (faces kept plus segment start states)."""
+    g = make_grid(scene.n)
+    p = make_pml(scene)
+    ns = scene.nsteps if nsteps is None else nsteps
+    return int(lib().fdtd_history_bytes(C.byref(g), C.byref(p), int(ns), int(segment_steps)))
 
 
 def set_byte_budget(nbytes: int):
@@ -347,6 +357,10 @@ class Solver:
 
     def fdtd_synchronize(self):
         check(lib().fdtd_synchronize(self.h))
+
+    def fdtd_set_segment_steps(self, steps: int):
+        """Keep the faces of the last `steps`-step segment only, regenerating the others (0: all)."""
+        check(lib().fdtd_set_segment_steps(self.h, int(steps)))
 
     def fdtd_poll_status(self):
         """Raise what the kernels flagged, without waiting for the stream (its work must be done)."""
