@@ -539,11 +539,12 @@ def run_serve(args, world, rank, local):
 def run_batched(args, world, rank, local):
     """A batch of designs of one scene (default: 16 designs of a 240x240x960 waveguide, 12-cell CPML,
     120^3 design box each, rho seeds 500..515, flux objective, 3000 steps) through the
-    torch.autograd.Function: forward of every design, then the backward. The designs whose face
-    histories fit in device memory beside all the states keep them from the forward pass; the others
-    recompute (forward again with the face record right before their reverse sweep, after the kept
-    histories have been freed). Beside the throughput, a central finite-difference check
-    of dL/drho of design 0 on 4 voxels (indices from seed 99) with delta rho 1e-2 and 1e-3."""
+    torch.autograd.Function: forward of every design, then the backward. Each design's face history is
+    kept whole while it fits in device memory beside the states and the histories planned before it,
+    else kept as segments (the faces of the last segment and the segment start states; the reverse
+    sweep regenerates the earlier segments), else recomputed (autograd.history_plan). Beside the
+    throughput: the directional derivative of design 0 along a uniform density shift against central
+    differences, and central differences on 4 voxels (indices from seed 99)."""
     import torch
     from paper_2412_12360_b300 import autograd, fdtd, ranks
 
@@ -553,18 +554,16 @@ def run_batched(args, world, rank, local):
     ids = ranks.shard(args.batch, world, rank)
     scs = [scenes.waveguide_batch_member(b, T) for b in ids]
     free, _ = torch.cuda.mem_get_info(dev)
-    # as many designs as fit keep their face histories; the others recompute theirs in backward
-    nkeep = autograd.histories_that_fit(scs, T, int(0.85 * free))
-    if nkeep < 0:
-        raise SystemExit("batch does not fit even one design at a time")
-    mode = "keep" if nkeep == len(scs) else ("recompute" if nkeep == 0 else nkeep)
+    plan, extra = autograd.history_plan(scs, T, int(0.85 * free))
     eps_lo, eps_hi = scs[0].extra["eps_lo"], scs[0].extra["eps_hi"]
     solvers = [fdtd.Solver(sc) for sc in scs]
+    for s in solvers:  # each design solves once: direct launches rather than captured graphs
+        s.fdtd_set_graphs(False)
     rho = torch.stack([torch.from_numpy(sc.extra["rho"]) for sc in scs]).to(dev).requires_grad_(True)
 
     def batch_step():
         rho.grad = None
-        det = autograd.solve(rho, solvers, eps_lo, eps_hi, T, mode)
+        det = autograd.solve(rho, solvers, eps_lo, eps_hi, T, plan)
         loss = det.sum()          # L = sum over steps of the flux through the detector plane, per design
         loss.backward()
         return det
@@ -580,14 +579,12 @@ def run_batched(args, world, rank, local):
     t = a.elapsed_time(b) * 1e-3
     cells = sum(sc.ncells * T for sc in scs)
     t_max, cells_all = ranks.reduce_time_and_work(t, cells)
-    grad0 = rho.grad[0].detach().cpu().numpy() if rank == 0 else None
+    grad0 = rho.grad[0].detach().clone() if rank == 0 else None
 
-    fd = None
+    checks = None
     if rank == 0 and not args.no_fd:
-        sc0, s0 = scs[0], solvers[0]
-        rng = np.random.default_rng(99)
-        shape = sc0.design_shape()
-        vox = [tuple(int(rng.integers(d)) for d in shape) for _ in range(4)]
+        s0 = solvers[0]
+        s0.fdtd_set_segment_steps(0)
         rho0 = rho[0].detach().clone()
 
         def loss_at(r):
@@ -595,28 +592,39 @@ def run_batched(args, world, rank, local):
             s0.fdtd_forward(T)
             return float(np.sum(s0.detectors()))
 
-        fd = []
+        checks = {"directional": [], "voxels": []}
+        g0 = grad0.double()
+        for h in (1e-3, 1e-2):   # every design voxel shifted by h: dL/dh = sum of dL/drho
+            fd = (loss_at(rho0 + h) - loss_at(rho0 - h)) / (2 * h)
+            ad = float(g0.sum())
+            checks["directional"].append({"delta_rho": h, "fd": fd, "autograd": ad, "rel_err": abs(fd - ad) / abs(fd)})
+        rng = np.random.default_rng(99)
+        shape = scs[0].design_shape()
+        vox = [tuple(int(rng.integers(d)) for d in shape) for _ in range(4)]
         for v in vox:
             row = {"voxel": list(v), "autograd": float(grad0[v])}
-            for h in (1e-2, 1e-3):
+            for h in (2e-2, 5e-2):
                 rp, rm = rho0.clone(), rho0.clone()
                 rp[v] += h
                 rm[v] -= h
                 row["fd_%g" % h] = (loss_at(rp) - loss_at(rm)) / (2 * h)
-            fd.append(row)
+            checks["voxels"].append(row)
         s0.fdtd_set_design_density(rho0, eps_lo, eps_hi)
     for s in solvers:
         s.close()
     if rank != 0:
         return
+    counts = {"whole": sum(1 for p in plan if p == 0), "segmented": sum(1 for p in plan if p > 0),
+              "recomputed": sum(1 for p in plan if p < 0)}
     line = {"metric": "Gcell-steps/s fwd+grad (batched autograd)", "unit": "Gcell-steps/s",
             "value": round(cells_all / t_max / 1e9, 4), "n_gpus": world, "higher_is_better": True,
-            "seconds": round(t_max, 3), "designs": args.batch, "mode": mode, "dtype": "f32", "data": "synthetic",
-            "scaling": "weak", "fd_check": fd,
+            "seconds": round(t_max, 3), "designs": args.batch, "plan": plan, "histories": counts,
+            "extra_forward_fraction": round(extra / (len(scs) * T), 4), "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "gradient_checks": checks,
             "config": {"workload": "%d designs of a 240x240x960 waveguide (along z), 12-cell CPML, 120^3 design box "
-                                   "each, rho~U[0,1) seeds 500.., flux objective, %d steps; mode = designs that keep "
-                                   "their face histories ('keep': all, 'recompute': none), the others re-run their "
-                                   "forward with the face record before their reverse sweep" % (args.batch, T)}}
+                                   "each, rho~U[0,1) seeds 500.., flux objective, %d steps; per design the face "
+                                   "history is kept whole (plan 0), as segments of L steps (plan L) or recomputed "
+                                   "(plan -1), whichever fits first in device memory" % (args.batch, T)}}
     print(json.dumps(line), flush=True)
 
 

@@ -310,6 +310,11 @@ int fdtd_set_segment_steps(fdtd_handle* h, int32_t steps);
  * bad input. */
 int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps, int32_t segment_steps);
 
+/* Bytes of the reverse sweep's adjoint state (both adjoint field buffers and their CPML memories), part
+ * of fdtd_footprint_bytes, held from a handle's first backward until fdtd_release_history. -1 on bad
+ * input. */
+int64_t fdtd_adjoint_bytes(const fdtd_grid* grid, const fdtd_pml* pml);
+
 /* Cap the device bytes any one handle may allocate (-1 = no cap, the default). Allocations past the
  * cap fail with FDTD_ERR_OOM before reaching the CUDA allocator; used to exercise admission and
  * out-of-memory paths without exhausting the GPU. Process-wide. */
@@ -345,10 +350,12 @@ int fdtd_profile_read(fdtd_handle* h, double* ms, int64_t* count, int32_t nkinds
 /* Device bytes currently held by the handle (or -1). */
 int64_t fdtd_bytes_allocated(fdtd_handle* h);
 
-/* Free the boundary-face history of the last recorded forward (stream-ordered on the handle's
- * stream), for callers that solve many designs one after another and cannot keep every history
- * (batched gradients in recompute mode). A later fdtd_backward then fails with FDTD_ERR_STATE until
- * a new fdtd_forward with FDTD_RECORD_FACES. Returns FDTD_OK, or FDTD_ERR_INVALID_ARG for NULL. */
+/* Free the reverse sweep's state of the handle (stream-ordered on the handle's stream): the boundary-face
+ * history and segment start states of the last recorded forward, and the adjoint fields and their CPML
+ * memories (allocated again by the next reverse sweep), for callers that solve many designs one after
+ * another and cannot keep every history (batched gradients). A later fdtd_backward then fails with
+ * FDTD_ERR_STATE until a new fdtd_forward with FDTD_RECORD_FACES. Returns FDTD_OK, or
+ * FDTD_ERR_INVALID_ARG for NULL. */
 int fdtd_release_history(fdtd_handle* h);
 
 /* Allocation-free Poynting flux: out = sum over the cell box [lo, hi) of (E x H)[axis] for the fields

@@ -11,14 +11,16 @@ solvers' streams against torch's current stream (events both ways), so that solv
 their own streams, or calls made under torch.cuda.stream(...), read inputs that are complete and
 hand back outputs that are.
 
-mode "keep" records the boundary faces during the forward pass and reverses from them (one forward
-and one reversed sweep per design). mode "recompute" runs a plain forward first and, in backward,
-runs the recorded forward again immediately before the reverse sweep of each design and frees that
-history afterwards, so only one face history at a time is held in device memory (used for batches
-whose histories do not fit). An integer mode k is the mix of the two: designs 0..k-1 keep their
-histories from the forward pass, the others recompute; the backward reverses the kept designs first
-and frees each history, so the recomputed ones find the room (for batches where some, but not all,
-histories fit beside the states).
+mode says how each design's reverse sweep gets its boundary-face history (Sec. 2.2):
+  "keep": recorded whole during the forward pass (one forward and one reversed sweep per design);
+  "recompute": a plain forward first and, in backward, the recorded forward again right before the
+    design's reverse sweep (only one history at a time in device memory);
+  an integer k: designs 0..k-1 keep, the others recompute;
+  a list plan[b] per design: 0 keeps the whole history, L > 0 keeps segments of L steps (the faces
+    of the last segment and the segment start states; the reverse sweep regenerates the earlier
+    segments, T - L extra forward steps instead of T), -1 recomputes (see history_plan).
+The backward reverses the designs that hold histories first and frees each design's reverse-sweep
+state after its sweep, so the recomputed ones find the room.
 """
 from __future__ import annotations
 
@@ -84,23 +86,22 @@ class FDTDSolve(torch.autograd.Function):
             raise TypeError("rho must be a CUDA float32 tensor [B, dz, dy, dx]")
         if rho.shape[0] != len(solvers):
             raise ValueError("one solver per design is needed")
-        if isinstance(mode, bool) or not (mode in ("keep", "recompute") or (isinstance(mode, int) and mode >= 0)):
-            raise ValueError("mode is 'keep', 'recompute' or the number of designs that keep their histories")
-        nkeep = len(solvers) if mode == "keep" else (0 if mode == "recompute" else min(int(mode), len(solvers)))
+        plan = _plan_of(mode, len(solvers))
         rho_c = rho.detach().contiguous()
         streams = _streams(solvers, rho.device)
-        outs: List[torch.Tensor] = [_det_buffer(s, rho.device) for s in solvers]
+        outs: List[torch.Tensor] = []
         _wait_for_torch(streams, rho.device)
         for b, s in enumerate(solvers):
             s.fdtd_set_design_density(rho_c[b], eps_lo, eps_hi)
-            s.fdtd_forward(nsteps, record_faces=b < nkeep)
+            s.fdtd_set_segment_steps(max(plan[b], 0))
+            s.fdtd_forward(nsteps, record_faces=plan[b] >= 0)
+            outs.append(_det_buffer(s, rho.device))  # (its size is known once a forward has run)
             s.fdtd_read_detectors(outs[b])
         _torch_waits(streams, rho.device, [rho_c] + outs)
         ctx.solvers = list(solvers)
         ctx.eps = (float(eps_lo), float(eps_hi))
         ctx.nsteps = int(nsteps)
-        ctx.mode = mode
-        ctx.nkeep = nkeep
+        ctx.plan = plan
         ctx.save_for_backward(rho_c)
         return torch.stack(outs)
 
@@ -111,15 +112,35 @@ class FDTDSolve(torch.autograd.Function):
         gd = g.detach().to(torch.float64).contiguous()
         streams = _streams(ctx.solvers, rho_c.device)
         _wait_for_torch(streams, rho_c.device)
-        for b, s in enumerate(ctx.solvers):  # the designs that kept their histories come first
-            if b >= ctx.nkeep:
+        order = [b for b in range(len(ctx.solvers)) if ctx.plan[b] >= 0] + \
+                [b for b in range(len(ctx.solvers)) if ctx.plan[b] < 0]   # histories held come first
+        for b in order:
+            s = ctx.solvers[b]
+            if ctx.plan[b] < 0:
                 s.fdtd_set_design_density(rho_c[b], *ctx.eps)
+                s.fdtd_set_segment_steps(0)
                 s.fdtd_forward(ctx.nsteps, record_faces=True)
             s.fdtd_backward_density(gd[b], grad[b])
-            if ctx.mode != "keep":
-                s.fdtd_release_history()  # room for the designs still to recompute
+            if len(ctx.solvers) > 1:
+                s.fdtd_release_history()  # room for the designs still to come
         _torch_waits(streams, rho_c.device, [rho_c, gd, grad])
         return grad, None, None, None, None, None
+
+
+def _plan_of(mode, n):
+    """Per-design history plan (0 whole, L > 0 segments of L steps, -1 recompute) for a mode."""
+    if isinstance(mode, bool):
+        raise ValueError("bad mode")
+    if mode == "keep":
+        return [0] * n
+    if mode == "recompute":
+        return [-1] * n
+    if isinstance(mode, int) and mode >= 0:
+        return [0 if b < mode else -1 for b in range(n)]
+    if isinstance(mode, (list, tuple)) and len(mode) == n and all(isinstance(v, int) and v >= -1 for v in mode):
+        return list(mode)
+    raise ValueError("mode is 'keep', 'recompute', the number of designs that keep their histories, or a "
+                     "per-design plan (0 whole history, L > 0 segments of L steps, -1 recompute)")
 
 
 def solve(rho: torch.Tensor, solvers: Sequence["fdtd.Solver"], eps_lo: float, eps_hi: float, nsteps: int,
@@ -141,6 +162,39 @@ def histories_that_fit(scenes, nsteps: int, budget_bytes: int) -> int:
         used += hist[k]
         k += 1
     return k
+
+
+def history_plan(scenes, nsteps: int, budget_bytes: int, max_segments: int = 16):
+    """Per design (in order): 0 when its whole face history still fits beside every design's state and
+    the histories planned so far, else the segment length L (segments of L steps; the fewest extra
+    forward steps, T - L, among the lengths whose history fits), else -1 (recompute in backward).
+    The backward frees each design's reverse-sweep state after its sweep, so one adjoint state at a
+    time is counted. Returns (plan, extra forward steps)."""
+    adj = [fdtd.adjoint_bytes(sc) for sc in scenes]
+    base = sum(fdtd.footprint_bytes(sc, nsteps, record_faces=False) for sc in scenes) - sum(adj) + max(adj, default=0)
+    used = base
+    plan, extra = [], 0
+    for sc in scenes:
+        whole = fdtd.history_bytes(sc, nsteps, 0)
+        if used + whole <= budget_bytes:
+            plan.append(0)
+            used += whole
+            continue
+        best = None
+        for S in range(2, max_segments + 1):
+            L = -(-nsteps // S)
+            hb = fdtd.history_bytes(sc, nsteps, L)
+            if used + hb <= budget_bytes:
+                best = (L, hb)
+                break
+        if best is None:
+            plan.append(-1)
+            extra += nsteps
+        else:
+            plan.append(best[0])
+            used += best[1]
+            extra += nsteps - best[0]
+    return plan, extra
 
 
 def fits_in_memory(scenes, nsteps: int, budget_bytes: int) -> bool:

@@ -2469,6 +2469,12 @@ int fdtd_release_history(fdtd_handle* h) {
   dev_free(h, h->seg_states, h->seg_cap * h->state_floats() * 4);
   h->seg_states = nullptr;
   h->seg_cap = 0;
+  // the adjoint state too (allocated again by the next reverse sweep)
+  const int64_t pf = h->psi_floats();
+  dev_free(h, h->adj, 12 * h->g.vol * 4);
+  h->adj = nullptr;
+  dev_free(h, h->psibar, pf > 0 ? 4 * pf * 4 : 0);
+  h->psibar = nullptr;
   h->recorded = false;
   return FDTD_OK;
 }
@@ -2478,6 +2484,12 @@ int fdtd_set_segment_steps(fdtd_handle* h, int32_t steps) {
   h->seg_steps = steps;
   h->recorded = false;  // a history recorded with the old setting is not used
   return FDTD_OK;
+}
+
+int64_t fdtd_adjoint_bytes(const fdtd_grid* grid, const fdtd_pml* pml) {
+  if (validate(grid, 0.5, pml) != FDTD_OK) return -1;
+  const Geo g = make_geo(*grid, *pml, 0.5);
+  return 12 * g.vol * 4 + 4 * psi_bytes(g);
 }
 
 int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t nsteps, int32_t segment_steps) {

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("fdtd_set_stream", C.c_int, [_VP, _VP]),
     ("fdtd_poll_status", C.c_int, [_VP]),
     ("fdtd_set_segment_steps", C.c_int, [_VP, C.c_int32]),
+    ("fdtd_adjoint_bytes", C.c_int64, [C.POINTER(fdtd_grid), C.POINTER(fdtd_pml)]),
     ("fdtd_history_bytes", C.c_int64, [C.POINTER(fdtd_grid), C.POINTER(fdtd_pml), C.c_int32, C.c_int32]),
     ("fdtd_begin", C.c_int, [_VP, C.c_int32, C.c_uint32]),
     ("fdtd_begin_backward", C.c_int, [_VP, _VP]),
@@ -192,6 +193,13 @@ def history_bytes(scene, nsteps: Optional[int] = None, segment_steps: int = 0) -
     p = make_pml(scene)
     ns = scene.nsteps if nsteps is None else nsteps
     return int(lib().fdtd_history_bytes(C.byref(g), C.byref(p), int(ns), int(segment_steps)))
+
+
+def adjoint_bytes(scene) -> int:
+    """Device bytes of a handle's reverse-sweep adjoint state (freed by fdtd_release_history)."""
+    g = make_grid(scene.n)
+    p = make_pml(scene)
+    return int(lib().fdtd_adjoint_bytes(C.byref(g), C.byref(p)))
 
 
 def set_byte_budget(nbytes: int):

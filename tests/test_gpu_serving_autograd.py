@@ -81,7 +81,7 @@ def test_served_admission_bounded_by_budget(cuda_ok):
     assert lat["p99_s"] >= lat["p50_s"] > 0
 
 
-@pytest.mark.parametrize("mode", ["keep", "recompute", 1])
+@pytest.mark.parametrize("mode", ["keep", "recompute", 1, [40, -1], [0, 55]])
 def test_autograd_density_gradient_matches_oracle(cuda_ok, mode):
     import torch
     from paper_2412_12360_b300 import autograd, fdtd

@@ -66,3 +66,23 @@ def test_segmented_backward_is_refused_by_the_grouped_form(cuda_ok):
             s.fdtd_begin(100, record_faces=True)
         assert e.value.code == F.FDTD_ERR_INVALID_ARG
         s.fdtd_begin(20, record_faces=True)      # a single segment is an ordinary whole history
+
+
+def test_history_plan_keeps_segments_or_recomputes_by_budget():
+    """autograd.history_plan: whole histories while they fit, then the longest segments that fit, then
+    recomputation; the extra forward steps are T - L per segmented design and T per recomputed one."""
+    import torch  # noqa: F401  (autograd imports torch)
+    from paper_2412_12360_b300 import autograd, fdtd as F
+    T = 300
+    scs = [S.design_box_scene((40, 36, 44), 6, 12, T, 71 + b, name="p%d" % b) for b in range(3)]
+    adj = [F.adjoint_bytes(sc) for sc in scs]
+    base = sum(F.footprint_bytes(sc, T, record_faces=False) for sc in scs) - sum(adj) + max(adj)
+    whole = F.history_bytes(scs[0], T, 0)
+    plan, extra = autograd.history_plan(scs, T, base + 3 * whole)
+    assert plan == [0, 0, 0] and extra == 0
+    seg2 = F.history_bytes(scs[0], T, 150)
+    plan, extra = autograd.history_plan(scs, T, base + whole + seg2)
+    assert plan == [0, 150, -1]
+    assert extra == (T - 150) + T
+    plan, extra = autograd.history_plan(scs, T, base)
+    assert plan == [-1, -1, -1] and extra == 3 * T
