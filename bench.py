@@ -498,7 +498,8 @@ def run_serve(args, world, rank, local):
     for load in args.serve_loads:
         arng = np.random.default_rng(8 + rank)
         gaps = arng.exponential(mean_service / load, size=len(mine))
-        with serve.Server(max_inflight=args.serve_slots, chunk_steps=args.serve_chunk) as srv:
+        with serve.Server(max_inflight=args.serve_slots, chunk_steps=args.serve_chunk,
+                          group_bytes=args.serve_group_mb << 20) as srv:
             t0 = time.perf_counter()
             futs = []
             for sc, gap in zip(mine, gaps):
@@ -524,7 +525,7 @@ def run_serve(args, world, rank, local):
             "served_over_sequential": round(top["value"] / (cells_all / t_seq_max / 1e9), 4),
             "p50_s": top["p50_s"], "p99_s": top["p99_s"], "offered_load": top["offered_load"],
             "loads": per_load, "requests": args.serve_requests, "slots": args.serve_slots,
-            "chunk_steps": args.serve_chunk,
+            "chunk_steps": args.serve_chunk, "group_mib": args.serve_group_mb,
             "results_equal_alone_and_in_mix": all(p["results_equal_alone_and_in_mix"] for p in per_load),
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": "served stream: Poisson arrivals (seed 8) at offered loads %s of the sequential "
@@ -799,6 +800,8 @@ def main():
     ap.add_argument("--serve-grids", choices=["mix", "small"], default="mix",
                     help="served grids: the four-size mix, or only the 64^3 and 96^3 requests")
     ap.add_argument("--serve-slots", type=int, default=4, help="requests in flight at once (at most 8)")
+    ap.add_argument("--serve-group-mb", type=int, default=64,
+                    help="running requests stepped in groups of at most this many MiB of step bytes (0: one group)")
     ap.add_argument("--batched", action="store_true", help="measure the batched autograd workload instead")
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--no-fd", action="store_true", help="skip the finite-difference check of --batched")

@@ -98,6 +98,31 @@ int choose_tz(int64_t nxy, int nz, int64_t slots) {
   return best;
 }
 
+// The z-chunk of the requests of a grouped launch whose results do not depend on it (free[r]; the
+// others keep own[r]), chosen as choose_tz chooses one grid's: the group's blocks in waves of `slots`
+// resident blocks, a wave costing its longest march plus two planes of start-up. Each request alone
+// fills the GPU with short chunks; side by side they fill it with longer ones, which recompute fewer
+// halo planes per plane marched.
+int group_tz(int n, const int64_t* nxy, const int* nz, const int* own, const bool* free_, int64_t slots, int tz_max) {
+  int best = 1;
+  double bestc = 1e300;
+  for (int tz = 1; tz <= tz_max; ++tz) {
+    int64_t blocks = 0;
+    int longest = 0;
+    for (int r = 0; r < n; ++r) {
+      const int t = free_[r] ? std::min(tz, nz[r]) : own[r];
+      blocks += nxy[r] * ((nz[r] + t - 1) / t);
+      longest = std::max(longest, std::min(t, nz[r]));
+    }
+    const double c = double((blocks + slots - 1) / slots) * (longest + 2);
+    if (c <= bestc) {
+      bestc = c;
+      best = tz;
+    }
+  }
+  return best;
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -334,6 +359,12 @@ struct fdtd_handle {
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
   int tz_inv = 8, inv_nstage = 4; // fused inverse step: z-planes per block, ring stages
   int tz_adj = 8, adj_nstage = 4; // fused adjoint step
+  // for grouped launches, whose z-chunks follow the group: column tiles of the 32 x 16 kernels
+  // (forward, inverse, adjoint) and of the in-place pair, and resident-block slots of each kernel
+  int64_t nxy_f = 1, nxy_r = 1;
+  int64_t slots_fwd = 1, slots_rev = 1, slots_inv = 1, slots_adj = 1;
+  bool tz_free = true;      // not pinned by FDTD_TZ
+  bool fwd_tz_free = true;  // no flux detector summed by the fused forward (its slots follow tz)
   // reverse step kind: the fused inverse + adjoint kernels (52 + 52 B per cell, double-buffered
   // fields; faster on large grids with thin layers), or the in-place pair rev_E + rev_H (76 + 72 B per
   // cell, one cell per thread and more blocks per SM; faster on small grids and thick layers)
@@ -1431,6 +1462,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     const int64_t slots_r = rev_ring4 ? slots_r4 : slots_r3;
     h->tz = choose_tz(nxy, n[2], slots_f);
     h->tz_rev = choose_tz(nxy_rev, n[2], slots_r);
+    h->nxy_f = nxy;
+    h->nxy_r = nxy_rev;
+    h->slots_fwd = slots_f;
+    h->slots_rev = slots_r;
     // fused inverse and adjoint steps: like the forward, a 4-stage ring when it keeps as many blocks
     // resident per SM as 3 stages do, else 3 stages; z-chunks for their own resident blocks
     for (int which = 0; which < 2; ++which) {
@@ -1442,10 +1477,12 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       const int tzv = std::min(choose_tz(nxy, n[2], slots), which == 0 ? inv_max_tz() : adj_max_tz());
       (which == 0 ? h->inv_nstage : h->adj_nstage) = r4 ? 4 : 3;
       (which == 0 ? h->tz_inv : h->tz_adj) = tzv;
+      (which == 0 ? h->slots_inv : h->slots_adj) = slots;
     }
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
       const int v = std::atoi(e);
       if (v >= 1) h->tz = h->tz_rev = h->tz_inv = h->tz_adj = std::min(v, n[2]);
+      h->tz_free = v < 1;
     }
     h->tz_inv = std::min(h->tz_inv, inv_max_tz());
     h->tz_adj = std::min(h->tz_adj, adj_max_tz());
@@ -1577,6 +1614,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     const bool inl = d.kind <= FDTD_DET_PLANE_FLUX && ninline < kMaxDet;
     if (d.kind == FDTD_DET_PLANE_FLUX || d.kind == FDTD_DET_PLANE_FLUX_INTERP) {
       if (inl) {  // summed inside the fused kernel: one slot per block that meets the box
+        h->fwd_tz_free = false;
         const int tx = fused_tile_x(), ty = fused_tile_y();
         dd.nblk = ((d.hi[0] - 1) / tx - d.lo[0] / tx + 1) * ((d.hi[1] - 1) / ty - d.lo[1] / ty + 1) *
                   ((d.hi[2] - 1) / h->tz - d.lo[2] / h->tz + 1);
@@ -1848,6 +1886,36 @@ int fdtd_finish_backward_density(fdtd_handle* h, float* dL_drho) {
   return finish_backward_scaled(h, dL_drho, h->eps_hi - h->eps_lo);
 }
 
+}  // extern "C"
+
+namespace {
+// The z-chunks of the n requests of a grouped launch of one kernel (0 the forward, 1 the inverse step,
+// 2 the adjoint step, 3 either kernel of the in-place pair), chosen together by group_tz; a[r] holds
+// request r's arguments with its own z-chunk, hs[r] its handle. The results do not depend on them.
+template <class Args>
+void group_chunks(Args* a, fdtd_handle* const* hs, int n, int kind) {
+  if (n < 2) return;
+  int64_t nxy[FDTD_MAX_GROUP];
+  int nz[FDTD_MAX_GROUP], own[FDTD_MAX_GROUP];
+  bool fr[FDTD_MAX_GROUP];
+  for (int r = 0; r < n; ++r) {
+    const fdtd_handle* h = hs[r];
+    nxy[r] = kind == 3 ? h->nxy_r : h->nxy_f;
+    nz[r] = h->g.n[2];
+    own[r] = a[r].tz;
+    fr[r] = h->tz_free && (kind != 0 || h->fwd_tz_free);
+  }
+  const fdtd_handle* h0 = hs[0];  // the launch runs request 0's ring stages, so its slots per SM
+  const int64_t slots = kind == 0 ? h0->slots_fwd : kind == 1 ? h0->slots_inv : kind == 2 ? h0->slots_adj : h0->slots_rev;
+  const int cap = kind == 1 ? inv_max_tz() : kind == 2 ? adj_max_tz() : fused_max_tz();
+  const int tz = group_tz(n, nxy, nz, own, fr, slots, std::min(64, cap));
+  for (int r = 0; r < n; ++r)
+    if (fr[r]) a[r].tz = std::min(tz, nz[r]);
+}
+}  // namespace
+
+extern "C" {
+
 int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
   NvtxRange range("fdtd_group_step");
   if (!hs || n < 1 || n > FDTD_MAX_GROUP || nsteps < 0)
@@ -1885,6 +1953,7 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
         FG.m[r] = h->fmaps[h->cur];
       }
       FG.n = nf;
+      group_chunks(FG.a, F, nf, 0);
       launch_fwd_group(FG, st);
       for (int r = 0; r < nf; ++r) {
         fdtd_handle* h = F[r];
@@ -1936,6 +2005,8 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
       }
       if (faces.n > 0) launch_face_copy_group(faces, st);
       // first halves: the fused inverse steps, and rev_E of the in-place pairs
+      fdtd_handle* fh[FDTD_MAX_GROUP];  // the handles of the fused kind, and of the in-place pair
+      fdtd_handle* sh[FDTD_MAX_GROUP];
       IG.n = RG.n = 0;
       for (int r = 0; r < nr; ++r) {
         fdtd_handle* h = Rv[r];
@@ -1943,15 +2014,19 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
           InvArgs& ia = IG.a[IG.n];
           ia = inv_base(h);
           inv_step_args(h, ia, h->step_next, h->rev_pc, h->rev_ac);
+          fh[IG.n] = h;
           IG.m[IG.n++] = h->imaps[h->rev_pc];
         } else {
           RevArgs& ra = RG.a[RG.n];
           ra = split_base(h);
           split_step_args(h, ra, h->step_next, h->rev_pc, h->rev_pb, 0);
+          sh[RG.n] = h;
           RG.m[RG.n++] = h->rmaps[h->rev_pc];
         }
         h->launches += 1;
       }
+      group_chunks(IG.a, fh, IG.n, 1);
+      group_chunks(RG.a, sh, RG.n, 3);
       if (IG.n > 0) launch_inv_group(IG, st);
       if (RG.n > 0) launch_rev_group(RG, 0, st);
       // second halves: the fused adjoint steps, and rev_H of the in-place pairs
@@ -1973,6 +2048,8 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
         }
         h->launches += 1;
       }
+      group_chunks(AG.a, fh, AG.n, 2);
+      group_chunks(RG.a, sh, RG.n, 3);
       if (AG.n > 0) launch_adj_group(AG, st);
       if (RG.n > 0) launch_rev_group(RG, 1, st);
       for (int r = 0; r < nr; ++r) {

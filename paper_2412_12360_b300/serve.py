@@ -4,10 +4,11 @@ Requests (a scene: grid, sources, detectors, design box and densities, step coun
 time. A scheduler thread admits them in arrival order whenever a slot is free and the request's
 device footprint (fdtd_footprint_bytes: fields, CPML memories, adjoint state and the boundary-face
 history) fits in the memory budget still free. An admitted request's handle is created and its
-inputs uploaded on a private stream, then it joins the group: all running requests are advanced
-together by fdtd_group_step, which launches the fused forward (or inverse and adjoint) kernel once
-per time step for the blocks of every request, so requests that arrive while others run share the
-GPU's SMs with them rather than queueing behind their launches. A request moves from its forward
+inputs uploaded on a private stream, then it joins the running requests, which are advanced in
+chunks of steps by fdtd_group_step: it launches each kernel of a time step (the forward, or the
+reverse pair) once for the blocks of every request of a group, so small requests that run at the
+same time share the GPU's SMs rather than queueing behind each other's launches. The running requests
+form groups whose per-step bytes fit in about half of the L2, stepped one group after another. A request moves from its forward
 to its reverse sweep, and leaves the group, at the step where it finishes; finished requests return
 their detector outputs and dL/deps and free their memory (stream-ordered), which admits the next
 ones.
@@ -50,6 +51,30 @@ def admit_count(queue_footprints, inflight: int, used: int, budget: int, max_inf
     return n
 
 
+def step_bytes(scene) -> int:
+    """The bytes one time step of a request reads and writes at least: its fields (or its primal and
+    adjoint fields) and inverse permittivity, 52 B per cell. Requests stepped together keep the GPU's
+    L2 to themselves only while these sum to less than it holds."""
+    nx, ny, nz = scene.n
+    return 52 * nx * ny * nz
+
+
+def partition(sizes, budget: int, max_group: int):
+    """Split requests (in order) into consecutive groups whose sizes sum to at most `budget` (a request
+    larger than the budget forms a group of its own), each of at most max_group; budget <= 0: groups of
+    max_group regardless of size. Returns lists of indices."""
+    groups, cur, used = [], [], 0
+    for i, b in enumerate(sizes):
+        if cur and (len(cur) >= max_group or (budget > 0 and used + b > budget)):
+            groups.append(cur)
+            cur, used = [], 0
+        cur.append(i)
+        used += b
+    if cur:
+        groups.append(cur)
+    return groups
+
+
 @dataclass
 class Result:
     detectors: np.ndarray
@@ -87,10 +112,16 @@ class Server:
     chunk_steps: time steps per grouped call between scheduling decisions (admission, phase changes).
     ahead: grouped calls enqueued ahead of the GPU at most (enough to cover a request's set-up on the
     host, few enough that a request that arrives meanwhile joins soon).
+    group_bytes: the running requests are stepped in groups whose step bytes (step_bytes) sum to at
+    most this, one group after another for chunk_steps each (0: all in one group). Small requests fill
+    the GPU only side by side; larger ones run fastest in few at a time, each group's state staying in
+    L2 across its chunk of steps. The default, 64 MiB (about half of a B300's 126 MB L2), served a
+    stream of 64^3 and 96^3 requests at 12.1 Gcell-steps/s on one B300, against 11.6 with all running
+    requests in one group and 11.7 / 12.0 with 100 / 128 MiB.
     """
 
     def __init__(self, budget_bytes: Optional[int] = None, max_inflight: int = 4, device: int = 0,
-                 footprint=None, chunk_steps: int = 32, ahead: int = 4):
+                 footprint=None, chunk_steps: int = 32, ahead: int = 4, group_bytes: int = 64 << 20):
         import torch
         from . import fdtd
 
@@ -104,6 +135,7 @@ class Server:
         self.max_inflight = max(1, min(int(max_inflight), fdtd.MAX_GROUP))
         self.chunk_steps = int(chunk_steps)
         self.ahead = max(1, int(ahead))
+        self.group_bytes = int(group_bytes)
         self._footprint = footprint or (lambda sc: fdtd.footprint_bytes(sc, sc.nsteps, record_faces=True))
         self._queue: Deque[_Job] = collections.deque()
         self._inflight: List[_Job] = []
@@ -198,8 +230,8 @@ class Server:
                 job.error = e
                 continue
             stepping.append(job)
-        if stepping:
-            fdtd.group_step([j.solver for j in stepping], self.chunk_steps)
+        for grp in partition([step_bytes(j.scene) for j in stepping], self.group_bytes, fdtd.MAX_GROUP):
+            fdtd.group_step([stepping[i].solver for i in grp], self.chunk_steps)
             self.group_calls += 1
             ev = self._torch.cuda.Event()
             ev.record(self.stream)
