@@ -26,6 +26,13 @@
 // The adjoints of detectors that read only E after a step (points on E components, |E|^2 boxes) of
 // step det_step are added to Ebar_new here, from E of that step in the primal buffer `prim`.
 // Each thread updates two x-adjacent cells.
+//
+// Tiles that touch an x or y layer run a second copy of the plane loop. There, each thread copies the
+// x/y psi-bar values of its own cells (and the halo threads those of their halo cells) into private
+// shared-memory slots one phase before they are used (cp.async), and a neighbour's coefficient is
+// taken from the thread that computed it for its own cell (warp shuffles along x and between the two
+// rows of a warp) wherever that thread is in the same warp. Every coefficient is still computed by the
+// same function from the same values, so the bits are those of the direct form.
 #include "../../include/fdtd.h"
 #include "fdtd_internal.cuh"
 #include "fdtd_tma.cuh"
@@ -68,6 +75,12 @@ struct Flag {
 
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
@@ -223,64 +236,97 @@ __device__ __forceinline__ ZPlane zplane(const Geo& g, const Tables& T, int k) {
   return z;
 }
 
-// (A) at one cell: Hbar_new components in WANT (bit h) from the u values and the old Hbar (g0..g2);
-// (cx, cy) the cell's columns in the x and y tables, zk / zu the z data of planes k and k + 1.
-// STORE: write this cell's psi-bar_E memories (own cells only). XY: x/y layers may be present.
-template <int WANT, bool STORE, bool XY>
-__device__ __forceinline__ void phase_a(const AdjArgs& A, const float (*tabX)[TABX], const float (*tabY)[TABY], int x,
-                                        int y, int k, int cx, int cy, const Slabs& sl, const UA& u, float g0,
-                                        float g1, float g2, const ZPlane& zk, const ZPlane& zu, float out[3]) {
-  const Geo& g = A.g;
-  float cbx = 0.f, cby = 0.f, cbz = 0.f;
-  const PsiSet& Pi = A.pinE;
-  const PsiSet& Po = A.poutE;
-  if constexpr (XY) {
-    if (sl.sX >= 0 || sl.sX1 >= 0) {  // along x: P1 of E_z (2, 0) and P2 of E_y (1, 0), own and at +x
-      float c1z = 0.f, c2y = 0.f, n1z = 0.f, n2y = 0.f;
-      if (sl.sX >= 0) {
-        const int z = zx_of(g, y, k, sl.sX);
-        const Coef cf = coef_at(tabX, 0, cx);
-        const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
-        c1z = acorr(u.uz, cf.ik, cf.c, p20);
-        c2y = acorr(-u.uy, cf.ik, cf.c, p10);
-        if (STORE) {
-          Po.p[2][0][z] = amem(u.uz, cf.b, p20);
-          Po.p[1][0][z] = amem(-u.uy, cf.b, p10);
-        }
-      }
-      if (sl.sX1 >= 0) {
-        const int z = zx_of(g, y, k, sl.sX1);
-        const Coef cf = coef_at(tabX, 0, cx + 1);
-        n1z = acorr(u.uz_x, cf.ik, cf.c, Pi.p[2][0][z]);
-        n2y = acorr(-u.uy_x, cf.ik, cf.c, Pi.p[1][0][z]);
-      }
-      cby = __fadd_rn(cby, __fsub_rn(c1z, n1z));
-      cbz = __fadd_rn(cbz, __fsub_rn(c2y, n2y));
-    }
-    if (sl.sY >= 0 || sl.sY1 >= 0) {  // along y: P1 of E_x (0, 1) and P2 of E_z (2, 1), own and at +y
-      float c1x = 0.f, c2z = 0.f, n1x = 0.f, n2z = 0.f;
-      if (sl.sY >= 0) {
-        const int z = zy_of(g, x, k, sl.sY);
-        const Coef cf = coef_at(tabY, 0, cy);
-        const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
-        c1x = acorr(u.ux, cf.ik, cf.c, p01);
-        c2z = acorr(-u.uz, cf.ik, cf.c, p21);
-        if (STORE) {
-          Po.p[0][1][z] = amem(u.ux, cf.b, p01);
-          Po.p[2][1][z] = amem(-u.uz, cf.b, p21);
-        }
-      }
-      if (sl.sY1 >= 0) {
-        const int z = zy_of(g, x, k, sl.sY1);
-        const Coef cf = coef_at(tabY, 0, cy + 1);
-        n1x = acorr(u.ux_y, cf.ik, cf.c, Pi.p[0][1][z]);
-        n2z = acorr(-u.uz_y, cf.ik, cf.c, Pi.p[2][1][z]);
-      }
-      cbx = __fadd_rn(cbx, __fsub_rn(c2z, n2z));
-      cbz = __fadd_rn(cbz, __fsub_rn(c1x, n1x));
-    }
+// The CPML coefficients of one cell along x or y, as (A) and (B) gather them: the pair (P1, P2) of the
+// two E components transverse to the axis (A), or (Q1, Q2) of the two H components (B). A cell's
+// coefficient is computed by these functions alone, whether for the cell itself (STORE: also its
+// psi-bar memory update) or as the neighbour of another cell, so every evaluation gives the same bits.
+struct CP {
+  float a, b;
+};
+__device__ __forceinline__ CP cp0() { return CP{0.f, 0.f}; }
+
+// (A) along x at (x, y, k), slab s: P1 of E_z from uz, P2 of E_y from -uy
+// (psi-bar values given: p20, p10 the memories of E_z and E_y along x)
+template <bool STORE>
+__device__ __forceinline__ CP cpa_xv(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float uz,
+                                     float uy, float p20, float p10) {
+  const Coef cf = coef_at(tabX, 0, cx);
+  if (STORE) {
+    const int z = zx_of(A.g, y, k, s);
+    A.poutE.p[2][0][z] = amem(uz, cf.b, p20);
+    A.poutE.p[1][0][z] = amem(-uy, cf.b, p10);
   }
-  if (zk.s >= 0 || zu.s >= 0) {  // along z: P1 of E_y (1, 2) and P2 of E_x (0, 2), own and at +z
+  return CP{acorr(uz, cf.ik, cf.c, p20), acorr(-uy, cf.ik, cf.c, p10)};
+}
+template <bool STORE>
+__device__ __forceinline__ CP cpa_x(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float uz,
+                                    float uy) {
+  const int z = zx_of(A.g, y, k, s);
+  return cpa_xv<STORE>(A, tabX, y, k, cx, s, uz, uy, A.pinE.p[2][0][z], A.pinE.p[1][0][z]);
+}
+// (A) along y: P1 of E_x from ux, P2 of E_z from -uz
+template <bool STORE>
+__device__ __forceinline__ CP cpa_yv(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float ux,
+                                     float uz, float p01, float p21) {
+  const Coef cf = coef_at(tabY, 0, cy);
+  if (STORE) {
+    const int z = zy_of(A.g, x, k, s);
+    A.poutE.p[0][1][z] = amem(ux, cf.b, p01);
+    A.poutE.p[2][1][z] = amem(-uz, cf.b, p21);
+  }
+  return CP{acorr(ux, cf.ik, cf.c, p01), acorr(-uz, cf.ik, cf.c, p21)};
+}
+template <bool STORE>
+__device__ __forceinline__ CP cpa_y(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float ux,
+                                    float uz) {
+  const int z = zy_of(A.g, x, k, s);
+  return cpa_yv<STORE>(A, tabY, x, k, cy, s, ux, uz, A.pinE.p[0][1][z], A.pinE.p[2][1][z]);
+}
+// (B) along x: Q1 of H_z from wz, Q2 of H_y from -wy (half-position tables)
+template <bool STORE>
+__device__ __forceinline__ CP cpb_xv(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float wz,
+                                     float wy, float p20, float p10) {
+  const Coef cf = coef_at(tabX, 3, cx);
+  if (STORE) {
+    const int z = zx_of(A.g, y, k, s);
+    A.poutH.p[2][0][z] = amem(wz, cf.b, p20);
+    A.poutH.p[1][0][z] = amem(-wy, cf.b, p10);
+  }
+  return CP{acorr(wz, cf.ik, cf.c, p20), acorr(-wy, cf.ik, cf.c, p10)};
+}
+template <bool STORE>
+__device__ __forceinline__ CP cpb_x(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float wz,
+                                    float wy) {
+  const int z = zx_of(A.g, y, k, s);
+  return cpb_xv<STORE>(A, tabX, y, k, cx, s, wz, wy, A.pinH.p[2][0][z], A.pinH.p[1][0][z]);
+}
+// (B) along y: Q1 of H_x from wx, Q2 of H_z from -wz
+template <bool STORE>
+__device__ __forceinline__ CP cpb_yv(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float wx,
+                                     float wz, float p01, float p21) {
+  const Coef cf = coef_at(tabY, 3, cy);
+  if (STORE) {
+    const int z = zy_of(A.g, x, k, s);
+    A.poutH.p[0][1][z] = amem(wx, cf.b, p01);
+    A.poutH.p[2][1][z] = amem(-wz, cf.b, p21);
+  }
+  return CP{acorr(wx, cf.ik, cf.c, p01), acorr(-wz, cf.ik, cf.c, p21)};
+}
+template <bool STORE>
+__device__ __forceinline__ CP cpb_y(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float wx,
+                                    float wz) {
+  const int z = zy_of(A.g, x, k, s);
+  return cpb_yv<STORE>(A, tabY, x, k, cy, s, wx, wz, A.pinH.p[0][1][z], A.pinH.p[2][1][z]);
+}
+
+// (A) along z at (x, y): the own and +z terms into cbx, cby
+template <bool STORE>
+__device__ __forceinline__ void za_terms(const AdjArgs& A, int x, int y, const UA& u, const ZPlane& zk, const ZPlane& zu,
+                                         float& cbx, float& cby) {
+  if (zk.s >= 0 || zu.s >= 0) {  // P1 of E_y (1, 2) and P2 of E_x (0, 2), own and at +z
+    const Geo& g = A.g;
+    const PsiSet& Pi = A.pinE;
+    const PsiSet& Po = A.poutE;
     float d1y = 0.f, d2x = 0.f, m1y = 0.f, m2x = 0.f;
     if (zk.s >= 0) {
       const int z = zz_of(g, x, y, zk.s);
@@ -300,15 +346,84 @@ __device__ __forceinline__ void phase_a(const AdjArgs& A, const float (*tabX)[TA
     cbx = __fadd_rn(cbx, __fsub_rn(d1y, m1y));
     cby = __fadd_rn(cby, __fsub_rn(d2x, m2x));
   }
+}
+
+// (A) output from the CPML sums: Hbar_new components in WANT from the u values and the old Hbar
+template <int WANT>
+__device__ __forceinline__ void a_out(const UA& u, float g0, float g1, float g2, float cbx, float cby, float cbz,
+                                      float out[3]) {
   if (WANT & 1) out[0] = __fadd_rn(g0, __fadd_rn(__fadd_rn(__fsub_rn(u.uy, u.uy_z), __fsub_rn(u.uz_y, u.uz)), cbx));
   if (WANT & 2) out[1] = __fadd_rn(g1, __fadd_rn(__fadd_rn(__fsub_rn(u.uz, u.uz_x), __fsub_rn(u.ux_z, u.ux)), cby));
   if (WANT & 4) out[2] = __fadd_rn(g2, __fadd_rn(__fadd_rn(__fsub_rn(u.ux, u.ux_y), __fsub_rn(u.uy_x, u.uy)), cbz));
 }
 
+// (A) at one cell: Hbar_new components in WANT (bit h) from the u values and the old Hbar (g0..g2);
+// (cx, cy) the cell's columns in the x and y tables, zk / zu the z data of planes k and k + 1.
+// STORE: write this cell's psi-bar_E memories (own cells only). XY: x/y layers may be present.
+template <int WANT, bool STORE, bool XY>
+__device__ __forceinline__ void phase_a(const AdjArgs& A, const float (*tabX)[TABX], const float (*tabY)[TABY], int x,
+                                        int y, int k, int cx, int cy, const Slabs& sl, const UA& u, float g0,
+                                        float g1, float g2, const ZPlane& zk, const ZPlane& zu, float out[3]) {
+  float cbx = 0.f, cby = 0.f, cbz = 0.f;
+  if constexpr (XY) {
+    if (sl.sX >= 0 || sl.sX1 >= 0) {  // along x: own and at +x
+      const CP o = sl.sX >= 0 ? cpa_x<STORE>(A, tabX, y, k, cx, sl.sX, u.uz, u.uy) : cp0();
+      const CP n = sl.sX1 >= 0 ? cpa_x<false>(A, tabX, y, k, cx + 1, sl.sX1, u.uz_x, u.uy_x) : cp0();
+      cby = __fadd_rn(cby, __fsub_rn(o.a, n.a));
+      cbz = __fadd_rn(cbz, __fsub_rn(o.b, n.b));
+    }
+    if (sl.sY >= 0 || sl.sY1 >= 0) {  // along y: own and at +y
+      const CP o = sl.sY >= 0 ? cpa_y<STORE>(A, tabY, x, k, cy, sl.sY, u.ux, u.uz) : cp0();
+      const CP n = sl.sY1 >= 0 ? cpa_y<false>(A, tabY, x, k, cy + 1, sl.sY1, u.ux_y, u.uz_y) : cp0();
+      cbx = __fadd_rn(cbx, __fsub_rn(o.b, n.b));
+      cbz = __fadd_rn(cbz, __fsub_rn(o.a, n.a));
+    }
+  }
+  za_terms<STORE>(A, x, y, u, zk, zu, cbx, cby);
+  a_out<WANT>(u, g0, g1, g2, cbx, cby, cbz, out);
+}
+
+// The x/y CPML memories one (A) evaluation reads: at the cell and at its +x and +y neighbours.
+struct PsiXY {
+  float xo20, xo10, xn20, xn10, yo01, yo21, yn01, yn21;
+};
+
+// phase_a (no psi-bar stores) with the x/y memories given rather than loaded
+template <int WANT>
+__device__ __forceinline__ void phase_a_given(const AdjArgs& A, const float (*tabX)[TABX], const float (*tabY)[TABY],
+                                              int x, int y, int k, int cx, int cy, const Slabs& sl, const UA& u,
+                                              float g0, float g1, float g2, const PsiXY& p, const ZPlane& zk,
+                                              const ZPlane& zu, float out[3]) {
+  float cbx = 0.f, cby = 0.f, cbz = 0.f;
+  if (sl.sX >= 0 || sl.sX1 >= 0) {
+    const CP o = sl.sX >= 0 ? cpa_xv<false>(A, tabX, y, k, cx, sl.sX, u.uz, u.uy, p.xo20, p.xo10) : cp0();
+    const CP n = sl.sX1 >= 0 ? cpa_xv<false>(A, tabX, y, k, cx + 1, sl.sX1, u.uz_x, u.uy_x, p.xn20, p.xn10) : cp0();
+    cby = __fadd_rn(cby, __fsub_rn(o.a, n.a));
+    cbz = __fadd_rn(cbz, __fsub_rn(o.b, n.b));
+  }
+  if (sl.sY >= 0 || sl.sY1 >= 0) {
+    const CP o = sl.sY >= 0 ? cpa_yv<false>(A, tabY, x, k, cy, sl.sY, u.ux, u.uz, p.yo01, p.yo21) : cp0();
+    const CP n = sl.sY1 >= 0 ? cpa_yv<false>(A, tabY, x, k, cy + 1, sl.sY1, u.ux_y, u.uz_y, p.yn01, p.yn21) : cp0();
+    cbx = __fadd_rn(cbx, __fsub_rn(o.b, n.b));
+    cbz = __fadd_rn(cbz, __fsub_rn(o.a, n.a));
+  }
+  za_terms<false>(A, x, y, u, zk, zu, cbx, cby);
+  a_out<WANT>(u, g0, g1, g2, cbx, cby, cbz, out);
+}
+
 // shared memory besides the Hbar_new tiles: the x and y tables
 constexpr int TXT_OFF = round128(PF_OFF + MAXTZ);                  // [6][TABX]
 constexpr int TYT_OFF = TXT_OFF + 6 * TABX * 4;                    // [6][TABY]
-constexpr int BAR2_OFF = round128(TYT_OFF + 6 * TABY * 4);
+// x/y CPML memories of the own cells, copied ahead by each thread for itself (cp.async) one phase
+// before they are used: psi-bar_E (for (A)) and psi-bar_H (for (B)), slot 4 c + m for cell c with
+// m: the x memories of the z and y components, the y memories of the x and z components
+constexpr int NPS = 8;
+constexpr int PSE_OFF = round128(TYT_OFF + 6 * TABY * 4);          // [NPS][NT]
+constexpr int PSH_OFF = PSE_OFF + NPS * NT * 4;                    // [NPS][NT]
+// the same for the low halo row (lane lx: its pair, 8 c + the PsiXY member) and column (lane lx)
+constexpr int PHR_OFF = PSH_OFF + NPS * NT * 4;                    // [16][LX]
+constexpr int PHC_OFF = PHR_OFF + 16 * LX * 4;                     // [8][LX]
+constexpr int BAR2_OFF = round128(PHC_OFF + 8 * LX * 4);
 constexpr int RING2_OFF = round128(BAR2_OFF + 4 * 8);
 constexpr int smem_total(int ns) { return RING2_OFF + ns * STAGE_BYTES + 128; }
 
@@ -321,6 +436,10 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
   unsigned char* pflag = sm + PF_OFF;
   float(*tabX)[TABX] = reinterpret_cast<float(*)[TABX]>(sm + TXT_OFF);
   float(*tabY)[TABY] = reinterpret_cast<float(*)[TABY]>(sm + TYT_OFF);
+  float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PSE_OFF);
+  float(*sPH)[NT] = reinterpret_cast<float(*)[NT]>(sm + PSH_OFF);
+  float(*sHR)[LX] = reinterpret_cast<float(*)[LX]>(sm + PHR_OFF);
+  float(*sHC)[LX] = reinterpret_cast<float(*)[LX]>(sm + PHC_OFF);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -401,6 +520,54 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
 
   auto march = [&](auto xy_tag) {
     constexpr bool XY = decltype(xy_tag)::value;
+    // copies of the own cells' x/y CPML memories of plane kk (psi-bar_E for (A), psi-bar_H for (B))
+    // into this thread's slots, one commit group each (tiles with x/y layers only)
+    auto fetch_slots = [&](const PsiSet& P, float (*slot)[NT], int kk, bool halo) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!(c == 0 ? own0 : own1)) continue;
+        const Slabs& sl = c ? sl1 : sl0;
+        if (sl.sX >= 0) {
+          const int z = zx_of(g, j, kk, sl.sX);
+          cp4(&slot[4 * c + 0][tid], P.p[2][0] + z);
+          cp4(&slot[4 * c + 1][tid], P.p[1][0] + z);
+        }
+        if (sl.sY >= 0) {
+          const int z = zy_of(g, i + c, kk, sl.sY);
+          cp4(&slot[4 * c + 2][tid], P.p[0][1] + z);
+          cp4(&slot[4 * c + 3][tid], P.p[2][1] + z);
+        }
+      }
+      // (A) of the halo row and column reads the memories at the halo cell and its +x, +y neighbours
+      auto fetch_halo = [&](float (*hs)[LX], int m0, int x, int y, const Slabs& sl) {
+        if (sl.sX >= 0) {
+          const int z = zx_of(g, y, kk, sl.sX);
+          cp4(&hs[m0 + 0][lx], P.p[2][0] + z);
+          cp4(&hs[m0 + 1][lx], P.p[1][0] + z);
+        }
+        if (sl.sX1 >= 0) {
+          const int z = zx_of(g, y, kk, sl.sX1);
+          cp4(&hs[m0 + 2][lx], P.p[2][0] + z);
+          cp4(&hs[m0 + 3][lx], P.p[1][0] + z);
+        }
+        if (sl.sY >= 0) {
+          const int z = zy_of(g, x, kk, sl.sY);
+          cp4(&hs[m0 + 4][lx], P.p[0][1] + z);
+          cp4(&hs[m0 + 5][lx], P.p[2][1] + z);
+        }
+        if (sl.sY1 >= 0) {
+          const int z = zy_of(g, x, kk, sl.sY1);
+          cp4(&hs[m0 + 6][lx], P.p[0][1] + z);
+          cp4(&hs[m0 + 7][lx], P.p[2][1] + z);
+        }
+      };
+      if (halo && hrow) {
+        fetch_halo(sHR, 0, i, j0 - 1, slr0);
+        if (hrow1) fetch_halo(sHR, 8, i + 1, j0 - 1, slr1);
+      }
+      if (halo && hcol) fetch_halo(sHC, 0, i0 - 1, yc, slc);
+      cp_commit();
+    };
     // Hbar_new (x and y components) of the own pair at the plane below the one being updated
     float hxm[2] = {0.f, 0.f}, hym[2] = {0.f, 0.f};
     waited &= R.wait(kb);
@@ -430,6 +597,10 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
       }
     }
 
+    if constexpr (XY) {
+      fetch_slots(A.pinE, sPE, k0, true);
+      fetch_slots(A.pinH, sPH, k0, false);
+    }
     for (int k = k0; k < k1; ++k) {
       const int it = k - k0;
       const int q = k * plane + q0;
@@ -447,15 +618,77 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
       // (A) Hbar_new of the own pair, and Ebar of the pair (kept for (B))
       float hn[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
       float2 eo[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      if (own0) {
+      if constexpr (XY) {
+        // x/y layers: the own cells' coefficients first; a +x or +y neighbour's coefficient is then
+        // taken from the thread that owns it (+x of cell 1: the next lane's cell 0; +y of the warp's
+        // first row: the lane 16 above), and computed here only where that owner is in another warp
+        // or tile (the tile row's last pair, the warp's second row)
+        UA u[2];
+        CP ox[2] = {cp0(), cp0()}, oy[2] = {cp0(), cp0()};
+        cp_wait_all_but_one();  // this plane's psi-bar_E slots (its psi-bar_H copies may still be in flight)
+        if (own0) {
+          pair_u(S, i, j, k, bx0, by0, Ek, Ak, Eu, Au, u);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (c == 1 && !own1) continue;
+            const Slabs& sl = c ? sl1 : sl0;
+            if (sl.sX >= 0)
+              ox[c] = cpa_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, u[c].uz, u[c].uy, sPE[4 * c][tid], sPE[4 * c + 1][tid]);
+            if (sl.sY >= 0)
+              oy[c] = cpa_yv<true>(A, tabY, i + c, k, cy0, sl.sY, u[c].ux, u[c].uz, sPE[4 * c + 2][tid],
+                                   sPE[4 * c + 3][tid]);
+          }
+        }
+        CP nx1, ny[2];
+        nx1.a = __shfl_down_sync(0xffffffffu, ox[0].a, 1, LX);
+        nx1.b = __shfl_down_sync(0xffffffffu, ox[0].b, 1, LX);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          ny[c].a = __shfl_down_sync(0xffffffffu, oy[c].a, LX);
+          ny[c].b = __shfl_down_sync(0xffffffffu, oy[c].b, LX);
+        }
+        if (own0) {
+          const float2 g0 = ld2(&Gk[0][by0][bx0]), g1 = ld2(&Gk[1][by0][bx0]), g2 = ld2(&Gk[2][by0][bx0]);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (c == 1 && !own1) continue;
+            const Slabs& sl = c ? sl1 : sl0;
+            float cbx = 0.f, cby = 0.f, cbz = 0.f;
+            if (sl.sX >= 0 || sl.sX1 >= 0) {
+              const CP n = c == 0 ? ox[1]  // cell 1 (0 beyond the grid)
+                                  : (lx < LX - 1 ? nx1
+                                                 : (sl.sX1 >= 0 ? cpa_x<false>(A, tabX, j, k, cx0 + 2, sl.sX1, u[1].uz_x,
+                                                                               u[1].uy_x)
+                                                                : cp0()));
+              cby = __fadd_rn(cby, __fsub_rn(ox[c].a, n.a));
+              cbz = __fadd_rn(cbz, __fsub_rn(ox[c].b, n.b));
+            }
+            if (sl.sY >= 0 || sl.sY1 >= 0) {
+              const CP n = lane < LX ? ny[c]
+                                     : (sl.sY1 >= 0 ? cpa_y<false>(A, tabY, i + c, k, cy0 + 1, sl.sY1, u[c].ux_y,
+                                                                   u[c].uz_y)
+                                                    : cp0());
+              cbx = __fadd_rn(cbx, __fsub_rn(oy[c].b, n.b));
+              cbz = __fadd_rn(cbz, __fsub_rn(oy[c].a, n.a));
+            }
+            za_terms<true>(A, i + c, j, u[c], zk, zu, cbx, cby);
+            a_out<7>(u[c], c ? g0.y : g0.x, c ? g1.y : g1.x, c ? g2.y : g2.x, cbx, cby, cbz, hn[c]);
+          }
+#pragma unroll
+          for (int e = 0; e < 3; ++e) eo[e] = ld2(&Ek[e][by0][bx0]);
+          st2(&A.nxt.f[3][q], hn[0][0], hn[1][0]);
+          st2(&A.nxt.f[4][q], hn[0][1], hn[1][1]);
+          st2(&A.nxt.f[5][q], hn[0][2], hn[1][2]);
+        }
+      } else if (own0) {
         UA u[2];
         pair_u(S, i, j, k, bx0, by0, Ek, Ak, Eu, Au, u);
         const float2 g0 = ld2(&Gk[0][by0][bx0]), g1 = ld2(&Gk[1][by0][bx0]), g2 = ld2(&Gk[2][by0][bx0]);
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
           if (c == 1 && !own1) continue;
-          phase_a<7, true, XY>(A, tabX, tabY, i + c, j, k, cx0 + c, cy0, c ? sl1 : sl0, u[c], c ? g0.y : g0.x,
-                               c ? g1.y : g1.x, c ? g2.y : g2.x, zk, zu, hn[c]);
+          phase_a<7, true, false>(A, tabX, tabY, i + c, j, k, cx0 + c, cy0, c ? sl1 : sl0, u[c], c ? g0.y : g0.x,
+                                  c ? g1.y : g1.x, c ? g2.y : g2.x, zk, zu, hn[c]);
         }
 #pragma unroll
         for (int e = 0; e < 3; ++e) eo[e] = ld2(&Ek[e][by0][bx0]);
@@ -475,8 +708,15 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
           for (int c = 0; c < 2; ++c) {
             if (c == 1 && !hrow1) continue;
             float o[3];
-            phase_a<5, false, XY>(A, tabX, tabY, i + c, j0 - 1, k, cx0 + c, 0, c ? slr1 : slr0, u[c],
-                                  Gk[0][0][bx0 + c], 0.f, Gk[2][0][bx0 + c], zk, zu, o);
+            if constexpr (XY) {
+              const PsiXY ps{sHR[8 * c][lx],     sHR[8 * c + 1][lx], sHR[8 * c + 2][lx], sHR[8 * c + 3][lx],
+                             sHR[8 * c + 4][lx], sHR[8 * c + 5][lx], sHR[8 * c + 6][lx], sHR[8 * c + 7][lx]};
+              phase_a_given<5>(A, tabX, tabY, i + c, j0 - 1, k, cx0 + c, 0, c ? slr1 : slr0, u[c], Gk[0][0][bx0 + c],
+                               0.f, Gk[2][0][bx0 + c], ps, zk, zu, o);
+            } else {
+              phase_a<5, false, false>(A, tabX, tabY, i + c, j0 - 1, k, cx0 + c, 0, c ? slr1 : slr0, u[c],
+                                       Gk[0][0][bx0 + c], 0.f, Gk[2][0][bx0 + c], zk, zu, o);
+            }
             r0[c] = o[0];
             r2[c] = o[2];
           }
@@ -490,11 +730,22 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
         if (hcol) {
           UA u;
           cell_u(S, i0 - 1, yc, k, XO - 1, lx + 1, Ek, Ak, Eu, Au, u);
-          phase_a<6, false, XY>(A, tabX, tabY, i0 - 1, yc, k, 0, lx + 1, slc, u, 0.f, Gk[1][lx + 1][XO - 1],
-                                Gk[2][lx + 1][XO - 1], zk, zu, o);
+          if constexpr (XY) {
+            const PsiXY ps{sHC[0][lx], sHC[1][lx], sHC[2][lx], sHC[3][lx],
+                           sHC[4][lx], sHC[5][lx], sHC[6][lx], sHC[7][lx]};
+            phase_a_given<6>(A, tabX, tabY, i0 - 1, yc, k, 0, lx + 1, slc, u, 0.f, Gk[1][lx + 1][XO - 1],
+                             Gk[2][lx + 1][XO - 1], ps, zk, zu, o);
+          } else {
+            phase_a<6, false, false>(A, tabX, tabY, i0 - 1, yc, k, 0, lx + 1, slc, u, 0.f, Gk[1][lx + 1][XO - 1],
+                                     Gk[2][lx + 1][XO - 1], zk, zu, o);
+          }
         }
         sH[1][lx + 1][1] = o[1];
         sH[2][lx + 1][1] = o[2];
+      }
+      if constexpr (XY) {  // the next plane's psi-bar_E, into the slots (A) has just read
+        if (k + 1 < k1) fetch_slots(A.pinE, sPE, k + 1, true);
+        else cp_commit();
       }
       __syncthreads();  // the Hbar_new tile is complete; every thread is done with plane k's stage
       if (tid == 0 && k + NSTAGE <= klast) {
@@ -502,7 +753,35 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
         R.issue(M, i0, j0, k + NSTAGE);
       }
 
-      // (B) Ebar_new of the own pair from Hbar_new of this plane (tile and halo) and of the plane below
+      // (B) Ebar_new of the own pair from Hbar_new of this plane (tile and halo) and of the plane below.
+      // x/y layers: the own cells' coefficients first, a -x or -y neighbour's taken from the thread that
+      // owns it (-x of cell 0: the previous lane's cell 1; -y of the warp's second row: the lane 16
+      // below) or computed here where that owner is in another warp or tile
+      CP bxo[2] = {cp0(), cp0()}, byo[2] = {cp0(), cp0()}, bxp = cp0(), byp[2] = {cp0(), cp0()};
+      if constexpr (XY) {
+        cp_wait_all_but_one();  // this plane's psi-bar_H slots (the next plane's psi-bar_E may be in flight)
+        if (own0) {
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (c == 1 && !own1) continue;
+            const Slabs& sl = c ? sl1 : sl0;
+            const float wx = __fmul_rn(-S, hn[c][0]), wy = __fmul_rn(-S, hn[c][1]), wz = __fmul_rn(-S, hn[c][2]);
+            if (sl.sX >= 0)
+              bxo[c] = cpb_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, wz, wy, sPH[4 * c][tid], sPH[4 * c + 1][tid]);
+            if (sl.sY >= 0)
+              byo[c] = cpb_yv<true>(A, tabY, i + c, k, cy0, sl.sY, wx, wz, sPH[4 * c + 2][tid], sPH[4 * c + 3][tid]);
+          }
+        }
+        if (k + 1 < k1) fetch_slots(A.pinH, sPH, k + 1, false);
+        else cp_commit();
+        bxp.a = __shfl_up_sync(0xffffffffu, bxo[1].a, 1, LX);
+        bxp.b = __shfl_up_sync(0xffffffffu, bxo[1].b, 1, LX);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          byp[c].a = __shfl_up_sync(0xffffffffu, byo[c].a, LX);
+          byp[c].b = __shfl_up_sync(0xffffffffu, byo[c].b, LX);
+        }
+      }
       if (own0) {
         const float2 hzs = ld2(&sH[2][ry - 1][rx]), hxs = ld2(&sH[0][ry - 1][rx]);  // at y - 1
         const float hyl = sH[1][ry][rx - 1], hzl = sH[2][ry][rx - 1];             // at x - 1 of cell 0
@@ -527,45 +806,20 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
           const PsiSet& Po = A.poutH;
           const bool ok = c == 0 || own1;
           if constexpr (XY) {
-            if (ok && (sl.sX >= 0 || sl.sXm >= 0)) {  // along x: Q1 of H_z (2, 0), Q2 of H_y (1, 0), own and -x
-              float e1z = 0.f, e2y = 0.f, n1z = 0.f, n2y = 0.f;
-              if (sl.sX >= 0) {
-                const int z = zx_of(g, j, k, sl.sX);
-                const Coef cf = coef_at(tabX, 3, cx);
-                const float p20 = Pi.p[2][0][z], p10 = Pi.p[1][0][z];
-                e1z = acorr(wz, cf.ik, cf.c, p20);
-                e2y = acorr(-wy, cf.ik, cf.c, p10);
-                Po.p[2][0][z] = amem(wz, cf.b, p20);
-                Po.p[1][0][z] = amem(-wy, cf.b, p10);
-              }
-              if (sl.sXm >= 0) {
-                const int z = zx_of(g, j, k, sl.sXm);
-                const Coef cf = coef_at(tabX, 3, cx - 1);
-                n1z = acorr(wz_x, cf.ik, cf.c, Pi.p[2][0][z]);
-                n2y = acorr(-wy_x, cf.ik, cf.c, Pi.p[1][0][z]);
-              }
-              cey = __fadd_rn(cey, __fsub_rn(n1z, e1z));
-              cez = __fadd_rn(cez, __fsub_rn(n2y, e2y));
+            if (ok && (sl.sX >= 0 || sl.sXm >= 0)) {  // along x: Q1 of H_z, Q2 of H_y, own and -x
+              const CP n = c == 1 ? bxo[0]  // cell 0
+                                  : (lx > 0 ? bxp
+                                            : (sl.sXm >= 0 ? cpb_x<false>(A, tabX, j, k, cx - 1, sl.sXm, wz_x, wy_x)
+                                                           : cp0()));
+              cey = __fadd_rn(cey, __fsub_rn(n.a, bxo[c].a));
+              cez = __fadd_rn(cez, __fsub_rn(n.b, bxo[c].b));
             }
-            if (ok && (sl.sY >= 0 || sl.sYm >= 0)) {  // along y: Q1 of H_x (0, 1), Q2 of H_z (2, 1), own and -y
-              float e1x = 0.f, e2z = 0.f, n1x = 0.f, n2z = 0.f;
-              if (sl.sY >= 0) {
-                const int z = zy_of(g, x, k, sl.sY);
-                const Coef cf = coef_at(tabY, 3, cy0);
-                const float p01 = Pi.p[0][1][z], p21 = Pi.p[2][1][z];
-                e1x = acorr(wx, cf.ik, cf.c, p01);
-                e2z = acorr(-wz, cf.ik, cf.c, p21);
-                Po.p[0][1][z] = amem(wx, cf.b, p01);
-                Po.p[2][1][z] = amem(-wz, cf.b, p21);
-              }
-              if (sl.sYm >= 0) {
-                const int z = zy_of(g, x, k, sl.sYm);
-                const Coef cf = coef_at(tabY, 3, cy0 - 1);
-                n1x = acorr(wx_y, cf.ik, cf.c, Pi.p[0][1][z]);
-                n2z = acorr(-wz_y, cf.ik, cf.c, Pi.p[2][1][z]);
-              }
-              cex = __fadd_rn(cex, __fsub_rn(n2z, e2z));
-              cez = __fadd_rn(cez, __fsub_rn(n1x, e1x));
+            if (ok && (sl.sY >= 0 || sl.sYm >= 0)) {  // along y: Q1 of H_x, Q2 of H_z, own and -y
+              const CP n = lane >= LX ? byp[c]
+                                      : (sl.sYm >= 0 ? cpb_y<false>(A, tabY, x, k, cy0 - 1, sl.sYm, wx_y, wz_y)
+                                                     : cp0());
+              cex = __fadd_rn(cex, __fsub_rn(n.b, byo[c].b));
+              cez = __fadd_rn(cez, __fsub_rn(n.a, byo[c].a));
             }
           }
           if (ok && (zk.s >= 0 || zm.s >= 0)) {  // along z: Q1 of H_y (1, 2), Q2 of H_x (0, 2), own and -z
@@ -641,6 +895,7 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
   };
   if (tile_xy) march(Flag<true>{});
   else march(Flag<false>{});
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no slot copy outlives the block
   if (!waited) atomicOr(A.status, kStatusTimeout);
 }
 
