@@ -191,7 +191,11 @@ def roofline(prof, sc, args, fwd_step_ms, rev_step_ms):
             "frac": round(achieved / peak, 4), "peak_source": src,
             "traffic": args.traffic if args.traffic is not None else recorded_traffic(kname, args.workload),
             "bytes_per_launch": nbytes, "avg_launch_ms": round(avg_ms, 5),
-            "kernel_ms_per_launch": {k: round(v, 5) for k, v in ms.items()},
+            "kernel_ms_per_launch": {k: round(v, 5) for k, v in ms.items() if k in FWD_KERNELS or k in REV_KERNELS},
+            # the face copies run on a second stream beside the stencil kernels: their brackets measure the
+            # time from their start until they finish, waiting for SM slots included
+            "side_stream_ms_per_launch": {k: round(v, 5) for k, v in ms.items()
+                                          if k not in FWD_KERNELS and k not in REV_KERNELS},
             "kernel_frac": {k: round(algorithmic_bytes(k, sc) / (v * 1e-3) / 1e9 / peak, 4)
                             for k, v in ms.items() if algorithmic_bytes(k, sc)},
             "timing": {"method": "CUDA events around every %d-th launch of each kernel on its own stream inside "

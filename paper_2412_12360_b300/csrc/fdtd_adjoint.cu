@@ -76,14 +76,22 @@ struct Flag {
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 
-__device__ __forceinline__ void cp4(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+__device__ __forceinline__ void cp8(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 __device__ __forceinline__ int box_offset(const int lo[3], const int hi[3], int x, int y, int k) {
   return ((k - lo[2]) * (hi[1] - lo[1]) + (y - lo[1])) * (hi[0] - lo[0]) + (x - lo[0]);
+}
+
+// This kernel keeps the two psi-bar memories of one axis side by side, one float2 per position (axis
+// x: the y then the z component; axis y: x then z; axis z: x then y), in the space a PsiSet gives that
+// axis's two arrays, so a cell's pair of memories is one 8-byte access. (The arrays are the adjoint
+// step's own: zeroed before the sweep and read by no other kernel.)
+__device__ __forceinline__ float2* psi2(const PsiSet& P, int d) {
+  return reinterpret_cast<float2*>(P.p[d == 0 ? 1 : 0][d]);
 }
 
 // psi index of (x, y, k) for the derivative along x, y or z, slab index s
@@ -253,8 +261,7 @@ __device__ __forceinline__ CP cpa_xv(const AdjArgs& A, const float (*tabX)[TABX]
   const Coef cf = coef_at(tabX, 0, cx);
   if (STORE) {
     const int z = zx_of(A.g, y, k, s);
-    A.poutE.p[2][0][z] = amem(uz, cf.b, p20);
-    A.poutE.p[1][0][z] = amem(-uy, cf.b, p10);
+    psi2(A.poutE, 0)[z] = make_float2(amem(-uy, cf.b, p10), amem(uz, cf.b, p20));
   }
   return CP{acorr(uz, cf.ik, cf.c, p20), acorr(-uy, cf.ik, cf.c, p10)};
 }
@@ -262,7 +269,8 @@ template <bool STORE>
 __device__ __forceinline__ CP cpa_x(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float uz,
                                     float uy) {
   const int z = zx_of(A.g, y, k, s);
-  return cpa_xv<STORE>(A, tabX, y, k, cx, s, uz, uy, A.pinE.p[2][0][z], A.pinE.p[1][0][z]);
+  const float2 v = psi2(A.pinE, 0)[z];
+  return cpa_xv<STORE>(A, tabX, y, k, cx, s, uz, uy, v.y, v.x);
 }
 // (A) along y: P1 of E_x from ux, P2 of E_z from -uz
 template <bool STORE>
@@ -271,8 +279,7 @@ __device__ __forceinline__ CP cpa_yv(const AdjArgs& A, const float (*tabY)[TABY]
   const Coef cf = coef_at(tabY, 0, cy);
   if (STORE) {
     const int z = zy_of(A.g, x, k, s);
-    A.poutE.p[0][1][z] = amem(ux, cf.b, p01);
-    A.poutE.p[2][1][z] = amem(-uz, cf.b, p21);
+    psi2(A.poutE, 1)[z] = make_float2(amem(ux, cf.b, p01), amem(-uz, cf.b, p21));
   }
   return CP{acorr(ux, cf.ik, cf.c, p01), acorr(-uz, cf.ik, cf.c, p21)};
 }
@@ -280,7 +287,8 @@ template <bool STORE>
 __device__ __forceinline__ CP cpa_y(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float ux,
                                     float uz) {
   const int z = zy_of(A.g, x, k, s);
-  return cpa_yv<STORE>(A, tabY, x, k, cy, s, ux, uz, A.pinE.p[0][1][z], A.pinE.p[2][1][z]);
+  const float2 v = psi2(A.pinE, 1)[z];
+  return cpa_yv<STORE>(A, tabY, x, k, cy, s, ux, uz, v.x, v.y);
 }
 // (B) along x: Q1 of H_z from wz, Q2 of H_y from -wy (half-position tables)
 template <bool STORE>
@@ -289,8 +297,7 @@ __device__ __forceinline__ CP cpb_xv(const AdjArgs& A, const float (*tabX)[TABX]
   const Coef cf = coef_at(tabX, 3, cx);
   if (STORE) {
     const int z = zx_of(A.g, y, k, s);
-    A.poutH.p[2][0][z] = amem(wz, cf.b, p20);
-    A.poutH.p[1][0][z] = amem(-wy, cf.b, p10);
+    psi2(A.poutH, 0)[z] = make_float2(amem(-wy, cf.b, p10), amem(wz, cf.b, p20));
   }
   return CP{acorr(wz, cf.ik, cf.c, p20), acorr(-wy, cf.ik, cf.c, p10)};
 }
@@ -298,7 +305,8 @@ template <bool STORE>
 __device__ __forceinline__ CP cpb_x(const AdjArgs& A, const float (*tabX)[TABX], int y, int k, int cx, int s, float wz,
                                     float wy) {
   const int z = zx_of(A.g, y, k, s);
-  return cpb_xv<STORE>(A, tabX, y, k, cx, s, wz, wy, A.pinH.p[2][0][z], A.pinH.p[1][0][z]);
+  const float2 v = psi2(A.pinH, 0)[z];
+  return cpb_xv<STORE>(A, tabX, y, k, cx, s, wz, wy, v.y, v.x);
 }
 // (B) along y: Q1 of H_x from wx, Q2 of H_z from -wz
 template <bool STORE>
@@ -307,8 +315,7 @@ __device__ __forceinline__ CP cpb_yv(const AdjArgs& A, const float (*tabY)[TABY]
   const Coef cf = coef_at(tabY, 3, cy);
   if (STORE) {
     const int z = zy_of(A.g, x, k, s);
-    A.poutH.p[0][1][z] = amem(wx, cf.b, p01);
-    A.poutH.p[2][1][z] = amem(-wz, cf.b, p21);
+    psi2(A.poutH, 1)[z] = make_float2(amem(wx, cf.b, p01), amem(-wz, cf.b, p21));
   }
   return CP{acorr(wx, cf.ik, cf.c, p01), acorr(-wz, cf.ik, cf.c, p21)};
 }
@@ -316,7 +323,8 @@ template <bool STORE>
 __device__ __forceinline__ CP cpb_y(const AdjArgs& A, const float (*tabY)[TABY], int x, int k, int cy, int s, float wx,
                                     float wz) {
   const int z = zy_of(A.g, x, k, s);
-  return cpb_yv<STORE>(A, tabY, x, k, cy, s, wx, wz, A.pinH.p[0][1][z], A.pinH.p[2][1][z]);
+  const float2 v = psi2(A.pinH, 1)[z];
+  return cpb_yv<STORE>(A, tabY, x, k, cy, s, wx, wz, v.x, v.y);
 }
 
 // (A) along z at (x, y): the own and +z terms into cbx, cby
@@ -330,18 +338,17 @@ __device__ __forceinline__ void za_terms(const AdjArgs& A, int x, int y, const U
     float d1y = 0.f, d2x = 0.f, m1y = 0.f, m2x = 0.f;
     if (zk.s >= 0) {
       const int z = zz_of(g, x, y, zk.s);
-      const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
+      const float2 v = psi2(Pi, 2)[z];
+      const float p12 = v.y, p02 = v.x;
       d1y = acorr(u.uy, zk.e.ik, zk.e.c, p12);
       d2x = acorr(-u.ux, zk.e.ik, zk.e.c, p02);
-      if (STORE) {
-        Po.p[1][2][z] = amem(u.uy, zk.e.b, p12);
-        Po.p[0][2][z] = amem(-u.ux, zk.e.b, p02);
-      }
+      if (STORE) psi2(Po, 2)[z] = make_float2(amem(-u.ux, zk.e.b, p02), amem(u.uy, zk.e.b, p12));
     }
     if (zu.s >= 0) {
       const int z = zz_of(g, x, y, zu.s);
-      m1y = acorr(u.uy_z, zu.e.ik, zu.e.c, Pi.p[1][2][z]);
-      m2x = acorr(-u.ux_z, zu.e.ik, zu.e.c, Pi.p[0][2][z]);
+      const float2 v = psi2(Pi, 2)[z];
+      m1y = acorr(u.uy_z, zu.e.ik, zu.e.c, v.y);
+      m2x = acorr(-u.ux_z, zu.e.ik, zu.e.c, v.x);
     }
     cbx = __fadd_rn(cbx, __fsub_rn(d1y, m1y));
     cby = __fadd_rn(cby, __fsub_rn(d2x, m2x));
@@ -415,14 +422,15 @@ __device__ __forceinline__ void phase_a_given(const AdjArgs& A, const float (*ta
 constexpr int TXT_OFF = round128(PF_OFF + MAXTZ);                  // [6][TABX]
 constexpr int TYT_OFF = TXT_OFF + 6 * TABX * 4;                    // [6][TABY]
 // x/y CPML memories of the own cells, copied ahead by each thread for itself (cp.async) one phase
-// before they are used: psi-bar_E (for (A)) and psi-bar_H (for (B)), slot 4 c + m for cell c with
-// m: the x memories of the z and y components, the y memories of the x and z components
+// before they are used: psi-bar_E (for (A)) and psi-bar_H (for (B)), as the float2 pairs of psi2, slot
+// 2 c for cell c's x pair and 2 c + 1 for its y pair
 constexpr int NPS = 8;
-constexpr int PSE_OFF = round128(TYT_OFF + 6 * TABY * 4);          // [NPS][NT]
-constexpr int PSH_OFF = PSE_OFF + NPS * NT * 4;                    // [NPS][NT]
-// the same for the low halo row (lane lx: its pair, 8 c + the PsiXY member) and column (lane lx)
-constexpr int PHR_OFF = PSH_OFF + NPS * NT * 4;                    // [16][LX]
-constexpr int PHC_OFF = PHR_OFF + 16 * LX * 4;                     // [8][LX]
+constexpr int PSE_OFF = round128(TYT_OFF + 6 * TABY * 4);          // [NPS / 2][NT] float2
+constexpr int PSH_OFF = PSE_OFF + NPS * NT * 4;                    // [NPS / 2][NT] float2
+// the same for the low halo row (lane lx: cell c of its pair at 4 c + (x pair, x pair at +x, y pair, y
+// pair at +y)) and column (lane lx: its cell at 0..3 likewise)
+constexpr int PHR_OFF = PSH_OFF + NPS * NT * 4;                    // [8][LX] float2
+constexpr int PHC_OFF = PHR_OFF + 16 * LX * 4;                     // [4][LX] float2
 constexpr int BAR2_OFF = round128(PHC_OFF + 8 * LX * 4);
 constexpr int RING2_OFF = round128(BAR2_OFF + 4 * 8);
 constexpr int smem_total(int ns) { return RING2_OFF + ns * STAGE_BYTES + 128; }
@@ -436,10 +444,12 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
   unsigned char* pflag = sm + PF_OFF;
   float(*tabX)[TABX] = reinterpret_cast<float(*)[TABX]>(sm + TXT_OFF);
   float(*tabY)[TABY] = reinterpret_cast<float(*)[TABY]>(sm + TYT_OFF);
-  float(*sPE)[NT] = reinterpret_cast<float(*)[NT]>(sm + PSE_OFF);
-  float(*sPH)[NT] = reinterpret_cast<float(*)[NT]>(sm + PSH_OFF);
-  float(*sHR)[LX] = reinterpret_cast<float(*)[LX]>(sm + PHR_OFF);
-  float(*sHC)[LX] = reinterpret_cast<float(*)[LX]>(sm + PHC_OFF);
+  // slots of float2 pairs (one axis's two memories): own cell c at 2 c + (0: x, 1: y); halo cell c at
+  // 4 c + (x own, x at +x, y own, y at +y)
+  float2(*sPE)[NT] = reinterpret_cast<float2(*)[NT]>(sm + PSE_OFF);
+  float2(*sPH)[NT] = reinterpret_cast<float2(*)[NT]>(sm + PSH_OFF);
+  float2(*sHR)[LX] = reinterpret_cast<float2(*)[LX]>(sm + PHR_OFF);
+  float2(*sHC)[LX] = reinterpret_cast<float2(*)[LX]>(sm + PHC_OFF);
 
   const Geo& g = A.g;
   const Tables& T = A.T;
@@ -522,48 +532,26 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
     constexpr bool XY = decltype(xy_tag)::value;
     // copies of the own cells' x/y CPML memories of plane kk (psi-bar_E for (A), psi-bar_H for (B))
     // into this thread's slots, one commit group each (tiles with x/y layers only)
-    auto fetch_slots = [&](const PsiSet& P, float (*slot)[NT], int kk, bool halo) {
+    auto fetch_slots = [&](const PsiSet& P, float2 (*slot)[NT], int kk, bool halo) {
+      const float2* px = psi2(P, 0);
+      const float2* py = psi2(P, 1);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         if (!(c == 0 ? own0 : own1)) continue;
         const Slabs& sl = c ? sl1 : sl0;
-        if (sl.sX >= 0) {
-          const int z = zx_of(g, j, kk, sl.sX);
-          cp4(&slot[4 * c + 0][tid], P.p[2][0] + z);
-          cp4(&slot[4 * c + 1][tid], P.p[1][0] + z);
-        }
-        if (sl.sY >= 0) {
-          const int z = zy_of(g, i + c, kk, sl.sY);
-          cp4(&slot[4 * c + 2][tid], P.p[0][1] + z);
-          cp4(&slot[4 * c + 3][tid], P.p[2][1] + z);
-        }
+        if (sl.sX >= 0) cp8(&slot[2 * c][tid], px + zx_of(g, j, kk, sl.sX));
+        if (sl.sY >= 0) cp8(&slot[2 * c + 1][tid], py + zy_of(g, i + c, kk, sl.sY));
       }
       // (A) of the halo row and column reads the memories at the halo cell and its +x, +y neighbours
-      auto fetch_halo = [&](float (*hs)[LX], int m0, int x, int y, const Slabs& sl) {
-        if (sl.sX >= 0) {
-          const int z = zx_of(g, y, kk, sl.sX);
-          cp4(&hs[m0 + 0][lx], P.p[2][0] + z);
-          cp4(&hs[m0 + 1][lx], P.p[1][0] + z);
-        }
-        if (sl.sX1 >= 0) {
-          const int z = zx_of(g, y, kk, sl.sX1);
-          cp4(&hs[m0 + 2][lx], P.p[2][0] + z);
-          cp4(&hs[m0 + 3][lx], P.p[1][0] + z);
-        }
-        if (sl.sY >= 0) {
-          const int z = zy_of(g, x, kk, sl.sY);
-          cp4(&hs[m0 + 4][lx], P.p[0][1] + z);
-          cp4(&hs[m0 + 5][lx], P.p[2][1] + z);
-        }
-        if (sl.sY1 >= 0) {
-          const int z = zy_of(g, x, kk, sl.sY1);
-          cp4(&hs[m0 + 6][lx], P.p[0][1] + z);
-          cp4(&hs[m0 + 7][lx], P.p[2][1] + z);
-        }
+      auto fetch_halo = [&](float2 (*hs)[LX], int m0, int x, int y, const Slabs& sl) {
+        if (sl.sX >= 0) cp8(&hs[m0][lx], px + zx_of(g, y, kk, sl.sX));
+        if (sl.sX1 >= 0) cp8(&hs[m0 + 1][lx], px + zx_of(g, y, kk, sl.sX1));
+        if (sl.sY >= 0) cp8(&hs[m0 + 2][lx], py + zy_of(g, x, kk, sl.sY));
+        if (sl.sY1 >= 0) cp8(&hs[m0 + 3][lx], py + zy_of(g, x, kk, sl.sY1));
       };
       if (halo && hrow) {
         fetch_halo(sHR, 0, i, j0 - 1, slr0);
-        if (hrow1) fetch_halo(sHR, 8, i + 1, j0 - 1, slr1);
+        if (hrow1) fetch_halo(sHR, 4, i + 1, j0 - 1, slr1);
       }
       if (halo && hcol) fetch_halo(sHC, 0, i0 - 1, yc, slc);
       cp_commit();
@@ -633,10 +621,10 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
             if (c == 1 && !own1) continue;
             const Slabs& sl = c ? sl1 : sl0;
             if (sl.sX >= 0)
-              ox[c] = cpa_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, u[c].uz, u[c].uy, sPE[4 * c][tid], sPE[4 * c + 1][tid]);
+              ox[c] = cpa_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, u[c].uz, u[c].uy, sPE[2 * c][tid].y, sPE[2 * c][tid].x);
             if (sl.sY >= 0)
-              oy[c] = cpa_yv<true>(A, tabY, i + c, k, cy0, sl.sY, u[c].ux, u[c].uz, sPE[4 * c + 2][tid],
-                                   sPE[4 * c + 3][tid]);
+              oy[c] = cpa_yv<true>(A, tabY, i + c, k, cy0, sl.sY, u[c].ux, u[c].uz, sPE[2 * c + 1][tid].x,
+                                   sPE[2 * c + 1][tid].y);
           }
         }
         CP nx1, ny[2];
@@ -709,8 +697,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
             if (c == 1 && !hrow1) continue;
             float o[3];
             if constexpr (XY) {
-              const PsiXY ps{sHR[8 * c][lx],     sHR[8 * c + 1][lx], sHR[8 * c + 2][lx], sHR[8 * c + 3][lx],
-                             sHR[8 * c + 4][lx], sHR[8 * c + 5][lx], sHR[8 * c + 6][lx], sHR[8 * c + 7][lx]};
+              const float2 hx = sHR[4 * c][lx], hxn = sHR[4 * c + 1][lx];
+              const float2 hy = sHR[4 * c + 2][lx], hyn = sHR[4 * c + 3][lx];
+              const PsiXY ps{hx.y, hx.x, hxn.y, hxn.x, hy.x, hy.y, hyn.x, hyn.y};
               phase_a_given<5>(A, tabX, tabY, i + c, j0 - 1, k, cx0 + c, 0, c ? slr1 : slr0, u[c], Gk[0][0][bx0 + c],
                                0.f, Gk[2][0][bx0 + c], ps, zk, zu, o);
             } else {
@@ -731,8 +720,8 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
           UA u;
           cell_u(S, i0 - 1, yc, k, XO - 1, lx + 1, Ek, Ak, Eu, Au, u);
           if constexpr (XY) {
-            const PsiXY ps{sHC[0][lx], sHC[1][lx], sHC[2][lx], sHC[3][lx],
-                           sHC[4][lx], sHC[5][lx], sHC[6][lx], sHC[7][lx]};
+            const float2 hx = sHC[0][lx], hxn = sHC[1][lx], hy = sHC[2][lx], hyn = sHC[3][lx];
+            const PsiXY ps{hx.y, hx.x, hxn.y, hxn.x, hy.x, hy.y, hyn.x, hyn.y};
             phase_a_given<6>(A, tabX, tabY, i0 - 1, yc, k, 0, lx + 1, slc, u, 0.f, Gk[1][lx + 1][XO - 1],
                              Gk[2][lx + 1][XO - 1], ps, zk, zu, o);
           } else {
@@ -767,9 +756,9 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
             const Slabs& sl = c ? sl1 : sl0;
             const float wx = __fmul_rn(-S, hn[c][0]), wy = __fmul_rn(-S, hn[c][1]), wz = __fmul_rn(-S, hn[c][2]);
             if (sl.sX >= 0)
-              bxo[c] = cpb_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, wz, wy, sPH[4 * c][tid], sPH[4 * c + 1][tid]);
+              bxo[c] = cpb_xv<true>(A, tabX, j, k, cx0 + c, sl.sX, wz, wy, sPH[2 * c][tid].y, sPH[2 * c][tid].x);
             if (sl.sY >= 0)
-              byo[c] = cpb_yv<true>(A, tabY, i + c, k, cy0, sl.sY, wx, wz, sPH[4 * c + 2][tid], sPH[4 * c + 3][tid]);
+              byo[c] = cpb_yv<true>(A, tabY, i + c, k, cy0, sl.sY, wx, wz, sPH[2 * c + 1][tid].x, sPH[2 * c + 1][tid].y);
           }
         }
         if (k + 1 < k1) fetch_slots(A.pinH, sPH, k + 1, false);
@@ -826,16 +815,17 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
             float e1y = 0.f, e2x = 0.f, m1y = 0.f, m2x = 0.f;
             if (zk.s >= 0) {
               const int z = zz_of(g, x, j, zk.s);
-              const float p12 = Pi.p[1][2][z], p02 = Pi.p[0][2][z];
+              const float2 v = psi2(Pi, 2)[z];
+              const float p12 = v.y, p02 = v.x;
               e1y = acorr(wy, zk.h.ik, zk.h.c, p12);
               e2x = acorr(-wx, zk.h.ik, zk.h.c, p02);
-              Po.p[1][2][z] = amem(wy, zk.h.b, p12);
-              Po.p[0][2][z] = amem(-wx, zk.h.b, p02);
+              psi2(Po, 2)[z] = make_float2(amem(-wx, zk.h.b, p02), amem(wy, zk.h.b, p12));
             }
             if (zm.s >= 0) {
               const int z = zz_of(g, x, j, zm.s);
-              m1y = acorr(wy_m, zm.h.ik, zm.h.c, Pi.p[1][2][z]);
-              m2x = acorr(-wx_m, zm.h.ik, zm.h.c, Pi.p[0][2][z]);
+              const float2 v = psi2(Pi, 2)[z];
+              m1y = acorr(wy_m, zm.h.ik, zm.h.c, v.y);
+              m2x = acorr(-wx_m, zm.h.ik, zm.h.c, v.x);
             }
             cex = __fadd_rn(cex, __fsub_rn(m1y, e1y));
             cey = __fadd_rn(cey, __fsub_rn(m2x, e2x));
