@@ -436,7 +436,9 @@ constexpr int RING2_OFF = round128(BAR2_OFF + 4 * 8);
 constexpr int smem_total(int ns) { return RING2_OFF + ns * STAGE_BYTES + 128; }
 
 // The adjoint step of one request for the block at tile (bx, by), z-chunk bz.
-template <int NSTAGE>
+// PATH 0: a block runs the plane loop its tile needs (both loops compiled in); 1: the plain loop only;
+// 2: the x/y CPML loop only (the caller maps the block to a tile that needs it)
+template <int NSTAGE, int PATH>
 __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, const int bx, const int by, const int bz) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = smem_raw + ((128 - (smem_addr(smem_raw) & 127)) & 127);
@@ -883,15 +885,49 @@ __device__ __forceinline__ void adj_body(const AdjArgs& A, const AdjMaps& M, con
       zk = zu;
     }
   };
-  if (tile_xy) march(Flag<true>{});
-  else march(Flag<false>{});
+  if constexpr (PATH == 1) {
+    march(Flag<false>{});
+  } else if constexpr (PATH == 2) {
+    march(Flag<true>{});
+  } else {
+    if (tile_xy) march(Flag<true>{});
+    else march(Flag<false>{});
+  }
   asm volatile("cp.async.wait_all;" ::: "memory");  // no slot copy outlives the block
   if (!waited) atomicOr(A.status, kStatusTimeout);
 }
 
 template <int NSTAGE>
 __global__ void __launch_bounds__(NT, 2) k_adj_fused(const __grid_constant__ AdjArgs A, const __grid_constant__ AdjMaps M) {
-  adj_body<NSTAGE>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+  adj_body<NSTAGE, 0>(A, M, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// The plain tiles of a split step: the rectangle of tile columns [xl, ntx - xh) and rows [yl, nty - yh).
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_adj_plain(const __grid_constant__ AdjArgs A, const __grid_constant__ AdjMaps M) {
+  adj_body<NSTAGE, 1>(A, M, A.xl + (int)blockIdx.x, A.yl + (int)blockIdx.y, blockIdx.z);
+}
+
+// The x/y CPML tiles of a split step, blockIdx.x numbering the frame: the first yl rows whole, then the
+// last yh rows whole, then the xl first and xh last columns of the rows between; blockIdx.y the z-chunk.
+template <int NSTAGE>
+__global__ void __launch_bounds__(NT, 2) k_adj_frame(const __grid_constant__ AdjArgs A, const __grid_constant__ AdjMaps M) {
+  const int ntx = (A.g.n[0] + TX - 1) / TX, nty = (A.g.n[1] + TY - 1) / TY;
+  int t = blockIdx.x, bx, by;
+  if (t < A.yl * ntx) {
+    by = t / ntx;
+    bx = t % ntx;
+  } else if ((t -= A.yl * ntx) < A.yh * ntx) {
+    by = nty - A.yh + t / ntx;
+    bx = t % ntx;
+  } else {
+    t -= A.yh * ntx;
+    const int w = A.xl + A.xh;
+    by = A.yl + t / w;
+    const int r = t % w;
+    bx = r < A.xl ? r : ntx - A.xh + (r - A.xl);
+  }
+  adj_body<NSTAGE, 2>(A, M, bx, by, blockIdx.y);
 }
 
 // Several requests in one launch (see k_fwd_fused_group).
@@ -899,7 +935,7 @@ template <int NSTAGE>
 __global__ void __launch_bounds__(NT, 2) k_adj_fused_group(const __grid_constant__ AdjGroup G) {
   int bx, by, bz;
   const int r = group_locate(G.grid, bx, by, bz);
-  adj_body<NSTAGE>(G.a[r], G.m[r], bx, by, bz);
+  adj_body<NSTAGE, 0>(G.a[r], G.m[r], bx, by, bz);
 }
 
 }  // namespace
@@ -922,20 +958,51 @@ MapBox adj_box_h() { return {GW, GH}; }
 int prepare_adj(int nstage, int* blocks_per_sm) {
   auto k = nstage == 4 ? k_adj_fused<4> : k_adj_fused<3>;
   auto kg = nstage == 4 ? k_adj_fused_group<4> : k_adj_fused_group<3>;
+  auto kp = nstage == 4 ? k_adj_plain<4> : k_adj_plain<3>;
+  auto kf = nstage == 4 ? k_adj_frame<4> : k_adj_frame<3>;
   const int smem = smem_total(nstage);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, NT, smem);
   return e == cudaSuccess ? FDTD_OK : set_error(FDTD_ERR_CUDA, cudaGetErrorString(e));
 }
 
 int adj_max_tz() { return MAXTZ; }
 
-void launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s) {
+int adj_tiles_x(const Geo& g) { return (g.n[0] + TX - 1) / TX; }
+int adj_tiles_y(const Geo& g) { return (g.n[1] + TY - 1) / TY; }
+
+// Whether tile column bx (axis 0) or row by (axis 1) needs the x/y CPML path: the tile, its halo or
+// their neighbours reach a layer (the test the plane loop makes per block).
+bool adj_tile_xy(const Geo& g, int axis, int b) {
+  const int t = axis == 0 ? TX : TY, o = b * t, n = g.n[axis];
+  return o - 1 < g.pml[2 * axis] || o + t >= n - g.pml[2 * axis + 1] - 1;
+}
+
+int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s) {
   const Geo& g = a.g;
-  dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  if (a.nstage == 4) launch_pdl(k_adj_fused<4>, grid, dim3(NT), smem_total(4), s, a, m);
-  else launch_pdl(k_adj_fused<3>, grid, dim3(NT), smem_total(3), s, a, m);
+  const int ntx = adj_tiles_x(g), nty = adj_tiles_y(g);
+  if (!a.split) {
+    dim3 grid(ntx, nty, (g.n[2] + a.tz - 1) / a.tz);
+    if (a.nstage == 4) launch_pdl(k_adj_fused<4>, grid, dim3(NT), smem_total(4), s, a, m);
+    else launch_pdl(k_adj_fused<3>, grid, dim3(NT), smem_total(3), s, a, m);
+    return 1;
+  }
+  const int frame = (a.yl + a.yh) * ntx + (nty - a.yl - a.yh) * (a.xl + a.xh);
+  dim3 gf(frame, (g.n[2] + a.tz_xy - 1) / a.tz_xy);
+  dim3 gp(ntx - a.xl - a.xh, nty - a.yl - a.yh, (g.n[2] + a.tz - 1) / a.tz);
+  AdjArgs af = a;
+  af.tz = a.tz_xy;
+  if (a.nstage == 4) {
+    launch_pdl(k_adj_frame<4>, gf, dim3(NT), smem_total(4), s, af, m);
+    launch_pdl(k_adj_plain<4>, gp, dim3(NT), smem_total(4), s, a, m);
+  } else {
+    launch_pdl(k_adj_frame<3>, gf, dim3(NT), smem_total(3), s, af, m);
+    launch_pdl(k_adj_plain<3>, gp, dim3(NT), smem_total(3), s, a, m);
+  }
+  return 2;
 }
 
 }  // namespace fdtd

@@ -359,6 +359,8 @@ struct fdtd_handle {
   int fwd_nstage = 3;             // stages of the forward kernel's plane ring
   int tz_inv = 8, inv_nstage = 4; // fused inverse step: z-planes per block, ring stages
   int tz_adj = 8, adj_nstage = 4; // fused adjoint step
+  // the fused adjoint step as two launches (x/y CPML frame, plain rectangle): see AdjArgs::split
+  int adj_split = 0, adj_xl = 0, adj_xh = 0, adj_yl = 0, adj_yh = 0, tz_adj_xy = 8;
   // for grouped launches, whose z-chunks follow the group: column tiles of the 32 x 16 kernels
   // (forward, inverse, adjoint) and of the in-place pair, and resident-block slots of each kernel
   int64_t nxy_f = 1, nxy_r = 1;
@@ -1004,6 +1006,12 @@ AdjArgs adj_base(fdtd_handle* h) {
   aa.a = h->a;
   aa.tz = h->tz_adj;
   aa.nstage = h->adj_nstage;
+  aa.split = h->adj_split;
+  aa.xl = h->adj_xl;
+  aa.xh = h->adj_xh;
+  aa.yl = h->adj_yl;
+  aa.yh = h->adj_yh;
+  aa.tz_xy = h->tz_adj_xy;
   aa.status = h->status;
   aa.gy = h->dLddet;
   aa.ndet = 0;
@@ -1159,9 +1167,9 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_ADJ_FUSED, n);
       adj_step_args(h, aa, n, pc, ac, pb);
-      launch_adj(aa, h->amaps[ac], st);
+      launches += launch_adj(aa, h->amaps[ac], st);
     }
-    launches += 2;
+    launches += 1;
     launches += rev_step_post(h, n, 1 - pc, 1 - ac, st);
     pc = 1 - pc;
     ac = 1 - ac;
@@ -1478,14 +1486,39 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       (which == 0 ? h->inv_nstage : h->adj_nstage) = r4 ? 4 : 3;
       (which == 0 ? h->tz_inv : h->tz_adj) = tzv;
       (which == 0 ? h->slots_inv : h->slots_adj) = slots;
+      if (which == 1) {
+        // the tiles of the split adjoint step: leading and trailing tile columns and rows that need
+        // the x/y CPML loop, each launch's z-chunks for its own tiles
+        const int ntx = adj_tiles_x(g), nty = adj_tiles_y(g);
+        int xl = 0, xh = 0, yl = 0, yh = 0;
+        while (xl < ntx && adj_tile_xy(g, 0, xl)) ++xl;
+        while (xh < ntx - xl && adj_tile_xy(g, 0, ntx - 1 - xh)) ++xh;
+        while (yl < nty && adj_tile_xy(g, 1, yl)) ++yl;
+        while (yh < nty - yl && adj_tile_xy(g, 1, nty - 1 - yh)) ++yh;
+        bool ok = xl + xh < ntx && yl + yh < nty;
+        for (int b = xl; ok && b < ntx - xh; ++b) ok = !adj_tile_xy(g, 0, b);
+        for (int b = yl; ok && b < nty - yh; ++b) ok = !adj_tile_xy(g, 1, b);
+        if (const char* e = std::getenv("FDTD_ADJ_SPLIT")) ok &= std::atoi(e) != 0;  // override
+        h->adj_split = ok ? 1 : 0;
+        h->adj_xl = xl;
+        h->adj_xh = xh;
+        h->adj_yl = yl;
+        h->adj_yh = yh;
+        if (ok) {
+          const int64_t rect = (int64_t)(ntx - xl - xh) * (nty - yl - yh), frame = (int64_t)ntx * nty - rect;
+          h->tz_adj = std::min(choose_tz(rect, n[2], slots), adj_max_tz());
+          h->tz_adj_xy = std::min(choose_tz(frame, n[2], slots), adj_max_tz());
+        }
+      }
     }
     if (const char* e = std::getenv("FDTD_TZ")) {  // tuning override: z-planes per block
       const int v = std::atoi(e);
-      if (v >= 1) h->tz = h->tz_rev = h->tz_inv = h->tz_adj = std::min(v, n[2]);
+      if (v >= 1) h->tz = h->tz_rev = h->tz_inv = h->tz_adj = h->tz_adj_xy = std::min(v, n[2]);
       h->tz_free = v < 1;
     }
     h->tz_inv = std::min(h->tz_inv, inv_max_tz());
     h->tz_adj = std::min(h->tz_adj, adj_max_tz());
+    h->tz_adj_xy = std::min(h->tz_adj_xy, adj_max_tz());
     if (const char* e = std::getenv("FDTD_REV_NSTAGE")) {  // override: ring stages of the reverse kernels
       const int v = std::atoi(e);
       if (v == 3 || v == 4) h->rev_nstage = h->inv_nstage = h->adj_nstage = v;

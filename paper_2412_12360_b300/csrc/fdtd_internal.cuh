@@ -236,6 +236,13 @@ struct AdjArgs {
   int det_step = -1;
   const double* gy = nullptr;
   DetDev det[kMaxDet];
+  // A split step (split = 1) runs as two launches: the tiles that need the x/y CPML path (a frame:
+  // the first xl and last xh tile columns, the first yl and last yh tile rows) with z-chunks of tz_xy,
+  // then the plain tiles inside it with z-chunks of tz. Each launch's kernel holds only its own plane
+  // loop, which runs faster than a loop that also holds the other. split = 0: one launch of all tiles.
+  int split = 0;
+  int xl = 0, xh = 0, yl = 0, yh = 0;
+  int tz_xy = 8;
 };
 
 int fused_tile_x();

@@ -68,7 +68,10 @@ MapBox adj_box_e();   // Ebar and a
 MapBox adj_box_h();   // Hbar
 int prepare_adj(int nstage, int* blocks_per_sm);
 int adj_max_tz();
-void launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s);
+int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s);  // returns the launches made
+int adj_tiles_x(const Geo& g);                    // tile columns and rows of the adjoint step
+int adj_tiles_y(const Geo& g);
+bool adj_tile_xy(const Geo& g, int axis, int b);  // column (axis 0) / row (axis 1) b needs the x/y CPML loop
 
 // ---- grouped launches: several requests (solver handles) advanced by one launch -------------------
 constexpr int kMaxGroup = 8;

@@ -70,6 +70,58 @@ def odd_scene(nsteps=400, seed=43, pml=(5, 7, 4, 6, 6, 3)):
                        nsteps=nsteps, name="odd_x")
 
 
+def wide_scene(nsteps=150, seed=47):
+    """A grid whose adjoint-step tiles form a frame of x/y CPML tiles (first and last two columns, first
+    and last two rows) around a rectangle of plain tiles, with ragged tails in x and y, unequal
+    layers, and detectors and a design box in both parts."""
+    n = (133, 99, 36)
+    pml = (6, 5, 7, 4, 5, 6)
+    nx, ny, nz = n
+    rng = np.random.default_rng(seed)
+    eps_inv = np.ones((nz, ny, nx), dtype=np.float32)
+    dlo, dhi = (10, 12, 9), (120, 90, 28)
+    eps_inv[dlo[2]:dhi[2], dlo[1]:dhi[1], dlo[0]:dhi[0]] = S.inv(
+        1.0 + 11.1 * rng.random((dhi[2] - dlo[2], dhi[1] - dlo[1], dhi[0] - dlo[0])))
+    prof = S.gaussian_sheet((ny - 11, nx - 11), 20.0)[None]
+    sheet = S.default_pulse(S.Source(S.EX, (6, 7, 6), (nx - 5, ny - 4, 7), prof, 1.0, 14.0), S.courant_from_factor())
+    pt = H.point_source(S.EZ, (70, 40, 18), wavelength=10.0, amplitude=0.5)
+    dets = [H.point_probe(S.HY, (125, 50, 20)), H.point_probe(S.EY, (8, 92, 15)),
+            S.Detector(S.DET_PLANE_E2_SUM, (6, 7, 25), (128, 95, 26)),
+            S.Detector(S.DET_PLANE_FLUX, (126, 7, 8), (127, 95, 29), axis=0)]
+    return H.box_scene(n, pml=pml, eps_inv=eps_inv, sources=[sheet, pt], detectors=dets, design=(dlo, dhi),
+                       nsteps=nsteps, name="wide")
+
+
+def test_split_adjoint_step_equals_one_launch(F, monkeypatch):
+    """The fused adjoint step as two launches (the frame of tiles that need the x/y CPML loop, then the
+    rectangle of plain tiles, each with its own z-chunks) gives bitwise the detectors, dL/deps and
+    fields of one launch over all tiles, also with other z-chunks, and matches the oracle."""
+    sc = wide_scene()
+    g = np.random.default_rng(16).standard_normal(O.detector_total(sc, sc.nsteps))
+    monkeypatch.setenv("FDTD_REV_FUSED", "1")
+    out = {}
+    for name, split, tz in (("one", "0", None), ("split", "1", None), ("split_tz5", "1", "5")):
+        monkeypatch.setenv("FDTD_ADJ_SPLIT", split)
+        if tz is None:
+            monkeypatch.delenv("FDTD_TZ", raising=False)
+        else:
+            monkeypatch.setenv("FDTD_TZ", tz)
+        with F.Solver(sc) as s:
+            s.fdtd_forward(sc.nsteps, record_faces=True)
+            det = s.detectors()
+            l0 = s.fdtd_launch_count()
+            grad = s.gradient(g)
+            out[name] = (det, grad, s.fields(), s.fdtd_launch_count() - l0)
+    assert out["split"][3] == out["one"][3] + sc.nsteps  # one more launch per reverse step
+    for name in ("split", "split_tz5"):
+        for a, b in zip(out[name][:3], out["one"][:3]):
+            assert np.array_equal(a, b), name
+    grad_o, _, det_o = O.gradient(sc, sc.nsteps, g, O.METHOD_TIME_REVERSAL)
+    e, ed = rel_l2(out["split"][1], grad_o), rel_l2(out["split"][0], det_o)
+    print("split adjoint step: dL/deps rel L2 %.3e, detectors %.3e" % (e, ed))
+    assert e < 1e-3 and ed < 1e-4
+
+
 def test_forward_pec_cavity_1000_steps(F):
     sc = S.cavity_32(1000)
     f_o, d_o = O.forward(sc, 1000)
