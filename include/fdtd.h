@@ -387,6 +387,17 @@ int fdtd_plane_flux_noalloc(const float* fields6, const fdtd_grid* grid, int32_t
  * report the same way. */
 int fdtd_synchronize(fdtd_handle* h);
 
+/* Diagnostic of the timeout path (failure detection without a fault). Every wait of the stencil
+ * kernels for a TMA copy (an mbarrier phase) is bounded: it gives up after 1 s of the GPU's global
+ * timer (or 2^30 polls), sets the handle's timeout status and lets the block finish, so a lost copy
+ * ends as FDTD_ERR_TIMEOUT from fdtd_synchronize, not as a hang. This call runs that same bounded wait,
+ * with a limit of limit_ms milliseconds (1..2000), in a one-block kernel on an mbarrier that nothing
+ * arrives on, on a private stream of the current device, and waits for it. It returns FDTD_ERR_TIMEOUT
+ * (the expected outcome) with *waited_ns the nanoseconds the wait lasted; FDTD_OK would mean the wait
+ * returned without its phase completing. Allocates 12 bytes (stream-ordered) and frees them.
+ * INVALID_ARG for a limit out of range or a NULL waited_ns. */
+int fdtd_wait_probe(int32_t limit_ms, int64_t* waited_ns);
+
 /* Where the face copies run (default 1): with enable != 0 the per-step face record (forward) and
  * replay (backward) are captured on a second stream beside the stencil kernels, which shortens a
  * step on small grids when the captured loop is replayed many times; with 0 they run in line on the

@@ -2612,6 +2612,35 @@ int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t n
   return per_step * segment_steps + std::max<int64_t>(0, S - 2) * state;
 }
 
+int fdtd_wait_probe(int32_t limit_ms, int64_t* waited_ns) {
+  if (limit_ms < 1 || limit_ms > 2000 || !waited_ns)
+    return fail(FDTD_ERR_INVALID_ARG, "limit_ms in 1..2000 and a waited_ns pointer");
+  cudaStream_t st = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_ns = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  cudaError_t e = cudaMallocAsync(&d_status, 4, st);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_ns, 8, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, 4, st);
+  if (e == cudaSuccess) {
+    launch_wait_probe(d_status, d_ns, (unsigned long long)limit_ms * 1000000ull, st);
+    e = cudaGetLastError();
+  }
+  int status = 0;
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d_status, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ns, d_ns, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d_status) cudaFreeAsync(d_status, st);
+  if (d_ns) cudaFreeAsync(d_ns, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (e != cudaSuccess) return fail(FDTD_ERR_CUDA, "wait probe: %s", cudaGetErrorString(e));
+  *waited_ns = (int64_t)ns;
+  if (status & kStatusTimeout) return fail(FDTD_ERR_TIMEOUT, "the probe's bounded wait gave up after %lld ns", (long long)ns);
+  return FDTD_OK;
+}
+
 int fdtd_synchronize(fdtd_handle* h) {
   if (!h) return fail(FDTD_ERR_INVALID_ARG, "NULL handle");
   return sync_status(h);

@@ -163,6 +163,7 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
 // Flag kStatusNonFinite in *status if one of the grid cells of the n floats at p (whole pitch-padded
 // arrays: n a multiple of 4, p 16-byte aligned) is NaN or infinite; the pitch padding is not read.
 void launch_check_finite(const Geo& g, const float* p, int64_t n, int* status, int nsm, cudaStream_t s);
+void launch_wait_probe(int* status, unsigned long long* waited_ns, unsigned long long limit_ns, cudaStream_t s);
 // Pitch-padding canaries of nrows rows at base, in columns x0 .. nxp-1: fill them with v, or add the
 // number of them that are not NaN to *count (a debugging aid against writes out of a row).
 void launch_fill_padding(const Geo& g, float* base, int64_t nrows, int x0, float v, int nsm, cudaStream_t s);

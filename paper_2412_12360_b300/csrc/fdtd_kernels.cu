@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "fdtd_internal.cuh"
+#include "fdtd_tma.cuh"
 
 namespace fdtd {
 
@@ -368,6 +369,24 @@ void launch_detector_adjoint(const Geo& g, const Fields& F, const Fields& A, con
                              const double* dL_ddet, cudaStream_t s) {
   const int64_t n = d.kind == 0 ? 1 : (int64_t)(d.hi[0] - d.lo[0]) * (d.hi[1] - d.lo[1]) * (d.hi[2] - d.lo[2]);
   launch_pdl(k_det_adjoint, dim3(blocks_for(n, 256)), dim3(256), 0, s, g, F, A, d, step, dL_ddet);
+}
+
+// One bounded wait, as the stencil kernels make it, on an mbarrier that nothing arrives on: it gives up
+// after limit_ns, sets the timeout bit in *status and writes the nanoseconds it waited (diagnostic of
+// the timeout path; no copy is ever issued to the barrier, so none is in flight when the block exits).
+__global__ void k_wait_probe(int* status, unsigned long long* waited_ns, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  const uint64_t t0 = global_ns();
+  const bool ok = mbar_wait_for(&bar, 0, limit_ns);
+  *waited_ns = global_ns() - t0;
+  if (!ok) atomicOr(status, kStatusTimeout);
+}
+
+void launch_wait_probe(int* status, unsigned long long* waited_ns, unsigned long long limit_ns, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(status, waited_ns, limit_ns);
 }
 
 void launch_check_finite(const Geo& g, const float* p, int64_t n, int* status, int nsm, cudaStream_t s) {

@@ -175,14 +175,33 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity to complete; false if it gave up (the caller
-// records a timeout status and carries on, so the block's barriers stay matched).
-constexpr int kWaitLimit = 1 << 22;
+// records a timeout status and carries on, so the block's barriers stay matched). It gives up after
+// limit_ns nanoseconds of the global timer (read every 64 polls, from the first poll that fails) or
+// kWaitLimit polls (a backstop far beyond the time limit), whichever comes first; a TMA copy of a
+// plane lands within microseconds.
+constexpr int kWaitLimit = 1 << 30;
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_wait_for(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  uint64_t t0 = 0;
+  for (int it = 0; it < kWaitLimit; ++it) {
     if (mbar_test(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      const uint64_t t = global_ns();
+      if (it == 0) t0 = t;
+      else if (t - t0 > limit_ns) return false;
+    }
+  }
   return false;
 }
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) { return mbar_wait_for(bar, parity, kWaitNs); }
 
 // Tiled 4-d bulk tensor load of one box at (x, y, z, c) into shared memory, completing on `bar`.
 // x * 4 bytes must be a multiple of 16 (x a multiple of 4); the destination 128-byte aligned.

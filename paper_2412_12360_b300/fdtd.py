@@ -93,6 +93,7 @@ SIGNATURES = [
     ("fdtd_bytes_allocated", C.c_int64, [_VP]),
     ("fdtd_release_history", C.c_int, [_VP]),
     ("fdtd_launch_count", C.c_int64, [_VP]),
+    ("fdtd_wait_probe", C.c_int, [C.c_int32, C.POINTER(C.c_int64)]),
     ("fdtd_profile", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
     ("fdtd_plane_flux_noalloc", C.c_int, [_VP, C.POINTER(fdtd_grid), C.c_int32, _I3, _I3, _VP, _VP]),
@@ -200,6 +201,14 @@ def adjoint_bytes(scene) -> int:
     g = make_grid(scene.n)
     p = make_pml(scene)
     return int(lib().fdtd_adjoint_bytes(C.byref(g), C.byref(p)))
+
+
+def wait_probe(limit_ms: int):
+    """Run one bounded device-side wait that nothing completes (fdtd_wait_probe): returns (code, the
+    nanoseconds it waited); the code is FDTD_ERR_TIMEOUT when the wait gave up as it should."""
+    ns = C.c_int64(0)
+    rc = lib().fdtd_wait_probe(int(limit_ms), C.byref(ns))
+    return rc, int(ns.value)
 
 
 def set_byte_budget(nbytes: int):

@@ -171,6 +171,14 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.fdtd_set_graphs(None, 0) == F.FDTD_ERR_INVALID_ARG
 
 
+def test_wait_probe_rejects_bad_arguments_before_any_device_work(L):
+    ns = C.c_int64(-5)
+    assert L.fdtd_wait_probe(0, C.byref(ns)) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_wait_probe(2001, C.byref(ns)) == F.FDTD_ERR_INVALID_ARG
+    assert L.fdtd_wait_probe(10, None) == F.FDTD_ERR_INVALID_ARG
+    assert ns.value == -5
+
+
 def test_noalloc_flux_refuses_host_buffers_before_any_launch(L):
     """The allocation-free flux call takes device memory of the current device only: host buffers (or,
     with no GPU, anything) are refused with INVALID_ARG before a kernel is launched."""

@@ -122,6 +122,22 @@ def test_split_adjoint_step_equals_one_launch(F, monkeypatch):
     assert e < 1e-3 and ed < 1e-4
 
 
+def test_bounded_wait_ends_with_a_timeout_status_and_the_context_stays_usable(F):
+    """The stencil kernels' bounded wait, run on an mbarrier that nothing completes, gives up after its
+    limit and reports FDTD_ERR_TIMEOUT instead of hanging; the process then solves a scene to the
+    oracle's result (no GPU fault is involved: the wait only polls its own shared-memory barrier)."""
+    for limit_ms in (20, 200):
+        rc, ns = F.wait_probe(limit_ms)
+        print("wait probe, limit %d ms: code %d after %.1f ms" % (limit_ms, rc, ns / 1e6))
+        assert rc == F.FDTD_ERR_TIMEOUT
+        assert limit_ms * 1e6 <= ns < limit_ms * 1e6 + 50e6
+    sc = S.cavity_32(200)
+    f_o, d_o = O.forward(sc, 200)
+    with F.Solver(sc) as s:
+        s.fdtd_forward(200)
+        assert rel_l2(s.detectors(), d_o) < 1e-4
+
+
 def test_forward_pec_cavity_1000_steps(F):
     sc = S.cavity_32(1000)
     f_o, d_o = O.forward(sc, 1000)
