@@ -981,7 +981,7 @@ bool adj_tile_xy(const Geo& g, int axis, int b) {
   return o - 1 < g.pml[2 * axis] || o + t >= n - g.pml[2 * axis + 1] - 1;
 }
 
-int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s) {
+int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s, cudaStream_t s2, cudaEvent_t fork, cudaEvent_t join) {
   const Geo& g = a.g;
   const int ntx = adj_tiles_x(g), nty = adj_tiles_y(g);
   if (!a.split) {
@@ -995,12 +995,24 @@ int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s) {
   dim3 gp(ntx - a.xl - a.xh, nty - a.yl - a.yh, (g.n[2] + a.tz - 1) / a.tz);
   AdjArgs af = a;
   af.tz = a.tz_xy;
+  // with a second stream the two launches run side by side (they write disjoint tiles of the same
+  // buffers): s2 waits for s's work so far, then s waits for s2's launch
+  cudaStream_t sf = s;
+  if (s2) {
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(s2, fork, 0);
+    sf = s2;
+  }
   if (a.nstage == 4) {
-    launch_pdl(k_adj_frame<4>, gf, dim3(NT), smem_total(4), s, af, m);
+    launch_pdl(k_adj_frame<4>, gf, dim3(NT), smem_total(4), sf, af, m);
     launch_pdl(k_adj_plain<4>, gp, dim3(NT), smem_total(4), s, a, m);
   } else {
-    launch_pdl(k_adj_frame<3>, gf, dim3(NT), smem_total(3), s, af, m);
+    launch_pdl(k_adj_frame<3>, gf, dim3(NT), smem_total(3), sf, af, m);
     launch_pdl(k_adj_plain<3>, gp, dim3(NT), smem_total(3), s, a, m);
+  }
+  if (s2) {
+    cudaEventRecord(join, s2);
+    cudaStreamWaitEvent(s, join, 0);
   }
   return 2;
 }

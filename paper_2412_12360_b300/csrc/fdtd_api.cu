@@ -348,6 +348,9 @@ struct fdtd_handle {
   cudaStream_t cap = nullptr;     // private stream used only to capture the time loops
   cudaStream_t side = nullptr;    // captured beside `cap`: the face copies, off the critical path
   cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};  // fork / join points of `side`
+  cudaStream_t side2 = nullptr;   // the frame launch of a split adjoint step, beside its plain launch
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  bool adj_overlap = true;        // use side2 (FDTD_ADJ_OVERLAP=0: one stream)
   bool face_overlap = true;  // face copies on `side`, beside the stencil kernels (else in line on the stream)
   bool use_graphs = true;    // time loops captured into CUDA graphs (else launched directly)
   bool capturing = false;    // a time loop is being captured
@@ -1167,7 +1170,8 @@ int64_t enqueue_backward(fdtd_handle* h, int nsteps, cudaStream_t st, std::vecto
     {
       ProfScope ps(h, evs, st, FDTD_KERNEL_ADJ_FUSED, n);
       adj_step_args(h, aa, n, pc, ac, pb);
-      launches += launch_adj(aa, h->amaps[ac], st);
+      launches += h->adj_overlap ? launch_adj(aa, h->amaps[ac], st, h->side2, h->ev_fork2, h->ev_join2)
+                                 : launch_adj(aa, h->amaps[ac], st);
     }
     launches += 1;
     launches += rev_step_post(h, n, 1 - pc, 1 - ac, st);
@@ -1432,6 +1436,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
   int rc;
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->side2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&h->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
@@ -1499,6 +1506,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
         for (int b = xl; ok && b < ntx - xh; ++b) ok = !adj_tile_xy(g, 0, b);
         for (int b = yl; ok && b < nty - yh; ++b) ok = !adj_tile_xy(g, 1, b);
         if (const char* e = std::getenv("FDTD_ADJ_SPLIT")) ok &= std::atoi(e) != 0;  // override
+        if (const char* e = std::getenv("FDTD_ADJ_OVERLAP")) h->adj_overlap = std::atoi(e) != 0;  // override
         h->adj_split = ok ? 1 : 0;
         h->adj_xl = xl;
         h->adj_xh = xh;
@@ -1692,6 +1700,9 @@ int fdtd_destroy(fdtd_handle* h) {
     if (p) cudaFreeAsync(p, h->stream);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->side) cudaStreamDestroy(h->side);
+  if (h->side2) cudaStreamDestroy(h->side2);
+  if (h->ev_fork2) cudaEventDestroy(h->ev_fork2);
+  if (h->ev_join2) cudaEventDestroy(h->ev_join2);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   for (cudaEvent_t e : h->ev_join)
     if (e) cudaEventDestroy(e);

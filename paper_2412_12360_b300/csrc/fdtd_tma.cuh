@@ -68,7 +68,10 @@ MapBox adj_box_e();   // Ebar and a
 MapBox adj_box_h();   // Hbar
 int prepare_adj(int nstage, int* blocks_per_sm);
 int adj_max_tz();
-int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s);  // returns the launches made
+// returns the launches made; s2 (with the events fork and join), if not null: the stream on which a
+// split step's frame launch runs beside its plain launch on s
+int launch_adj(const AdjArgs& a, const AdjMaps& m, cudaStream_t s, cudaStream_t s2 = nullptr,
+               cudaEvent_t fork = nullptr, cudaEvent_t join = nullptr);
 int adj_tiles_x(const Geo& g);                    // tile columns and rows of the adjoint step
 int adj_tiles_y(const Geo& g);
 bool adj_tile_xy(const Geo& g, int axis, int b);  // column (axis 0) / row (axis 1) b needs the x/y CPML loop
