@@ -1533,17 +1533,20 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
     }
     {
       // The fused pair moves 104 B per cell against 148 but does its CPML work (the adjoint's
-      // coefficients gathered from both neighbours) in every tile that touches an x or y layer. On
-      // one B300: 600^3 with 12-cell layers (18 % of the tiles touch one) 5.16 vs 5.58 ms per reverse
-      // step; 96^3 with 10-cell layers (78 %) 70 vs 42 us. So: the fused pair for grids of at least
-      // 64 M cells whose tiles touch an x or y layer in at most a fifth of the cases.
+      // coefficients gathered from both neighbours) in every tile that touches an x or y layer, and
+      // its 32 x 16 tiles give small grids fewer blocks. On one B300, fwd+grad ms per step with the
+      // fused / in-place pair (fraction of tiles touching an x or y layer): 600^3 7.1 / 7.6 (18 %),
+      // 400^3 2.42 / 2.63 (22 %), 240x240x960 2.29 / 2.40 (35 %), 256^3 0.765 / 0.796 (34 %), 200^3
+      // 0.501 / 0.473 (56 %), 128x128x256 0.306 / 0.266 (63 %), 96^3 (78 %) slower still. So: the
+      // fused pair for grids of at least 12 M cells whose tiles touch a layer in at most 40 % of the
+      // cases.
       const int tx = fused_tile_x(), ty = fused_tile_y();
       const int ntx = (n[0] + tx - 1) / tx, nty = (n[1] + ty - 1) / ty;
       int plain_x = 0, plain_y = 0;
       for (int b = 0; b < ntx; ++b) plain_x += !(b * tx - 1 < g.pml[0] || b * tx + tx >= n[0] - g.pml[1] - 1);
       for (int b = 0; b < nty; ++b) plain_y += !(b * ty - 1 < g.pml[2] || b * ty + ty >= n[1] - g.pml[3] - 1);
       const double xy_frac = 1.0 - (double)plain_x * plain_y / ((double)ntx * nty);
-      h->rev_fused = (int64_t)n[0] * n[1] * n[2] >= (int64_t)64 << 20 && xy_frac <= 0.2;
+      h->rev_fused = (int64_t)n[0] * n[1] * n[2] >= (int64_t)12 << 20 && xy_frac <= 0.4;
       if (const char* e = std::getenv("FDTD_REV_FUSED")) h->rev_fused = std::atoi(e) != 0;  // override
     }
     h->tz = std::min(h->tz, fused_max_tz());
