@@ -2001,7 +2001,10 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
       }
       FG.n = nf;
       group_chunks(FG.a, F, nf, 0);
-      launch_fwd_group(FG, st);
+      // a launch of one request goes through the single-request kernels (same arithmetic, small
+      // parameter blocks; a lone served request then steps as fast as a solo solve)
+      if (nf == 1) launch_fwd_fused(FG.a[0], FG.m[0], st);
+      else launch_fwd_group(FG, st);
       for (int r = 0; r < nf; ++r) {
         fdtd_handle* h = F[r];
         h->launches += 1;
@@ -2014,7 +2017,8 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
           h->launches += 1;
         }
       }
-      if (faces.n > 0) launch_face_copy_group(faces, st);
+      if (faces.n == 1) launch_face_copy(faces.e[0].g, faces.e[0].F, faces.e[0].fs, faces.e[0].rec, faces.to_record, st);
+      else if (faces.n > 0) launch_face_copy_group(faces, st);
       for (int r = 0; r < nf; ++r) {
         fdtd_handle* h = F[r];
         h->launches += fwd_step_post(h, h->step_next, h->last_nsteps, st);
@@ -2050,7 +2054,8 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
           h->launches += 1;
         }
       }
-      if (faces.n > 0) launch_face_copy_group(faces, st);
+      if (faces.n == 1) launch_face_copy(faces.e[0].g, faces.e[0].F, faces.e[0].fs, faces.e[0].rec, faces.to_record, st);
+      else if (faces.n > 0) launch_face_copy_group(faces, st);
       // first halves: the fused inverse steps, and rev_E of the in-place pairs
       fdtd_handle* fh[FDTD_MAX_GROUP];  // the handles of the fused kind, and of the in-place pair
       fdtd_handle* sh[FDTD_MAX_GROUP];
@@ -2074,8 +2079,10 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
       }
       group_chunks(IG.a, fh, IG.n, 1);
       group_chunks(RG.a, sh, RG.n, 3);
-      if (IG.n > 0) launch_inv_group(IG, st);
-      if (RG.n > 0) launch_rev_group(RG, 0, st);
+      if (IG.n == 1) launch_inv(IG.a[0], IG.m[0], st);
+      else if (IG.n > 0) launch_inv_group(IG, st);
+      if (RG.n == 1) launch_rev_E(RG.a[0], RG.m[0], st);
+      else if (RG.n > 0) launch_rev_group(RG, 0, st);
       // second halves: the fused adjoint steps, and rev_H of the in-place pairs
       AG.n = RG.n = 0;
       for (int r = 0; r < nr; ++r) {
@@ -2097,8 +2104,10 @@ int fdtd_group_step(fdtd_handle* const* hs, int32_t n, int32_t nsteps) {
       }
       group_chunks(AG.a, fh, AG.n, 2);
       group_chunks(RG.a, sh, RG.n, 3);
-      if (AG.n > 0) launch_adj_group(AG, st);
-      if (RG.n > 0) launch_rev_group(RG, 1, st);
+      if (AG.n == 1) fh[0]->launches += launch_adj(AG.a[0], AG.m[0], st) - 1;  // one or two launches
+      else if (AG.n > 0) launch_adj_group(AG, st);
+      if (RG.n == 1) launch_rev_H(RG.a[0], RG.m[0], st);
+      else if (RG.n > 0) launch_rev_group(RG, 1, st);
       for (int r = 0; r < nr; ++r) {
         fdtd_handle* h = Rv[r];
         if (h->rev_fused) {
