@@ -315,6 +315,19 @@ int64_t fdtd_history_bytes(const fdtd_grid* grid, const fdtd_pml* pml, int32_t n
  * input. */
 int64_t fdtd_adjoint_bytes(const fdtd_grid* grid, const fdtd_pml* pml);
 
+/* The launch plan fdtd_create chooses for a grid, computed on the host (no device work; the
+ * environment overrides FDTD_REV_FUSED and FDTD_ADJ_SPLIT that fdtd_create reads are not applied).
+ * fdtd_reverse_kind: 1 when the reverse sweep uses the fused pair (the inverse step, then the adjoint
+ * step, each in one sweep with double-buffered fields: grids of at least 12 M cells whose 32 x 16
+ * column tiles touch an x or y CPML layer in at most 40 % of the cases), 0 for the in-place pair.
+ * fdtd_adjoint_frame: writes the frame of the fused adjoint step's tiles that need the x/y CPML loop,
+ * frame[0..3] = leading and trailing tile columns, leading and trailing tile rows (32 x 16 tiles), and
+ * returns 1 when a rectangle of plain tiles is left inside it (the step then runs as two launches, the
+ * frame and the rectangle), 0 when not (one launch). Both: INVALID_ARG for a bad grid or pml (or a
+ * NULL frame). */
+int fdtd_reverse_kind(const fdtd_grid* grid, const fdtd_pml* pml);
+int fdtd_adjoint_frame(const fdtd_grid* grid, const fdtd_pml* pml, int32_t frame[4]);
+
 /* Cap the device bytes any one handle may allocate (-1 = no cap, the default). Allocations past the
  * cap fail with FDTD_ERR_OOM before reaching the CUDA allocator; used to exercise admission and
  * out-of-memory paths without exhausting the GPU. Process-wide. */

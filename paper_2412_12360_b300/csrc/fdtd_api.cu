@@ -123,6 +123,44 @@ int group_tz(int n, const int64_t* nxy, const int* nz, const int* own, const boo
   return best;
 }
 
+// The frame of the split adjoint step: the leading and trailing tile columns (f[0], f[1]) and rows
+// (f[2], f[3]) whose march needs the x/y CPML loop; false when no rectangle of plain tiles is left
+// inside them (the step is then one launch).
+bool adjoint_frame(const Geo& g, int f[4]) {
+  const int ntx = adj_tiles_x(g), nty = adj_tiles_y(g);
+  int xl = 0, xh = 0, yl = 0, yh = 0;
+  while (xl < ntx && adj_tile_xy(g, 0, xl)) ++xl;
+  while (xh < ntx - xl && adj_tile_xy(g, 0, ntx - 1 - xh)) ++xh;
+  while (yl < nty && adj_tile_xy(g, 1, yl)) ++yl;
+  while (yh < nty - yl && adj_tile_xy(g, 1, nty - 1 - yh)) ++yh;
+  bool ok = xl + xh < ntx && yl + yh < nty;
+  for (int b = xl; ok && b < ntx - xh; ++b) ok = !adj_tile_xy(g, 0, b);
+  for (int b = yl; ok && b < nty - yh; ++b) ok = !adj_tile_xy(g, 1, b);
+  f[0] = xl;
+  f[1] = xh;
+  f[2] = yl;
+  f[3] = yh;
+  return ok;
+}
+
+// The reverse-step kind of a grid. The fused pair moves 104 B per cell against 148 but does its CPML
+// work (the adjoint's coefficients gathered from both neighbours) in every tile that touches an x or y
+// layer, and its 32 x 16 tiles give small grids fewer blocks. On one B300, fwd+grad ms per step with
+// the fused / in-place pair (fraction of tiles touching an x or y layer): 600^3 7.1 / 7.6 (18 %), 400^3
+// 2.42 / 2.63 (22 %), 240x240x960 2.29 / 2.40 (35 %), 256^3 0.765 / 0.796 (34 %), 200^3 0.501 / 0.473
+// (56 %), 128x128x256 0.306 / 0.266 (63 %), 96^3 (78 %) slower still. So: the fused pair for grids of
+// at least 12 M cells whose tiles touch a layer in at most 40 % of the cases.
+bool fused_reverse(const Geo& g) {
+  const int tx = fused_tile_x(), ty = fused_tile_y();
+  const int nx = g.n[0], ny = g.n[1];
+  const int ntx = (nx + tx - 1) / tx, nty = (ny + ty - 1) / ty;
+  int plain_x = 0, plain_y = 0;
+  for (int b = 0; b < ntx; ++b) plain_x += !(b * tx - 1 < g.pml[0] || b * tx + tx >= nx - g.pml[1] - 1);
+  for (int b = 0; b < nty; ++b) plain_y += !(b * ty - 1 < g.pml[2] || b * ty + ty >= ny - g.pml[3] - 1);
+  const double xy_frac = 1.0 - (double)plain_x * plain_y / ((double)ntx * nty);
+  return (int64_t)nx * ny * g.n[2] >= (int64_t)12 << 20 && xy_frac <= 0.4;
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime (no link to libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1497,14 +1535,9 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
         // the tiles of the split adjoint step: leading and trailing tile columns and rows that need
         // the x/y CPML loop, each launch's z-chunks for its own tiles
         const int ntx = adj_tiles_x(g), nty = adj_tiles_y(g);
-        int xl = 0, xh = 0, yl = 0, yh = 0;
-        while (xl < ntx && adj_tile_xy(g, 0, xl)) ++xl;
-        while (xh < ntx - xl && adj_tile_xy(g, 0, ntx - 1 - xh)) ++xh;
-        while (yl < nty && adj_tile_xy(g, 1, yl)) ++yl;
-        while (yh < nty - yl && adj_tile_xy(g, 1, nty - 1 - yh)) ++yh;
-        bool ok = xl + xh < ntx && yl + yh < nty;
-        for (int b = xl; ok && b < ntx - xh; ++b) ok = !adj_tile_xy(g, 0, b);
-        for (int b = yl; ok && b < nty - yh; ++b) ok = !adj_tile_xy(g, 1, b);
+        int f[4];
+        bool ok = adjoint_frame(g, f);
+        const int xl = f[0], xh = f[1], yl = f[2], yh = f[3];
         if (const char* e = std::getenv("FDTD_ADJ_SPLIT")) ok &= std::atoi(e) != 0;  // override
         if (const char* e = std::getenv("FDTD_ADJ_OVERLAP")) h->adj_overlap = std::atoi(e) != 0;  // override
         h->adj_split = ok ? 1 : 0;
@@ -1532,21 +1565,7 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       if (v == 3 || v == 4) h->rev_nstage = h->inv_nstage = h->adj_nstage = v;
     }
     {
-      // The fused pair moves 104 B per cell against 148 but does its CPML work (the adjoint's
-      // coefficients gathered from both neighbours) in every tile that touches an x or y layer, and
-      // its 32 x 16 tiles give small grids fewer blocks. On one B300, fwd+grad ms per step with the
-      // fused / in-place pair (fraction of tiles touching an x or y layer): 600^3 7.1 / 7.6 (18 %),
-      // 400^3 2.42 / 2.63 (22 %), 240x240x960 2.29 / 2.40 (35 %), 256^3 0.765 / 0.796 (34 %), 200^3
-      // 0.501 / 0.473 (56 %), 128x128x256 0.306 / 0.266 (63 %), 96^3 (78 %) slower still. So: the
-      // fused pair for grids of at least 12 M cells whose tiles touch a layer in at most 40 % of the
-      // cases.
-      const int tx = fused_tile_x(), ty = fused_tile_y();
-      const int ntx = (n[0] + tx - 1) / tx, nty = (n[1] + ty - 1) / ty;
-      int plain_x = 0, plain_y = 0;
-      for (int b = 0; b < ntx; ++b) plain_x += !(b * tx - 1 < g.pml[0] || b * tx + tx >= n[0] - g.pml[1] - 1);
-      for (int b = 0; b < nty; ++b) plain_y += !(b * ty - 1 < g.pml[2] || b * ty + ty >= n[1] - g.pml[3] - 1);
-      const double xy_frac = 1.0 - (double)plain_x * plain_y / ((double)ntx * nty);
-      h->rev_fused = (int64_t)n[0] * n[1] * n[2] >= (int64_t)12 << 20 && xy_frac <= 0.4;
+      h->rev_fused = fused_reverse(g);
       if (const char* e = std::getenv("FDTD_REV_FUSED")) h->rev_fused = std::atoi(e) != 0;  // override
     }
     h->tz = std::min(h->tz, fused_max_tz());
@@ -2617,6 +2636,19 @@ int fdtd_set_segment_steps(fdtd_handle* h, int32_t steps) {
   h->seg_steps = steps;
   h->recorded = false;  // a history recorded with the old setting is not used
   return FDTD_OK;
+}
+
+int fdtd_reverse_kind(const fdtd_grid* grid, const fdtd_pml* pml) {
+  if (validate(grid, 0.5, pml) != FDTD_OK) return FDTD_ERR_INVALID_ARG;
+  return fused_reverse(make_geo(*grid, *pml, 0.5)) ? 1 : 0;
+}
+
+int fdtd_adjoint_frame(const fdtd_grid* grid, const fdtd_pml* pml, int32_t frame[4]) {
+  if (!frame || validate(grid, 0.5, pml) != FDTD_OK) return FDTD_ERR_INVALID_ARG;
+  int f[4];
+  const bool ok = adjoint_frame(make_geo(*grid, *pml, 0.5), f);
+  for (int q = 0; q < 4; ++q) frame[q] = f[q];
+  return ok ? 1 : 0;
 }
 
 int64_t fdtd_adjoint_bytes(const fdtd_grid* grid, const fdtd_pml* pml) {

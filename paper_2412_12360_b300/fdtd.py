@@ -93,6 +93,8 @@ SIGNATURES = [
     ("fdtd_bytes_allocated", C.c_int64, [_VP]),
     ("fdtd_release_history", C.c_int, [_VP]),
     ("fdtd_launch_count", C.c_int64, [_VP]),
+    ("fdtd_reverse_kind", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("fdtd_adjoint_frame", C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]),
     ("fdtd_wait_probe", C.c_int, [C.c_int32, C.POINTER(C.c_int64)]),
     ("fdtd_profile", C.c_int, [_VP, C.c_int32, C.c_int32]),
     ("fdtd_profile_read", C.c_int, [_VP, _VP, _VP, C.c_int32]),
@@ -201,6 +203,26 @@ def adjoint_bytes(scene) -> int:
     g = make_grid(scene.n)
     p = make_pml(scene)
     return int(lib().fdtd_adjoint_bytes(C.byref(g), C.byref(p)))
+
+
+def reverse_kind(scene) -> int:
+    """1 when fdtd_create gives this scene's grid the fused reverse pair, 0 for the in-place pair."""
+    g, p = make_grid(scene.n), make_pml(scene)
+    rc = lib().fdtd_reverse_kind(C.byref(g), C.byref(p))
+    if rc < 0:
+        raise FDTDError(rc, last_error())
+    return rc
+
+
+def adjoint_frame(scene):
+    """(split, (xl, xh, yl, yh)): whether the fused adjoint step of this grid runs as a frame launch and
+    a plain-rectangle launch, and the frame's leading/trailing tile columns and rows."""
+    g, p = make_grid(scene.n), make_pml(scene)
+    f = (C.c_int32 * 4)()
+    rc = lib().fdtd_adjoint_frame(C.byref(g), C.byref(p), f)
+    if rc < 0:
+        raise FDTDError(rc, last_error())
+    return rc, tuple(int(v) for v in f)
 
 
 def wait_probe(limit_ms: int):
