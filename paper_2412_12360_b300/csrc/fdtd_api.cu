@@ -1548,7 +1548,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
         if (ok) {
           const int64_t rect = (int64_t)(ntx - xl - xh) * (nty - yl - yh), frame = (int64_t)ntx * nty - rect;
           h->tz_adj = std::min(choose_tz(rect, n[2], slots), adj_max_tz());
-          h->tz_adj_xy = std::min(choose_tz(frame, n[2], slots), adj_max_tz());
+          // the frame launch runs beside the plain one and does best in long chunks: on 600^3 the
+          // adjoint step took 2.76 / 2.73 / 2.72 / 2.71 ms with frame chunks of 24 (choose_tz) / 48 /
+          // 96 / 256 planes, 2.81 and 2.86 ms with 12 and 8
+          h->tz_adj_xy = std::min(std::min(std::max(choose_tz(frame, n[2], slots), 96), n[2]), adj_max_tz());
         }
       }
     }
@@ -1558,6 +1561,10 @@ int fdtd_create(fdtd_handle** out, const fdtd_grid* grid, double spacing, double
       h->tz_free = v < 1;
     }
     h->tz_inv = std::min(h->tz_inv, inv_max_tz());
+    if (const char* e = std::getenv("FDTD_TZ_FRAME")) {  // tuning override: z-planes per block of the frame launch
+      const int v = std::atoi(e);
+      if (v >= 1) h->tz_adj_xy = std::min(v, n[2]);
+    }
     h->tz_adj = std::min(h->tz_adj, adj_max_tz());
     h->tz_adj_xy = std::min(h->tz_adj_xy, adj_max_tz());
     if (const char* e = std::getenv("FDTD_REV_NSTAGE")) {  // override: ring stages of the reverse kernels
